@@ -1,0 +1,739 @@
+// melbm_oracle.cpp -- TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, FP64 CPU restatement of the moment-encoded lattice Boltzmann
+// (HOME-LBM) update of arXiv 2602.05295, written from the paper's equations so
+// that the CUDA path can be checked against it.  Only tests, the smoke check and
+// the benchmark's CPU-baseline leg may load this library; the product never does.
+// It shares no code, header, table or constant with the CUDA path.
+//
+// Every routine follows the paper's definitions in the paper's order, with no
+// blocking, fusion or reordering beyond what is stated next to it:
+//   * lattice:        D3Q27, c_i in {-1,0,1}^3, w = product of 1D weights
+//                     (2/3 at rest, 1/6 moving), c_s^2 = 1/3          (Sec. 3.1, App. D)
+//   * collision:      moment-space HOME collision with forcing         (App. A)
+//   * reconstruction: third-order Hermite expansion h(rho,u,S)         (Sec. 3.2, Eq. three_order_f)
+//   * streaming:      pull form f_i(x) = f+_i(x - c_i)                 (Eq. streaming; Alg. 2)
+//   * moments:        rho, rho u (+F/2), rho S                          (Eq. rho_u_stress)
+//   * boundaries:     halfway bounce-back f_i(x) = f+_{opp(i)}(x) for solid
+//                     links, equilibrium inflow, zero-gradient outflow  (split-kernel design, Sec. 4.2)
+//   * codec:          range, normalisation, dithered rounding to 16 bits (Sec. 5.4)
+//
+// Readings of the paper that it takes (each is also listed in the design notes):
+//   * the xyz third-order Hermite term carries 1/c_s^6 (the other six triples
+//     carry 1/(2 c_s^6)), which is the reading under which the reconstruction
+//     reproduces its own third moments; `literal_xyz` selects the printed factor.
+//   * the public state is the post-streaming (rho, u, S) at integer time (Alg. 2).
+//   * S is the per-mass Hermite second moment, so its equilibrium is u u.
+//   * the forcing terms of App. A are applied literally, with F at the colliding
+//     and at the recovering cell.
+//
+// Parity pins: every function here is pinned by a CPU test against closed
+// forms, invariants, symmetries or brute force (tests/test_oracle_pins.py).
+// The amplification matrix G(k) that the oracle can build by complex step is
+// pinned only through its closed-form limits; the paper's own analytic 2D
+// matrices are not rebuilt ("parity unpinned" for those).
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ----------------------------------------------------------------------------
+// Lattice (Sec. 3.1).  Direction index i = (cx+1) + 3 (cy+1) + 9 (cz+1);
+// the rest direction is i = 13 and the opposite of i is 26 - i.
+// ----------------------------------------------------------------------------
+constexpr double CS2 = 1.0 / 3.0;
+
+struct Lattice {
+  int c[27][3];
+  double w[27];
+  Lattice() {
+    for (int i = 0; i < 27; ++i) {
+      c[i][0] = i % 3 - 1;
+      c[i][1] = (i / 3) % 3 - 1;
+      c[i][2] = i / 9 - 1;
+      double wi = 1.0;
+      for (int a = 0; a < 3; ++a) wi *= (c[i][a] == 0) ? 2.0 / 3.0 : 1.0 / 6.0;
+      w[i] = wi;
+    }
+  }
+};
+const Lattice L;
+
+inline int opposite(int i) { return 26 - i; }
+
+// Symmetric 3x3 tensor stored as (xx, yy, zz, xy, xz, yz).
+inline int sidx(int a, int b) {
+  if (a == b) return a;
+  if (a > b) { int t = a; a = b; b = t; }
+  return (a == 0) ? (b == 1 ? 3 : 4) : 5;
+}
+
+template <class T>
+struct Mom {  // rho, u_alpha, S_alphabeta (per-mass Hermite second moment)
+  T rho;
+  T u[3];
+  T S[6];
+};
+
+// Cell types (priority SOLID > INFLOW > OUTFLOW > FLUID_BOUNDARY > FLUID).
+enum : uint8_t { FLUID = 0, FLUID_BOUNDARY = 1, INFLOW = 2, OUTFLOW = 3, SOLID = 4 };
+
+// ----------------------------------------------------------------------------
+// Collision in moment space with forcing (App. A, Eqs. ourmomentcollision_*).
+// Input: the post-streaming moments (rho*, u*, S*) of one cell and the force F.
+// ----------------------------------------------------------------------------
+template <class T>
+Mom<T> collide(const Mom<T>& m, const T F[3], double tau) {
+  Mom<T> o;
+  const T rho = m.rho;
+  o.rho = rho;                                                  // rho(t+1) = rho*
+  for (int a = 0; a < 3; ++a) o.u[a] = m.u[a] + F[a] / (2.0 * rho);  // u + F/(2 rho)
+  // Off-diagonal: (1 - 1/tau) S* + u*u*/tau + (2tau-1)/(2 tau rho) (F_a u_b + F_b u_a)
+  for (int a = 0; a < 3; ++a)
+    for (int b = a + 1; b < 3; ++b) {
+      o.S[sidx(a, b)] = (1.0 - 1.0 / tau) * m.S[sidx(a, b)] + m.u[a] * m.u[b] / tau +
+                        (2.0 * tau - 1.0) / (2.0 * tau * rho) * (F[a] * m.u[b] + F[b] * m.u[a]);
+    }
+  // Diagonal, with (b, g) the two other axes.
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, g = (a + 2) % 3;
+    const T Saa = m.S[a], Sbb = m.S[b], Sgg = m.S[g];
+    const T ua = m.u[a], ub = m.u[b], ug = m.u[g];
+    o.S[a] = (tau - 1.0) / (3.0 * tau) * (2.0 * Saa - Sbb - Sgg) +
+             (1.0 / 3.0) * (ua * ua + ub * ub + ug * ug) +
+             (1.0 / (3.0 * tau)) * (2.0 * ua * ua - ub * ub - ug * ug) + F[a] * ua / rho +
+             (tau - 1.0) / (3.0 * tau * rho) * (2.0 * F[a] * ua - F[b] * ub - F[g] * ug);
+  }
+  return o;
+}
+
+// ----------------------------------------------------------------------------
+// Third-order Hermite reconstruction h_i(rho, u, S) (Eq. three_order_f).
+//   f_i = rho w_i [1 + c.u/cs2 + H2(c):S/(2 cs2^2) + sum_{abg} k_abg H3_abg(c) T_abg]
+//   T_abg = S_ab u_g + S_ag u_b + S_bg u_a - 2 u_a u_b u_g
+// over the triples xxy, xyy, xxz, xzz, yzz, yyz, xyz.  k = 1/(2 cs2^3) for the
+// six triples with a repeated index and 1/cs2^3 for xyz (see header), or the
+// printed 1/(2 cs2^3) for all seven when literal_xyz is set.
+// ----------------------------------------------------------------------------
+inline double H2(int a, int b, const int* c) { return c[a] * c[b] - (a == b ? CS2 : 0.0); }
+inline double H3(int a, int b, int g, const int* c) {
+  return c[a] * c[b] * c[g] -
+         CS2 * (c[a] * (b == g ? 1 : 0) + c[b] * (a == g ? 1 : 0) + c[g] * (a == b ? 1 : 0));
+}
+template <class T>
+T Tabg(const Mom<T>& m, int a, int b, int g) {
+  return m.S[sidx(a, b)] * m.u[g] + m.S[sidx(a, g)] * m.u[b] + m.S[sidx(b, g)] * m.u[a] -
+         2.0 * m.u[a] * m.u[b] * m.u[g];
+}
+const int TRIPLES[7][3] = {{0, 0, 1}, {0, 1, 1}, {0, 0, 2}, {0, 2, 2}, {1, 2, 2}, {1, 1, 2}, {0, 1, 2}};
+
+template <class T>
+T reconstruct(int i, const Mom<T>& m, int literal_xyz) {
+  const int* c = L.c[i];
+  T cu = 0.0;
+  for (int a = 0; a < 3; ++a) cu += double(c[a]) * m.u[a];
+  T h2 = 0.0;  // H2:S summed over all nine (a, b)
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) h2 += H2(a, b, c) * m.S[sidx(a, b)];
+  T h3 = 0.0;
+  for (int t = 0; t < 7; ++t) {
+    const int a = TRIPLES[t][0], b = TRIPLES[t][1], g = TRIPLES[t][2];
+    const bool xyz = (t == 6);
+    const double k = (xyz && !literal_xyz) ? 1.0 / (CS2 * CS2 * CS2) : 1.0 / (2.0 * CS2 * CS2 * CS2);
+    h3 += k * H3(a, b, g, c) * Tabg(m, a, b, g);
+  }
+  return m.rho * L.w[i] * (1.0 + cu / CS2 + h2 / (2.0 * CS2 * CS2) + h3);
+}
+
+// ----------------------------------------------------------------------------
+// Moments of the streamed populations (Eq. rho_u_stress):
+//   rho = sum f, rho u = sum c f + F/2, rho S_ab = sum (c_a c_b - cs2 delta_ab) f.
+// ----------------------------------------------------------------------------
+template <class T>
+Mom<T> moments(const T* f, const T F[3]) {
+  Mom<T> o;
+  T rho = 0.0, J[3] = {0.0, 0.0, 0.0}, P[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i < 27; ++i) {
+    rho += f[i];
+    for (int a = 0; a < 3; ++a) J[a] += double(L.c[i][a]) * f[i];
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b) P[sidx(a, b)] += H2(a, b, L.c[i]) * f[i];
+  }
+  o.rho = rho;
+  for (int a = 0; a < 3; ++a) o.u[a] = (J[a] + 0.5 * F[a]) / rho;
+  for (int k = 0; k < 6; ++k) o.S[k] = P[k] / rho;
+  return o;
+}
+
+// ----------------------------------------------------------------------------
+// Grid helpers.  Linear index n = x + nx (y + ny z); SoA with 10 components
+// (rho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz), component-major.
+// ----------------------------------------------------------------------------
+struct Grid {
+  int nx, ny, nz;
+  int64_t N() const { return int64_t(nx) * ny * nz; }
+  int64_t idx(int x, int y, int z) const { return x + int64_t(nx) * (y + int64_t(ny) * z); }
+  // x - c_i with periodic wrap
+  int64_t pull_src(int64_t n, int i) const {
+    int x = int(n % nx), y = int((n / nx) % ny), z = int(n / (int64_t(nx) * ny));
+    x = (x - L.c[i][0] + nx) % nx;
+    y = (y - L.c[i][1] + ny) % ny;
+    z = (z - L.c[i][2] + nz) % nz;
+    return idx(x, y, z);
+  }
+};
+
+template <class T>
+Mom<T> load(const T* m, int64_t N, int64_t n) {
+  Mom<T> o;
+  o.rho = m[n];
+  for (int a = 0; a < 3; ++a) o.u[a] = m[(1 + a) * N + n];
+  for (int k = 0; k < 6; ++k) o.S[k] = m[(4 + k) * N + n];
+  return o;
+}
+template <class T>
+void store(T* m, int64_t N, int64_t n, const Mom<T>& v) {
+  m[n] = v.rho;
+  for (int a = 0; a < 3; ++a) m[(1 + a) * N + n] = v.u[a];
+  for (int k = 0; k < 6; ++k) m[(4 + k) * N + n] = v.S[k];
+}
+template <class T>
+void load_force(const T* F, int64_t N, int64_t n, T out[3]) {
+  for (int a = 0; a < 3; ++a) out[a] = F ? F[a * N + n] : T(0.0);
+}
+
+// The update of one non-solid cell from the post-collision moments `mp`
+// (Alg. 2 streaming + moments, with bounce-back for solid links).
+template <class T>
+Mom<T> pull_and_moments(const Grid& g, const std::vector<Mom<T>>& mp, const uint8_t* type,
+                        const T* F, int64_t n, int literal_xyz) {
+  T f[27];
+  for (int i = 0; i < 27; ++i) {
+    const int64_t src = g.pull_src(n, i);
+    if (type && type[src] == SOLID)
+      f[i] = reconstruct(opposite(i), mp[n], literal_xyz);  // halfway bounce-back
+    else
+      f[i] = reconstruct(i, mp[src], literal_xyz);
+  }
+  T Fx[3];
+  load_force(F, g.N(), n, Fx);
+  return moments(f, Fx);
+}
+
+template <class T>
+Mom<T> inflow_state(const double* inflow) {
+  Mom<T> o;
+  o.rho = inflow[0];
+  for (int a = 0; a < 3; ++a) o.u[a] = inflow[1 + a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b) o.S[sidx(a, b)] = inflow[1 + a] * inflow[1 + b];
+  return o;
+}
+
+// One full step over the grid.  Pass 1 collides every non-solid cell; pass 2
+// pulls and re-forms the moments; pass 3 applies the zero-gradient outflow copy.
+template <class T>
+void step_grid(const Grid& g, double tau, const T* m, const T* F, const uint8_t* type,
+               const double* inflow, T* out, int literal_xyz) {
+  const int64_t N = g.N();
+  std::vector<Mom<T>> mp(N);
+#pragma omp parallel for schedule(static)
+  for (int64_t n = 0; n < N; ++n) {
+    if (type && type[n] == SOLID) continue;
+    T Fx[3];
+    load_force(F, N, n, Fx);
+    mp[n] = collide(load(m, N, n), Fx, tau);
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t n = 0; n < N; ++n) {
+    const uint8_t t = type ? type[n] : FLUID;
+    if (t == SOLID) {
+      store(out, N, n, load(m, N, n));  // solid cells keep their value
+    } else if (t == INFLOW) {
+      store(out, N, n, inflow_state<T>(inflow));
+    } else {
+      store(out, N, n, pull_and_moments(g, mp, type, F, n, literal_xyz));
+    }
+  }
+  if (type) {
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+      if (type[n] != OUTFLOW) continue;
+      const int64_t s = n - 1;  // (nx-2, y, z): the outflow plane is x = nx-1
+      store(out, N, n, load(out, N, s));
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Hand-written reverse mode (vector-Jacobian products) of collide, reconstruct
+// and moments, used by the discrete adjoint of one step.
+// ----------------------------------------------------------------------------
+// d(moments)/d(f, F) transposed: given (rho_bar, u_bar, S_bar) of the output.
+inline void moments_vjp(const double* f, const double F[3], const Mom<double>& ob, double* fb,
+                        double Fb[3]) {
+  double rho = 0.0, J[3] = {0, 0, 0}, P[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < 27; ++i) {
+    rho += f[i];
+    for (int a = 0; a < 3; ++a) J[a] += L.c[i][a] * f[i];
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b) P[sidx(a, b)] += H2(a, b, L.c[i]) * f[i];
+  }
+  for (int a = 0; a < 3; ++a) J[a] += 0.5 * F[a];
+  // u = J/rho, S = P/rho
+  double Jb[3], Pb[6], rhob = ob.rho;
+  for (int a = 0; a < 3; ++a) {
+    Jb[a] = ob.u[a] / rho;
+    rhob -= ob.u[a] * J[a] / (rho * rho);
+  }
+  for (int k = 0; k < 6; ++k) {
+    Pb[k] = ob.S[k] / rho;
+    rhob -= ob.S[k] * P[k] / (rho * rho);
+  }
+  for (int i = 0; i < 27; ++i) {
+    double s = rhob;
+    for (int a = 0; a < 3; ++a) s += L.c[i][a] * Jb[a];
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b) s += H2(a, b, L.c[i]) * Pb[sidx(a, b)];
+    fb[i] = s;
+  }
+  for (int a = 0; a < 3; ++a) Fb[a] += 0.5 * Jb[a];
+}
+
+// d(h_i)/d(rho, u, S) transposed, accumulated into mb.
+inline void reconstruct_vjp(int i, const Mom<double>& m, double fb, Mom<double>& mb, int literal_xyz) {
+  const int* c = L.c[i];
+  const double w = L.w[i];
+  double cu = 0.0, h2 = 0.0, h3 = 0.0;
+  for (int a = 0; a < 3; ++a) cu += c[a] * m.u[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) h2 += H2(a, b, c) * m.S[sidx(a, b)];
+  double kt[7];
+  for (int t = 0; t < 7; ++t) {
+    const int a = TRIPLES[t][0], b = TRIPLES[t][1], g = TRIPLES[t][2];
+    const double k = (t == 6 && !literal_xyz) ? 1.0 / (CS2 * CS2 * CS2) : 1.0 / (2.0 * CS2 * CS2 * CS2);
+    kt[t] = k * H3(a, b, g, c);
+    h3 += kt[t] * Tabg(m, a, b, g);
+  }
+  const double bracket = 1.0 + cu / CS2 + h2 / (2.0 * CS2 * CS2) + h3;
+  // f = rho w bracket
+  mb.rho += fb * w * bracket;
+  const double gb = fb * m.rho * w;  // d f / d bracket
+  for (int a = 0; a < 3; ++a) mb.u[a] += gb * c[a] / CS2;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) mb.S[sidx(a, b)] += gb * H2(a, b, c) / (2.0 * CS2 * CS2);
+  for (int t = 0; t < 7; ++t) {
+    const int a = TRIPLES[t][0], b = TRIPLES[t][1], g = TRIPLES[t][2];
+    const double tb = gb * kt[t];  // d f / d T_abg
+    // T = S_ab u_g + S_ag u_b + S_bg u_a - 2 u_a u_b u_g
+    mb.S[sidx(a, b)] += tb * m.u[g];
+    mb.S[sidx(a, g)] += tb * m.u[b];
+    mb.S[sidx(b, g)] += tb * m.u[a];
+    mb.u[g] += tb * (m.S[sidx(a, b)] - 2.0 * m.u[a] * m.u[b]);
+    mb.u[b] += tb * (m.S[sidx(a, g)] - 2.0 * m.u[a] * m.u[g]);
+    mb.u[a] += tb * (m.S[sidx(b, g)] - 2.0 * m.u[b] * m.u[g]);
+  }
+}
+
+// d(collide)/d(m, F) transposed.
+inline void collide_vjp(const Mom<double>& m, const double F[3], double tau, const Mom<double>& ob,
+                        Mom<double>& mb, double Fb[3]) {
+  const double rho = m.rho;
+  mb.rho += ob.rho;
+  for (int a = 0; a < 3; ++a) {  // u+ = u + F/(2 rho)
+    mb.u[a] += ob.u[a];
+    Fb[a] += ob.u[a] / (2.0 * rho);
+    mb.rho += -ob.u[a] * F[a] / (2.0 * rho * rho);
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = a + 1; b < 3; ++b) {
+      const double sb = ob.S[sidx(a, b)];
+      const double kf = (2.0 * tau - 1.0) / (2.0 * tau);
+      const double G = F[a] * m.u[b] + F[b] * m.u[a];
+      mb.S[sidx(a, b)] += sb * (1.0 - 1.0 / tau);
+      mb.u[a] += sb * (m.u[b] / tau + kf / rho * F[b]);
+      mb.u[b] += sb * (m.u[a] / tau + kf / rho * F[a]);
+      Fb[a] += sb * kf / rho * m.u[b];
+      Fb[b] += sb * kf / rho * m.u[a];
+      mb.rho += -sb * kf * G / (rho * rho);
+    }
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, g = (a + 2) % 3;
+    const double sb = ob.S[a];
+    const double k1 = (tau - 1.0) / (3.0 * tau);
+    mb.S[a] += sb * 2.0 * k1;
+    mb.S[b] += -sb * k1;
+    mb.S[g] += -sb * k1;
+    const double ua = m.u[a], ub = m.u[b], ug = m.u[g];
+    // (1/3)|u|^2 + (1/(3 tau))(2ua^2 - ub^2 - ug^2)
+    mb.u[a] += sb * ((2.0 / 3.0) * ua + (4.0 / (3.0 * tau)) * ua);
+    mb.u[b] += sb * ((2.0 / 3.0) * ub - (2.0 / (3.0 * tau)) * ub);
+    mb.u[g] += sb * ((2.0 / 3.0) * ug - (2.0 / (3.0 * tau)) * ug);
+    // F_a u_a / rho
+    Fb[a] += sb * ua / rho;
+    mb.u[a] += sb * F[a] / rho;
+    mb.rho += -sb * F[a] * ua / (rho * rho);
+    // (tau-1)/(3 tau rho) (2 F_a u_a - F_b u_b - F_g u_g)
+    const double k2 = (tau - 1.0) / (3.0 * tau);
+    const double Q = 2.0 * F[a] * ua - F[b] * ub - F[g] * ug;
+    Fb[a] += sb * k2 / rho * 2.0 * ua;
+    Fb[b] += -sb * k2 / rho * ub;
+    Fb[g] += -sb * k2 / rho * ug;
+    mb.u[a] += sb * k2 / rho * 2.0 * F[a];
+    mb.u[b] += -sb * k2 / rho * F[b];
+    mb.u[g] += -sb * k2 / rho * F[g];
+    mb.rho += -sb * k2 * Q / (rho * rho);
+  }
+}
+
+Mom<double> zero_mom() {
+  Mom<double> z;
+  z.rho = 0.0;
+  for (int a = 0; a < 3; ++a) z.u[a] = 0.0;
+  for (int k = 0; k < 6; ++k) z.S[k] = 0.0;
+  return z;
+}
+
+// ----------------------------------------------------------------------------
+// Counter-based dither generator: pcg4d of Jarzynski & Olano, "Hash Functions
+// for GPU Rendering", JCGT 9(3), 2020, on the counter (x, y, z, t ^ seed).
+// ----------------------------------------------------------------------------
+inline void pcg4d(uint32_t v[4]) {
+  for (int k = 0; k < 4; ++k) v[k] = v[k] * 1664525u + 1013904223u;
+  v[0] += v[1] * v[3];
+  v[1] += v[2] * v[0];
+  v[2] += v[0] * v[1];
+  v[3] += v[1] * v[2];
+  for (int k = 0; k < 4; ++k) v[k] ^= v[k] >> 16;
+  v[0] += v[1] * v[3];
+  v[1] += v[2] * v[0];
+  v[2] += v[0] * v[1];
+  v[3] += v[1] * v[2];
+}
+
+// Ten dither values d_k in [0, 1) for one cell and one time index.
+// Components 0..7 take 12-bit fields of the four words (bits 0-11 for even k,
+// bits 12-23 for odd k, word k/2); components 8 and 9 take 16-bit fields built
+// from the top bytes of words (0, 1) and (2, 3).
+inline void dither10(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t seed, float d[10]) {
+  uint32_t v[4] = {x, y, z, t ^ seed};
+  pcg4d(v);
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t w = v[k / 2];
+    const uint32_t field = (k % 2 == 0) ? (w & 0xFFFu) : ((w >> 12) & 0xFFFu);
+    d[k] = float(field) / 4096.0f;
+  }
+  const uint32_t f8 = (v[0] >> 24) | ((v[1] >> 24) << 8);
+  const uint32_t f9 = (v[2] >> 24) | ((v[3] >> 24) << 8);
+  d[8] = float(f8) / 65536.0f;
+  d[9] = float(f9) / 65536.0f;
+}
+
+// Stored-variable ranges (Sec. 5.4 moment range analysis and range reduction):
+// rho in [0.8, 1.5]; u_a in [-0.4, 0.4]; rho S^neq_ab = rho (S_ab - u_a u_b) in [-0.1, 0.1].
+const double QLO[10] = {0.8, -0.4, -0.4, -0.4, -0.1, -0.1, -0.1, -0.1, -0.1, -0.1};
+const double QHI[10] = {1.5, 0.4, 0.4, 0.4, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1};
+
+// Encoding in FP32, the precision the kernels take this decision in:
+//   t = clamp(fma(m, 1/(hi-lo), -lo/(hi-lo)), 0, 1);  v = fma(t, 2^b - 1, d);  q = floor(v).
+// This is q = floor(m' (2^b - 1) + 1/2 + e) with e uniform in [-1/2, 1/2) (dithering),
+// d = 1/2 gives the deterministic round-to-nearest of the paper's formula.
+inline uint16_t encode_one(float m, int k, float d) {
+  const float s = float(1.0 / (QHI[k] - QLO[k]));
+  const float o = float(-QLO[k] / (QHI[k] - QLO[k]));
+  float t = std::fma(m, s, o);
+  if (!(t > 0.0f)) t = 0.0f;  // also maps NaN to 0
+  if (t > 1.0f) t = 1.0f;
+  const float v = std::fma(t, 65535.0f, d);
+  return uint16_t(std::floor(v));
+}
+
+// Dequantisation in FP64: m = m_min + q (m_max - m_min)/(2^b - 1).
+inline double decode_one(uint16_t q, int k) { return QLO[k] + double(q) * (QHI[k] - QLO[k]) / 65535.0; }
+
+}  // namespace
+
+// ============================================================================
+// C interface for the Python test harness.
+// ============================================================================
+extern "C" {
+
+int orc_num_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+void orc_lattice(int* c /*27x3*/, double* w /*27*/) {
+  for (int i = 0; i < 27; ++i) {
+    for (int a = 0; a < 3; ++a) c[3 * i + a] = L.c[i][a];
+    w[i] = L.w[i];
+  }
+}
+
+// Per-cell primitives on arrays of cells (10 moments per cell, cell-major).
+void orc_collide(int64_t ncell, const double* m, const double* F, double tau, double* out) {
+  for (int64_t n = 0; n < ncell; ++n) {
+    Mom<double> v = load(m + 10 * n, 1, 0);
+    double Fx[3] = {F ? F[3 * n] : 0.0, F ? F[3 * n + 1] : 0.0, F ? F[3 * n + 2] : 0.0};
+    store(out + 10 * n, 1, 0, collide(v, Fx, tau));
+  }
+}
+
+void orc_reconstruct(int64_t ncell, const double* m, int literal_xyz, double* f /*27 per cell*/) {
+  for (int64_t n = 0; n < ncell; ++n) {
+    Mom<double> v = load(m + 10 * n, 1, 0);
+    for (int i = 0; i < 27; ++i) f[27 * n + i] = reconstruct(i, v, literal_xyz);
+  }
+}
+
+void orc_moments(int64_t ncell, const double* f, const double* F, double* out) {
+  for (int64_t n = 0; n < ncell; ++n) {
+    double Fx[3] = {F ? F[3 * n] : 0.0, F ? F[3 * n + 1] : 0.0, F ? F[3 * n + 2] : 0.0};
+    store(out + 10 * n, 1, 0, moments(f + 27 * n, Fx));
+  }
+}
+
+// Cell classification and boundary list (analogue of the surface marking of Sec. 4.2).
+//   type: SOLID if mask; else INFLOW if inflow and x == 0; else OUTFLOW if outflow,
+//   x == nx-1 and (nx-2, y, z) is not solid; else FLUID_BOUNDARY if any x - c_i is
+//   solid (periodic wrap); else FLUID.
+//   link: bit i set iff x - c_i is solid (0 for solid cells).
+//   list: ascending linear index of INFLOW and FLUID_BOUNDARY cells; returns its length.
+int64_t orc_classify(int nx, int ny, int nz, const uint8_t* mask, int inflow, int outflow,
+                     uint8_t* type, uint32_t* link, uint32_t* list_cell, uint32_t* list_word) {
+  Grid g{nx, ny, nz};
+  const int64_t N = g.N();
+  for (int64_t n = 0; n < N; ++n) {
+    const int x = int(n % nx);
+    uint32_t bits = 0;
+    if (!mask[n]) {
+      for (int i = 0; i < 27; ++i)
+        if (mask[g.pull_src(n, i)]) bits |= (1u << i);
+    }
+    uint8_t t;
+    if (mask[n]) t = SOLID;
+    else if (inflow && x == 0) t = INFLOW;
+    else if (outflow && x == nx - 1 && nx >= 2 && !mask[n - 1]) t = OUTFLOW;
+    else if (bits) t = FLUID_BOUNDARY;
+    else t = FLUID;
+    type[n] = t;
+    link[n] = bits;
+  }
+  int64_t L_ = 0;
+  for (int64_t n = 0; n < N; ++n) {
+    if (type[n] == INFLOW || type[n] == FLUID_BOUNDARY) {
+      if (list_cell) list_cell[L_] = uint32_t(n);
+      if (list_word) list_word[L_] = (uint32_t(type[n]) << 27) | link[n];
+      ++L_;
+    }
+  }
+  return L_;
+}
+
+// One step on the whole grid, public state (rho, u, S) in FP64.
+void orc_step_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                  const uint8_t* type, const double* inflow, int literal_xyz, double* out) {
+  step_grid<double>(Grid{nx, ny, nz}, tau, m, F, type, inflow, out, literal_xyz);
+}
+
+// The same step on complex numbers (interleaved re/im), for complex-step derivatives.
+void orc_step_c128(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                   const uint8_t* type, const double* inflow, int literal_xyz, double* out) {
+  using C = std::complex<double>;
+  step_grid<C>(Grid{nx, ny, nz}, tau, reinterpret_cast<const C*>(m), reinterpret_cast<const C*>(F),
+               type, inflow, reinterpret_cast<C*>(out), literal_xyz);
+}
+
+// The step evaluated at selected cells only (cell-major output, 10 per cell), for
+// sampled checks on grids too large to step whole.  Outflow cells return the new
+// value of (nx-2, y, z); solid cells their old value.
+void orc_step_cells_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                        const uint8_t* type, const double* inflow, const int64_t* cells,
+                        int64_t ncells, double* out) {
+  Grid g{nx, ny, nz};
+  const int64_t N = g.N();
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t k = 0; k < ncells; ++k) {
+    int64_t n = cells[k];
+    uint8_t t = type ? type[n] : FLUID;
+    if (t == OUTFLOW) {
+      n = n - 1;
+      t = type[n];
+    }
+    Mom<double> r;
+    if (t == SOLID) {
+      r = load(m, N, n);
+    } else if (t == INFLOW) {
+      r = inflow_state<double>(inflow);
+    } else {
+      // collide only the 27 cells this one pulls from
+      double f[27];
+      for (int i = 0; i < 27; ++i) {
+        const int64_t src = g.pull_src(n, i);
+        if (type && type[src] == SOLID) {
+          double Fx[3];
+          load_force(F, N, n, Fx);
+          f[i] = reconstruct(opposite(i), collide(load(m, N, n), Fx, tau), 0);
+        } else {
+          double Fx[3];
+          load_force(F, N, src, Fx);
+          f[i] = reconstruct(i, collide(load(m, N, src), Fx, tau), 0);
+        }
+      }
+      double Fx[3];
+      load_force(F, N, n, Fx);
+      r = moments(f, Fx);
+    }
+    store(out + 10 * k, 1, 0, r);
+  }
+}
+
+// Discrete adjoint of one orc_step_f64 (vector-Jacobian product): given
+// lam_out = dL/d(out), returns lam_in = dL/d(m) and adds dL/dF into gF (if gF).
+void orc_step_vjp_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                      const uint8_t* type, const double* lam_out, double* lam_in, double* gF) {
+  Grid g{nx, ny, nz};
+  const int64_t N = g.N();
+  // Outflow copy (pass 3) reversed: the outflow cell's output came from (nx-2).
+  std::vector<double> lo(lam_out, lam_out + 10 * N);
+  if (type) {
+    for (int64_t n = 0; n < N; ++n) {
+      if (type[n] != OUTFLOW) continue;
+      for (int k = 0; k < 10; ++k) {
+        lo[k * N + n - 1] += lo[k * N + n];
+        lo[k * N + n] = 0.0;
+      }
+    }
+  }
+  // Forward quantities: post-collision moments.
+  std::vector<Mom<double>> mp(N);
+  for (int64_t n = 0; n < N; ++n) {
+    if (type && type[n] == SOLID) continue;
+    double Fx[3];
+    load_force(F, N, n, Fx);
+    mp[n] = collide(load(m, N, n), Fx, tau);
+  }
+  // Pass 2 reversed: scatter population adjoints onto the post-collision moments.
+  std::vector<Mom<double>> mpb(N, zero_mom());
+  std::vector<double> Fb(3 * N, 0.0);
+  for (int64_t n = 0; n < N; ++n) {
+    const uint8_t t = type ? type[n] : FLUID;
+    if (t == SOLID) {
+      for (int k = 0; k < 10; ++k) lam_in[k * N + n] = lo[k * N + n];  // identity
+      continue;
+    }
+    if (t == INFLOW) continue;  // output independent of the input
+    double f[27];
+    int src_of[27];
+    int64_t srcs[27];
+    for (int i = 0; i < 27; ++i) {
+      const int64_t src = g.pull_src(n, i);
+      srcs[i] = src;
+      if (type && type[src] == SOLID) {
+        f[i] = reconstruct(opposite(i), mp[n], 0);
+        src_of[i] = -1;
+      } else {
+        f[i] = reconstruct(i, mp[src], 0);
+        src_of[i] = 1;
+      }
+    }
+    double Fx[3];
+    load_force(F, N, n, Fx);
+    Mom<double> ob = load(lo.data(), N, n);
+    double fb[27], Fbn[3] = {0, 0, 0};
+    moments_vjp(f, Fx, ob, fb, Fbn);
+    for (int a = 0; a < 3; ++a) Fb[3 * n + a] += Fbn[a];
+    for (int i = 0; i < 27; ++i) {
+      if (src_of[i] < 0)
+        reconstruct_vjp(opposite(i), mp[n], fb[i], mpb[n], 0);
+      else
+        reconstruct_vjp(i, mp[srcs[i]], fb[i], mpb[srcs[i]], 0);
+    }
+  }
+  // Pass 1 reversed: through the collision.
+  for (int64_t n = 0; n < N; ++n) {
+    const uint8_t t = type ? type[n] : FLUID;
+    if (t == SOLID) continue;
+    double Fx[3];
+    load_force(F, N, n, Fx);
+    Mom<double> mb = zero_mom();
+    double Fbn[3] = {0, 0, 0};
+    collide_vjp(load(m, N, n), Fx, tau, mpb[n], mb, Fbn);
+    store(lam_in, N, n, mb);
+    for (int a = 0; a < 3; ++a) Fb[3 * n + a] += Fbn[a];
+  }
+  if (gF)
+    for (int64_t n = 0; n < N; ++n)
+      for (int a = 0; a < 3; ++a) gF[a * N + n] += Fb[3 * n + a];
+}
+
+// FP64 mass and kinetic energy over non-solid cells.
+void orc_reduce(int64_t N, const double* m, const uint8_t* type, double* mass, double* ke) {
+  double M = 0.0, E = 0.0;
+  for (int64_t n = 0; n < N; ++n) {
+    if (type && type[n] == SOLID) continue;
+    const double rho = m[n];
+    const double u2 = m[N + n] * m[N + n] + m[2 * N + n] * m[2 * N + n] + m[3 * N + n] * m[3 * N + n];
+    M += rho;
+    E += 0.5 * rho * u2;
+  }
+  *mass = M;
+  *ke = E;
+}
+
+// Dither values of one cell (for tests of the generator).
+void orc_dither(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t seed, float* d) {
+  dither10(x, y, z, t, seed, d);
+}
+
+// Encode stored variables (FP32, component-major 10 x N) into 16-bit codes.
+// deterministic != 0 uses d = 1/2 (round to nearest) for every component.
+void orc_encode(int nx, int ny, int nz, const float* v, uint32_t t, uint32_t seed, int deterministic,
+                uint16_t* q) {
+  Grid g{nx, ny, nz};
+  const int64_t N = g.N();
+#pragma omp parallel for schedule(static)
+  for (int64_t n = 0; n < N; ++n) {
+    float d[10];
+    if (deterministic) {
+      for (int k = 0; k < 10; ++k) d[k] = 0.5f;
+    } else {
+      const uint32_t x = uint32_t(n % nx), y = uint32_t((n / nx) % ny), z = uint32_t(n / (int64_t(nx) * ny));
+      dither10(x, y, z, t, seed, d);
+    }
+    for (int k = 0; k < 10; ++k) q[k * N + n] = encode_one(v[k * N + n], k, d[k]);
+  }
+}
+
+void orc_decode(int64_t N, const uint16_t* q, double* v) {
+#pragma omp parallel for schedule(static)
+  for (int64_t n = 0; n < N; ++n)
+    for (int k = 0; k < 10; ++k) v[k * N + n] = decode_one(q[k * N + n], k);
+}
+
+void orc_ranges(double* lo, double* hi) {
+  for (int k = 0; k < 10; ++k) {
+    lo[k] = QLO[k];
+    hi[k] = QHI[k];
+  }
+}
+
+}  // extern "C"
