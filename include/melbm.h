@@ -1,0 +1,172 @@
+/* melbm.h -- C ABI of the GB300 moment-encoded lattice Boltzmann library.
+ *
+ * The library advances a D3Q27 moment-encoded (HOME-LBM) fluid in which every
+ * cell stores only its ten low-order moments (rho, u, S) instead of the 27
+ * populations (arXiv 2602.05295, Sec. 3.2).  One step (Sec. 4.2, Alg. 2 and the
+ * split-kernel design) is:
+ *   1. a branch-free fluid kernel over all cells: load the moments, collide in
+ *      moment space (App. A), rebuild the post-collision populations by the
+ *      third-order Hermite expansion (Eq. three_order_f), pull them from the
+ *      neighbours (Eq. streaming) and re-form the moments (Eq. rho_u_stress);
+ *   2. a boundary kernel over a compacted list of boundary cells: halfway
+ *      bounce-back recompute of cells with solid links and the inflow reset;
+ *   3. a zero-gradient copy onto the outflow plane.
+ * Moments are stored either as FP32 or in the paper's 16-bit stability-bounded
+ * fixed-point form (Sec. 5.4): rho in [0.8, 1.5], u in [-0.4, 0.4] and
+ * rho S^neq = rho (S - u u) in [-0.1, 0.1], dithered rounding, two codes per
+ * 32-bit word, five words per cell.
+ *
+ * Conventions shared by every entry point
+ *   Grid nx x ny x nz, linear cell index n = x + nx (y + ny z) (x fastest),
+ *   N = nx ny nz.  Field arrays are structure-of-arrays, component-major:
+ *   rho[N]; u[3][N] = (ux, uy, uz); S[6][N] = (Sxx, Syy, Szz, Sxy, Sxz, Syz).
+ *   S is the per-mass Hermite second moment, S = sum (c c - c_s^2 I) f / rho,
+ *   whose equilibrium value is u u.  rho and u are the post-streaming values at
+ *   integer time (the physical velocity, which includes F/2).
+ *   Lattice directions i = (cx+1) + 3 (cy+1) + 9 (cz+1), opposite = 26 - i.
+ *   Every call returns an int status (melbm_status); on failure the handle keeps
+ *   a message for melbm_last_error().  No C++ exception crosses the ABI.
+ *   Unless stated otherwise pointers are CUDA device pointers on the current
+ *   device, owned by the caller, contiguous, not aliased with library memory.
+ *   Work is enqueued on the handle's stream (melbm_set_stream); calls that
+ *   return host values synchronise that stream.
+ */
+#ifndef MELBM_H
+#define MELBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MELBM_API __attribute__((visibility("default")))
+#else
+#define MELBM_API
+#endif
+
+typedef struct melbm_sim* melbm_t;
+
+typedef enum melbm_status {
+  MELBM_OK = 0,
+  MELBM_EINVAL = 1,      /* bad argument: NULL handle/pointer, size, tau <= 1/2, ... */
+  MELBM_ENOMEM = 2,      /* a device or host allocation failed */
+  MELBM_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  MELBM_ESTATE = 4,      /* call out of order (e.g. step after a failed call) */
+  MELBM_WSATURATED = 5   /* warning: some 16-bit codes sit on the range limits */
+} melbm_status;
+
+enum { MELBM_D3Q27 = 27 };
+enum { MELBM_F32 = 0, MELBM_Q16 = 1 };
+/* cell types, priority SOLID > INFLOW > OUTFLOW > FLUID_BOUNDARY > FLUID */
+enum { MELBM_FLUID = 0, MELBM_FLUID_BOUNDARY = 1, MELBM_INFLOW = 2, MELBM_OUTFLOW = 3,
+       MELBM_SOLID = 4 };
+
+/* Create a simulation (Sec. 4.2).  lattice must be MELBM_D3Q27; tau > 1/2 is the
+ * relaxation time (nu = (tau - 1/2)/3); storage is MELBM_F32 (40 B/cell per
+ * buffer) or MELBM_Q16 (20 B/cell per buffer, Sec. 5.4).  Allocates two state
+ * buffers on the current device, initialised to rest (rho = 1, u = 0, S = 0).
+ * N must be below 2^31.  *out receives the handle (NULL on failure). */
+MELBM_API int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, melbm_t* out);
+
+/* Free every device and host resource of the handle.  NULL is accepted. */
+MELBM_API int melbm_destroy(melbm_t h);
+
+/* Stream on which all later work of the handle is enqueued (a cudaStream_t;
+ * NULL = the legacy default stream). */
+MELBM_API int melbm_set_stream(melbm_t h, void* cuda_stream);
+
+/* Seed of the dither generator (Sec. 5.4 dithering), default 0.  The dither of
+ * the state at time t is pcg4d(x, y, z, t ^ seed) (Jarzynski & Olano 2020). */
+MELBM_API int melbm_set_seed(melbm_t h, uint32_t seed);
+
+/* Set the state at time t = 0 from rho[N], u[3N] and S[6N] (S may be NULL, which
+ * means S = u u, the equilibrium).  The pointers may be device or host memory
+ * (pinned or pageable); host data is copied in on the handle's stream.  In
+ * 16-bit storage the values are encoded with the dither of time index 0;
+ * values outside the ranges saturate.  Resets the time index to 0. */
+MELBM_API int melbm_set_state(melbm_t h, const float* rho, const float* u, const float* S);
+
+/* Read the current state as FP32 (rho[N], u[3N], S[6N]; S may be NULL).
+ * Device or host pointers; 16-bit storage is dequantised
+ * m = m_min + q (m_max - m_min)/(2^16 - 1) (Sec. 5.4).  Values of SOLID cells are
+ * unspecified (the fluid kernel updates them uniformly; nothing reads them). */
+MELBM_API int melbm_get_moments(melbm_t h, float* rho, float* u, float* S);
+
+/* Solid mask[N] (uint8, nonzero = solid; device pointer, NULL = no solid).
+ * Runs the classification and compaction kernels (analogue of the surface
+ * marking of Sec. 4.2): every cell gets a type and a 27-bit mask whose bit i is
+ * set iff x - c_i is SOLID (periodic wrap); INFLOW and FLUID_BOUNDARY cells are
+ * listed in ascending n.  Synchronises to read the list length. */
+MELBM_API int melbm_set_solid(melbm_t h, const uint8_t* mask);
+
+/* Equilibrium inflow on face 0 (x = 0): INFLOW cells are reset every step to
+ * (rho, u, u u).  Re-classifies.  Only face 0 is supported. */
+MELBM_API int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float uz);
+
+/* Zero-gradient outflow on face 1 (x = nx-1): OUTFLOW cells copy the stored
+ * state of (nx-2, y, z) after each step.  Re-classifies.  Only face 1. */
+MELBM_API int melbm_set_outflow(melbm_t h, int face);
+
+/* Boundary list (device pointers, capacity entries each; either may be NULL).
+ * cells[k] = n, words[k] = (type << 27) | link mask.  *count (host) = list length. */
+MELBM_API int melbm_get_boundary_list(melbm_t h, uint32_t* cells, uint32_t* words, int64_t capacity,
+                            int64_t* count);
+
+/* Cell types[N] (uint8, device pointer). */
+MELBM_API int melbm_get_types(melbm_t h, uint8_t* types);
+
+/* Body force F[3N] (device pointer, copied; NULL removes the force).  Applied
+ * in the collision and in the moment recovery exactly as App. A and
+ * Eq. rho_u_stress state (momentum gain F per step). */
+MELBM_API int melbm_set_force(melbm_t h, const float* F);
+
+/* Advance n >= 0 steps, asynchronously on the handle's stream. */
+MELBM_API int melbm_step(melbm_t h, int n);
+
+/* FP64 total mass sum(rho) and kinetic energy sum(rho |u|^2 / 2) over non-solid
+ * cells (host pointers; synchronises).  In 16-bit storage returns
+ * MELBM_WSATURATED (values still written) when any non-solid code is 0 or 65535. */
+MELBM_API int melbm_reduce(melbm_t h, double* mass, double* kinetic_energy);
+
+/* Steps taken since the last melbm_set_state (host pointer). */
+MELBM_API int melbm_time_index(melbm_t h, int64_t* t);
+
+/* Device bytes held by the handle (host pointer). */
+MELBM_API int melbm_memory_bytes(melbm_t h, int64_t* bytes);
+
+/* Raw packed state for bit-exact checkpoint/resume: bytes = 40 N (F32) or 20 N
+ * (Q16); dst/src device or host.  set_raw_state also sets the time index. */
+MELBM_API int melbm_state_bytes(melbm_t h, int64_t* bytes);
+MELBM_API int melbm_get_raw_state(melbm_t h, void* dst, int64_t bytes);
+MELBM_API int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int64_t time_index);
+
+/* Differentiation (not in the paper; inverse problems motivate it, Sec. 1).
+ * melbm_forward_checkpointed: from the initial velocity u0[3N] (device) with
+ * rho = 1 and S = u0 u0, runs nsteps FP32-storage steps with the current force,
+ * storing a 16-bit checkpoint (deterministic rounding) every K steps.
+ * melbm_backward: given dL/d(rho, u, S) of the final state (10N device floats,
+ * component-major as melbm_get_moments), writes dL/du0[3N] and dL/dF[3N]
+ * (device; dL_dF may be NULL) by the hand-written discrete adjoint, recomputing
+ * each segment in FP32 from its checkpoint.  Requires MELBM_F32 storage. */
+MELBM_API int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps, int K);
+MELBM_API int melbm_backward(melbm_t h, const float* dL_dm_final, float* dL_du0, float* dL_dF);
+
+/* 16-bit codec of Sec. 5.4 on caller buffers (device pointers), for tests and
+ * tools.  stored[10][N] are the stored variables (rho, u, rho S^neq) in FP32;
+ * words[5][N] holds codes (2k, 2k+1) in the low and high half of word k.
+ * deterministic != 0 rounds to nearest (dither 1/2); otherwise the dither of
+ * (x, y, z, t ^ seed).  cuda_stream may be NULL. */
+MELBM_API int melbm_q16_encode(const float* stored, int nx, int ny, int nz, uint32_t t, uint32_t seed,
+                     int deterministic, uint32_t* words, void* cuda_stream);
+MELBM_API int melbm_q16_decode(const uint32_t* words, int64_t N, float* stored, void* cuda_stream);
+
+/* Message of the last failure of h (or of the last handle-less call if h is
+ * NULL).  Valid until the next call on the same handle. */
+MELBM_API const char* melbm_last_error(melbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MELBM_H */

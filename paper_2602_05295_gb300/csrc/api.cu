@@ -1,0 +1,471 @@
+// api.cu -- the extern "C" entry points declared in include/melbm.h: handle
+// life cycle, argument checks, host/device pointer handling and the step loop
+// (fluid kernel -> boundary kernel -> outflow copy, Sec. 4.2).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/melbm.h"
+#include "melbm_device.cuh"
+#include "melbm_launch.h"
+#include "melbm_adjoint.h"
+
+using namespace melbm;
+
+struct melbm_sim {
+  int nx = 0, ny = 0, nz = 0;
+  int64_t N = 0;
+  int storage = 0;
+  float tau = 0.f;
+  uint32_t seed = 0;
+  int64_t t = 0;
+  cudaStream_t stream = nullptr;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  // boundaries
+  uint8_t* mask = nullptr;
+  uint8_t* type = nullptr;
+  uint32_t* list_cell = nullptr;
+  uint32_t* list_word = nullptr;
+  int64_t L = 0;
+  uint32_t* cl_counts = nullptr;
+  uint32_t* cl_offsets = nullptr;
+  uint32_t* cl_total = nullptr;
+  int inflow_on = 0;
+  float inflow[4] = {1.f, 0.f, 0.f, 0.f};
+  int outflow_on = 0;
+  // force, staging, reductions
+  float* force = nullptr;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  double* red_partials = nullptr;
+  double* red_out = nullptr;
+  int64_t mem_bytes = 0;
+  bool poisoned = false;
+  std::string err;
+  melbm::AdjointState* adj = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(melbm_t h, int code, const char* fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (h) h->err = msg;
+  else g_err = msg;
+  return code;
+}
+
+int cuda_fail(melbm_t h, cudaError_t e, const char* where) {
+  if (h) h->poisoned = true;
+  return fail(h, MELBM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define MELBM_CUDA(h, call)                                       \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);        \
+  } while (0)
+
+int dev_alloc(melbm_t h, void** p, size_t bytes) {
+  if (bytes == 0) {
+    *p = nullptr;
+    return MELBM_OK;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(h, MELBM_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  if (h) h->mem_bytes += int64_t(bytes);
+  return MELBM_OK;
+}
+
+void dev_free(melbm_t h, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  if (h) h->mem_bytes -= int64_t(bytes);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t state_bytes(const melbm_sim* h) {
+  return size_t(h->N) * (h->storage == MELBM_Q16 ? 20 : 40);
+}
+
+int ensure_staging(melbm_t h, size_t bytes) {
+  if (h->staging_bytes >= bytes) return MELBM_OK;
+  dev_free(h, h->staging, h->staging_bytes);
+  h->staging = nullptr;
+  h->staging_bytes = 0;
+  int rc = dev_alloc(h, &h->staging, bytes);
+  if (rc) return rc;
+  h->staging_bytes = bytes;
+  return MELBM_OK;
+}
+
+void free_list(melbm_t h) {
+  dev_free(h, h->list_cell, size_t(h->L) * 4);
+  dev_free(h, h->list_word, size_t(h->L) * 4);
+  h->list_cell = h->list_word = nullptr;
+  h->L = 0;
+}
+
+// (Re)build types and the boundary list from the mask and the inflow/outflow flags.
+int reclassify(melbm_t h) {
+  free_list(h);
+  if (!h->mask && !h->inflow_on && !h->outflow_on) {
+    dev_free(h, h->type, size_t(h->N));
+    h->type = nullptr;
+    return MELBM_OK;
+  }
+  int rc;
+  if (!h->type && (rc = dev_alloc(h, (void**)&h->type, size_t(h->N)))) return rc;
+  const int64_t nb = classify_blocks(h->N);
+  if (!h->cl_counts) {
+    if ((rc = dev_alloc(h, (void**)&h->cl_counts, size_t(nb) * 4))) return rc;
+    if ((rc = dev_alloc(h, (void**)&h->cl_offsets, size_t(nb) * 4))) return rc;
+    if ((rc = dev_alloc(h, (void**)&h->cl_total, 4))) return rc;
+  }
+  MELBM_CUDA(h, launch_classify_count(h->nx, h->ny, h->nz, h->mask, h->inflow_on, h->outflow_on,
+                                     h->type, h->cl_counts, h->stream));
+  MELBM_CUDA(h, launch_exclusive_scan(h->cl_counts, h->cl_offsets, nb, h->cl_total, h->stream));
+  uint32_t total = 0;
+  MELBM_CUDA(h, cudaMemcpyAsync(&total, h->cl_total, 4, cudaMemcpyDeviceToHost, h->stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (total) {
+    if ((rc = dev_alloc(h, (void**)&h->list_cell, size_t(total) * 4))) return rc;
+    if ((rc = dev_alloc(h, (void**)&h->list_word, size_t(total) * 4))) return rc;
+    h->L = total;
+    MELBM_CUDA(h, launch_classify_scatter(h->nx, h->ny, h->nz, h->mask, h->type, h->cl_offsets,
+                                          h->list_cell, h->list_word, h->stream));
+  }
+  return MELBM_OK;
+}
+
+}  // namespace
+
+namespace melbm {
+// Accessors used by the adjoint translation unit.
+int sim_dims(melbm_t h, int* nx, int* ny, int* nz) {
+  *nx = h->nx;
+  *ny = h->ny;
+  *nz = h->nz;
+  return 0;
+}
+}  // namespace melbm
+
+extern "C" {
+
+int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, melbm_t* out) {
+  if (!out) return fail(nullptr, MELBM_EINVAL, "melbm_create: out is NULL");
+  *out = nullptr;
+  if (lattice != MELBM_D3Q27)
+    return fail(nullptr, MELBM_EINVAL, "melbm_create: lattice %d unsupported (only 27)", lattice);
+  if (nx < 1 || ny < 1 || nz < 1)
+    return fail(nullptr, MELBM_EINVAL, "melbm_create: bad grid %d x %d x %d", nx, ny, nz);
+  const int64_t N = int64_t(nx) * ny * nz;
+  if (N >= (int64_t(1) << 31))
+    return fail(nullptr, MELBM_EINVAL, "melbm_create: %lld cells exceed 2^31 - 1", (long long)N);
+  if (!(tau > 0.5f) || !(tau < 1e6f))
+    return fail(nullptr, MELBM_EINVAL, "melbm_create: tau = %g must exceed 1/2", double(tau));
+  if (storage != MELBM_F32 && storage != MELBM_Q16)
+    return fail(nullptr, MELBM_EINVAL, "melbm_create: storage %d unknown", storage);
+  melbm_sim* h = new (std::nothrow) melbm_sim;
+  if (!h) return fail(nullptr, MELBM_ENOMEM, "melbm_create: host allocation failed");
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->N = N;
+  h->tau = tau;
+  h->storage = storage;
+  const size_t sb = state_bytes(h);
+  int rc;
+  if ((rc = dev_alloc(h, &h->buf[0], sb)) || (rc = dev_alloc(h, &h->buf[1], sb)) ||
+      (rc = dev_alloc(h, (void**)&h->red_partials, size_t(reduce_blocks()) * 3 * 8)) ||
+      (rc = dev_alloc(h, (void**)&h->red_out, 3 * 8))) {
+    g_err = h->err;
+    melbm_destroy(h);
+    return rc;
+  }
+  // rest state (rho = 1, u = 0, S = 0) at time index 0
+  cudaError_t e = launch_rest_state(storage, nx, ny, nz, h->buf[0], 0, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cuda_fail(h, e, "melbm_create: initialising the rest state");
+    g_err = h->err;
+    melbm_destroy(h);
+    return MELBM_ECUDA;
+  }
+  *out = h;
+  return MELBM_OK;
+}
+
+int melbm_destroy(melbm_t h) {
+  if (!h) return MELBM_OK;
+  if (h->adj) adjoint_free(h->adj);
+  dev_free(h, h->buf[0], state_bytes(h));
+  dev_free(h, h->buf[1], state_bytes(h));
+  dev_free(h, h->mask, size_t(h->N));
+  dev_free(h, h->type, size_t(h->N));
+  free_list(h);
+  dev_free(h, h->cl_counts, 0);
+  dev_free(h, h->cl_offsets, 0);
+  dev_free(h, h->cl_total, 0);
+  dev_free(h, h->force, 0);
+  dev_free(h, h->staging, 0);
+  dev_free(h, h->red_partials, 0);
+  dev_free(h, h->red_out, 0);
+  delete h;
+  return MELBM_OK;
+}
+
+int melbm_set_stream(melbm_t h, void* s) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_stream: NULL handle");
+  h->stream = static_cast<cudaStream_t>(s);
+  return MELBM_OK;
+}
+
+int melbm_set_seed(melbm_t h, uint32_t seed) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_seed: NULL handle");
+  h->seed = seed;
+  return MELBM_OK;
+}
+
+int melbm_set_state(melbm_t h, const float* rho, const float* u, const float* S) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_state: NULL handle");
+  if (!rho || !u) return fail(h, MELBM_EINVAL, "melbm_set_state: rho and u are required");
+  const size_t N = size_t(h->N);
+  const bool dev = is_device_ptr(rho) && is_device_ptr(u) && (!S || is_device_ptr(S));
+  const float *r = rho, *uu = u, *ss = S;
+  if (!dev) {
+    int rc = ensure_staging(h, N * 4 * (S ? 10 : 4));
+    if (rc) return rc;
+    float* st = static_cast<float*>(h->staging);
+    const cudaMemcpyKind k = cudaMemcpyDefault;
+    MELBM_CUDA(h, cudaMemcpyAsync(st, rho, N * 4, k, h->stream));
+    MELBM_CUDA(h, cudaMemcpyAsync(st + N, u, N * 12, k, h->stream));
+    if (S) MELBM_CUDA(h, cudaMemcpyAsync(st + 4 * N, S, N * 24, k, h->stream));
+    r = st;
+    uu = st + N;
+    ss = S ? st + 4 * N : nullptr;
+  }
+  MELBM_CUDA(h, launch_set_state(h->storage, h->nx, h->ny, h->nz, r, uu, ss, h->buf[h->cur], 0,
+                                 h->seed, 0, h->stream));
+  if (!dev) MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->t = 0;
+  h->poisoned = false;
+  return MELBM_OK;
+}
+
+int melbm_get_moments(melbm_t h, float* rho, float* u, float* S) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_get_moments: NULL handle");
+  if (!rho && !u && !S) return fail(h, MELBM_EINVAL, "melbm_get_moments: no output");
+  const size_t N = size_t(h->N);
+  const bool dev = (!rho || is_device_ptr(rho)) && (!u || is_device_ptr(u)) && (!S || is_device_ptr(S));
+  if (dev) {
+    MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], rho, u, S, h->stream));
+    return MELBM_OK;
+  }
+  int rc = ensure_staging(h, N * 40);
+  if (rc) return rc;
+  float* st = static_cast<float*>(h->staging);
+  MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], st, st + N, st + 4 * N,
+                                   h->stream));
+  const cudaMemcpyKind k = cudaMemcpyDefault;
+  if (rho) MELBM_CUDA(h, cudaMemcpyAsync(rho, st, N * 4, k, h->stream));
+  if (u) MELBM_CUDA(h, cudaMemcpyAsync(u, st + N, N * 12, k, h->stream));
+  if (S) MELBM_CUDA(h, cudaMemcpyAsync(S, st + 4 * N, N * 24, k, h->stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MELBM_OK;
+}
+
+int melbm_set_solid(melbm_t h, const uint8_t* mask) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_solid: NULL handle");
+  if (mask && !is_device_ptr(mask)) return fail(h, MELBM_EINVAL, "melbm_set_solid: mask must be a device pointer");
+  if (!mask) {
+    dev_free(h, h->mask, size_t(h->N));
+    h->mask = nullptr;
+  } else {
+    int rc;
+    if (!h->mask && (rc = dev_alloc(h, (void**)&h->mask, size_t(h->N)))) return rc;
+    MELBM_CUDA(h, cudaMemcpyAsync(h->mask, mask, size_t(h->N), cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return reclassify(h);
+}
+
+int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float uz) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_inflow: NULL handle");
+  if (face != 0) return fail(h, MELBM_EINVAL, "melbm_set_inflow: only face 0 (x = 0) is supported");
+  if (!(rho > 0.f)) return fail(h, MELBM_EINVAL, "melbm_set_inflow: rho must be positive");
+  h->inflow_on = 1;
+  h->inflow[0] = rho;
+  h->inflow[1] = ux;
+  h->inflow[2] = uy;
+  h->inflow[3] = uz;
+  return reclassify(h);
+}
+
+int melbm_set_outflow(melbm_t h, int face) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_outflow: NULL handle");
+  if (face != 1) return fail(h, MELBM_EINVAL, "melbm_set_outflow: only face 1 (x = nx-1) is supported");
+  h->outflow_on = 1;
+  return reclassify(h);
+}
+
+int melbm_get_boundary_list(melbm_t h, uint32_t* cells, uint32_t* words, int64_t capacity,
+                            int64_t* count) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_get_boundary_list: NULL handle");
+  if (count) *count = h->L;
+  if ((cells || words) && capacity < h->L)
+    return fail(h, MELBM_EINVAL, "melbm_get_boundary_list: capacity %lld < %lld",
+                (long long)capacity, (long long)h->L);
+  if (h->L) {
+    if (cells) MELBM_CUDA(h, cudaMemcpyAsync(cells, h->list_cell, size_t(h->L) * 4, cudaMemcpyDefault, h->stream));
+    if (words) MELBM_CUDA(h, cudaMemcpyAsync(words, h->list_word, size_t(h->L) * 4, cudaMemcpyDefault, h->stream));
+    MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return MELBM_OK;
+}
+
+int melbm_get_types(melbm_t h, uint8_t* types) {
+  if (!h || !types) return fail(h, MELBM_EINVAL, "melbm_get_types: NULL argument");
+  if (h->type) {
+    MELBM_CUDA(h, cudaMemcpyAsync(types, h->type, size_t(h->N), cudaMemcpyDefault, h->stream));
+  } else {
+    MELBM_CUDA(h, cudaMemsetAsync(types, 0, size_t(h->N), h->stream));
+  }
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MELBM_OK;
+}
+
+int melbm_set_force(melbm_t h, const float* F) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_force: NULL handle");
+  if (!F) {
+    dev_free(h, h->force, size_t(h->N) * 12);
+    h->force = nullptr;
+    return MELBM_OK;
+  }
+  int rc;
+  if (!h->force && (rc = dev_alloc(h, (void**)&h->force, size_t(h->N) * 12))) return rc;
+  MELBM_CUDA(h, cudaMemcpyAsync(h->force, F, size_t(h->N) * 12, cudaMemcpyDefault, h->stream));
+  return MELBM_OK;
+}
+
+int melbm_step(melbm_t h, int n) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_step: NULL handle");
+  if (n < 0) return fail(h, MELBM_EINVAL, "melbm_step: n = %d < 0", n);
+  if (h->poisoned) return fail(h, MELBM_ESTATE, "melbm_step: an earlier CUDA failure left the state undefined; call melbm_set_state");
+  const float omega = 1.0f / h->tau;
+  for (int s = 0; s < n; ++s) {
+    const uint32_t t_out = uint32_t(h->t + 1);
+    void* in = h->buf[h->cur];
+    void* out = h->buf[1 - h->cur];
+    MELBM_CUDA(h, launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
+                               h->seed, h->stream));
+    if (h->L)
+      MELBM_CUDA(h, launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega,
+                                    h->list_cell, h->list_word, h->L, h->inflow, t_out, h->seed,
+                                    h->stream));
+    if (h->outflow_on && h->type)
+      MELBM_CUDA(h, launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream));
+    h->cur = 1 - h->cur;
+    h->t += 1;
+  }
+  return MELBM_OK;
+}
+
+int melbm_reduce(melbm_t h, double* mass, double* ke) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_reduce: NULL handle");
+  MELBM_CUDA(h, launch_reduce(h->storage, h->N, h->buf[h->cur], h->type, h->red_partials,
+                              h->red_out, h->stream));
+  double out[3];
+  MELBM_CUDA(h, cudaMemcpyAsync(out, h->red_out, sizeof out, cudaMemcpyDeviceToHost, h->stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (mass) *mass = out[0];
+  if (ke) *ke = out[1];
+  if (h->storage == MELBM_Q16 && out[2] > 0.0)
+    return fail(h, MELBM_WSATURATED, "melbm_reduce: %.0f non-solid 16-bit codes on a range limit", out[2]);
+  return MELBM_OK;
+}
+
+int melbm_time_index(melbm_t h, int64_t* t) {
+  if (!h || !t) return fail(h, MELBM_EINVAL, "melbm_time_index: NULL argument");
+  *t = h->t;
+  return MELBM_OK;
+}
+
+int melbm_memory_bytes(melbm_t h, int64_t* bytes) {
+  if (!h || !bytes) return fail(h, MELBM_EINVAL, "melbm_memory_bytes: NULL argument");
+  *bytes = h->mem_bytes;
+  return MELBM_OK;
+}
+
+int melbm_state_bytes(melbm_t h, int64_t* bytes) {
+  if (!h || !bytes) return fail(h, MELBM_EINVAL, "melbm_state_bytes: NULL argument");
+  *bytes = int64_t(state_bytes(h));
+  return MELBM_OK;
+}
+
+int melbm_get_raw_state(melbm_t h, void* dst, int64_t bytes) {
+  if (!h || !dst) return fail(h, MELBM_EINVAL, "melbm_get_raw_state: NULL argument");
+  if (bytes != int64_t(state_bytes(h)))
+    return fail(h, MELBM_EINVAL, "melbm_get_raw_state: bytes %lld != %lld", (long long)bytes,
+                (long long)state_bytes(h));
+  MELBM_CUDA(h, cudaMemcpyAsync(dst, h->buf[h->cur], size_t(bytes), cudaMemcpyDefault, h->stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MELBM_OK;
+}
+
+int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int64_t time_index) {
+  if (!h || !src) return fail(h, MELBM_EINVAL, "melbm_set_raw_state: NULL argument");
+  if (bytes != int64_t(state_bytes(h)))
+    return fail(h, MELBM_EINVAL, "melbm_set_raw_state: bytes %lld != %lld", (long long)bytes,
+                (long long)state_bytes(h));
+  if (time_index < 0) return fail(h, MELBM_EINVAL, "melbm_set_raw_state: negative time index");
+  MELBM_CUDA(h, cudaMemcpyAsync(h->buf[h->cur], src, size_t(bytes), cudaMemcpyDefault, h->stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->t = time_index;
+  h->poisoned = false;
+  return MELBM_OK;
+}
+
+int melbm_q16_encode(const float* stored, int nx, int ny, int nz, uint32_t t, uint32_t seed,
+                     int deterministic, uint32_t* words, void* stream) {
+  if (!stored || !words) return fail(nullptr, MELBM_EINVAL, "melbm_q16_encode: NULL pointer");
+  if (nx < 1 || ny < 1 || nz < 1 || int64_t(nx) * ny * nz >= (int64_t(1) << 31))
+    return fail(nullptr, MELBM_EINVAL, "melbm_q16_encode: bad grid");
+  cudaError_t e = launch_q16_encode(stored, nx, ny, nz, t, seed, deterministic,
+                                    words, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "melbm_q16_encode");
+  return MELBM_OK;
+}
+
+int melbm_q16_decode(const uint32_t* words, int64_t N, float* stored, void* stream) {
+  if (!stored || !words || N < 0 || N >= (int64_t(1) << 31))
+    return fail(nullptr, MELBM_EINVAL, "melbm_q16_decode: bad argument");
+  if (N == 0) return MELBM_OK;
+  cudaError_t e = launch_q16_decode(words, N, stored, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "melbm_q16_decode");
+  return MELBM_OK;
+}
+
+const char* melbm_last_error(melbm_t h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

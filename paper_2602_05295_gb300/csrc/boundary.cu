@@ -1,0 +1,165 @@
+// boundary.cu -- the boundary side of the split design (Sec. 4.2): after the
+// uniform fluid kernel has written every cell, the listed cells are rewritten.
+//   * FLUID_BOUNDARY: the full update is recomputed from the input state with
+//     halfway bounce-back for solid links, f_i(x) = f+_{opp(i)}(x) when x - c_i is
+//     solid (in place of the paper's additive triangle correction, which needs a
+//     mesh; recomputing from the input gives the post-streaming moments directly,
+//     with no atomics and no second rounding of the 16-bit state).
+//   * INFLOW: reset to the equilibrium (rho_in, u_in, S = u_in u_in).
+// The outflow pass then copies the stored state of x = nx-2 onto x = nx-1.
+#include "melbm_device.cuh"
+#include "melbm_launch.h"
+
+namespace melbm {
+
+struct BoundaryParams {
+  int nx, ny, nz;
+  const void* in;
+  void* out;
+  const float* force;
+  float omega;
+  const uint32_t* cells;
+  const uint32_t* words;
+  int64_t count;
+  float in_rho, in_ux, in_uy, in_uz;
+  uint32_t t_out, seed;
+};
+
+// f+_i / w_i - 1 from the tensor-product Hermite coefficients (P_2(c) = c^2 - 1/3).
+__device__ __forceinline__ float hermite_eval(const Coef& A, int cx, int cy, int cz) {
+  const float fx = float(cx), fy = float(cy), fz = float(cz);
+  const float qx = fx * fx - (1.0f / 3.0f), qy = fy * fy - (1.0f / 3.0f),
+              qz = fz * fz - (1.0f / 3.0f);
+  return A.a000 + A.a100 * fx + A.a010 * fy + A.a001 * fz + A.a200 * qx + A.a020 * qy +
+         A.a002 * qz + A.a110 * fx * fy + A.a101 * fx * fz + A.a011 * fy * fz + A.a210 * qx * fy +
+         A.a120 * fx * qy + A.a201 * qx * fz + A.a102 * fx * qz + A.a021 * qy * fz +
+         A.a012 * fy * qz + A.a111 * fx * fy * fz;
+}
+
+template <int STORAGE, bool FORCE>
+__global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= P.count) return;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const size_t N = size_t(nx) * ny * nz;
+  const uint32_t n = P.cells[k];
+  const uint32_t word = P.words[k];
+  const uint32_t type = word >> 27;
+  const int x = int(n % uint32_t(nx));
+  const int y = int((n / uint32_t(nx)) % uint32_t(ny));
+  const int z = int(n / (uint32_t(nx) * uint32_t(ny)));
+  if (type == T_INFLOW) {
+    Stored s;
+    s.drho = P.in_rho - 1.0f;
+    s.ux = P.in_ux;
+    s.uy = P.in_uy;
+    s.uz = P.in_uz;
+    s.nxx = s.nyy = s.nzz = s.nxy = s.nxz = s.nyz = 0.f;
+    store_stored<STORAGE>(P.out, N, n, s, x, y, z, P.t_out, P.seed);
+    return;
+  }
+  float m000 = 0.f, m100 = 0.f, m010 = 0.f, m001 = 0.f, m200 = 0.f, m020 = 0.f, m002 = 0.f,
+        m110 = 0.f, m101 = 0.f, m011 = 0.f;
+  // post-collision coefficients of the cell itself (used by every bounced link)
+  float fx0 = 0.f, fy0 = 0.f, fz0 = 0.f;
+  if (FORCE) {
+    fx0 = P.force[n];
+    fy0 = P.force[N + n];
+    fz0 = P.force[2 * N + n];
+  }
+  const Coef Aself = collide_coef<FORCE>(load_stored<STORAGE>(P.in, N, n), P.omega, fx0, fy0, fz0);
+  for (int i = 0; i < 27; ++i) {
+    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    float g;  // (f_i / w_i - 1)
+    if ((word >> i) & 1u) {
+      g = hermite_eval(Aself, -cx, -cy, -cz);  // bounce-back: population opp(i) of x
+    } else {
+      const size_t src = size_t(wrapi(x - cx, nx)) +
+                         size_t(nx) * (size_t(wrapi(y - cy, ny)) + size_t(ny) * wrapi(z - cz, nz));
+      float fx = 0.f, fy = 0.f, fz = 0.f;
+      if (FORCE) {
+        fx = P.force[src];
+        fy = P.force[N + src];
+        fz = P.force[2 * N + src];
+      }
+      const Coef A = collide_coef<FORCE>(load_stored<STORAGE>(P.in, N, src), P.omega, fx, fy, fz);
+      g = hermite_eval(A, cx, cy, cz);
+    }
+    const float w = (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *
+                    (cz ? (1.0f / 6.0f) : (2.0f / 3.0f));
+    const float f = w * g;
+    m000 += f;
+    m100 += cx * f;
+    m010 += cy * f;
+    m001 += cz * f;
+    m200 += (cx * cx - (1.0f / 3.0f)) * f;
+    m020 += (cy * cy - (1.0f / 3.0f)) * f;
+    m002 += (cz * cz - (1.0f / 3.0f)) * f;
+    m110 += float(cx * cy) * f;
+    m101 += float(cx * cz) * f;
+    m011 += float(cy * cz) * f;
+  }
+  const Stored o = finish_moments<FORCE>(m000, m100, m010, m001, m200, m020, m002, m110, m101,
+                                         m011, fx0, fy0, fz0);
+  store_stored<STORAGE>(P.out, N, n, o, x, y, z, P.t_out, P.seed);
+}
+
+cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
+                            const float* force, float omega, const uint32_t* cells,
+                            const uint32_t* words, int64_t count, const float inflow[4],
+                            uint32_t t_out, uint32_t seed, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  BoundaryParams p;
+  p.nx = nx;
+  p.ny = ny;
+  p.nz = nz;
+  p.in = in;
+  p.out = out;
+  p.force = force;
+  p.omega = omega;
+  p.cells = cells;
+  p.words = words;
+  p.count = count;
+  p.in_rho = inflow[0];
+  p.in_ux = inflow[1];
+  p.in_uy = inflow[2];
+  p.in_uz = inflow[3];
+  p.t_out = t_out;
+  p.seed = seed;
+  const unsigned blocks = unsigned((count + 127) / 128);
+  if (storage == ST_Q16) {
+    if (force) boundary_kernel<ST_Q16, true><<<blocks, 128, 0, st>>>(p);
+    else boundary_kernel<ST_Q16, false><<<blocks, 128, 0, st>>>(p);
+  } else {
+    if (force) boundary_kernel<ST_F32, true><<<blocks, 128, 0, st>>>(p);
+    else boundary_kernel<ST_F32, false><<<blocks, 128, 0, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- outflow
+template <int WORDS>
+__global__ void outflow_kernel(int nx, int ny, int nz, uint32_t* buf, const uint8_t* type) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // (y, z) index
+  const int64_t M = int64_t(ny) * nz;
+  if (k >= M) return;
+  const size_t N = size_t(nx) * ny * nz;
+  const size_t n = size_t(nx - 1) + size_t(nx) * size_t(k);
+  if (type[n] != T_OUTFLOW) return;
+#pragma unroll
+  for (int w = 0; w < WORDS; ++w) buf[w * N + n] = buf[w * N + n - 1];
+}
+
+cudaError_t launch_outflow(int storage, int nx, int ny, int nz, void* buf, const uint8_t* type,
+                           cudaStream_t st) {
+  if (nx < 2) return cudaSuccess;
+  const int64_t M = int64_t(ny) * nz;
+  const unsigned blocks = unsigned((M + 255) / 256);
+  if (storage == ST_Q16)
+    outflow_kernel<5><<<blocks, 256, 0, st>>>(nx, ny, nz, static_cast<uint32_t*>(buf), type);
+  else
+    outflow_kernel<10><<<blocks, 256, 0, st>>>(nx, ny, nz, static_cast<uint32_t*>(buf), type);
+  return cudaGetLastError();
+}
+
+}  // namespace melbm
