@@ -25,15 +25,18 @@ struct BoundaryParams {
   uint32_t t_out, seed;
 };
 
-// f+_i / w_i - 1 from the tensor-product Hermite coefficients (P_2(c) = c^2 - 1/3).
-__device__ __forceinline__ float hermite_eval(const Coef& A, int cx, int cy, int cz) {
+// f+_i / w_i - 1 from the Hermite moments: the coefficient of P_p P_q P_r is
+// mu_pqr divided by the D1Q3 norms (1, 1/3, 2/9) of each factor (P_2(c) = c^2 - 1/3).
+__device__ __forceinline__ float hermite_eval(const Mom17& A, int cx, int cy, int cz) {
   const float fx = float(cx), fy = float(cy), fz = float(cz);
   const float qx = fx * fx - (1.0f / 3.0f), qy = fy * fy - (1.0f / 3.0f),
               qz = fz * fz - (1.0f / 3.0f);
-  return A.a000 + A.a100 * fx + A.a010 * fy + A.a001 * fz + A.a200 * qx + A.a020 * qy +
-         A.a002 * qz + A.a110 * fx * fy + A.a101 * fx * fz + A.a011 * fy * fz + A.a210 * qx * fy +
-         A.a120 * fx * qy + A.a201 * qx * fz + A.a102 * fx * qz + A.a021 * qy * fz +
-         A.a012 * fy * qz + A.a111 * fx * fy * fz;
+  return A.m000 + 3.0f * (A.m100 * fx + A.m010 * fy + A.m001 * fz) +
+         4.5f * (A.m200 * qx + A.m020 * qy + A.m002 * qz) +
+         9.0f * (A.m110 * fx * fy + A.m101 * fx * fz + A.m011 * fy * fz) +
+         13.5f * (A.m210 * qx * fy + A.m120 * fx * qy + A.m201 * qx * fz + A.m102 * fx * qz +
+                  A.m021 * qy * fz + A.m012 * fy * qz) +
+         27.0f * A.m111 * fx * fy * fz;
 }
 
 template <int STORAGE, bool FORCE>
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
     fy0 = P.force[N + n];
     fz0 = P.force[2 * N + n];
   }
-  const Coef Aself = collide_coef<FORCE>(load_stored<STORAGE>(P.in, N, n), P.omega, fx0, fy0, fz0);
+  const Mom17 Aself = collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n), P.omega, fx0, fy0, fz0);
   for (int i = 0; i < 27; ++i) {
     const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
     float g;  // (f_i / w_i - 1)
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
         fy = P.force[N + src];
         fz = P.force[2 * N + src];
       }
-      const Coef A = collide_coef<FORCE>(load_stored<STORAGE>(P.in, N, src), P.omega, fx, fy, fz);
+      const Mom17 A = collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, src), P.omega, fx, fy, fz);
       g = hermite_eval(A, cx, cy, cz);
     }
     const float w = (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *

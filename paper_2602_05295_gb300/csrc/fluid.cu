@@ -9,7 +9,7 @@
 // Streaming and moment recovery are done separably: the populations of D3Q27 are
 // the tensor product of three D1Q3 sets, so "pull f_i from x - c_i, then take
 // moments" factors into three 1D passes (x, then y, then z) on the Hermite
-// coefficients, each a 3-point stencil.  Only the coefficients that can reach the
+// moments of f+, each a 3-point stencil.  Only the moments that can reach the
 // ten output moments are carried: 17 -> 24 after x, -> 18 after y, -> 10 after z.
 //
 // Work decomposition (one thread per (x, y) column, marching along z):
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(FX* FY, 1) fluid_kernel(FluidParams P) {
       fy = __ldg(P.force + N + n);
       fz = __ldg(P.force + 2 * N + n);
     }
-    const Coef A = collide_coef<FORCE>(s, omega, fx, fy, fz);
+    const Mom17 A = collide_moments<FORCE>(s, omega, fx, fy, fz);
 
     // ---------------- x pass: slices (q', r'), inputs p' = 0, 1, 2 -> outputs p = 0, 1, 2
     float X[3][3][3];  // X[p][q'][r'] (only the 24 reachable entries are set/used)
@@ -86,16 +86,16 @@ __global__ void __launch_bounds__(FX* FY, 1) fluid_kernel(FluidParams P) {
     const float mr = __shfl_down_sync(FULL, ph.m, 1);                   \
     X[0][Q][R] = proj0(pl, ph.z, mr);                                   \
     X[1][Q][R] = proj1(pl, mr);                                         \
-    X[2][Q][R] = proj2(X[0][Q][R], ph.z);                               \
+    X[2][Q][R] = proj2(pl, mr, X[0][Q][R]);                               \
   }
-    MELBM_XPASS(0, 0, A.a000, A.a100, A.a200)
-    MELBM_XPASS(1, 0, A.a010, A.a110, A.a210)
-    MELBM_XPASS(0, 1, A.a001, A.a101, A.a201)
-    MELBM_XPASS(2, 0, A.a020, A.a120, 0.f)
-    MELBM_XPASS(0, 2, A.a002, A.a102, 0.f)
-    MELBM_XPASS(1, 1, A.a011, A.a111, 0.f)
-    MELBM_XPASS(2, 1, A.a021, 0.f, 0.f)
-    MELBM_XPASS(1, 2, A.a012, 0.f, 0.f)
+    MELBM_XPASS(0, 0, A.m000, A.m100, A.m200)
+    MELBM_XPASS(1, 0, A.m010, A.m110, A.m210)
+    MELBM_XPASS(0, 1, A.m001, A.m101, A.m201)
+    MELBM_XPASS(2, 0, A.m020, A.m120, 0.f)
+    MELBM_XPASS(0, 2, A.m002, A.m102, 0.f)
+    MELBM_XPASS(1, 1, A.m011, A.m111, 0.f)
+    MELBM_XPASS(2, 1, A.m021, 0.f, 0.f)
+    MELBM_XPASS(1, 2, A.m012, 0.f, 0.f)
 #undef MELBM_XPASS
     X[2][2][2] = 0.f;  // (q', r') = (2, 2) has no input coefficient
     X[0][2][2] = X[1][2][2] = 0.f;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(FX* FY, 1) fluid_kernel(FluidParams P) {
         const float mr = sp[((NSY + s_) * FY + row + 1) * FX + lane];
         Y[p][0][r] = proj0(pl, yz0[s_], mr);
         if (p <= 1) Y[p][1][r] = proj1(pl, mr);
-        if (p == 0) Y[p][2][r] = proj2(Y[p][0][r], yz0[s_]);
+        if (p == 0) Y[p][2][r] = proj2(pl, mr, Y[p][0][r]);
       }
 
     // ---------------- z pass: directional populations along z for slices (p, q)
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(FX* FY, 1) fluid_kernel(FluidParams P) {
       for (int k = 0; k < 6; ++k) {
         M[k][0] = proj0(zpm[k], zp0[k], zm[k]);
         M[k][1] = proj1(zpm[k], zm[k]);
-        M[k][2] = proj2(M[k][0], zp0[k]);
+        M[k][2] = proj2(zpm[k], zm[k], M[k][0]);
       }
       // slices: 0:(0,0) 1:(1,0) 2:(0,1) 3:(2,0) 4:(1,1) 5:(0,2)
       const Stored o = finish_moments<FORCE>(M[0][0], M[1][0], M[2][0], M[0][1], M[3][0], M[5][0],

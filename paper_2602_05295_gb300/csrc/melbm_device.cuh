@@ -105,10 +105,11 @@ __device__ __forceinline__ Dither dither10(uint32_t x, uint32_t y, uint32_t z, u
   const uint32_t w[4] = {v0, v1, v2, v3};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    // (2^23 + f) / 4096 - 2048 = f / 4096 and (2^23 + f 2^12) 2^-24 - 1/2 = f / 4096, exactly
+    // the float with bits 0x4B000000 | f (f < 2^23) is 2^23 + f, so
+    // (2^23 + f) / 4096 - 2048 = f / 4096 exactly
     r.d[2 * k] = __fmaf_rn(__uint_as_float(0x4B000000u | (w[k] & 0xFFFu)), 1.0f / 4096.0f, -2048.0f);
     r.d[2 * k + 1] =
-        __fmaf_rn(__uint_as_float(0x4B000000u | (w[k] & 0xFFF000u)), 1.0f / 16777216.0f, -0.5f);
+        __fmaf_rn(__uint_as_float(0x4B000000u | ((w[k] >> 12) & 0xFFFu)), 1.0f / 4096.0f, -2048.0f);
   }
   const uint32_t f8 = (v0 >> 24) | ((v1 >> 24) << 8);
   const uint32_t f9 = (v2 >> 24) | ((v3 >> 24) << 8);
@@ -208,26 +209,27 @@ __device__ __forceinline__ void store_stored<ST_Q16>(void* buf, size_t N, size_t
 }
 
 // ----------------------------------------------------------------- collision
-// The 17 nonzero coefficients A_pqr of the post-collision populations in the
-// tensor-product Hermite basis P_0 = 1, P_1 = c, P_2 = c^2 - 1/3:
-//   f+_i = w_i (1 + sum_pqr A_pqr P_p(cx) P_q(cy) P_r(cz)),
-// i.e. Eq. three_order_f with A_000 = rho - 1 (rest removed), A_a = 3 rho u_a,
-// A_aa = 9/2 rho S_aa, A_ab = 9 rho S_ab, A_aab = 27/2 rho T_aab, A_xyz = 27 rho T_xyz.
-struct Coef {
-  float a000, a100, a010, a001;
-  float a200, a020, a002, a110, a101, a011;
-  float a210, a120, a201, a102, a021, a012, a111;
+// The 17 nonzero Hermite moments mu_pqr = sum_i P_p(cx) P_q(cy) P_r(cz) f+_i of
+// the post-collision populations, with P_0 = 1, P_1 = c, P_2 = c^2 - 1/3 and the
+// rest populations w_i removed (mu_000 = rho - 1):
+//   mu_a = rho u_a, mu_aa = rho S_aa, mu_ab = rho S_ab, mu_aab = rho T_aab,
+//   mu_xyz = rho T_xyz   (Eq. three_order_f: f+ is the third-order Hermite
+// expansion with exactly these moments, T_abg = S_ab u_g + S_ag u_b + S_bg u_a - 2 u_a u_b u_g).
+struct Mom17 {
+  float m000, m100, m010, m001;
+  float m200, m020, m002, m110, m101, m011;
+  float m210, m120, m201, m102, m021, m012, m111;
 };
 
-// Moment-space collision of App. A applied to the stored variables, then the
-// Hermite coefficients.  With S = n/rho + u u the collision reads
+// Moment-space collision of App. A applied to the stored variables.  With
+// S = n/rho + u u the collision reads
 //   u+ = u + F/(2 rho)
 //   rho (S+ - u+ u+) = (1 - 1/tau) dev(n + sym(F u)) - F F / (4 rho)
 // where dev() removes the trace and sym(F u)_ab = (F_a u_b + F_b u_a)/2: the
 // trace of the non-equilibrium stress is reset, its deviator relaxes by (1 - 1/tau).
 template <bool FORCE>
-__device__ __forceinline__ Coef collide_coef(const Stored& s, float omega, float fx, float fy,
-                                             float fz) {
+__device__ __forceinline__ Mom17 collide_moments(const Stored& s, float omega, float fx, float fy,
+                                                 float fz) {
   const float rho = 1.0f + s.drho;
   const float om1 = 1.0f - omega;
   float ux = s.ux, uy = s.uy, uz = s.uz;
@@ -260,53 +262,58 @@ __device__ __forceinline__ Coef collide_coef(const Stored& s, float omega, float
   }
   // rho u+, rho S+ = rho u+ u+ + rho E
   const float rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
-  const float sxx = rux * ux + exx, syy = ruy * uy + eyy, szz = ruz * uz + ezz;
-  const float sxy = rux * uy + exy, sxz = rux * uz + exz, syz = ruy * uz + eyz;
-  Coef A;
-  A.a000 = s.drho;
-  A.a100 = 3.0f * rux;
-  A.a010 = 3.0f * ruy;
-  A.a001 = 3.0f * ruz;
-  A.a200 = 4.5f * sxx;
-  A.a020 = 4.5f * syy;
-  A.a002 = 4.5f * szz;
-  A.a110 = 9.0f * sxy;
-  A.a101 = 9.0f * sxz;
-  A.a011 = 9.0f * syz;
+  Mom17 A;
+  A.m000 = s.drho;
+  A.m100 = rux;
+  A.m010 = ruy;
+  A.m001 = ruz;
+  A.m200 = rux * ux + exx;
+  A.m020 = ruy * uy + eyy;
+  A.m002 = ruz * uz + ezz;
+  A.m110 = rux * uy + exy;
+  A.m101 = rux * uz + exz;
+  A.m011 = ruy * uz + eyz;
   // rho T_aab = u_b rho S_aa + 2 u_a rho E_ab
-  A.a210 = 13.5f * (uy * sxx + 2.0f * ux * exy);  // xxy
-  A.a120 = 13.5f * (ux * syy + 2.0f * uy * exy);  // xyy
-  A.a201 = 13.5f * (uz * sxx + 2.0f * ux * exz);  // xxz
-  A.a102 = 13.5f * (ux * szz + 2.0f * uz * exz);  // xzz
-  A.a021 = 13.5f * (uz * syy + 2.0f * uy * eyz);  // yyz
-  A.a012 = 13.5f * (uy * szz + 2.0f * uz * eyz);  // yzz
+  A.m210 = uy * A.m200 + 2.0f * ux * exy;  // xxy
+  A.m120 = ux * A.m020 + 2.0f * uy * exy;  // xyy
+  A.m201 = uz * A.m200 + 2.0f * ux * exz;  // xxz
+  A.m102 = ux * A.m002 + 2.0f * uz * exz;  // xzz
+  A.m021 = uz * A.m020 + 2.0f * uy * eyz;  // yyz
+  A.m012 = uy * A.m002 + 2.0f * uz * eyz;  // yzz
   // rho T_xyz = rho ux uy uz + rho (E_xy uz + E_xz uy + E_yz ux)
-  A.a111 = 27.0f * (rux * uy * uz + exy * uz + exz * uy + eyz * ux);
+  A.m111 = rux * uy * uz + exy * uz + exz * uy + eyz * ux;
   return A;
 }
 
 // ----------------------------------------------------------------- 1D lattice pass
 // One axis of the separable stream: D3Q27 is the tensor product of three D1Q3
-// lattices (c in {-1, 0, 1}, weights 1/6, 2/3, 1/6).  Along one axis the
-// coefficients (a0, a1, a2) of P_0, P_1, P_2 become the three directional
-// populations phi_c = w(c) sum_p a_p P_p(c); streaming pulls phi_+ from x-1 and
-// phi_- from x+1; projecting back on P_p gives the new coefficients.
+// lattices (c in {-1, 0, 1}, weights 1/6, 2/3, 1/6).  Along one axis the local
+// moments (mu0, mu1, mu2) on (P_0, P_1, P_2) define the three directional
+// populations  phi_c = w(c) (mu0 + 3 c mu1 + 9/2 P_2(c) mu2):
+//   phi_s = mu0/6 + mu2/2,  phi_0 = mu0 - 2 phi_s,  phi_(+-1) = phi_s +- mu1/2.
+// Streaming pulls phi_+ from x-1 and phi_- from x+1; the new moments are
+//   m0 = phi_+ + phi_0 + phi_-,  m1 = phi_+ - phi_-,  m2 = phi_+ + phi_- - m0/3.
+// Written this way the sums of m0 and m1 over the grid equal those of mu0 and
+// mu1 whatever the FP32 rounding of 1/6: mass and momentum are conserved up to
+// unbiased rounding instead of drifting with the rounded lattice weights.
 struct Phi {
   float p, z, m;  // phi_{+1}, phi_0, phi_{-1}
 };
-__device__ __forceinline__ Phi phi3(float a0, float a1, float a2) {
+__device__ __forceinline__ Phi phi3(float mu0, float mu1, float mu2) {
   Phi r;
-  r.z = (2.0f / 3.0f) * a0 - (2.0f / 9.0f) * a2;
-  const float t = (1.0f / 6.0f) * a0 + (1.0f / 9.0f) * a2;
-  r.p = t + (1.0f / 6.0f) * a1;
-  r.m = t - (1.0f / 6.0f) * a1;
+  const float s = __fmaf_rn(mu0, 1.0f / 6.0f, 0.5f * mu2);
+  r.z = __fmaf_rn(-2.0f, s, mu0);
+  r.p = __fmaf_rn(0.5f, mu1, s);
+  r.m = __fmaf_rn(-0.5f, mu1, s);
   return r;
 }
 // Projection after streaming: pl = phi_+ pulled from the minus side, z = own
 // phi_0, mr = phi_- pulled from the plus side.
 __device__ __forceinline__ float proj0(float pl, float z, float mr) { return pl + z + mr; }
 __device__ __forceinline__ float proj1(float pl, float mr) { return pl - mr; }
-__device__ __forceinline__ float proj2(float o0, float z) { return (2.0f / 3.0f) * o0 - z; }
+__device__ __forceinline__ float proj2(float pl, float mr, float o0) {
+  return __fmaf_rn(-1.0f / 3.0f, o0, pl + mr);
+}
 
 // Stored variables from the ten streamed moments (rest removed):
 //   rho' = 1 + m000, rho' u' = m_a + F_a/2, rho' S'_ab = m_ab, n'_ab = m_ab - (rho' u'_a) u'_b.

@@ -269,7 +269,9 @@ def test_reduce_matches_oracle_and_host_io(M, orc):
         g = read(sim)
         Mg, Eg = sim.reduce()
         Mo, Eo = orc.reduce(g)
-        assert abs(Mg - Mo) / Mo < 1e-12 and abs(Eg - Eo) / Eo < 1e-6
+        # the GPU sums rho - 1 as stored; g holds rho rounded to FP32 (f32 storage)
+        tol = 1e-12 if storage == "q16" else 1e-9
+        assert abs(Mg - Mo) / Mo < tol and abs(Eg - Eo) / Eo < 1e-6, (Mg, Mo, Eg, Eo)
         # host-pointer path gives the same values as the device path
         rho = torch.empty(N, dtype=torch.float32).pin_memory()
         u = torch.empty(3, N, dtype=torch.float32).pin_memory()
