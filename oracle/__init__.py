@@ -76,6 +76,7 @@ def lib():
             L.orc_encode.argtypes = [I, I, I, P, U32, U32, I, P]
             L.orc_decode.argtypes = [I64, P, P]
             L.orc_ranges.argtypes = [P, P]
+            L.orc_codec_constants.argtypes = [I, P]
             _lib = L
     return _lib
 
@@ -230,6 +231,13 @@ def dither(x, y, z, t, seed):
     return d
 
 
+def codec_constants(k):
+    """(qc, step, c, K, b) of component k's 16-bit grid (FP32 values)."""
+    out = np.empty(5)
+    lib().orc_codec_constants(int(k), _p(out))
+    return out
+
+
 def public_to_stored(m):
     """(rho, u, S) -> (rho, u, rho S^neq) with rho S^neq = rho (S - u u) (Sec. 5.4)."""
     m = _f64(m)
@@ -242,6 +250,14 @@ def public_to_stored(m):
     for k, (a, b) in enumerate(pairs):
         out[4 + k] = rho * (S[k] - u[a] * u[b])
     return out
+
+
+def stored_for_codec(s):
+    """FP64 stored variables -> the FP32 codec input (component 0 = rho - 1,
+    formed in FP64 before the cast)."""
+    v = np.array(s, dtype=np.float64, copy=True)
+    v[0] = v[0] - 1.0
+    return v.astype(np.float32)
 
 
 def stored_to_public(s):
@@ -257,7 +273,7 @@ def stored_to_public(s):
 
 
 def encode(stored32, shape, t, seed, deterministic=False):
-    """FP32 stored variables (10, N) -> uint16 codes (10, N)."""
+    """FP32 stored variables (10, N), component 0 = rho - 1, -> uint16 codes (10, N)."""
     nx, ny, nz = shape
     v = np.ascontiguousarray(stored32, np.float32)
     q = np.empty(v.shape, np.uint16)
@@ -279,7 +295,7 @@ def q16_step(codes, shape, tau, t_out, seed, F=None, typ=None, inflow=None):
     take the codes of (nx-2, y, z)."""
     pub = stored_to_public(decode(codes))
     new = step(pub, shape, tau, F=F, typ=typ, inflow=inflow)
-    q = encode(public_to_stored(new).astype(np.float32), shape, t_out, seed)
+    q = encode(stored_for_codec(public_to_stored(new)), shape, t_out, seed)
     if typ is not None:
         solid = typ == SOLID
         q[:, solid] = codes[:, solid]

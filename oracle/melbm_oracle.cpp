@@ -441,22 +441,61 @@ inline void dither10(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t se
 const double QLO[10] = {0.8, -0.4, -0.4, -0.4, -0.1, -0.1, -0.1, -0.1, -0.1, -0.1};
 const double QHI[10] = {1.5, 0.4, 0.4, 0.4, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1};
 
-// Encoding in FP32, the precision the kernels take this decision in:
-//   t = clamp(fma(m, 1/(hi-lo), -lo/(hi-lo)), 0, 1);  v = fma(t, 2^b - 1, d);  q = floor(v).
-// This is q = floor(m' (2^b - 1) + 1/2 + e) with e uniform in [-1/2, 1/2) (dithering),
-// d = 1/2 gives the deterministic round-to-nearest of the paper's formula.
-inline uint16_t encode_one(float m, int k, float d) {
-  const float s = float(1.0 / (QHI[k] - QLO[k]));
-  const float o = float(-QLO[k] / (QHI[k] - QLO[k]));
-  float t = std::fma(m, s, o);
-  if (!(t > 0.0f)) t = 0.0f;  // also maps NaN to 0
-  if (t > 1.0f) t = 1.0f;
-  const float v = std::fma(t, 65535.0f, d);
-  return uint16_t(std::floor(v));
+// The fixed-point map of Sec. 5.4, q = floor((m - m_min)/step + d) with
+// step = (m_max - m_min)/(2^b - 1) and the dither d in [0, 1), taken in FP32 (the
+// precision the kernels take this decision in).  It is evaluated relative to the
+// code qc nearest to the centre of the values (rho = 1, u = 0, rho S^neq = 0),
+// whose value is c = m_min + qc step:
+//   w = m' K + b       with m' = rho - 1 for the density and m' = m otherwise,
+//                      K = 1/step, b = (centre - m_min)/step - qc
+//   q = qc + floor(clamp(w, -qc, 2^b - 1 - qc) + d)
+//   decoded value  m' = c + (q - qc) step.
+// This is the same formula in exact arithmetic; in FP32 the rounding of the
+// constants then only scales the (zero-mean) deviation from the centre, and the
+// floor of w + d is exact, so the rounding stays unbiased (Sec. 5.4 dithering).
+// All constants are the FP32 roundings of their FP64 values.
+struct QGroup {
+  double lo, hi, centre;  // range and centre in the shifted variable m'
+  double qc;
+};
+inline QGroup qgroup(int k) {
+  QGroup g;
+  const double shift = (k == 0) ? 1.0 : 0.0;
+  g.lo = QLO[k] - shift;
+  g.hi = QHI[k] - shift;
+  g.centre = 0.0;
+  g.qc = std::floor((g.centre - g.lo) * 65535.0 / (g.hi - g.lo) + 0.5);
+  return g;
+}
+inline float q_step(int k) { QGroup g = qgroup(k); return float((g.hi - g.lo) / 65535.0); }
+inline float q_K(int k) { QGroup g = qgroup(k); return float(65535.0 / (g.hi - g.lo)); }
+inline float q_b(int k) {
+  QGroup g = qgroup(k);
+  return float((g.centre - g.lo) * 65535.0 / (g.hi - g.lo) - g.qc);
+}
+inline float q_c(int k) {
+  QGroup g = qgroup(k);
+  return float(g.lo + g.qc * (g.hi - g.lo) / 65535.0);
 }
 
-// Dequantisation in FP64: m = m_min + q (m_max - m_min)/(2^b - 1).
-inline double decode_one(uint16_t q, int k) { return QLO[k] + double(q) * (QHI[k] - QLO[k]) / 65535.0; }
+// Encode the shifted value mp (rho - 1 for k = 0) with dither d.
+inline uint16_t encode_one(float mp, int k, float d) {
+  const QGroup g = qgroup(k);
+  float w = std::fma(mp, q_K(k), q_b(k));
+  const float wlo = float(-g.qc), whi = float(65535.0 - g.qc);
+  w = std::fmax(w, wlo);  // fmax/fmin return the other operand for NaN: NaN -> code 0
+  w = std::fmin(w, whi);
+  const double f = std::floor(double(w) + double(d));  // exact in double
+  return uint16_t(int(g.qc) + int(f));
+}
+
+// Dequantisation: m = c + (q - qc) step, returned for the unshifted variable
+// (rho for k = 0), in FP64 from the FP32 grid constants.
+inline double decode_one(uint16_t q, int k) {
+  const QGroup g = qgroup(k);
+  const double shift = (k == 0) ? 1.0 : 0.0;
+  return shift + double(q_c(k)) + (double(q) - g.qc) * double(q_step(k));
+}
 
 }  // namespace
 
@@ -704,8 +743,9 @@ void orc_dither(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t seed, f
   dither10(x, y, z, t, seed, d);
 }
 
-// Encode stored variables (FP32, component-major 10 x N) into 16-bit codes.
-// deterministic != 0 uses d = 1/2 (round to nearest) for every component.
+// Encode stored variables (FP32, component-major 10 x N; component 0 is
+// rho - 1) into 16-bit codes.  deterministic != 0 uses d = 1/2 (round to nearest)
+// for every component.
 void orc_encode(int nx, int ny, int nz, const float* v, uint32_t t, uint32_t seed, int deterministic,
                 uint16_t* q) {
   Grid g{nx, ny, nz};
@@ -734,6 +774,16 @@ void orc_ranges(double* lo, double* hi) {
     lo[k] = QLO[k];
     hi[k] = QHI[k];
   }
+}
+
+// Grid constants of component k: centre code, FP32 step, FP32 value of the
+// centre code (shifted variable), K and b of the encoding.
+void orc_codec_constants(int k, double* out /*5*/) {
+  out[0] = qgroup(k).qc;
+  out[1] = q_step(k);
+  out[2] = q_c(k);
+  out[3] = q_K(k);
+  out[4] = q_b(k);
 }
 
 }  // extern "C"
