@@ -1,6 +1,6 @@
 // fluid.cu -- the fluid-interior kernel of the split design (Sec. 4.2, Alg. 2):
 // one uniform, branch-free update of every cell:
-//   load stored moments -> collide (App. A) -> Hermite coefficients of f+
+//   load stored moments -> collide (App. A) -> Hermite moments of f+
 //   (Eq. three_order_f) -> pull stream (Eq. streaming) -> moments (Eq. rho_u_stress)
 //   -> store (FP32, or 16-bit with dither, Sec. 5.4).
 // Boundary cells are overwritten afterwards by the boundary kernel; the stream
@@ -15,10 +15,13 @@
 // Work decomposition (one thread per (x, y) column, marching along z):
 //   * a block is 32 lanes (x) by FY warps (y); lanes cover x0-1 .. x0+30 and warps
 //     y0-1 .. y0+FY-2, so lanes 0/31 and warps 0/FY-1 are a recomputed halo ring;
+//   * each iteration advances two z-planes held as the two halves of float2
+//     values, so every arithmetic step is one packed FP32x2 instruction;
 //   * the x pass exchanges directional populations with warp shuffles;
-//   * the y pass exchanges them through double-buffered shared memory (one
-//     barrier per plane);
-//   * the z pass keeps the previous planes' populations in registers.
+//   * the y pass exchanges them through double-buffered shared memory (64-bit
+//     accesses, one barrier per plane pair);
+//   * the z pass keeps the previous pair's populations in registers;
+//   * the next pair's loads are issued before the current pair is processed.
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
 
@@ -28,8 +31,9 @@ constexpr int FX = 32;
 constexpr int FY = 16;
 constexpr int FXI = FX - 2;
 constexpr int FYI = FY - 2;
-constexpr int NSY = 9;  // y-pass slices exchanged through shared memory
-constexpr int SM_PLANE = 2 * NSY * FY * FX;  // floats per buffer (phi+ and phi-)
+constexpr int NSY = 9;                      // y-pass slices exchanged through shared memory
+constexpr int SM_BUF = 2 * NSY * FY * FX;  // float2 per buffer (phi+ and phi-)
+constexpr int ZCHUNK = 32;                  // planes per block (even)
 
 struct FluidParams {
   int nx, ny, nz, zc;
@@ -40,10 +44,128 @@ struct FluidParams {
   uint32_t t_out, seed;
 };
 
+// ----------------------------------------------------------------- plane-pair I/O
+template <int STORAGE> struct RawPair;
+template <> struct RawPair<ST_Q16> { uint32_t a[5], b[5]; };
+template <> struct RawPair<ST_F32> { float a[10], b[10]; };
+
+__device__ __forceinline__ void load_pair(RawPair<ST_Q16>& r, const void* buf, size_t N, size_t na,
+                                          size_t nb) {
+  const uint32_t* p = static_cast<const uint32_t*>(buf);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    r.a[k] = __ldg(p + k * N + na);
+    r.b[k] = __ldg(p + k * N + nb);
+  }
+}
+__device__ __forceinline__ void load_pair(RawPair<ST_F32>& r, const void* buf, size_t N, size_t na,
+                                          size_t nb) {
+  const float* p = static_cast<const float*>(buf);
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    r.a[k] = __ldg(p + k * N + na);
+    r.b[k] = __ldg(p + k * N + nb);
+  }
+}
+
+__device__ __forceinline__ StoredT<float2> decode_pair(const RawPair<ST_Q16>& r) {
+  StoredT<float2> s;
+  s.drho = q_decode<0>(make_float2(q_lo_magic(r.a[0]), q_lo_magic(r.b[0])));
+  s.ux = q_decode<1>(make_float2(q_hi_magic(r.a[0]), q_hi_magic(r.b[0])));
+  s.uy = q_decode<1>(make_float2(q_lo_magic(r.a[1]), q_lo_magic(r.b[1])));
+  s.uz = q_decode<1>(make_float2(q_hi_magic(r.a[1]), q_hi_magic(r.b[1])));
+  s.nxx = q_decode<2>(make_float2(q_lo_magic(r.a[2]), q_lo_magic(r.b[2])));
+  s.nyy = q_decode<2>(make_float2(q_hi_magic(r.a[2]), q_hi_magic(r.b[2])));
+  s.nzz = q_decode<2>(make_float2(q_lo_magic(r.a[3]), q_lo_magic(r.b[3])));
+  s.nxy = q_decode<2>(make_float2(q_hi_magic(r.a[3]), q_hi_magic(r.b[3])));
+  s.nxz = q_decode<2>(make_float2(q_lo_magic(r.a[4]), q_lo_magic(r.b[4])));
+  s.nyz = q_decode<2>(make_float2(q_hi_magic(r.a[4]), q_hi_magic(r.b[4])));
+  return s;
+}
+__device__ __forceinline__ StoredT<float2> decode_pair(const RawPair<ST_F32>& r) {
+  StoredT<float2> s;
+  s.drho = make_float2(r.a[0], r.b[0]);
+  s.ux = make_float2(r.a[1], r.b[1]);
+  s.uy = make_float2(r.a[2], r.b[2]);
+  s.uz = make_float2(r.a[3], r.b[3]);
+  s.nxx = make_float2(r.a[4], r.b[4]);
+  s.nyy = make_float2(r.a[5], r.b[5]);
+  s.nzz = make_float2(r.a[6], r.b[6]);
+  s.nxy = make_float2(r.a[7], r.b[7]);
+  s.nxz = make_float2(r.a[8], r.b[8]);
+  s.nyz = make_float2(r.a[9], r.b[9]);
+  return s;
+}
+
+// Store the pair (planes za, zb = za + 1) -- each half only if its flag is set.
+template <int STORAGE>
+__device__ __forceinline__ void store_pair(void* buf, size_t N, size_t na, size_t nb,
+                                           const StoredT<float2>& o, bool sa, bool sb, uint32_t x,
+                                           uint32_t y, uint32_t za, uint32_t zb, uint32_t t,
+                                           uint32_t seed);
+
+template <>
+__device__ __forceinline__ void store_pair<ST_F32>(void* buf, size_t N, size_t na, size_t nb,
+                                                   const StoredT<float2>& o, bool sa, bool sb,
+                                                   uint32_t, uint32_t, uint32_t, uint32_t, uint32_t,
+                                                   uint32_t) {
+  float* p = static_cast<float*>(buf);
+  const float2 v[10] = {o.drho, o.ux, o.uy, o.uz, o.nxx, o.nyy, o.nzz, o.nxy, o.nxz, o.nyz};
+  if (sa) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) p[k * N + na] = v[k].x;
+  }
+  if (sb) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) p[k * N + nb] = v[k].y;
+  }
+}
+
+template <>
+__device__ __forceinline__ void store_pair<ST_Q16>(void* buf, size_t N, size_t na, size_t nb,
+                                                   const StoredT<float2>& o, bool sa, bool sb,
+                                                   uint32_t x, uint32_t y, uint32_t za, uint32_t zb,
+                                                   uint32_t t, uint32_t seed) {
+  const DitherBits ha = pcg4d(x, y, za, t, seed);
+  const DitherBits hb = pcg4d(x, y, zb, t, seed);
+  float2 d[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k)
+    d[k] = dither_value(make_float2(dither_magic(ha, k), dither_magic(hb, k)), k);
+  const uint2 e0 = q_encode_bits<0>(o.drho, d[0]), e1 = q_encode_bits<1>(o.ux, d[1]);
+  const uint2 e2 = q_encode_bits<1>(o.uy, d[2]), e3 = q_encode_bits<1>(o.uz, d[3]);
+  const uint2 e4 = q_encode_bits<2>(o.nxx, d[4]), e5 = q_encode_bits<2>(o.nyy, d[5]);
+  const uint2 e6 = q_encode_bits<2>(o.nzz, d[6]), e7 = q_encode_bits<2>(o.nxy, d[7]);
+  const uint2 e8 = q_encode_bits<2>(o.nxz, d[8]), e9 = q_encode_bits<2>(o.nyz, d[9]);
+  uint32_t* p = static_cast<uint32_t*>(buf);
+  if (sa) {
+    p[na] = q_pack(e0.x, e1.x);
+    p[N + na] = q_pack(e2.x, e3.x);
+    p[2 * N + na] = q_pack(e4.x, e5.x);
+    p[3 * N + na] = q_pack(e6.x, e7.x);
+    p[4 * N + na] = q_pack(e8.x, e9.x);
+  }
+  if (sb) {
+    p[nb] = q_pack(e0.y, e1.y);
+    p[N + nb] = q_pack(e2.y, e3.y);
+    p[2 * N + nb] = q_pack(e4.y, e5.y);
+    p[3 * N + nb] = q_pack(e6.y, e7.y);
+    p[4 * N + nb] = q_pack(e8.y, e9.y);
+  }
+}
+
+__device__ __forceinline__ float2 shfl_up2(float2 v) {
+  return make_float2(__shfl_up_sync(FULL, v.x, 1), __shfl_up_sync(FULL, v.y, 1));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v) {
+  return make_float2(__shfl_down_sync(FULL, v.x, 1), __shfl_down_sync(FULL, v.y, 1));
+}
+
+// ----------------------------------------------------------------- kernel
 // The y-pass slices are indexed s = 3 p + r' (p: x-order, r': input z-order).
 template <int STORAGE, bool FORCE>
 __global__ void __launch_bounds__(FX* FY, 1) fluid_kernel(FluidParams P) {
-  extern __shared__ float smem[];
+  extern __shared__ float2 sm2[];
   const int lane = threadIdx.x, row = threadIdx.y;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const size_t N = size_t(nx) * ny * nz;
@@ -51,63 +173,71 @@ __global__ void __launch_bounds__(FX* FY, 1) fluid_kernel(FluidParams P) {
   const int y = int(blockIdx.y) * FYI - 1 + row;
   const int xw = wrapi(x, nx), yw = wrapi(y, ny);
   const bool mid_row = (row >= 1 && row <= FY - 2);  // warp-uniform
-  const bool do_store = mid_row && lane >= 1 && lane <= FX - 2 && x < nx && y < ny;
+  const bool col_ok = mid_row && lane >= 1 && lane <= FX - 2 && x < nx && y < ny;
   const int z0 = int(blockIdx.z) * P.zc;
   const int z1 = min(z0 + P.zc, nz);
   const size_t col = size_t(xw) + size_t(nx) * yw;
   const size_t plane = size_t(nx) * ny;
   const float omega = P.omega;
 
-  // z-march state for the six (p, q) slices: phi+ of plane z-1, phi0 and phi+ of z
-  float zpm[6], zp0[6], zpp[6];
+  // z-march state of the six (p, q) slices: phi+ of the previous pair's two
+  // planes and phi0 of its second plane
+  float2 zP[6];
+  float zZ[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) zpm[k] = zp0[k] = zpp[k] = 0.f;
+  for (int k = 0; k < 6; ++k) {
+    zP[k] = make_float2(0.f, 0.f);
+    zZ[k] = 0.f;
+  }
   float fprev[3] = {0.f, 0.f, 0.f};
 
+  RawPair<STORAGE> raw;
+  load_pair(raw, P.in, N, col + plane * wrapi(z0 - 1, nz), col + plane * wrapi(z0, nz));
   int parity = 0;
-  for (int zz = z0 - 1; zz <= z1; ++zz, parity ^= 1) {
-    const int zw = wrapi(zz, nz);
-    const size_t n = col + plane * zw;
-    const Stored s = load_stored<STORAGE>(P.in, N, n);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+  for (int zz = z0 - 1; zz <= z1; zz += 2, parity ^= 1) {
+    const StoredT<float2> s = decode_pair(raw);
+    float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
     if (FORCE) {
-      fx = __ldg(P.force + n);
-      fy = __ldg(P.force + N + n);
-      fz = __ldg(P.force + 2 * N + n);
+      const size_t na = col + plane * wrapi(zz, nz), nb = col + plane * wrapi(zz + 1, nz);
+      fx = make_float2(__ldg(P.force + na), __ldg(P.force + nb));
+      fy = make_float2(__ldg(P.force + N + na), __ldg(P.force + N + nb));
+      fz = make_float2(__ldg(P.force + 2 * N + na), __ldg(P.force + 2 * N + nb));
     }
-    const Mom17 A = collide_moments<FORCE>(s, omega, fx, fy, fz);
+    if (zz + 2 <= z1)  // prefetch the next pair
+      load_pair(raw, P.in, N, col + plane * wrapi(zz + 2, nz), col + plane * wrapi(zz + 3, nz));
+    const Mom17T<float2> A = collide_moments<FORCE>(s, omega, fx, fy, fz);
 
     // ---------------- x pass: slices (q', r'), inputs p' = 0, 1, 2 -> outputs p = 0, 1, 2
-    float X[3][3][3];  // X[p][q'][r'] (only the 24 reachable entries are set/used)
-#define MELBM_XPASS(Q, R, A0, A1, A2)                                   \
-  {                                                                     \
-    const Phi ph = phi3(A0, A1, A2);                                    \
-    const float pl = __shfl_up_sync(FULL, ph.p, 1);                     \
-    const float mr = __shfl_down_sync(FULL, ph.m, 1);                   \
-    X[0][Q][R] = proj0(pl, ph.z, mr);                                   \
-    X[1][Q][R] = proj1(pl, mr);                                         \
-    X[2][Q][R] = proj2(pl, mr, X[0][Q][R]);                               \
+    float2 X[3][3][3];
+    const float2 zero = make_float2(0.f, 0.f);
+#define MELBM_XPASS(Q, R, A0, A1, A2)                 \
+  {                                                   \
+    const PhiT<float2> ph = phi3(A0, A1, A2);         \
+    const float2 pl = shfl_up2(ph.p);                 \
+    const float2 mr = shfl_down2(ph.m);               \
+    X[0][Q][R] = proj0(pl, ph.z, mr);                 \
+    X[1][Q][R] = proj1(pl, mr);                       \
+    X[2][Q][R] = proj2(pl, mr, X[0][Q][R]);           \
   }
     MELBM_XPASS(0, 0, A.m000, A.m100, A.m200)
     MELBM_XPASS(1, 0, A.m010, A.m110, A.m210)
     MELBM_XPASS(0, 1, A.m001, A.m101, A.m201)
-    MELBM_XPASS(2, 0, A.m020, A.m120, 0.f)
-    MELBM_XPASS(0, 2, A.m002, A.m102, 0.f)
-    MELBM_XPASS(1, 1, A.m011, A.m111, 0.f)
-    MELBM_XPASS(2, 1, A.m021, 0.f, 0.f)
-    MELBM_XPASS(1, 2, A.m012, 0.f, 0.f)
+    MELBM_XPASS(2, 0, A.m020, A.m120, zero)
+    MELBM_XPASS(0, 2, A.m002, A.m102, zero)
+    MELBM_XPASS(1, 1, A.m011, A.m111, zero)
+    MELBM_XPASS(2, 1, A.m021, zero, zero)
+    MELBM_XPASS(1, 2, A.m012, zero, zero)
 #undef MELBM_XPASS
-    X[2][2][2] = 0.f;  // (q', r') = (2, 2) has no input coefficient
-    X[0][2][2] = X[1][2][2] = 0.f;
+    X[0][2][2] = X[1][2][2] = X[2][2][2] = zero;  // (q', r') = (2, 2) has no input moment
 
     // ---------------- y pass, part 1: directional populations along y
-    float* sp = smem + parity * SM_PLANE;
-    float yz0[NSY];
+    float2* sp = sm2 + parity * SM_BUF;
+    float2 yz0[NSY];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const Phi ph = phi3(X[p][0][r], X[p][1][r], X[p][2][r]);
+        const PhiT<float2> ph = phi3(X[p][0][r], X[p][1][r], X[p][2][r]);
         const int s_ = 3 * p + r;
         sp[(s_ * FY + row) * FX + lane] = ph.p;
         sp[((NSY + s_) * FY + row) * FX + lane] = ph.m;
@@ -117,66 +247,63 @@ __global__ void __launch_bounds__(FX* FY, 1) fluid_kernel(FluidParams P) {
     if (!mid_row) continue;  // halo rows only feed their neighbours
 
     // ---------------- y pass, part 2: pull and project -> Y[p][q][r'], q <= 2 - p
-    float Y[3][3][3];
+    float2 Y[3][3][3];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const int s_ = 3 * p + r;
-        const float pl = sp[(s_ * FY + row - 1) * FX + lane];
-        const float mr = sp[((NSY + s_) * FY + row + 1) * FX + lane];
+        const float2 pl = sp[(s_ * FY + row - 1) * FX + lane];
+        const float2 mr = sp[((NSY + s_) * FY + row + 1) * FX + lane];
         Y[p][0][r] = proj0(pl, yz0[s_], mr);
         if (p <= 1) Y[p][1][r] = proj1(pl, mr);
         if (p == 0) Y[p][2][r] = proj2(pl, mr, Y[p][0][r]);
       }
 
-    // ---------------- z pass: directional populations along z for slices (p, q)
+    // ---------------- z pass for slices (p, q): planes (zz, zz+1) in, (zz-1, zz) out
     const int PQ[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
-    float zm[6], z0n[6], zpn[6];
+    float2 M[6][3];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const int p = PQ[k][0], q = PQ[k][1];
-      const Phi ph = phi3(Y[p][q][0], Y[p][q][1], Y[p][q][2]);
-      zm[k] = ph.m;
-      z0n[k] = ph.z;
-      zpn[k] = ph.p;
+      const PhiT<float2> ph = phi3(Y[p][q][0], Y[p][q][1], Y[p][q][2]);
+      // out(zz-1) = proj(phi+(zz-2), phi0(zz-1), phi-(zz)); out(zz) = proj(phi+(zz-1), phi0(zz), phi-(zz+1))
+      const float2 pl = zP[k];
+      const float2 zc = make_float2(zZ[k], ph.z.x);
+      const float2 mr = ph.m;
+      M[k][0] = proj0(pl, zc, mr);
+      M[k][1] = proj1(pl, mr);
+      M[k][2] = proj2(pl, mr, M[k][0]);
+      zP[k] = ph.p;
+      zZ[k] = ph.z.y;
     }
-    if (zz >= z0 + 1) {
-      // finish plane zz-1 from phi+(zz-2), phi0(zz-1), phi-(zz)
-      float M[6][3];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        M[k][0] = proj0(zpm[k], zp0[k], zm[k]);
-        M[k][1] = proj1(zpm[k], zm[k]);
-        M[k][2] = proj2(zpm[k], zm[k], M[k][0]);
+    if (zz - 1 >= z0) {
+      float2 ox = zero, oy = zero, oz = zero;
+      if (FORCE) {
+        ox = make_float2(fprev[0], fx.x);
+        oy = make_float2(fprev[1], fy.x);
+        oz = make_float2(fprev[2], fz.x);
       }
       // slices: 0:(0,0) 1:(1,0) 2:(0,1) 3:(2,0) 4:(1,1) 5:(0,2)
-      const Stored o = finish_moments<FORCE>(M[0][0], M[1][0], M[2][0], M[0][1], M[3][0], M[5][0],
-                                             M[0][2], M[4][0], M[1][1], M[2][1], fprev[0],
-                                             fprev[1], fprev[2]);
-      if (do_store) {
-        const int zo = zz - 1;
-        store_stored<STORAGE>(P.out, N, col + plane * zo, o, uint32_t(xw), uint32_t(yw),
-                              uint32_t(zo), P.t_out, P.seed);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      zpm[k] = zpp[k];
-      zp0[k] = z0n[k];
-      zpp[k] = zpn[k];
+      const StoredT<float2> o =
+          finish_moments<FORCE>(M[0][0], M[1][0], M[2][0], M[0][1], M[3][0], M[5][0], M[0][2],
+                                M[4][0], M[1][1], M[2][1], ox, oy, oz);
+      const int za = zz - 1, zb = zz;
+      store_pair<STORAGE>(P.out, N, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
+                          col_ok && zb < z1, uint32_t(xw), uint32_t(yw), uint32_t(za),
+                          uint32_t(zb), P.t_out, P.seed);
     }
     if (FORCE) {
-      fprev[0] = fx;
-      fprev[1] = fy;
-      fprev[2] = fz;
+      fprev[0] = fx.y;
+      fprev[1] = fy.y;
+      fprev[2] = fz.y;
     }
   }
 }
 
 template <int STORAGE, bool FORCE>
 static cudaError_t launch_fluid_t(const FluidParams& p, dim3 grid, cudaStream_t st) {
-  const size_t smem = size_t(2) * SM_PLANE * sizeof(float);
+  const size_t smem = size_t(2) * SM_BUF * sizeof(float2);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE>,
@@ -195,7 +322,7 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
   p.nx = nx;
   p.ny = ny;
   p.nz = nz;
-  p.zc = nz < 32 ? nz : 32;
+  p.zc = ZCHUNK;
   p.in = in;
   p.out = out;
   p.force = force;

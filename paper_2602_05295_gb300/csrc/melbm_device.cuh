@@ -1,7 +1,10 @@
 // melbm_device.cuh -- device helpers shared by the CUDA kernels of the library:
 // stored-variable layout, the 16-bit codec of Sec. 5.4 with its dither, the
 // moment-space collision of App. A written in stored variables, and the
-// tensor-product form of the third-order Hermite reconstruction.
+// tensor-product (D1Q3 x D1Q3 x D1Q3) form of the streaming of the third-order
+// Hermite populations.  The per-cell arithmetic is written once for T = float
+// and T = float2; the float2 form runs on the packed FP32x2 instructions
+// (FFMA2/FADD2/FMUL2) of sm_100-class GPUs and processes two cells at once.
 #pragma once
 
 #include <cstdint>
@@ -14,6 +17,31 @@ constexpr unsigned FULL = 0xffffffffu;
 enum : uint8_t { T_FLUID = 0, T_FLUID_BOUNDARY = 1, T_INFLOW = 2, T_OUTFLOW = 3, T_SOLID = 4 };
 enum { ST_F32 = 0, ST_Q16 = 1 };
 
+// ----------------------------------------------------------------- scalar / pair math
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+template <class T> __device__ __forceinline__ T vset(float a);
+template <> __device__ __forceinline__ float vset<float>(float a) { return a; }
+
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);  // exact negation, one rounding
+}
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+template <> __device__ __forceinline__ float2 vset<float2>(float a) { return make_float2(a, a); }
+// a * b + c with scalar constant b
+__device__ __forceinline__ float vfmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vfmac(float2 a, float b, float2 c) {
+  return __ffma2_rn(a, make_float2(b, b), c);
+}
+__device__ __forceinline__ float vmulc(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 vmulc(float2 a, float b) { return __fmul2_rn(a, make_float2(b, b)); }
+
 // ---------------------------------------------------------------------------
 // Stored variables of one cell.  Both storages keep the same ten quantities:
 //   drho = rho - 1, u_a, and n_ab = rho S^neq_ab = rho (S_ab - u_a u_b)
@@ -21,70 +49,99 @@ enum { ST_F32 = 0, ST_Q16 = 1 };
 // O(1) rest state from every FP32 sum (its populations w_i stream to themselves).
 // FP32 storage: ten planes [10][N] with plane 0 = drho.
 // Q16 storage:  five u32 planes [5][N]; word k holds components (2k, 2k+1) in its
-//               (low, high) halves; component 0 is rho itself in [0.8, 1.5].
+//               (low, high) halves.
 // ---------------------------------------------------------------------------
-struct Stored {
-  float drho;
-  float ux, uy, uz;
-  float nxx, nyy, nzz, nxy, nxz, nyz;
+template <class T>
+struct StoredT {
+  T drho;
+  T ux, uy, uz;
+  T nxx, nyy, nzz, nxy, nxz, nyz;
 };
+using Stored = StoredT<float>;
 
 // ----------------------------------------------------------------- 16-bit codec
-// Ranges (Sec. 5.4): rho [0.8, 1.5]; u [-0.4, 0.4]; rho S^neq [-0.1, 0.1].
-// Group 0 = rho, 1 = velocity, 2 = rho S^neq.  Constants are the FP32 roundings
-// of the exact FP64 values.
+// Sec. 5.4: ranges rho [0.8, 1.5], u [-0.4, 0.4], rho S^neq [-0.1, 0.1];
+// q = floor((m - m_min)/step + d), step = (m_max - m_min)/(2^16 - 1), d in [0, 1)
+// the dither.  The map is evaluated relative to the code qc nearest to the centre
+// of the values (rho = 1 in the variable rho - 1; u = 0; rho S^neq = 0), so that
+// the FP32 rounding of the constants only scales the zero-mean deviation from
+// the centre, and the floor of w + d is taken exactly with round-down adds:
+//   w = m' K + b,  q = qc + floor(clamp(w, -qc, 65535 - qc) + d),
+//   m' = c + (q - qc) step,  c = value of code qc.
+// Group 0 = rho (m' = rho - 1), 1 = velocity, 2 = rho S^neq.  Constants are the
+// FP32 roundings of the FP64 expressions.
 template <int G> struct QRange;
 template <> struct QRange<0> {
-  static constexpr float lo = 0.8f;
-  static constexpr float s = float(1.0 / (1.5 - 0.8));
-  static constexpr float o = float(-0.8 / (1.5 - 0.8));
-  static constexpr float step = float((1.5 - 0.8) / 65535.0);
+  static constexpr double lo = 0.8 - 1.0, hi = 1.5 - 1.0;
+  static constexpr float qc = 18724.0f;
 };
 template <> struct QRange<1> {
-  static constexpr float lo = -0.4f;
-  static constexpr float s = float(1.0 / 0.8);
-  static constexpr float o = float(0.4 / 0.8);
-  static constexpr float step = float(0.8 / 65535.0);
+  static constexpr double lo = -0.4, hi = 0.4;
+  static constexpr float qc = 32768.0f;
 };
 template <> struct QRange<2> {
-  static constexpr float lo = -0.1f;
-  static constexpr float s = float(1.0 / 0.2);
-  static constexpr float o = float(0.1 / 0.2);
-  static constexpr float step = float(0.2 / 65535.0);
+  static constexpr double lo = -0.1, hi = 0.1;
+  static constexpr float qc = 32768.0f;
+};
+template <int G> struct QConst {
+  static constexpr double lo = QRange<G>::lo, hi = QRange<G>::hi;
+  static constexpr double qcd = double(QRange<G>::qc);
+  static constexpr float step = float((hi - lo) / 65535.0);
+  static constexpr float K = float(65535.0 / (hi - lo));
+  static constexpr float b = float((0.0 - lo) * 65535.0 / (hi - lo) - qcd);
+  static constexpr float c = float(lo + qcd * (hi - lo) / 65535.0);
+  static constexpr float wlo = float(-qcd), whi = float(65535.0 - qcd);
+  static constexpr float magic = float(8388608.0 + qcd);  // 2^23 + qc
 };
 
-// Encode one value with dither d in [0, 1): q = floor(sat(m s + o) * 65535 + d).
-// Returns the bits of the float 2^23 + q, whose low 16 bits are q.
+// Encoded bits of one value: the float 2^23 + q, whose low 16 bits are q.
 template <int G>
 __device__ __forceinline__ uint32_t q_encode_bits(float m, float d) {
-  const float t = __saturatef(__fmaf_rn(m, QRange<G>::s, QRange<G>::o));
-  const float v = __fmaf_rn(t, 65535.0f, d);
-  return __float_as_uint(__fadd_rd(v, 8388608.0f));  // 2^23 + floor(v), exact for v < 2^23
+  float w = __fmaf_rn(m, QConst<G>::K, QConst<G>::b);
+  w = fminf(fmaxf(w, QConst<G>::wlo), QConst<G>::whi);  // NaN -> wlo (code 0)
+  const float z = __fadd_rd(__fadd_rd(w, d), QConst<G>::magic);
+  return __float_as_uint(z);
+}
+template <int G>
+__device__ __forceinline__ uint2 q_encode_bits(float2 m, float2 d) {
+  float2 w = __ffma2_rn(m, make_float2(QConst<G>::K, QConst<G>::K),
+                        make_float2(QConst<G>::b, QConst<G>::b));
+  w.x = fminf(fmaxf(w.x, QConst<G>::wlo), QConst<G>::whi);
+  w.y = fminf(fmaxf(w.y, QConst<G>::wlo), QConst<G>::whi);
+  const float2 z = __fadd2_rd(__fadd2_rd(w, d), make_float2(QConst<G>::magic, QConst<G>::magic));
+  return make_uint2(__float_as_uint(z.x), __float_as_uint(z.y));
 }
 __device__ __forceinline__ uint32_t q_pack(uint32_t lo_bits, uint32_t hi_bits) {
   return __byte_perm(lo_bits, hi_bits, 0x5410);
 }
-// Decode: the code as an exact float, then m = lo + q * step.
-__device__ __forceinline__ float q_lo(uint32_t w) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7610)) - 8388608.0f;
+// The float 2^23 + q of the low / high code of a word.
+__device__ __forceinline__ float q_lo_magic(uint32_t w) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7610));
 }
-__device__ __forceinline__ float q_hi(uint32_t w) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7632)) - 8388608.0f;
+__device__ __forceinline__ float q_hi_magic(uint32_t w) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7632));
+}
+// m' = c + (q - qc) step from the float 2^23 + q.
+template <int G>
+__device__ __forceinline__ float q_decode(float magic_q) {
+  return __fmaf_rn(magic_q - QConst<G>::magic, QConst<G>::step, QConst<G>::c);
 }
 template <int G>
-__device__ __forceinline__ float q_decode(float q) {
-  return __fmaf_rn(q, QRange<G>::step, QRange<G>::lo);
+__device__ __forceinline__ float2 q_decode(float2 magic_q) {
+  const float2 f = __fadd2_rn(magic_q, make_float2(-QConst<G>::magic, -QConst<G>::magic));
+  return __ffma2_rn(f, make_float2(QConst<G>::step, QConst<G>::step),
+                    make_float2(QConst<G>::c, QConst<G>::c));
 }
 
 // Counter-based dither: pcg4d of Jarzynski & Olano, "Hash Functions for GPU
 // Rendering", JCGT 9(3) 2020, on (x, y, z, t ^ seed).  Components 0..7 take the
 // 12-bit fields [0,12) (even) and [12,24) (odd) of word k/2; components 8 and 9
 // take 16 bits made of the top bytes of words (0,1) and (2,3).
-struct Dither {
-  float d[10];
+struct DitherBits {
+  uint32_t w[4];
 };
-__device__ __forceinline__ Dither dither10(uint32_t x, uint32_t y, uint32_t z, uint32_t t,
-                                           uint32_t seed) {
+__device__ __forceinline__ DitherBits pcg4d(uint32_t x, uint32_t y, uint32_t z, uint32_t t,
+                                            uint32_t seed) {
   uint32_t v0 = x * 1664525u + 1013904223u;
   uint32_t v1 = y * 1664525u + 1013904223u;
   uint32_t v2 = z * 1664525u + 1013904223u;
@@ -101,24 +158,45 @@ __device__ __forceinline__ Dither dither10(uint32_t x, uint32_t y, uint32_t z, u
   v1 += v2 * v0;
   v2 += v0 * v1;
   v3 += v1 * v2;
+  DitherBits r;
+  r.w[0] = v0;
+  r.w[1] = v1;
+  r.w[2] = v2;
+  r.w[3] = v3;
+  return r;
+}
+// The float 2^23 + f of dither field k (f has 12 or 16 bits); the dither is then
+// (2^23 + f) / 2^12 - 2^11 or (2^23 + f) / 2^16 - 2^7, exactly.
+__device__ __forceinline__ float dither_magic(const DitherBits& h, int k) {
+  uint32_t f;
+  if (k < 8) f = (k & 1) ? ((h.w[k >> 1] >> 12) & 0xFFFu) : (h.w[k >> 1] & 0xFFFu);
+  else if (k == 8) f = (h.w[0] >> 24) | ((h.w[1] >> 24) << 8);
+  else f = (h.w[2] >> 24) | ((h.w[3] >> 24) << 8);
+  return __uint_as_float(0x4B000000u | f);
+}
+__device__ __forceinline__ float dither_value(float magic, int k) {
+  return k < 8 ? __fmaf_rn(magic, 1.0f / 4096.0f, -2048.0f)
+               : __fmaf_rn(magic, 1.0f / 65536.0f, -128.0f);
+}
+__device__ __forceinline__ float2 dither_value(float2 magic, int k) {
+  return k < 8 ? __ffma2_rn(magic, make_float2(1.0f / 4096.0f, 1.0f / 4096.0f),
+                            make_float2(-2048.0f, -2048.0f))
+               : __ffma2_rn(magic, make_float2(1.0f / 65536.0f, 1.0f / 65536.0f),
+                            make_float2(-128.0f, -128.0f));
+}
+struct Dither {
+  float d[10];
+};
+__device__ __forceinline__ Dither dither10(uint32_t x, uint32_t y, uint32_t z, uint32_t t,
+                                           uint32_t seed) {
+  const DitherBits h = pcg4d(x, y, z, t, seed);
   Dither r;
-  const uint32_t w[4] = {v0, v1, v2, v3};
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    // the float with bits 0x4B000000 | f (f < 2^23) is 2^23 + f, so
-    // (2^23 + f) / 4096 - 2048 = f / 4096 exactly
-    r.d[2 * k] = __fmaf_rn(__uint_as_float(0x4B000000u | (w[k] & 0xFFFu)), 1.0f / 4096.0f, -2048.0f);
-    r.d[2 * k + 1] =
-        __fmaf_rn(__uint_as_float(0x4B000000u | ((w[k] >> 12) & 0xFFFu)), 1.0f / 4096.0f, -2048.0f);
-  }
-  const uint32_t f8 = (v0 >> 24) | ((v1 >> 24) << 8);
-  const uint32_t f9 = (v2 >> 24) | ((v3 >> 24) << 8);
-  r.d[8] = __fmaf_rn(__uint_as_float(0x4B000000u | f8), 1.0f / 65536.0f, -128.0f);
-  r.d[9] = __fmaf_rn(__uint_as_float(0x4B000000u | f9), 1.0f / 65536.0f, -128.0f);
+  for (int k = 0; k < 10; ++k) r.d[k] = dither_value(dither_magic(h, k), k);
   return r;
 }
 
-// ----------------------------------------------------------------- load / store
+// ----------------------------------------------------------------- scalar load / store
 template <int STORAGE>
 __device__ __forceinline__ Stored load_stored(const void* buf, size_t N, size_t n);
 
@@ -139,26 +217,39 @@ __device__ __forceinline__ Stored load_stored<ST_F32>(const void* buf, size_t N,
   return s;
 }
 
-template <>
-__device__ __forceinline__ Stored load_stored<ST_Q16>(const void* buf, size_t N, size_t n) {
-  const uint32_t* b = static_cast<const uint32_t*>(buf);
-  const uint32_t w0 = __ldg(b + n), w1 = __ldg(b + N + n), w2 = __ldg(b + 2 * N + n),
-                 w3 = __ldg(b + 3 * N + n), w4 = __ldg(b + 4 * N + n);
+__device__ __forceinline__ Stored decode_words(const uint32_t w[5]) {
   Stored s;
-  s.drho = q_decode<0>(q_lo(w0)) - 1.0f;
-  s.ux = q_decode<1>(q_hi(w0));
-  s.uy = q_decode<1>(q_lo(w1));
-  s.uz = q_decode<1>(q_hi(w1));
-  s.nxx = q_decode<2>(q_lo(w2));
-  s.nyy = q_decode<2>(q_hi(w2));
-  s.nzz = q_decode<2>(q_lo(w3));
-  s.nxy = q_decode<2>(q_hi(w3));
-  s.nxz = q_decode<2>(q_lo(w4));
-  s.nyz = q_decode<2>(q_hi(w4));
+  s.drho = q_decode<0>(q_lo_magic(w[0]));
+  s.ux = q_decode<1>(q_hi_magic(w[0]));
+  s.uy = q_decode<1>(q_lo_magic(w[1]));
+  s.uz = q_decode<1>(q_hi_magic(w[1]));
+  s.nxx = q_decode<2>(q_lo_magic(w[2]));
+  s.nyy = q_decode<2>(q_hi_magic(w[2]));
+  s.nzz = q_decode<2>(q_lo_magic(w[3]));
+  s.nxy = q_decode<2>(q_hi_magic(w[3]));
+  s.nxz = q_decode<2>(q_lo_magic(w[4]));
+  s.nyz = q_decode<2>(q_hi_magic(w[4]));
   return s;
 }
 
-// Store with the dither of (x, y, z, t ^ seed) (Q16) or as FP32.  deterministic
+template <>
+__device__ __forceinline__ Stored load_stored<ST_Q16>(const void* buf, size_t N, size_t n) {
+  const uint32_t* b = static_cast<const uint32_t*>(buf);
+  uint32_t w[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) w[k] = __ldg(b + k * N + n);
+  return decode_words(w);
+}
+
+__device__ __forceinline__ void encode_words(const Stored& s, const Dither& d, uint32_t w[5]) {
+  w[0] = q_pack(q_encode_bits<0>(s.drho, d.d[0]), q_encode_bits<1>(s.ux, d.d[1]));
+  w[1] = q_pack(q_encode_bits<1>(s.uy, d.d[2]), q_encode_bits<1>(s.uz, d.d[3]));
+  w[2] = q_pack(q_encode_bits<2>(s.nxx, d.d[4]), q_encode_bits<2>(s.nyy, d.d[5]));
+  w[3] = q_pack(q_encode_bits<2>(s.nzz, d.d[6]), q_encode_bits<2>(s.nxy, d.d[7]));
+  w[4] = q_pack(q_encode_bits<2>(s.nxz, d.d[8]), q_encode_bits<2>(s.nyz, d.d[9]));
+}
+
+// Store with the dither of (x, y, z, t ^ seed) (Q16) or as FP32; deterministic
 // rounding (dither 1/2) when det is true.
 template <int STORAGE>
 __device__ __forceinline__ void store_stored(void* buf, size_t N, size_t n, const Stored& s,
@@ -180,14 +271,6 @@ __device__ __forceinline__ void store_stored<ST_F32>(void* buf, size_t N, size_t
   b[7 * N + n] = s.nxy;
   b[8 * N + n] = s.nxz;
   b[9 * N + n] = s.nyz;
-}
-
-__device__ __forceinline__ void encode_words(const Stored& s, const Dither& d, uint32_t w[5]) {
-  w[0] = q_pack(q_encode_bits<0>(1.0f + s.drho, d.d[0]), q_encode_bits<1>(s.ux, d.d[1]));
-  w[1] = q_pack(q_encode_bits<1>(s.uy, d.d[2]), q_encode_bits<1>(s.uz, d.d[3]));
-  w[2] = q_pack(q_encode_bits<2>(s.nxx, d.d[4]), q_encode_bits<2>(s.nyy, d.d[5]));
-  w[3] = q_pack(q_encode_bits<2>(s.nzz, d.d[6]), q_encode_bits<2>(s.nxy, d.d[7]));
-  w[4] = q_pack(q_encode_bits<2>(s.nxz, d.d[8]), q_encode_bits<2>(s.nyz, d.d[9]));
 }
 
 template <>
@@ -215,11 +298,13 @@ __device__ __forceinline__ void store_stored<ST_Q16>(void* buf, size_t N, size_t
 //   mu_a = rho u_a, mu_aa = rho S_aa, mu_ab = rho S_ab, mu_aab = rho T_aab,
 //   mu_xyz = rho T_xyz   (Eq. three_order_f: f+ is the third-order Hermite
 // expansion with exactly these moments, T_abg = S_ab u_g + S_ag u_b + S_bg u_a - 2 u_a u_b u_g).
-struct Mom17 {
-  float m000, m100, m010, m001;
-  float m200, m020, m002, m110, m101, m011;
-  float m210, m120, m201, m102, m021, m012, m111;
+template <class T>
+struct Mom17T {
+  T m000, m100, m010, m001;
+  T m200, m020, m002, m110, m101, m011;
+  T m210, m120, m201, m102, m021, m012, m111;
 };
+using Mom17 = Mom17T<float>;
 
 // Moment-space collision of App. A applied to the stored variables.  With
 // S = n/rho + u u the collision reads
@@ -227,61 +312,62 @@ struct Mom17 {
 //   rho (S+ - u+ u+) = (1 - 1/tau) dev(n + sym(F u)) - F F / (4 rho)
 // where dev() removes the trace and sym(F u)_ab = (F_a u_b + F_b u_a)/2: the
 // trace of the non-equilibrium stress is reset, its deviator relaxes by (1 - 1/tau).
-template <bool FORCE>
-__device__ __forceinline__ Mom17 collide_moments(const Stored& s, float omega, float fx, float fy,
-                                                 float fz) {
-  const float rho = 1.0f + s.drho;
+template <bool FORCE, class T>
+__device__ __forceinline__ Mom17T<T> collide_moments(const StoredT<T>& s, float omega, T fx, T fy,
+                                                     T fz) {
+  const T rho = vadd(s.drho, vset<T>(1.0f));
   const float om1 = 1.0f - omega;
-  float ux = s.ux, uy = s.uy, uz = s.uz;
-  float mxx = s.nxx, myy = s.nyy, mzz = s.nzz, mxy = s.nxy, mxz = s.nxz, myz = s.nyz;
-  float inv = 0.f;
+  T ux = s.ux, uy = s.uy, uz = s.uz;
+  T mxx = s.nxx, myy = s.nyy, mzz = s.nzz, mxy = s.nxy, mxz = s.nxz, myz = s.nyz;
+  T inv = vset<T>(0.f);
   if (FORCE) {
-    inv = __frcp_rn(rho);
-    mxx += fx * ux;
-    myy += fy * uy;
-    mzz += fz * uz;
-    mxy += 0.5f * (fx * uy + fy * ux);
-    mxz += 0.5f * (fx * uz + fz * ux);
-    myz += 0.5f * (fy * uz + fz * uy);
+    inv = vrcp(rho);
+    mxx = vfma(fx, ux, mxx);
+    myy = vfma(fy, uy, myy);
+    mzz = vfma(fz, uz, mzz);
+    mxy = vfmac(vfma(fx, uy, vmul(fy, ux)), 0.5f, mxy);
+    mxz = vfmac(vfma(fx, uz, vmul(fz, ux)), 0.5f, mxz);
+    myz = vfmac(vfma(fy, uz, vmul(fz, uy)), 0.5f, myz);
   }
-  const float tr = (mxx + myy + mzz) * (1.0f / 3.0f);
-  float exx = om1 * (mxx - tr), eyy = om1 * (myy - tr), ezz = om1 * (mzz - tr);
-  float exy = om1 * mxy, exz = om1 * mxz, eyz = om1 * myz;
+  const T tr = vmulc(vadd(vadd(mxx, myy), mzz), 1.0f / 3.0f);
+  T exx = vmulc(vsub(mxx, tr), om1), eyy = vmulc(vsub(myy, tr), om1), ezz = vmulc(vsub(mzz, tr), om1);
+  T exy = vmulc(mxy, om1), exz = vmulc(mxz, om1), eyz = vmulc(myz, om1);
   if (FORCE) {
-    const float q = 0.25f * inv;
-    exx -= q * fx * fx;
-    eyy -= q * fy * fy;
-    ezz -= q * fz * fz;
-    exy -= q * fx * fy;
-    exz -= q * fx * fz;
-    eyz -= q * fy * fz;
-    const float h = 0.5f * inv;
-    ux += h * fx;
-    uy += h * fy;
-    uz += h * fz;
+    const T q = vmulc(inv, -0.25f);
+    exx = vfma(vmul(q, fx), fx, exx);
+    eyy = vfma(vmul(q, fy), fy, eyy);
+    ezz = vfma(vmul(q, fz), fz, ezz);
+    exy = vfma(vmul(q, fx), fy, exy);
+    exz = vfma(vmul(q, fx), fz, exz);
+    eyz = vfma(vmul(q, fy), fz, eyz);
+    const T h = vmulc(inv, 0.5f);
+    ux = vfma(h, fx, ux);
+    uy = vfma(h, fy, uy);
+    uz = vfma(h, fz, uz);
   }
   // rho u+, rho S+ = rho u+ u+ + rho E
-  const float rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
-  Mom17 A;
+  const T rux = vmul(rho, ux), ruy = vmul(rho, uy), ruz = vmul(rho, uz);
+  Mom17T<T> A;
   A.m000 = s.drho;
   A.m100 = rux;
   A.m010 = ruy;
   A.m001 = ruz;
-  A.m200 = rux * ux + exx;
-  A.m020 = ruy * uy + eyy;
-  A.m002 = ruz * uz + ezz;
-  A.m110 = rux * uy + exy;
-  A.m101 = rux * uz + exz;
-  A.m011 = ruy * uz + eyz;
+  A.m200 = vfma(rux, ux, exx);
+  A.m020 = vfma(ruy, uy, eyy);
+  A.m002 = vfma(ruz, uz, ezz);
+  A.m110 = vfma(rux, uy, exy);
+  A.m101 = vfma(rux, uz, exz);
+  A.m011 = vfma(ruy, uz, eyz);
   // rho T_aab = u_b rho S_aa + 2 u_a rho E_ab
-  A.m210 = uy * A.m200 + 2.0f * ux * exy;  // xxy
-  A.m120 = ux * A.m020 + 2.0f * uy * exy;  // xyy
-  A.m201 = uz * A.m200 + 2.0f * ux * exz;  // xxz
-  A.m102 = ux * A.m002 + 2.0f * uz * exz;  // xzz
-  A.m021 = uz * A.m020 + 2.0f * uy * eyz;  // yyz
-  A.m012 = uy * A.m002 + 2.0f * uz * eyz;  // yzz
+  const T ux2 = vadd(ux, ux), uy2 = vadd(uy, uy), uz2 = vadd(uz, uz);
+  A.m210 = vfma(uy, A.m200, vmul(ux2, exy));  // xxy
+  A.m120 = vfma(ux, A.m020, vmul(uy2, exy));  // xyy
+  A.m201 = vfma(uz, A.m200, vmul(ux2, exz));  // xxz
+  A.m102 = vfma(ux, A.m002, vmul(uz2, exz));  // xzz
+  A.m021 = vfma(uz, A.m020, vmul(uy2, eyz));  // yyz
+  A.m012 = vfma(uy, A.m002, vmul(uz2, eyz));  // yzz
   // rho T_xyz = rho ux uy uz + rho (E_xy uz + E_xz uy + E_yz ux)
-  A.m111 = rux * uy * uz + exy * uz + exz * uy + eyz * ux;
+  A.m111 = vfma(vmul(rux, uy), uz, vfma(exy, uz, vfma(exz, uy, vmul(eyz, ux))));
   return A;
 }
 
@@ -296,51 +382,54 @@ __device__ __forceinline__ Mom17 collide_moments(const Stored& s, float omega, f
 // Written this way the sums of m0 and m1 over the grid equal those of mu0 and
 // mu1 whatever the FP32 rounding of 1/6: mass and momentum are conserved up to
 // unbiased rounding instead of drifting with the rounded lattice weights.
-struct Phi {
-  float p, z, m;  // phi_{+1}, phi_0, phi_{-1}
+template <class T>
+struct PhiT {
+  T p, z, m;  // phi_{+1}, phi_0, phi_{-1}
 };
-__device__ __forceinline__ Phi phi3(float mu0, float mu1, float mu2) {
-  Phi r;
-  const float s = __fmaf_rn(mu0, 1.0f / 6.0f, 0.5f * mu2);
-  r.z = __fmaf_rn(-2.0f, s, mu0);
-  r.p = __fmaf_rn(0.5f, mu1, s);
-  r.m = __fmaf_rn(-0.5f, mu1, s);
+using Phi = PhiT<float>;
+template <class T>
+__device__ __forceinline__ PhiT<T> phi3(T mu0, T mu1, T mu2) {
+  PhiT<T> r;
+  const T s = vfmac(mu0, 1.0f / 6.0f, vmulc(mu2, 0.5f));
+  r.z = vfmac(s, -2.0f, mu0);
+  r.p = vfmac(mu1, 0.5f, s);
+  r.m = vfmac(mu1, -0.5f, s);
   return r;
 }
 // Projection after streaming: pl = phi_+ pulled from the minus side, z = own
 // phi_0, mr = phi_- pulled from the plus side.
-__device__ __forceinline__ float proj0(float pl, float z, float mr) { return pl + z + mr; }
-__device__ __forceinline__ float proj1(float pl, float mr) { return pl - mr; }
-__device__ __forceinline__ float proj2(float pl, float mr, float o0) {
-  return __fmaf_rn(-1.0f / 3.0f, o0, pl + mr);
-}
+template <class T>
+__device__ __forceinline__ T proj0(T pl, T z, T mr) { return vadd(vadd(pl, z), mr); }
+template <class T>
+__device__ __forceinline__ T proj1(T pl, T mr) { return vsub(pl, mr); }
+template <class T>
+__device__ __forceinline__ T proj2(T pl, T mr, T o0) { return vfmac(o0, -1.0f / 3.0f, vadd(pl, mr)); }
 
 // Stored variables from the ten streamed moments (rest removed):
 //   rho' = 1 + m000, rho' u' = m_a + F_a/2, rho' S'_ab = m_ab, n'_ab = m_ab - (rho' u'_a) u'_b.
-template <bool FORCE>
-__device__ __forceinline__ Stored finish_moments(float m000, float m100, float m010, float m001,
-                                                 float m200, float m020, float m002, float m110,
-                                                 float m101, float m011, float fx, float fy,
-                                                 float fz) {
-  Stored o;
+template <bool FORCE, class T>
+__device__ __forceinline__ StoredT<T> finish_moments(T m000, T m100, T m010, T m001, T m200,
+                                                     T m020, T m002, T m110, T m101, T m011, T fx,
+                                                     T fy, T fz) {
+  StoredT<T> o;
   o.drho = m000;
-  const float rho = 1.0f + m000;
-  const float inv = __frcp_rn(rho);
-  float jx = m100, jy = m010, jz = m001;
+  const T inv = vrcp(vadd(m000, vset<T>(1.0f)));
+  T jx = m100, jy = m010, jz = m001;
   if (FORCE) {
-    jx += 0.5f * fx;
-    jy += 0.5f * fy;
-    jz += 0.5f * fz;
+    jx = vfmac(fx, 0.5f, jx);
+    jy = vfmac(fy, 0.5f, jy);
+    jz = vfmac(fz, 0.5f, jz);
   }
-  o.ux = jx * inv;
-  o.uy = jy * inv;
-  o.uz = jz * inv;
-  o.nxx = m200 - jx * o.ux;
-  o.nyy = m020 - jy * o.uy;
-  o.nzz = m002 - jz * o.uz;
-  o.nxy = m110 - jx * o.uy;
-  o.nxz = m101 - jx * o.uz;
-  o.nyz = m011 - jy * o.uz;
+  o.ux = vmul(jx, inv);
+  o.uy = vmul(jy, inv);
+  o.uz = vmul(jz, inv);
+  const T njx = vmulc(jx, -1.0f), njy = vmulc(jy, -1.0f), njz = vmulc(jz, -1.0f);  // exact
+  o.nxx = vfma(njx, o.ux, m200);
+  o.nyy = vfma(njy, o.uy, m020);
+  o.nzz = vfma(njz, o.uz, m002);
+  o.nxy = vfma(njx, o.uy, m110);
+  o.nxz = vfma(njx, o.uz, m101);
+  o.nyz = vfma(njy, o.uz, m011);
   return o;
 }
 

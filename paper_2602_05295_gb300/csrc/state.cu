@@ -119,7 +119,8 @@ __global__ void q16_encode_kernel(const float* v, int nx, int ny, int nz, uint32
     d = dither10(uint32_t(n % nx), uint32_t((n / nx) % ny), uint32_t(n / (size_t(nx) * ny)), t,
                  seed);
   }
-  words[n] = q_pack(q_encode_bits<0>(v[n], d.d[0]), q_encode_bits<1>(v[N + n], d.d[1]));
+  // component 0 is rho; the codec works on rho - 1 (exact in FP32 for rho in [0.5, 2])
+  words[n] = q_pack(q_encode_bits<0>(v[n] - 1.0f, d.d[0]), q_encode_bits<1>(v[N + n], d.d[1]));
   words[N + n] = q_pack(q_encode_bits<1>(v[2 * N + n], d.d[2]), q_encode_bits<1>(v[3 * N + n], d.d[3]));
   words[2 * N + n] = q_pack(q_encode_bits<2>(v[4 * N + n], d.d[4]), q_encode_bits<2>(v[5 * N + n], d.d[5]));
   words[3 * N + n] = q_pack(q_encode_bits<2>(v[6 * N + n], d.d[6]), q_encode_bits<2>(v[7 * N + n], d.d[7]));
@@ -132,16 +133,18 @@ __global__ void q16_decode_kernel(const uint32_t* words, int64_t N_, float* v) {
   if (n >= N) return;
   const uint32_t w0 = words[n], w1 = words[N + n], w2 = words[2 * N + n], w3 = words[3 * N + n],
                  w4 = words[4 * N + n];
-  v[n] = q_decode<0>(q_lo(w0));
-  v[N + n] = q_decode<1>(q_hi(w0));
-  v[2 * N + n] = q_decode<1>(q_lo(w1));
-  v[3 * N + n] = q_decode<1>(q_hi(w1));
-  v[4 * N + n] = q_decode<2>(q_lo(w2));
-  v[5 * N + n] = q_decode<2>(q_hi(w2));
-  v[6 * N + n] = q_decode<2>(q_lo(w3));
-  v[7 * N + n] = q_decode<2>(q_hi(w3));
-  v[8 * N + n] = q_decode<2>(q_lo(w4));
-  v[9 * N + n] = q_decode<2>(q_hi(w4));
+  const uint32_t w[5] = {w0, w1, w2, w3, w4};
+  const Stored s = decode_words(w);
+  v[n] = 1.0f + s.drho;
+  v[N + n] = s.ux;
+  v[2 * N + n] = s.uy;
+  v[3 * N + n] = s.uz;
+  v[4 * N + n] = s.nxx;
+  v[5 * N + n] = s.nyy;
+  v[6 * N + n] = s.nzz;
+  v[7 * N + n] = s.nxy;
+  v[8 * N + n] = s.nxz;
+  v[9 * N + n] = s.nyz;
 }
 
 cudaError_t launch_q16_encode(const float* stored, int nx, int ny, int nz, uint32_t t,
