@@ -77,6 +77,10 @@ def lib():
             L.orc_decode.argtypes = [I64, P, P]
             L.orc_ranges.argtypes = [P, P]
             L.orc_codec_constants.argtypes = [I, P]
+            L.orc_mean_code_over_dither.argtypes = [ctypes.c_float, I]
+            L.orc_mean_code_over_dither.restype = D
+            L.orc_code_coordinate.argtypes = [ctypes.c_float, I]
+            L.orc_code_coordinate.restype = D
             _lib = L
     return _lib
 
@@ -236,6 +240,16 @@ def codec_constants(k):
     out = np.empty(5)
     lib().orc_codec_constants(int(k), _p(out))
     return out
+
+
+def mean_code_over_dither(value32, k):
+    """Expected code of an FP32 codec input over all dither values of component k."""
+    return lib().orc_mean_code_over_dither(float(value32), int(k))
+
+
+def code_coordinate(value32, k):
+    """Exact position of an FP32 codec input on the code axis (FP64)."""
+    return lib().orc_code_coordinate(float(value32), int(k))
 
 
 def public_to_stored(m):

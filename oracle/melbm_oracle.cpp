@@ -418,22 +418,26 @@ inline void pcg4d(uint32_t v[4]) {
   v[3] += v[1] * v[2];
 }
 
-// Ten dither values d_k in [0, 1) for one cell and one time index.
-// Components 0..7 take 12-bit fields of the four words (bits 0-11 for even k,
+// Ten dither values d_k in (0, 1) for one cell and one time index.
+// Components 0..7 take 12-bit fields f of the four words (bits 0-11 for even k,
 // bits 12-23 for odd k, word k/2); components 8 and 9 take 16-bit fields built
-// from the top bytes of words (0, 1) and (2, 3).
+// from the top bytes of words (0, 1) and (2, 3).  d = (f + 1/2) / 2^bits: the
+// midpoints of 2^bits equal cells of [0, 1), whose mean is exactly 1/2, so the
+// added noise d - 1/2 is zero-mean as Sec. 5.4 requires.
+inline int dither_bits(int k) { return k < 8 ? 12 : 16; }
+inline float dither_of_field(int k, uint32_t field) {
+  return (float(field) + 0.5f) / float(1u << dither_bits(k));
+}
 inline void dither10(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t seed, float d[10]) {
   uint32_t v[4] = {x, y, z, t ^ seed};
   pcg4d(v);
   for (int k = 0; k < 8; ++k) {
     const uint32_t w = v[k / 2];
     const uint32_t field = (k % 2 == 0) ? (w & 0xFFFu) : ((w >> 12) & 0xFFFu);
-    d[k] = float(field) / 4096.0f;
+    d[k] = dither_of_field(k, field);
   }
-  const uint32_t f8 = (v[0] >> 24) | ((v[1] >> 24) << 8);
-  const uint32_t f9 = (v[2] >> 24) | ((v[3] >> 24) << 8);
-  d[8] = float(f8) / 65536.0f;
-  d[9] = float(f9) / 65536.0f;
+  d[8] = dither_of_field(8, (v[0] >> 24) | ((v[1] >> 24) << 8));
+  d[9] = dither_of_field(9, (v[2] >> 24) | ((v[3] >> 24) << 8));
 }
 
 // Stored-variable ranges (Sec. 5.4 moment range analysis and range reduction):
@@ -761,6 +765,21 @@ void orc_encode(int nx, int ny, int nz, const float* v, uint32_t t, uint32_t see
     }
     for (int k = 0; k < 10; ++k) q[k * N + n] = encode_one(v[k * N + n], k, d[k]);
   }
+}
+
+// Mean code of the FP32 value mp (rho - 1 for k = 0) over every dither field
+// value of component k (the expectation of the stochastic rounding).
+double orc_mean_code_over_dither(float mp, int k) {
+  const uint32_t n = 1u << dither_bits(k);
+  double s = 0.0;
+  for (uint32_t f = 0; f < n; ++f) s += encode_one(mp, k, dither_of_field(k, f));
+  return s / double(n);
+}
+
+// Exact code-space coordinate (m' - c)/step + qc of an FP32 value, in FP64.
+double orc_code_coordinate(float mp, int k) {
+  const QGroup g = qgroup(k);
+  return (double(mp) - (g.lo + g.qc * (g.hi - g.lo) / 65535.0)) * 65535.0 / (g.hi - g.lo) + g.qc;
 }
 
 void orc_decode(int64_t N, const uint16_t* q, double* v) {

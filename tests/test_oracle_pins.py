@@ -456,7 +456,11 @@ def test_dither_is_uniform_and_rounding_unbiased(orc):
     """Dithering adds zero-mean uniform noise of one unit before rounding (Sec. 5.4),
     so the rounding is unbiased: the mean of decode(encode(m)) over cells is m."""
     ds = np.array([orc.dither(x, y, z, 7, 123) for x in range(8) for y in range(8) for z in range(8)])
-    assert ds.min() >= 0 and ds.max() < 1
+    assert ds.min() > 0 and ds.max() < 1
+    # the dither takes the midpoints (f + 1/2)/2^bits of equal cells of [0, 1)
+    for k, bits in enumerate([12] * 8 + [16] * 2):
+        f = ds[:, k] * 2 ** bits - 0.5
+        assert np.array_equal(f, np.round(f)) and f.min() >= 0 and f.max() <= 2 ** bits - 1
     assert np.abs(ds.mean(0) - 0.5).max() < 0.05
     assert np.abs(ds.var(0) - 1 / 12).max() < 0.015
     lo, hi = orc.ranges()
@@ -470,6 +474,31 @@ def test_dither_is_uniform_and_rounding_unbiased(orc):
         bias = (dec.mean(1) - val) / step
         sigma = 0.5 / np.sqrt(N)
         assert np.abs(bias).max() < 5 * sigma + 1e-3, bias
+
+
+def test_stochastic_rounding_is_unbiased_over_the_dither(orc):
+    """Sec. 5.4: the dither is zero-mean uniform noise of one unit, so the expected
+    code equals the value.  Enumerating every dither value: E[q] differs from the
+    exact code coordinate by at most half a dither quantum (1/8192 code for the
+    12-bit fields) plus the FP32 rounding of w, and by ~0 on average over values
+    spread across code cells (a dither f/4096 instead of (f + 1/2)/4096 would
+    under-round by 1/8192 code on average, a -1.3e-9 per-step drift of rho)."""
+    rng = np.random.default_rng(14)
+    devs = {0: [], 1: [], 4: []}
+    for k, centre, spread in ((0, 0.0, 0.01), (1, 0.0, 0.05), (4, 0.0, 0.005)):
+        for v in (centre + spread * rng.standard_normal(300)).astype(np.float32):
+            w = orc.code_coordinate(v, k) - orc.codec_constants(k)[0]
+            # half a dither quantum + the FP32 rounding of w (half an ulp, plus
+            # the relative error of the FP32 constant K times |w|)
+            bound = 1.0 / 8192 + float(np.spacing(np.float32(abs(w)))) / 2 + abs(w) * 2.0 ** -24
+            dev = orc.mean_code_over_dither(v, k) - orc.code_coordinate(v, k)
+            assert abs(dev) <= bound, (k, v, dev, bound)
+            devs[k].append(dev)
+    # On average the deviation is the tie effect only: when |w| < 2048 its FP32
+    # value has >= 13 fractional bits, w + d can be an exact integer and the
+    # exact floor keeps it (at most +6e-5 code on average).
+    for k, d in devs.items():
+        assert abs(np.mean(d)) < 6e-5, (k, np.mean(d))
 
 
 def test_repeated_requantisation_conserves_mass_and_momentum(orc):
