@@ -136,7 +136,8 @@ __device__ __forceinline__ float2 q_decode(float2 magic_q) {
 // Counter-based dither: pcg4d of Jarzynski & Olano, "Hash Functions for GPU
 // Rendering", JCGT 9(3) 2020, on (x, y, z, t ^ seed).  Components 0..7 take the
 // 12-bit fields [0,12) (even) and [12,24) (odd) of word k/2; components 8 and 9
-// take 16 bits made of the top bytes of words (0,1) and (2,3).
+// take 16 bits made of the top bytes of words (0,1) and (2,3).  The field f maps
+// to the dither (f + 1/2)/2^bits.
 struct DitherBits {
   uint32_t w[4];
 };
@@ -165,24 +166,26 @@ __device__ __forceinline__ DitherBits pcg4d(uint32_t x, uint32_t y, uint32_t z, 
   r.w[3] = v3;
   return r;
 }
-// The float 2^23 + f of dither field k (f has 12 or 16 bits); the dither is then
-// (2^23 + f) / 2^12 - 2^11 or (2^23 + f) / 2^16 - 2^7, exactly.
+// The dither of field f (12 bits for k < 8, 16 bits for k = 8, 9) is the
+// midpoint d = (f + 1/2) / 2^bits, whose mean over f is exactly 1/2.  It is
+// built exactly: the float with bits 0x4A800000 | (2 f + 1) is 2^22 + f + 1/2, and
+// (2^22 + f + 1/2) / 2^12 - 2^10  or  (2^22 + f + 1/2) / 2^16 - 2^6  is d.
 __device__ __forceinline__ float dither_magic(const DitherBits& h, int k) {
-  uint32_t f;
-  if (k < 8) f = (k & 1) ? ((h.w[k >> 1] >> 12) & 0xFFFu) : (h.w[k >> 1] & 0xFFFu);
-  else if (k == 8) f = (h.w[0] >> 24) | ((h.w[1] >> 24) << 8);
-  else f = (h.w[2] >> 24) | ((h.w[3] >> 24) << 8);
-  return __uint_as_float(0x4B000000u | f);
+  uint32_t f2;  // 2 f
+  if (k < 8) f2 = (k & 1) ? ((h.w[k >> 1] >> 11) & 0x1FFEu) : ((h.w[k >> 1] << 1) & 0x1FFEu);
+  else if (k == 8) f2 = ((h.w[0] >> 24) | ((h.w[1] >> 24) << 8)) << 1;
+  else f2 = ((h.w[2] >> 24) | ((h.w[3] >> 24) << 8)) << 1;
+  return __uint_as_float(0x4A800000u | f2 | 1u);
 }
 __device__ __forceinline__ float dither_value(float magic, int k) {
-  return k < 8 ? __fmaf_rn(magic, 1.0f / 4096.0f, -2048.0f)
-               : __fmaf_rn(magic, 1.0f / 65536.0f, -128.0f);
+  return k < 8 ? __fmaf_rn(magic, 1.0f / 4096.0f, -1024.0f)
+               : __fmaf_rn(magic, 1.0f / 65536.0f, -64.0f);
 }
 __device__ __forceinline__ float2 dither_value(float2 magic, int k) {
   return k < 8 ? __ffma2_rn(magic, make_float2(1.0f / 4096.0f, 1.0f / 4096.0f),
-                            make_float2(-2048.0f, -2048.0f))
+                            make_float2(-1024.0f, -1024.0f))
                : __ffma2_rn(magic, make_float2(1.0f / 65536.0f, 1.0f / 65536.0f),
-                            make_float2(-128.0f, -128.0f));
+                            make_float2(-64.0f, -64.0f));
 }
 struct Dither {
   float d[10];
