@@ -162,6 +162,28 @@ MELBM_API int melbm_q16_encode(const float* stored, int nx, int ny, int nz, uint
                      int deterministic, uint32_t* words, void* cuda_stream);
 MELBM_API int melbm_q16_decode(const uint32_t* words, int64_t N, float* stored, void* cuda_stream);
 
+/* Allocation-free diagnostics (this entry point has no counterpart in the paper;
+ * it is a service for callers that cannot allocate device memory where they
+ * need the numbers: a frame or control loop with a fixed memory budget, a host
+ * whose device pool is owned by another allocator, or code that must avoid the
+ * implicit synchronisation cudaMalloc/cudaFree can cause).  It computes what
+ * melbm_reduce computes -- out[0] = sum(rho), out[1] = sum(rho |u|^2 / 2) over
+ * non-solid cells, out[2] = number of non-solid 16-bit codes equal to 0 or 65535
+ * (always 0 for MELBM_F32) -- from a raw state buffer the caller owns (the layout
+ * of melbm_get_raw_state, storage MELBM_F32 or MELBM_Q16, N cells; type[N] as from
+ * melbm_get_types, or NULL when no cell is solid).  out is a device pointer to 3
+ * doubles, written asynchronously on cuda_stream (NULL = legacy stream).
+ * It allocates nothing: its scratch is a fixed 96 KiB array inside the library,
+ * held on every GPU that loads the library until the process exits, so N is
+ * limited to 2^28 cells (larger N returns MELBM_EINVAL without any GPU work).
+ * The first call on each device looks up the scratch address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All
+ * calls share the scratch: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Returns MELBM_EINVAL for bad arguments and
+ * MELBM_ECUDA if the address lookup or a launch fails (no message is stored). */
+MELBM_API int melbm_reduce_state_noalloc(const void* state, int storage, int64_t N,
+                                         const uint8_t* type, double* out, void* cuda_stream);
+
 /* Message of the last failure of h (or of the last handle-less call if h is
  * NULL).  Valid until the next call on the same handle. */
 MELBM_API const char* melbm_last_error(melbm_t h);
