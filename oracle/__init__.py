@@ -350,10 +350,10 @@ def amplification_matrix(rho0, U, tau, kvecs, h=1e-30):
 
 
 # ---------------------------------------------------------------- adjoint
-def forward_loss(u0, F, shape, tau, nsteps, loss_fn):
+def forward_loss(u0, F, shape, tau, nsteps, loss_fn, typ=None, inflow=None):
     """Initial state (1, u0, u0 u0) -> n FP64 steps -> loss_fn(final state)."""
     m = initial_state_from_velocity(u0)
-    m = step(m, shape, tau, F=F, n=nsteps)
+    m = step(m, shape, tau, F=F, typ=typ, inflow=inflow, n=nsteps)
     return loss_fn(m), m
 
 
@@ -380,7 +380,7 @@ def initial_state_vjp(u0, lam0):
     return g
 
 
-def adjoint(u0, F, shape, tau, nsteps, dloss_dm, K=10):
+def adjoint(u0, F, shape, tau, nsteps, dloss_dm, K=10, typ=None, inflow=None):
     """Gradient of loss(m_T) w.r.t. (u0, F) by the discrete adjoint of the FP64
     step, recomputing each K-step segment from an FP64 checkpoint."""
     m = initial_state_from_velocity(u0)
@@ -388,7 +388,7 @@ def adjoint(u0, F, shape, tau, nsteps, dloss_dm, K=10):
     for t in range(nsteps):
         if t % K == 0:
             ckpt[t] = m.copy()
-        m = step(m, shape, tau, F=F)
+        m = step(m, shape, tau, F=F, typ=typ, inflow=inflow)
     lam = _f64(dloss_dm(m)).copy()
     gF = np.zeros((3, m.shape[1]))
     seg_starts = sorted(ckpt)
@@ -396,8 +396,8 @@ def adjoint(u0, F, shape, tau, nsteps, dloss_dm, K=10):
         e = min(s + K, nsteps)
         states = [ckpt[s]]
         for _ in range(s, e - 1):
-            states.append(step(states[-1], shape, tau, F=F))
+            states.append(step(states[-1], shape, tau, F=F, typ=typ, inflow=inflow))
         for t in reversed(range(s, e)):
-            lam, g = step_vjp(states[t - s], shape, tau, lam, F=F)
+            lam, g = step_vjp(states[t - s], shape, tau, lam, F=F, typ=typ)
             gF += g
     return initial_state_vjp(u0, lam), gF

@@ -11,42 +11,10 @@
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
 #include "melbm_adjoint.h"
+#include "melbm_handle.h"
 
 using namespace melbm;
 
-struct melbm_sim {
-  int nx = 0, ny = 0, nz = 0;
-  int64_t N = 0;
-  int storage = 0;
-  float tau = 0.f;
-  uint32_t seed = 0;
-  int64_t t = 0;
-  cudaStream_t stream = nullptr;
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;
-  // boundaries
-  uint8_t* mask = nullptr;
-  uint8_t* type = nullptr;
-  uint32_t* list_cell = nullptr;
-  uint32_t* list_word = nullptr;
-  int64_t L = 0;
-  uint32_t* cl_counts = nullptr;
-  uint32_t* cl_offsets = nullptr;
-  uint32_t* cl_total = nullptr;
-  int inflow_on = 0;
-  float inflow[4] = {1.f, 0.f, 0.f, 0.f};
-  int outflow_on = 0;
-  // force, staging, reductions
-  float* force = nullptr;
-  void* staging = nullptr;
-  size_t staging_bytes = 0;
-  double* red_partials = nullptr;
-  double* red_out = nullptr;
-  int64_t mem_bytes = 0;
-  bool poisoned = false;
-  std::string err;
-  melbm::AdjointState* adj = nullptr;
-};
 
 namespace {
 
@@ -162,12 +130,16 @@ int reclassify(melbm_t h) {
 }  // namespace
 
 namespace melbm {
-// Accessors used by the adjoint translation unit.
-int sim_dims(melbm_t h, int* nx, int* ny, int* nz) {
-  *nx = h->nx;
-  *ny = h->ny;
-  *nz = h->nz;
-  return 0;
+cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out) {
+  const float omega = 1.0f / h->tau;
+  cudaError_t e = launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
+                               h->seed, h->stream);
+  if (e == cudaSuccess && h->L)
+    e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
+                        h->list_word, h->L, h->inflow, t_out, h->seed, h->stream);
+  if (e == cudaSuccess && h->outflow_on && h->type)
+    e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream);
+  return e;
 }
 }  // namespace melbm
 
@@ -372,19 +344,9 @@ int melbm_step(melbm_t h, int n) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_step: NULL handle");
   if (n < 0) return fail(h, MELBM_EINVAL, "melbm_step: n = %d < 0", n);
   if (h->poisoned) return fail(h, MELBM_ESTATE, "melbm_step: an earlier CUDA failure left the state undefined; call melbm_set_state");
-  const float omega = 1.0f / h->tau;
   for (int s = 0; s < n; ++s) {
     const uint32_t t_out = uint32_t(h->t + 1);
-    void* in = h->buf[h->cur];
-    void* out = h->buf[1 - h->cur];
-    MELBM_CUDA(h, launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                               h->seed, h->stream));
-    if (h->L)
-      MELBM_CUDA(h, launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega,
-                                    h->list_cell, h->list_word, h->L, h->inflow, t_out, h->seed,
-                                    h->stream));
-    if (h->outflow_on && h->type)
-      MELBM_CUDA(h, launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream));
+    MELBM_CUDA(h, forward_step(h, h->buf[h->cur], h->buf[1 - h->cur], t_out));
     h->cur = 1 - h->cur;
     h->t += 1;
   }

@@ -27,13 +27,25 @@
 
 namespace melbm {
 
+// Tile shape: FY warps per block (rows), ZCHUNK planes per block (even), and the
+// minimum number of resident blocks per SM requested from the compiler.
+#ifndef MELBM_FLUID_FY
+#define MELBM_FLUID_FY 16
+#endif
+#ifndef MELBM_FLUID_ZCHUNK
+#define MELBM_FLUID_ZCHUNK 32
+#endif
+#ifndef MELBM_FLUID_MINB
+#define MELBM_FLUID_MINB 1
+#endif
 constexpr int FX = 32;
-constexpr int FY = 16;
+constexpr int FY = MELBM_FLUID_FY;
 constexpr int FXI = FX - 2;
 constexpr int FYI = FY - 2;
 constexpr int NSY = 9;                      // y-pass slices exchanged through shared memory
 constexpr int SM_BUF = 2 * NSY * FY * FX;  // float2 per buffer (phi+ and phi-)
-constexpr int ZCHUNK = 32;                  // planes per block (even)
+constexpr int ZCHUNK = MELBM_FLUID_ZCHUNK;
+static_assert(ZCHUNK % 2 == 0, "planes are processed in pairs");
 
 struct FluidParams {
   int nx, ny, nz, zc;
@@ -164,7 +176,7 @@ __device__ __forceinline__ float2 shfl_down2(float2 v) {
 // ----------------------------------------------------------------- kernel
 // The y-pass slices are indexed s = 3 p + r' (p: x-order, r': input z-order).
 template <int STORAGE, bool FORCE>
-__global__ void __launch_bounds__(FX* FY, 1) fluid_kernel(FluidParams P) {
+__global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidParams P) {
   extern __shared__ float2 sm2[];
   const int lane = threadIdx.x, row = threadIdx.y;
   const int nx = P.nx, ny = P.ny, nz = P.nz;

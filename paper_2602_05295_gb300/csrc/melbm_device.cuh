@@ -32,7 +32,19 @@ __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 vsub(float2 a, float2 b) {
   return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);  // exact negation, one rounding
 }
+#ifdef MELBM_RCP_NEWTON
+// Reciprocal of a pair: the hardware approximation (PTX rcp.approx) refined by one
+// Newton-Raphson step r' = r + r (1 - a r) on packed FP32x2.
+__device__ __forceinline__ float2 vrcp(float2 a) {
+  float2 r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(a.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(a.y));
+  const float2 e = __ffma2_rn(make_float2(-a.x, -a.y), r, make_float2(1.0f, 1.0f));
+  return __ffma2_rn(r, e, r);
+}
+#else
 __device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+#endif
 template <> __device__ __forceinline__ float2 vset<float2>(float a) { return make_float2(a, a); }
 // a * b + c with scalar constant b
 __device__ __forceinline__ float vfmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }

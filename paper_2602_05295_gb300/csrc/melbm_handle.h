@@ -1,0 +1,51 @@
+// melbm_handle.h -- the simulation handle behind the opaque melbm_t (internal).
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+namespace melbm {
+struct AdjointState;
+}
+
+struct melbm_sim {
+  int nx = 0, ny = 0, nz = 0;
+  int64_t N = 0;
+  int storage = 0;
+  float tau = 0.f;
+  uint32_t seed = 0;
+  int64_t t = 0;
+  cudaStream_t stream = nullptr;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  // boundaries
+  uint8_t* mask = nullptr;
+  uint8_t* type = nullptr;
+  uint32_t* list_cell = nullptr;
+  uint32_t* list_word = nullptr;
+  int64_t L = 0;
+  uint32_t* cl_counts = nullptr;
+  uint32_t* cl_offsets = nullptr;
+  uint32_t* cl_total = nullptr;
+  int inflow_on = 0;
+  float inflow[4] = {1.f, 0.f, 0.f, 0.f};
+  int outflow_on = 0;
+  // force, staging, reductions
+  float* force = nullptr;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  double* red_partials = nullptr;
+  double* red_out = nullptr;
+  int64_t mem_bytes = 0;
+  bool poisoned = false;
+  std::string err;
+  melbm::AdjointState* adj = nullptr;  // checkpoints of melbm_forward_checkpointed
+};
+
+namespace melbm {
+// Launch one forward step in -> out with the handle's boundaries (used by the
+// adjoint's recomputation); t_out is the time index of the output state.
+cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out);
+}  // namespace melbm
