@@ -1,0 +1,181 @@
+"""Run the five synthetic workloads on the GPU and print one JSON line each.
+
+    python -m paper_2602_05295_gb300.configs [--only NAME] [--steps K]
+
+For every workload: throughput (MLUPS over all cells, and over fluid cells where
+solids exist), device memory of the 16-bit and FP32 forms, and a check that needs
+no reference solution: the Taylor-Green decay rate (tgv32), total-mass drift
+(FP64 reductions), boundary-list size and solid fraction (channel512, large1000),
+gradient norms and timing of the checkpointed adjoint (adjoint128).
+Timing uses CUDA events on the simulator's stream after warm-up steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import melbm
+from . import workloads as W
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _timed_steps(sim, steps, warmup=3):
+    sim.step(warmup)
+    a, b = _events()
+    a.record(sim.stream)
+    sim.step(steps)
+    b.record(sim.stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _state_from_velocity(u):
+    return (torch.ones(u.shape[-1], dtype=torch.float32, device="cuda"),
+            torch.from_numpy(np.ascontiguousarray(u, np.float32)).cuda())
+
+
+def run_tgv32(steps):
+    wl = W.TGV32
+    u, k = W.taylor_green(wl.shape, 0.05)
+    rho, ut = _state_from_velocity(W.flat(u))
+    sim = melbm.Simulator(wl.shape, wl.tau, "f32")
+    sim.set_state(rho, ut)
+    nx, ny, nz = wl.shape
+    x = np.arange(nx)[None, None, :]
+    y = np.arange(ny)[None, :, None]
+    mode = (np.sin(k * x) * np.cos(k * y) * np.ones((nz, 1, 1))).ravel()
+    amps, ts = [], []
+    for t in range(0, wl.steps + 1, 10):
+        if t:
+            sim.step(10)
+        if t >= 20:
+            _, uu, _ = sim.get_moments()
+            ux = uu[0].cpu().numpy().astype(np.float64)
+            amps.append((ux * mode).sum() / (mode * mode).sum())
+            ts.append(t)
+    nu_fit = -np.polyfit(ts, np.log(amps), 1)[0] / (2 * k * k)
+    nu = (wl.tau - 0.5) / 3.0
+    ms = _timed_steps(sim, steps)
+    return {"workload": wl.name, "storage": "f32", "cells": wl.cells, "ms_per_step": ms,
+            "MLUPS": wl.cells / ms / 1e3, "nu_fit_over_nu": nu_fit / nu}
+
+
+def run_turbulence256(steps):
+    wl = W.TURB256
+    rho, u = _state_from_velocity(W.flat(W.random_phase_field(wl.shape, 0.08)))
+    out = []
+    for storage in ("q16", "f32"):
+        sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602)
+        sim.set_state(rho, u)
+        M0, E0 = sim.reduce()
+        ms = _timed_steps(sim, steps)
+        M1, E1 = sim.reduce()
+        out.append({"workload": wl.name, "storage": storage, "cells": wl.cells, "ms_per_step": ms,
+                    "MLUPS": wl.cells / ms / 1e3, "memory_bytes": sim.memory_bytes(),
+                    "steps_run": steps + 3, "mass_drift": (M1 - M0) / M0, "ke_ratio": E1 / E0})
+        sim.close()
+    return out
+
+
+def _channel(wl, mask, inflow_u, steps, storage="q16"):
+    sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602)
+    N = wl.cells
+    u = np.zeros((3, N), np.float32)
+    u[0] = inflow_u
+    rho, ut = _state_from_velocity(u)
+    sim.set_state(rho, ut)
+    mt = torch.from_numpy(mask.ravel()).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_solid(mt)
+    sim.set_inflow(1.0, (inflow_u, 0.0, 0.0))
+    sim.set_outflow()
+    torch.cuda.synchronize()
+    classify_ms = 1e3 * (time.perf_counter() - t0)
+    cells, _ = sim.boundary_list()
+    types = sim.types()
+    fluid = int((types != melbm.SOLID).sum().item())
+    M0, _ = sim.reduce()
+    ms = _timed_steps(sim, steps)
+    M1, E1 = sim.reduce()
+    rec = {"workload": wl.name, "storage": storage, "cells": N, "fluid_cells": fluid,
+           "solid_fraction": 1.0 - fluid / N, "boundary_list": int(cells.numel()),
+           "classify_ms": classify_ms, "ms_per_step": ms, "MLUPS": N / ms / 1e3,
+           "fluid_MLUPS": fluid / ms / 1e3, "memory_bytes": sim.memory_bytes(),
+           "mass_change_open_boundaries": (M1 - M0) / M0}
+    sim.close()
+    return rec
+
+
+def run_channel512(steps):
+    wl = W.CHANNEL512
+    mask, spheres = W.sphere_pack(wl.shape)
+    rec = _channel(wl, mask, 0.05, steps)
+    rec["spheres"] = int(len(spheres))
+    return rec
+
+
+def run_large1000(steps):
+    wl = W.LARGE1000
+    mask, _ = W.procedural_obstacle(wl.shape)
+    rec = _channel(wl, mask, 0.06, steps)
+    # memory footprint of the two storage forms (state ping-pong only)
+    rec["state_pingpong_bytes"] = {"q16": 2 * 20 * wl.cells, "f32": 2 * 40 * wl.cells,
+                                   "paper_mixed": 60 * wl.cells}
+    return rec
+
+
+def run_adjoint128(steps):
+    from .autograd import MELBMFunction, kinetic_energy_in_region
+    wl = W.ADJOINT128
+    N = wl.cells
+    u0 = torch.from_numpy(W.flat(W.random_phase_field(wl.shape, 0.05)).astype(np.float32)).cuda()
+    F = torch.from_numpy(W.flat(W.force_field(wl.shape, 1e-5)).astype(np.float32)).cuda()
+    z, y, x = np.mgrid[0:128, 0:128, 0:128]
+    region = torch.from_numpy(((x >= 48) & (x < 80) & (y >= 48) & (y < 80) & (z >= 48)
+                               & (z < 80)).ravel()).cuda()
+    sim = melbm.Simulator(wl.shape, wl.tau, "f32")
+    u0.requires_grad_(True)
+    F.requires_grad_(True)
+    a, b, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), \
+        torch.cuda.Event(enable_timing=True)
+    a.record()
+    m = MELBMFunction.apply(u0, F, sim, wl.steps, 20)
+    L = kinetic_energy_in_region(m, region)
+    b.record()
+    L.backward()
+    c.record()
+    torch.cuda.synchronize()
+    return {"workload": wl.name, "storage": "f32 + 16-bit checkpoints (K=20)", "cells": N,
+            "steps": wl.steps, "loss": float(L.item()), "forward_ms": a.elapsed_time(b),
+            "backward_ms": b.elapsed_time(c), "grad_u0_norm": float(u0.grad.norm().item()),
+            "grad_F_norm": float(F.grad.norm().item()), "memory_bytes": sim.memory_bytes()}
+
+
+RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256, "channel512": run_channel512,
+           "large1000": run_large1000, "adjoint128": run_adjoint128}
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--only", default=None)
+    p.add_argument("--steps", type=int, default=100)
+    args = p.parse_args()
+    melbm.lib()
+    for name, fn in RUNNERS.items():
+        if args.only and name != args.only:
+            continue
+        recs = fn(args.steps)
+        for r in (recs if isinstance(recs, list) else [recs]):
+            print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -117,3 +117,41 @@ def test_checkpointed_adjoint_against_fp64_central_differences(M, orc):
     # error against the largest derivative.
     assert np.linalg.norm(ads - fds) / np.linalg.norm(fds) < 1e-4
     assert np.abs(ads - fds).max() / np.abs(fds).max() < 1e-4
+
+
+def test_adjoint128_full_size_directional_derivatives(M, orc):
+    """Workload adjoint128 at full size: 128^3, tau = 0.55, 200 steps, 16-bit
+    checkpoints every 20 steps, loss = kinetic energy in [48, 80)^3.  Two seeded
+    directions in (u0, F) against FP64 central differences of the oracle (each
+    oracle forward is 4e8 cell updates, so the 16-direction check runs at 32^3)."""
+    from paper_2602_05295_gb300.autograd import MELBMFunction, kinetic_energy_in_region
+    wl = W.ADJOINT128
+    shape, tau, nsteps = wl.shape, wl.tau, wl.steps
+    u0 = W.flat(W.random_phase_field(shape, 0.05))
+    F = W.flat(W.force_field(shape, 1e-5))
+    z, y, x = np.mgrid[0:128, 0:128, 0:128]
+    region = ((x >= 48) & (x < 80) & (y >= 48) & (y < 80) & (z >= 48) & (z < 80)).ravel()
+
+    def loss(m):
+        return 0.5 * (m[0] * (m[1:4] ** 2).sum(0))[region].sum()
+
+    sim = M.Simulator(shape, tau, "f32")
+    u0_t = cuda(u0).requires_grad_(True)
+    F_t = cuda(F).requires_grad_(True)
+    L = kinetic_energy_in_region(MELBMFunction.apply(u0_t, F_t, sim, nsteps, 20),
+                                 cuda(region, torch.bool))
+    L.backward()
+    gu = u0_t.grad.cpu().numpy().astype(np.float64)
+    gF = F_t.grad.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(38)
+    fds, ads = [], []
+    for _ in range(2):
+        vu = rng.standard_normal(u0.shape) * np.abs(u0).max()
+        vF = rng.standard_normal(F.shape) * np.abs(F).max()
+        eps = 1e-4
+        lp, _ = orc.forward_loss(u0 + eps * vu, F + eps * vF, shape, tau, nsteps, loss)
+        lm, _ = orc.forward_loss(u0 - eps * vu, F - eps * vF, shape, tau, nsteps, loss)
+        fds.append((lp - lm) / (2 * eps))
+        ads.append((gu * vu).sum() + (gF * vF).sum())
+    fds, ads = np.array(fds), np.array(ads)
+    assert np.abs(ads - fds).max() / np.abs(fds).max() < 1e-4, (ads, fds)
