@@ -144,11 +144,11 @@ __device__ __forceinline__ void store_pair<ST_Q16>(void* buf, size_t N, size_t n
 #pragma unroll
   for (int k = 0; k < 10; ++k)
     d[k] = dither_value(make_float2(dither_magic(ha, k), dither_magic(hb, k)), k);
-  const uint2 e0 = q_encode_bits<0>(o.drho, d[0]), e1 = q_encode_bits<1>(o.ux, d[1]);
-  const uint2 e2 = q_encode_bits<1>(o.uy, d[2]), e3 = q_encode_bits<1>(o.uz, d[3]);
-  const uint2 e4 = q_encode_bits<2>(o.nxx, d[4]), e5 = q_encode_bits<2>(o.nyy, d[5]);
-  const uint2 e6 = q_encode_bits<2>(o.nzz, d[6]), e7 = q_encode_bits<2>(o.nxy, d[7]);
-  const uint2 e8 = q_encode_bits<2>(o.nxz, d[8]), e9 = q_encode_bits<2>(o.nyz, d[9]);
+  const uint2 e0 = q_encode_codes<0>(o.drho, d[0]), e1 = q_encode_codes<1>(o.ux, d[1]);
+  const uint2 e2 = q_encode_codes<1>(o.uy, d[2]), e3 = q_encode_codes<1>(o.uz, d[3]);
+  const uint2 e4 = q_encode_codes<2>(o.nxx, d[4]), e5 = q_encode_codes<2>(o.nyy, d[5]);
+  const uint2 e6 = q_encode_codes<2>(o.nzz, d[6]), e7 = q_encode_codes<2>(o.nxy, d[7]);
+  const uint2 e8 = q_encode_codes<2>(o.nxz, d[8]), e9 = q_encode_codes<2>(o.nyz, d[9]);
   uint32_t* p = static_cast<uint32_t*>(buf);
   if (sa) {
     p[na] = q_pack(e0.x, e1.x);
@@ -219,42 +219,44 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
       load_pair(raw, P.in, N, col + plane * wrapi(zz + 2, nz), col + plane * wrapi(zz + 3, nz));
     const Mom17T<float2> A = collide_moments<FORCE>(s, omega, fx, fy, fz);
 
-    // ---------------- x pass: slices (q', r'), inputs p' = 0, 1, 2 -> outputs p = 0, 1, 2
-    float2 X[3][3][3];
+    // ---------------- x pass on slices (q', r'), then the y-pass populations of
+    // the slices (p, r') as soon as their three inputs X[p][0..2][r'] exist
+    // (grouped by r' so that only nine X values are live at a time)
     const float2 zero = make_float2(0.f, 0.f);
-#define MELBM_XPASS(Q, R, A0, A1, A2)                 \
+    float2* sp = sm2 + parity * SM_BUF;
+    float2 yz0[NSY];
+    float2 X[3][3];  // X[p][q'] of the current r'
+#define MELBM_XPASS(Q, A0, A1, A2)                    \
   {                                                   \
     const PhiT<float2> ph = phi3(A0, A1, A2);         \
     const float2 pl = shfl_up2(ph.p);                 \
     const float2 mr = shfl_down2(ph.m);               \
-    X[0][Q][R] = proj0(pl, ph.z, mr);                 \
-    X[1][Q][R] = proj1(pl, mr);                       \
-    X[2][Q][R] = proj2(pl, mr, X[0][Q][R]);           \
+    X[0][Q] = proj0(pl, ph.z, mr);                    \
+    X[1][Q] = proj1(pl, mr);                          \
+    X[2][Q] = proj2(pl, mr, X[0][Q]);                 \
   }
-    MELBM_XPASS(0, 0, A.m000, A.m100, A.m200)
-    MELBM_XPASS(1, 0, A.m010, A.m110, A.m210)
-    MELBM_XPASS(0, 1, A.m001, A.m101, A.m201)
-    MELBM_XPASS(2, 0, A.m020, A.m120, zero)
-    MELBM_XPASS(0, 2, A.m002, A.m102, zero)
-    MELBM_XPASS(1, 1, A.m011, A.m111, zero)
-    MELBM_XPASS(2, 1, A.m021, zero, zero)
-    MELBM_XPASS(1, 2, A.m012, zero, zero)
+#define MELBM_YPHI(R)                                                   \
+  _Pragma("unroll") for (int p = 0; p < 3; ++p) {                       \
+    const PhiT<float2> ph = phi3(X[p][0], X[p][1], X[p][2]);            \
+    const int s_ = 3 * p + (R);                                         \
+    sp[(s_ * FY + row) * FX + lane] = ph.p;                             \
+    sp[((NSY + s_) * FY + row) * FX + lane] = ph.m;                     \
+    yz0[s_] = ph.z;                                                     \
+  }
+    MELBM_XPASS(0, A.m000, A.m100, A.m200)  // r' = 0
+    MELBM_XPASS(1, A.m010, A.m110, A.m210)
+    MELBM_XPASS(2, A.m020, A.m120, zero)
+    MELBM_YPHI(0)
+    MELBM_XPASS(0, A.m001, A.m101, A.m201)  // r' = 1
+    MELBM_XPASS(1, A.m011, A.m111, zero)
+    MELBM_XPASS(2, A.m021, zero, zero)
+    MELBM_YPHI(1)
+    MELBM_XPASS(0, A.m002, A.m102, zero)    // r' = 2; (q', r') = (2, 2) has no input
+    MELBM_XPASS(1, A.m012, zero, zero)
+    X[0][2] = X[1][2] = X[2][2] = zero;
+    MELBM_YPHI(2)
 #undef MELBM_XPASS
-    X[0][2][2] = X[1][2][2] = X[2][2][2] = zero;  // (q', r') = (2, 2) has no input moment
-
-    // ---------------- y pass, part 1: directional populations along y
-    float2* sp = sm2 + parity * SM_BUF;
-    float2 yz0[NSY];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const PhiT<float2> ph = phi3(X[p][0][r], X[p][1][r], X[p][2][r]);
-        const int s_ = 3 * p + r;
-        sp[(s_ * FY + row) * FX + lane] = ph.p;
-        sp[((NSY + s_) * FY + row) * FX + lane] = ph.m;
-        yz0[s_] = ph.z;
-      }
+#undef MELBM_YPHI
     __syncthreads();
     if (!mid_row) continue;  // halo rows only feed their neighbours
 

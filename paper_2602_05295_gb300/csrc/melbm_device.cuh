@@ -32,9 +32,10 @@ __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 vsub(float2 a, float2 b) {
   return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);  // exact negation, one rounding
 }
-#ifdef MELBM_RCP_NEWTON
 // Reciprocal of a pair: the hardware approximation (PTX rcp.approx) refined by one
-// Newton-Raphson step r' = r + r (1 - a r) on packed FP32x2.
+// Newton-Raphson step r' = r + r (1 - a r) on packed FP32x2; for the densities
+// here (a ~ 1) the refined value is the correctly rounded one up to rare last-bit
+// differences, so it carries no systematic bias into u = J / rho.
 __device__ __forceinline__ float2 vrcp(float2 a) {
   float2 r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(a.x));
@@ -42,9 +43,6 @@ __device__ __forceinline__ float2 vrcp(float2 a) {
   const float2 e = __ffma2_rn(make_float2(-a.x, -a.y), r, make_float2(1.0f, 1.0f));
   return __ffma2_rn(r, e, r);
 }
-#else
-__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
-#endif
 template <> __device__ __forceinline__ float2 vset<float2>(float a) { return make_float2(a, a); }
 // a * b + c with scalar constant b
 __device__ __forceinline__ float vfmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -104,6 +102,7 @@ template <int G> struct QConst {
   static constexpr float c = float(lo + qcd * (hi - lo) / 65535.0);
   static constexpr float wlo = float(-qcd), whi = float(65535.0 - qcd);
   static constexpr float magic = float(8388608.0 + qcd);  // 2^23 + qc
+  static constexpr float qc = QRange<G>::qc;
 };
 
 // Encoded bits of one value: the float 2^23 + q, whose low 16 bits are q.
@@ -114,14 +113,19 @@ __device__ __forceinline__ uint32_t q_encode_bits(float m, float d) {
   const float z = __fadd_rd(__fadd_rd(w, d), QConst<G>::magic);
   return __float_as_uint(z);
 }
+// Pair form: q = qc + floor(w + d) as floor(fl_rd(fl_rd(w + d) + qc)) -- both
+// round-down adds keep the floor exact -- converted by cvt.rmi.u16, which
+// saturates to [0, 65535] (and maps NaN to 0), the same codes as clamping w first.
+// Returns the two codes (zero-extended).
 template <int G>
-__device__ __forceinline__ uint2 q_encode_bits(float2 m, float2 d) {
-  float2 w = __ffma2_rn(m, make_float2(QConst<G>::K, QConst<G>::K),
-                        make_float2(QConst<G>::b, QConst<G>::b));
-  w.x = fminf(fmaxf(w.x, QConst<G>::wlo), QConst<G>::whi);
-  w.y = fminf(fmaxf(w.y, QConst<G>::wlo), QConst<G>::whi);
-  const float2 z = __fadd2_rd(__fadd2_rd(w, d), make_float2(QConst<G>::magic, QConst<G>::magic));
-  return make_uint2(__float_as_uint(z.x), __float_as_uint(z.y));
+__device__ __forceinline__ uint2 q_encode_codes(float2 m, float2 d) {
+  const float2 w = __ffma2_rn(m, make_float2(QConst<G>::K, QConst<G>::K),
+                              make_float2(QConst<G>::b, QConst<G>::b));
+  const float2 z = __fadd2_rd(__fadd2_rd(w, d), make_float2(QConst<G>::qc, QConst<G>::qc));
+  unsigned short qa, qb;
+  asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qa) : "f"(z.x));
+  asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qb) : "f"(z.y));
+  return make_uint2(qa, qb);
 }
 __device__ __forceinline__ uint32_t q_pack(uint32_t lo_bits, uint32_t hi_bits) {
   return __byte_perm(lo_bits, hi_bits, 0x5410);
