@@ -13,8 +13,19 @@
 // ten output moments are carried: 17 -> 24 after x, -> 18 after y, -> 10 after z.
 //
 // Work decomposition (one thread per (x, y) column, marching along z):
-//   * a block is 32 lanes (x) by FY warps (y); lanes cover x0-1 .. x0+30 and warps
-//     y0-1 .. y0+FY-2, so lanes 0/31 and warps 0/FY-1 are a recomputed halo ring;
+//   * a block is 32 lanes (x) by FY warps (y); the lanes are the 32 columns
+//     x0 .. x0+31 and the warps cover rows y0-1 .. y0+FY-2, so warps 0 and FY-1
+//     are recomputed halo rows;
+//   * warp 0 also computes, one plane pair ahead, the x-pass populations of the
+//     columns x0-1 (phi+) and x0+32 (phi-) for every row and passes them through
+//     shared memory; after the x shuffles they replace the values that lane 0
+//     and lane 31 received from the far end of the warp.  The stored words of
+//     those two columns reach a double-buffered staging area by cp.async,
+//     issued two pairs ahead, so they occupy no registers while the warp does
+//     its own row.  In 16-bit storage each word is copied alone (4 bytes); in
+//     FP32 storage the 16-byte aligned chunk holding it is copied past L1, so
+//     the gather of 32 rows does not crowd the L1 lines that the other warps'
+//     loads are landing in;
 //   * each iteration advances two z-planes held as the two halves of float2
 //     values, so every arithmetic step is one packed FP32x2 instruction;
 //   * the x pass exchanges directional populations with warp shuffles;
@@ -40,12 +51,27 @@ namespace melbm {
 #endif
 constexpr int FX = 32;
 constexpr int FY = MELBM_FLUID_FY;
-constexpr int FXI = FX - 2;
 constexpr int FYI = FY - 2;
+constexpr int NSX = 8;                      // x-pass slices
 constexpr int NSY = 9;                      // y-pass slices exchanged through shared memory
 constexpr int SM_BUF = 2 * NSY * FY * FX;  // float2 per buffer (phi+ and phi-)
+constexpr int HALO_BUF = 2 * FY * NSX;     // float2 per halo buffer (two columns)
+static_assert(2 * FY <= 32, "warp 0 covers both halo columns of every row");
 constexpr int ZCHUNK = MELBM_FLUID_ZCHUNK;
 static_assert(ZCHUNK % 2 == 0, "planes are processed in pairs");
+
+// Warp 0's halo staging, two buffers: per halo lane, 2 W entries (word w of
+// plane h at entry 2 w + h) plus 6 for the forces; an entry is CHUNK 32-bit
+// words, laid out [buffer][entry][lane][CHUNK].
+template <int STORAGE, bool FORCE>
+struct HaloStage {
+  static constexpr int W = STORAGE == ST_Q16 ? 5 : 10;     // stored 32-bit words per cell
+  static constexpr int CHUNK = STORAGE == ST_Q16 ? 1 : 4;  // 4: a 16-byte aligned chunk
+  static constexpr int ENTRIES = 2 * W + (FORCE ? 6 : 0);
+  static constexpr int BUF_WORDS = ENTRIES * 32 * CHUNK;
+  static constexpr size_t SMEM =
+      size_t(2) * (SM_BUF + HALO_BUF) * sizeof(float2) + size_t(2) * BUF_WORDS * 4;
+};
 
 struct FluidParams {
   int nx, ny, nz, zc;
@@ -54,6 +80,7 @@ struct FluidParams {
   const float* force;
   float omega;
   uint32_t t_out, seed;
+  int chunk16;  // FP32 storage: 16-byte aligned rows, so the halo gather copies chunks
 };
 
 // ----------------------------------------------------------------- plane-pair I/O
@@ -166,31 +193,69 @@ __device__ __forceinline__ void store_pair<ST_Q16>(void* buf, size_t N, size_t n
   }
 }
 
-__device__ __forceinline__ float2 shfl_up2(float2 v) {
-  return make_float2(__shfl_up_sync(FULL, v.x, 1), __shfl_up_sync(FULL, v.y, 1));
+// Asynchronous global -> shared copies (cp.async, completed per thread): 4 bytes
+// through L1, or 16 bytes (aligned) cached in L2 only.
+__device__ __forceinline__ void cp_async4(uint32_t* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ float2 shfl_down2(float2 v) {
-  return make_float2(__shfl_down_sync(FULL, v.x, 1), __shfl_down_sync(FULL, v.y, 1));
+__device__ __forceinline__ void cp_async16_l2(uint32_t* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+template <int STORAGE>
+__device__ __forceinline__ void set_word(RawPair<STORAGE>& r, int h, int w, uint32_t v);
+template <>
+__device__ __forceinline__ void set_word<ST_Q16>(RawPair<ST_Q16>& r, int h, int w, uint32_t v) {
+  (h ? r.b : r.a)[w] = v;
+}
+template <>
+__device__ __forceinline__ void set_word<ST_F32>(RawPair<ST_F32>& r, int h, int w, uint32_t v) {
+  (h ? r.b : r.a)[w] = __uint_as_float(v);
+}
+
+__device__ __forceinline__ float2 shfl_idx2(float2 v, int src) {
+  return make_float2(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src));
 }
 
 // ----------------------------------------------------------------- kernel
 // The y-pass slices are indexed s = 3 p + r' (p: x-order, r': input z-order).
 template <int STORAGE, bool FORCE>
 __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidParams P) {
+  using HS = HaloStage<STORAGE, FORCE>;
   extern __shared__ float2 sm2[];
+  float2* const hb = sm2 + 2 * SM_BUF;  // halo populations [buffer][row][slice][side]
+  uint32_t* const stg = reinterpret_cast<uint32_t*>(hb + 2 * HALO_BUF);  // warp 0 staging
   const int lane = threadIdx.x, row = threadIdx.y;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const size_t N = size_t(nx) * ny * nz;
-  const int x = int(blockIdx.x) * FXI - 1 + lane;
-  const int y = int(blockIdx.y) * FYI - 1 + row;
+  const int x0 = int(blockIdx.x) * FX, y0 = int(blockIdx.y) * FYI - 1;
+  const int x = x0 + lane, y = y0 + row;
   const int xw = wrapi(x, nx), yw = wrapi(y, ny);
   const bool mid_row = (row >= 1 && row <= FY - 2);  // warp-uniform
-  const bool col_ok = mid_row && lane >= 1 && lane <= FX - 2 && x < nx && y < ny;
+  const bool col_ok = mid_row && x < nx && y < ny;
   const int z0 = int(blockIdx.z) * P.zc;
   const int z1 = min(z0 + P.zc, nz);
   const size_t col = size_t(xw) + size_t(nx) * yw;
   const size_t plane = size_t(nx) * ny;
   const float omega = P.omega;
+  const int src_up = (lane + 31) & 31, src_dn = (lane + 1) & 31;
+
+  // warp 0's halo cell of this lane: row (lane % FY) of column x0-1 (side 0) or
+  // x0+32 (side 1); lanes past 2 FY (FY < 16) compute a copy and store nothing
+  const bool halo_warp = (row == 0);  // warp-uniform
+  const int hrow = lane % FY, side = (lane / FY) & 1;
+  const bool halo_lane = lane < 2 * FY;
+  const size_t hcol =
+      size_t(wrapi(side ? x0 + FX : x0 - 1, nx)) + size_t(nx) * wrapi(y0 + hrow, ny);
 
   // z-march state of the six (p, q) slices: phi+ of the previous pair's two
   // planes and phi0 of its second plane
@@ -203,10 +268,89 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
   }
   float fprev[3] = {0.f, 0.f, 0.f};
 
+  // Issue the staging of the halo pair (za, za + 1) into staging buffer b.  The
+  // pair with index j = (za - z0 + 1) / 2 uses halo buffer j & 1, written one
+  // pair ahead (before the barrier of pair j - 1) and read by the x pass of pair j.
+  const bool chunk16 = HS::CHUNK == 4 && P.chunk16;
+  auto halo_issue = [&](int za, int b) {
+    const size_t na = hcol + plane * wrapi(za, nz), nb = hcol + plane * wrapi(za + 1, nz);
+    uint32_t* d = stg + b * HS::BUF_WORDS + lane * HS::CHUNK;
+    const uint32_t* src = static_cast<const uint32_t*>(P.in);
+    const float* fsrc = P.force;
+    auto copy = [&](int e, const void* g, size_t n) {  // entry e <- element n of g
+      if (chunk16)
+        cp_async16_l2(d + e * 32 * HS::CHUNK, static_cast<const uint32_t*>(g) + (n & ~size_t(3)));
+      else
+        cp_async4(d + e * 32 * HS::CHUNK, static_cast<const uint32_t*>(g) + n);
+    };
+#pragma unroll
+    for (int w = 0; w < HS::W; ++w) {
+      copy(2 * w, src + w * N, na);
+      copy(2 * w + 1, src + w * N, nb);
+    }
+    if (FORCE) {
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        copy(2 * HS::W + 2 * w, fsrc + w * N, na);
+        copy(2 * HS::W + 2 * w + 1, fsrc + w * N, nb);
+      }
+    }
+    cp_async_commit();
+  };
+  // Write the x-pass populations of the pair staged in buffer b (its copies have
+  // completed) into halo buffer hbuf, laid out [row][slice] as
+  // {phi+ of column x0-1, phi- of column x0+32}.
+  auto halo_finish = [&](int b, int hbuf) {
+    const uint32_t* d = stg + b * HS::BUF_WORDS + lane * HS::CHUNK + (chunk16 ? int(hcol & 3) : 0);
+    RawPair<STORAGE> hr;
+#pragma unroll
+    for (int w = 0; w < HS::W; ++w) {
+      set_word<STORAGE>(hr, 0, w, d[(2 * w) * 32 * HS::CHUNK]);
+      set_word<STORAGE>(hr, 1, w, d[(2 * w + 1) * 32 * HS::CHUNK]);
+    }
+    const StoredT<float2> hs = decode_pair(hr);
+    float2 hfx = make_float2(0.f, 0.f), hfy = hfx, hfz = hfx;
+    if (FORCE) {
+      const float* sf = reinterpret_cast<const float*>(d) + 2 * HS::W * 32 * HS::CHUNK;
+      hfx = make_float2(sf[0 * 32 * HS::CHUNK], sf[1 * 32 * HS::CHUNK]);
+      hfy = make_float2(sf[2 * 32 * HS::CHUNK], sf[3 * 32 * HS::CHUNK]);
+      hfz = make_float2(sf[4 * 32 * HS::CHUNK], sf[5 * 32 * HS::CHUNK]);
+    }
+    const Mom17T<float2> H = collide_moments<FORCE>(hs, omega, hfx, hfy, hfz);
+    const float2 zero = make_float2(0.f, 0.f);
+    const float2 mu[NSX][3] = {{H.m000, H.m100, H.m200}, {H.m010, H.m110, H.m210},
+                               {H.m020, H.m120, zero},   {H.m001, H.m101, H.m201},
+                               {H.m011, H.m111, zero},   {H.m021, zero, zero},
+                               {H.m002, H.m102, zero},   {H.m012, zero, zero}};
+    float2* dst = hb + hbuf * HALO_BUF + hrow * NSX * 2 + side;
+#pragma unroll
+    for (int k = 0; k < NSX; ++k) {
+      const PhiT<float2> ph = phi3(mu[k][0], mu[k][1], mu[k][2]);
+      if (halo_lane) dst[2 * k] = side ? ph.m : ph.p;
+    }
+  };
+
   RawPair<STORAGE> raw;
   load_pair(raw, P.in, N, col + plane * wrapi(z0 - 1, nz), col + plane * wrapi(z0, nz));
+  // Staging schedule (pair j = (zz - z0 + 1) / 2, window j = the work between the
+  // barriers of pairs j - 1 and j): pair j + 2 is issued at the start of window j
+  // into staging buffer j & 1, and pair j + 1 is consumed at its end.
+  if (halo_warp) {
+    halo_issue(z0 - 1, 0);
+    if (z0 + 1 <= z1) {
+      halo_issue(z0 + 1, 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    halo_finish(0, 0);
+  }
+  __syncthreads();
   int parity = 0;
   for (int zz = z0 - 1; zz <= z1; zz += 2, parity ^= 1) {
+    const bool halo_next = halo_warp && zz + 2 <= z1;
+    const bool halo_ahead = halo_warp && zz + 4 <= z1;
+    if (halo_ahead) halo_issue(zz + 4, parity);
     const StoredT<float2> s = decode_pair(raw);
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
     if (FORCE) {
@@ -226,14 +370,20 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
     float2* sp = sm2 + parity * SM_BUF;
     float2 yz0[NSY];
     float2 X[3][3];  // X[p][q'] of the current r'
-#define MELBM_XPASS(Q, A0, A1, A2)                    \
-  {                                                   \
-    const PhiT<float2> ph = phi3(A0, A1, A2);         \
-    const float2 pl = shfl_up2(ph.p);                 \
-    const float2 mr = shfl_down2(ph.m);               \
-    X[0][Q] = proj0(pl, ph.z, mr);                    \
-    X[1][Q] = proj1(pl, mr);                          \
-    X[2][Q] = proj2(pl, mr, X[0][Q]);                 \
+    const float4* hbp = reinterpret_cast<const float4*>(hb + parity * HALO_BUF) + row * NSX;
+    int xs = 0;  // x-pass slice index (halo buffer order)
+#define MELBM_XPASS(Q, A0, A1, A2)                                      \
+  {                                                                     \
+    const PhiT<float2> ph = phi3(A0, A1, A2);                           \
+    const float4 h = hbp[xs];                                           \
+    float2 pl = shfl_idx2(ph.p, src_up);                                \
+    float2 mr = shfl_idx2(ph.m, src_dn);                                \
+    if (lane == 0) pl = make_float2(h.x, h.y);                          \
+    if (lane == FX - 1) mr = make_float2(h.z, h.w);                     \
+    X[0][Q] = proj0(pl, ph.z, mr);                                      \
+    X[1][Q] = proj1(pl, mr);                                            \
+    X[2][Q] = proj2(pl, mr, X[0][Q]);                                   \
+    ++xs;                                                               \
   }
 #define MELBM_YPHI(R)                                                   \
   _Pragma("unroll") for (int p = 0; p < 3; ++p) {                       \
@@ -257,8 +407,13 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
     MELBM_YPHI(2)
 #undef MELBM_XPASS
 #undef MELBM_YPHI
+    if (halo_next) {
+      if (halo_ahead) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      halo_finish(parity ^ 1, parity ^ 1);
+    }
     __syncthreads();
-    if (!mid_row) continue;  // halo rows only feed their neighbours
+    if (!mid_row) continue;
 
     // ---------------- y pass, part 2: pull and project -> Y[p][q][r'], q <= 2 - p
     float2 Y[3][3][3];
@@ -317,7 +472,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
 
 template <int STORAGE, bool FORCE>
 static cudaError_t launch_fluid_t(const FluidParams& p, dim3 grid, cudaStream_t st) {
-  const size_t smem = size_t(2) * SM_BUF * sizeof(float2);
+  const size_t smem = HaloStage<STORAGE, FORCE>::SMEM;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE>,
@@ -343,7 +498,10 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
   p.omega = omega;
   p.t_out = t_out;
   p.seed = seed;
-  dim3 grid((nx + FXI - 1) / FXI, (ny + FYI - 1) / FYI, (nz + p.zc - 1) / p.zc);
+  // 16-byte chunks need 16-byte aligned rows: nx % 4 == 0 and aligned bases
+  p.chunk16 = nx % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
+              reinterpret_cast<uintptr_t>(force) % 16 == 0;
+  dim3 grid((nx + FX - 1) / FX, (ny + FYI - 1) / FYI, (nz + p.zc - 1) / p.zc);
   if (storage == ST_Q16)
     return force ? launch_fluid_t<ST_Q16, true>(p, grid, st) : launch_fluid_t<ST_Q16, false>(p, grid, st);
   return force ? launch_fluid_t<ST_F32, true>(p, grid, st) : launch_fluid_t<ST_F32, false>(p, grid, st);
