@@ -33,12 +33,16 @@
 //     accesses, one barrier per plane pair);
 //   * the z pass keeps the previous pair's populations in registers;
 //   * the next pair's loads are issued before the current pair is processed.
+#include <algorithm>
+#include <cstdint>
+
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
 
 namespace melbm {
 
-// Tile shape: FY warps per block (rows), ZCHUNK planes per block (even), and the
+// Tile shape: FY warps per block (rows), at most ZCHUNK planes per block (even;
+// the launcher picks the length per grid), and the
 // minimum number of resident blocks per SM requested from the compiler.
 #ifndef MELBM_FLUID_FY
 #define MELBM_FLUID_FY 16
@@ -470,16 +474,42 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
   }
 }
 
+// z-chunk length: the even length (ZCHUNK down to 4) minimising the number of
+// waves times the plane pairs a block iterates over (chunk / 2 + 1, the first
+// pair feeding the z pass only), so that small grids still fill the GPU.
+static int choose_zchunk(int64_t tiles_xy, int nz, int64_t resident_blocks) {
+  int best = ZCHUNK;
+  int64_t best_cost = INT64_MAX;
+  for (int zc = ZCHUNK; zc >= 4; zc -= 2) {
+    const int64_t blocks = tiles_xy * ((nz + zc - 1) / zc);
+    const int64_t cost = (blocks + resident_blocks - 1) / resident_blocks * (zc / 2 + 1);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = zc;
+    }
+  }
+  return best;
+}
+
 template <int STORAGE, bool FORCE>
-static cudaError_t launch_fluid_t(const FluidParams& p, dim3 grid, cudaStream_t st) {
+static cudaError_t launch_fluid_t(FluidParams& p, cudaStream_t st) {
   const size_t smem = HaloStage<STORAGE, FORCE>::SMEM;
-  static bool configured = false;
-  if (!configured) {
+  static int resident = 0;  // blocks resident on the whole GPU (device 0 of the process)
+  if (!resident) {
     cudaError_t e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_kernel<STORAGE, FORCE>,
+                                                        FX * FY, smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    resident = std::max(1, sms * per_sm);
   }
+  const int64_t tiles_xy = int64_t((p.nx + FX - 1) / FX) * ((p.ny + FYI - 1) / FYI);
+  p.zc = choose_zchunk(tiles_xy, p.nz, resident);
+  dim3 grid((p.nx + FX - 1) / FX, (p.ny + FYI - 1) / FYI, (p.nz + p.zc - 1) / p.zc);
   fluid_kernel<STORAGE, FORCE><<<grid, dim3(FX, FY), smem, st>>>(p);
   return cudaGetLastError();
 }
@@ -491,7 +521,6 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
   p.nx = nx;
   p.ny = ny;
   p.nz = nz;
-  p.zc = ZCHUNK;
   p.in = in;
   p.out = out;
   p.force = force;
@@ -501,10 +530,9 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
   // 16-byte chunks need 16-byte aligned rows: nx % 4 == 0 and aligned bases
   p.chunk16 = nx % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
               reinterpret_cast<uintptr_t>(force) % 16 == 0;
-  dim3 grid((nx + FX - 1) / FX, (ny + FYI - 1) / FYI, (nz + p.zc - 1) / p.zc);
   if (storage == ST_Q16)
-    return force ? launch_fluid_t<ST_Q16, true>(p, grid, st) : launch_fluid_t<ST_Q16, false>(p, grid, st);
-  return force ? launch_fluid_t<ST_F32, true>(p, grid, st) : launch_fluid_t<ST_F32, false>(p, grid, st);
+    return force ? launch_fluid_t<ST_Q16, true>(p, st) : launch_fluid_t<ST_Q16, false>(p, st);
+  return force ? launch_fluid_t<ST_F32, true>(p, st) : launch_fluid_t<ST_F32, false>(p, st);
 }
 
 }  // namespace melbm
