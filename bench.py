@@ -68,17 +68,18 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage):
-    """DRAM bytes per launch of the fluid kernel from the committed ncu summary,
-    or None when the kernel source changed since the capture."""
+def ncu_record(storage):
+    """The fluid kernel's committed ncu figures for this storage (DRAM bytes and
+    warp instructions per 256^3 launch), or {} when the kernel source changed
+    since the capture."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "fluid_traffic.json")))
         rec = t.get(storage)
         if rec and rec.get("source_hash") == source_hash():
-            return rec["bytes_per_launch_256cube"]
+            return rec
     except Exception:
         pass
-    return None
+    return {}
 
 
 class Clocks:
@@ -319,14 +320,26 @@ def main():
     f_total, f_kern, f_mem = time_storage(torch, melbm, wl, u_np, "f32", args.steps, args.warmup)
     f_total = max_over_ranks(torch, f_total)
 
+    clk = clocks.summary()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+
     def roof(storage, kern_ms):
         avg_s = statistics.mean(kern_ms) / 1e3
         achieved = BYTES_PER_CELL[storage] * N / avg_s / 1e9
-        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "frac_of_nominal_8000": achieved / 8000.0,
-                "traffic": ncu_traffic(storage), "peak_source": peak_src,
-                "kernel": f"fluid_kernel<{storage}>", "kernel_ms": avg_s * 1e3,
-                "algorithmic_bytes_per_launch": BYTES_PER_CELL[storage] * N}
+        rec = ncu_record(storage)
+        out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+               "frac": achieved / peak, "frac_of_nominal_8000": achieved / 8000.0,
+               "traffic": rec.get("bytes_per_launch_256cube"), "peak_source": peak_src,
+               "kernel": f"fluid_kernel<{storage}>", "kernel_ms": avg_s * 1e3,
+               "algorithmic_bytes_per_launch": BYTES_PER_CELL[storage] * N}
+        inst, mhz = rec.get("warp_inst_per_launch_256cube"), clk.get("sm_mhz")
+        if inst and mhz:
+            # instruction-issue ceiling: one warp instruction per scheduler per cycle
+            ipeak = sms * 4 * mhz * 1e6
+            out["issue"] = {"achieved": inst / avg_s, "peak": ipeak, "unit": "warp inst/s",
+                            "frac": inst / avg_s / ipeak, "warp_inst_per_launch": inst,
+                            "peak_from": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz (median sampled)"}
+        return out
 
     value = N * args.steps * world / (q_total / 1e3) / 1e6
     f_value = N * args.steps * world / (f_total / 1e3) / 1e6
@@ -343,7 +356,7 @@ def main():
                          "roofline": roof("f32", f_kern)},
         "memory_bytes": {"q16": q_mem, "f32": f_mem},
         "gpu_launches": args.steps,
-        "clocks": clocks.summary(),
+        "clocks": clk,
     }
     if not args.no_e2e:
         el, bi, bo = e2e_run(torch, melbm, wl, u_np, max(3, min(args.steps, 10)), 2)
