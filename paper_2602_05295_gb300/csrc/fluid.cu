@@ -48,7 +48,7 @@ namespace melbm {
 #define MELBM_FLUID_FY 16
 #endif
 #ifndef MELBM_FLUID_ZCHUNK
-#define MELBM_FLUID_ZCHUNK 32
+#define MELBM_FLUID_ZCHUNK 64
 #endif
 #ifndef MELBM_FLUID_MINB
 #define MELBM_FLUID_MINB 1
@@ -252,6 +252,11 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
   const size_t plane = size_t(nx) * ny;
   const float omega = P.omega;
   const int src_up = (lane + 31) & 31, src_dn = (lane + 1) & 31;
+  // plane index of z in [z0 - 1, z1 + 3]: one conditional wrap when nz > 3
+  const bool small_nz = nz <= 3;
+  auto wz = [&](int zv) {
+    return small_nz ? wrapi(zv, nz) : (zv < 0 ? zv + nz : (zv >= nz ? zv - nz : zv));
+  };
 
   // warp 0's halo cell of this lane: row (lane % FY) of column x0-1 (side 0) or
   // x0+32 (side 1); lanes past 2 FY (FY < 16) compute a copy and store nothing
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
   // pair ahead (before the barrier of pair j - 1) and read by the x pass of pair j.
   const bool chunk16 = HS::CHUNK == 4 && P.chunk16;
   auto halo_issue = [&](int za, int b) {
-    const size_t na = hcol + plane * wrapi(za, nz), nb = hcol + plane * wrapi(za + 1, nz);
+    const size_t na = hcol + plane * wz(za), nb = hcol + plane * wz(za + 1);
     uint32_t* d = stg + b * HS::BUF_WORDS + lane * HS::CHUNK;
     const uint32_t* src = static_cast<const uint32_t*>(P.in);
     const float* fsrc = P.force;
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
   };
 
   RawPair<STORAGE> raw;
-  load_pair(raw, P.in, N, col + plane * wrapi(z0 - 1, nz), col + plane * wrapi(z0, nz));
+  load_pair(raw, P.in, N, col + plane * wz(z0 - 1), col + plane * wz(z0));
   // Staging schedule (pair j = (zz - z0 + 1) / 2, window j = the work between the
   // barriers of pairs j - 1 and j): pair j + 2 is issued at the start of window j
   // into staging buffer j & 1, and pair j + 1 is consumed at its end.
@@ -358,13 +363,13 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
     const StoredT<float2> s = decode_pair(raw);
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
     if (FORCE) {
-      const size_t na = col + plane * wrapi(zz, nz), nb = col + plane * wrapi(zz + 1, nz);
+      const size_t na = col + plane * wz(zz), nb = col + plane * wz(zz + 1);
       fx = make_float2(__ldg(P.force + na), __ldg(P.force + nb));
       fy = make_float2(__ldg(P.force + N + na), __ldg(P.force + N + nb));
       fz = make_float2(__ldg(P.force + 2 * N + na), __ldg(P.force + 2 * N + nb));
     }
     if (zz + 2 <= z1)  // prefetch the next pair
-      load_pair(raw, P.in, N, col + plane * wrapi(zz + 2, nz), col + plane * wrapi(zz + 3, nz));
+      load_pair(raw, P.in, N, col + plane * wz(zz + 2), col + plane * wz(zz + 3));
     const Mom17T<float2> A = collide_moments<FORCE>(s, omega, fx, fy, fz);
 
     // ---------------- x pass on slices (q', r'), then the y-pass populations of
@@ -474,7 +479,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
   }
 }
 
-// z-chunk length: the even length (ZCHUNK down to 4) minimising the number of
+// z-chunk length: the even length (ZCHUNK = 64 down to 4) minimising the number of
 // waves times the plane pairs a block iterates over (chunk / 2 + 1, the first
 // pair feeding the z pass only), so that small grids still fill the GPU.
 static int choose_zchunk(int64_t tiles_xy, int nz, int64_t resident_blocks) {
