@@ -87,10 +87,27 @@ struct FluidParams {
   int chunk16;  // FP32 storage: 16-byte aligned rows, so the halo gather copies chunks
 };
 
+// Kernel parameters per storage: the FP32 kernel also gets per-word plane
+// pointers of in / out and of the force components.
+template <int STORAGE>
+struct KernelParams : FluidParams {};
+template <>
+struct KernelParams<ST_F32> : FluidParams {
+  const uint32_t* in_w[10];
+  uint32_t* out_w[10];
+  const uint32_t* f_w[3];
+};
+
 // ----------------------------------------------------------------- plane-pair I/O
 template <int STORAGE> struct RawPair;
 template <> struct RawPair<ST_Q16> { uint32_t a[5], b[5]; };
 template <> struct RawPair<ST_F32> { float a[10], b[10]; };
+
+// FP32 word planes are addressed through per-word base pointers held in the
+// kernel parameters (uniform), so each access adds one per-thread offset; the
+// five 16-bit planes are addressed as base + k N (each form measured the faster
+// one for its storage).
+using WordPlanes = const uint32_t* const*;
 
 __device__ __forceinline__ void load_pair(RawPair<ST_Q16>& r, const void* buf, size_t N, size_t na,
                                           size_t nb) {
@@ -101,13 +118,11 @@ __device__ __forceinline__ void load_pair(RawPair<ST_Q16>& r, const void* buf, s
     r.b[k] = __ldg(p + k * N + nb);
   }
 }
-__device__ __forceinline__ void load_pair(RawPair<ST_F32>& r, const void* buf, size_t N, size_t na,
-                                          size_t nb) {
-  const float* p = static_cast<const float*>(buf);
+__device__ __forceinline__ void load_pair(RawPair<ST_F32>& r, WordPlanes w, size_t na, size_t nb) {
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
-    r.a[k] = __ldg(p + k * N + na);
-    r.b[k] = __ldg(p + k * N + nb);
+    r.a[k] = __uint_as_float(__ldg(w[k] + na));
+    r.b[k] = __uint_as_float(__ldg(w[k] + nb));
   }
 }
 
@@ -141,34 +156,25 @@ __device__ __forceinline__ StoredT<float2> decode_pair(const RawPair<ST_F32>& r)
 }
 
 // Store the pair (planes za, zb = za + 1) -- each half only if its flag is set.
-template <int STORAGE>
-__device__ __forceinline__ void store_pair(void* buf, size_t N, size_t na, size_t nb,
-                                           const StoredT<float2>& o, bool sa, bool sb, uint32_t x,
-                                           uint32_t y, uint32_t za, uint32_t zb, uint32_t t,
-                                           uint32_t seed);
+using OutPlanes = uint32_t* const*;
 
-template <>
-__device__ __forceinline__ void store_pair<ST_F32>(void* buf, size_t N, size_t na, size_t nb,
-                                                   const StoredT<float2>& o, bool sa, bool sb,
-                                                   uint32_t, uint32_t, uint32_t, uint32_t, uint32_t,
-                                                   uint32_t) {
-  float* p = static_cast<float*>(buf);
+__device__ __forceinline__ void store_pair_f32(OutPlanes w, size_t na, size_t nb,
+                                               const StoredT<float2>& o, bool sa, bool sb) {
   const float2 v[10] = {o.drho, o.ux, o.uy, o.uz, o.nxx, o.nyy, o.nzz, o.nxy, o.nxz, o.nyz};
   if (sa) {
 #pragma unroll
-    for (int k = 0; k < 10; ++k) p[k * N + na] = v[k].x;
+    for (int k = 0; k < 10; ++k) w[k][na] = __float_as_uint(v[k].x);
   }
   if (sb) {
 #pragma unroll
-    for (int k = 0; k < 10; ++k) p[k * N + nb] = v[k].y;
+    for (int k = 0; k < 10; ++k) w[k][nb] = __float_as_uint(v[k].y);
   }
 }
 
-template <>
-__device__ __forceinline__ void store_pair<ST_Q16>(void* buf, size_t N, size_t na, size_t nb,
-                                                   const StoredT<float2>& o, bool sa, bool sb,
-                                                   uint32_t x, uint32_t y, uint32_t za, uint32_t zb,
-                                                   uint32_t t, uint32_t seed) {
+__device__ __forceinline__ void store_pair_q16(void* buf, size_t N, size_t na, size_t nb,
+                                               const StoredT<float2>& o, bool sa, bool sb, uint32_t x,
+                                               uint32_t y, uint32_t za, uint32_t zb, uint32_t t,
+                                               uint32_t seed) {
   const DitherBits ha = pcg4d(x, y, za, t, seed);
   const DitherBits hb = pcg4d(x, y, zb, t, seed);
   float2 d[10];
@@ -233,7 +239,7 @@ __device__ __forceinline__ float2 shfl_idx2(float2 v, int src) {
 // ----------------------------------------------------------------- kernel
 // The y-pass slices are indexed s = 3 p + r' (p: x-order, r': input z-order).
 template <int STORAGE, bool FORCE>
-__global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidParams P) {
+__global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelParams<STORAGE> P) {
   using HS = HaloStage<STORAGE, FORCE>;
   extern __shared__ float2 sm2[];
   float2* const hb = sm2 + 2 * SM_BUF;  // halo populations [buffer][row][slice][side]
@@ -294,14 +300,24 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
     };
 #pragma unroll
     for (int w = 0; w < HS::W; ++w) {
-      copy(2 * w, src + w * N, na);
-      copy(2 * w + 1, src + w * N, nb);
+      if constexpr (STORAGE == ST_Q16) {
+        copy(2 * w, src + w * N, na);
+        copy(2 * w + 1, src + w * N, nb);
+      } else {
+        copy(2 * w, P.in_w[w], na);
+        copy(2 * w + 1, P.in_w[w], nb);
+      }
     }
     if (FORCE) {
 #pragma unroll
       for (int w = 0; w < 3; ++w) {
-        copy(2 * HS::W + 2 * w, fsrc + w * N, na);
-        copy(2 * HS::W + 2 * w + 1, fsrc + w * N, nb);
+        if constexpr (STORAGE == ST_Q16) {
+          copy(2 * HS::W + 2 * w, fsrc + w * N, na);
+          copy(2 * HS::W + 2 * w + 1, fsrc + w * N, nb);
+        } else {
+          copy(2 * HS::W + 2 * w, P.f_w[w], na);
+          copy(2 * HS::W + 2 * w + 1, P.f_w[w], nb);
+        }
       }
     }
     cp_async_commit();
@@ -340,7 +356,10 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
   };
 
   RawPair<STORAGE> raw;
-  load_pair(raw, P.in, N, col + plane * wz(z0 - 1), col + plane * wz(z0));
+  if constexpr (STORAGE == ST_Q16)
+    load_pair(raw, P.in, N, col + plane * wz(z0 - 1), col + plane * wz(z0));
+  else
+    load_pair(raw, P.in_w, col + plane * wz(z0 - 1), col + plane * wz(z0));
   // Staging schedule (pair j = (zz - z0 + 1) / 2, window j = the work between the
   // barriers of pairs j - 1 and j): pair j + 2 is issued at the start of window j
   // into staging buffer j & 1, and pair j + 1 is consumed at its end.
@@ -364,12 +383,23 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
     if (FORCE) {
       const size_t na = col + plane * wz(zz), nb = col + plane * wz(zz + 1);
-      fx = make_float2(__ldg(P.force + na), __ldg(P.force + nb));
-      fy = make_float2(__ldg(P.force + N + na), __ldg(P.force + N + nb));
-      fz = make_float2(__ldg(P.force + 2 * N + na), __ldg(P.force + 2 * N + nb));
+      if constexpr (STORAGE == ST_Q16) {
+        fx = make_float2(__ldg(P.force + na), __ldg(P.force + nb));
+        fy = make_float2(__ldg(P.force + N + na), __ldg(P.force + N + nb));
+        fz = make_float2(__ldg(P.force + 2 * N + na), __ldg(P.force + 2 * N + nb));
+      } else {
+        fx = make_float2(__uint_as_float(__ldg(P.f_w[0] + na)), __uint_as_float(__ldg(P.f_w[0] + nb)));
+        fy = make_float2(__uint_as_float(__ldg(P.f_w[1] + na)), __uint_as_float(__ldg(P.f_w[1] + nb)));
+        fz = make_float2(__uint_as_float(__ldg(P.f_w[2] + na)), __uint_as_float(__ldg(P.f_w[2] + nb)));
+      }
     }
     if (zz + 2 <= z1)  // prefetch the next pair
-      load_pair(raw, P.in, N, col + plane * wz(zz + 2), col + plane * wz(zz + 3));
+    {
+      if constexpr (STORAGE == ST_Q16)
+        load_pair(raw, P.in, N, col + plane * wz(zz + 2), col + plane * wz(zz + 3));
+      else
+        load_pair(raw, P.in_w, col + plane * wz(zz + 2), col + plane * wz(zz + 3));
+    }
     const Mom17T<float2> A = collide_moments<FORCE>(s, omega, fx, fy, fz);
 
     // ---------------- x pass on slices (q', r'), then the y-pass populations of
@@ -467,9 +497,13 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(FluidPa
           finish_moments<FORCE>(M[0][0], M[1][0], M[2][0], M[0][1], M[3][0], M[5][0], M[0][2],
                                 M[4][0], M[1][1], M[2][1], ox, oy, oz);
       const int za = zz - 1, zb = zz;
-      store_pair<STORAGE>(P.out, N, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
-                          col_ok && zb < z1, uint32_t(xw), uint32_t(yw), uint32_t(za),
-                          uint32_t(zb), P.t_out, P.seed);
+      if constexpr (STORAGE == ST_Q16)
+        store_pair_q16(P.out, N, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
+                       col_ok && zb < z1, uint32_t(xw), uint32_t(yw), uint32_t(za), uint32_t(zb),
+                       P.t_out, P.seed);
+      else
+        store_pair_f32(P.out_w, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
+                       col_ok && zb < z1);
     }
     if (FORCE) {
       fprev[0] = fx.y;
@@ -497,7 +531,7 @@ static int choose_zchunk(int64_t tiles_xy, int nz, int64_t resident_blocks) {
 }
 
 template <int STORAGE, bool FORCE>
-static cudaError_t launch_fluid_t(FluidParams& p, cudaStream_t st) {
+static cudaError_t launch_fluid_t(KernelParams<STORAGE>& p, cudaStream_t st) {
   const size_t smem = HaloStage<STORAGE, FORCE>::SMEM;
   static int resident = 0;  // blocks resident on the whole GPU (device 0 of the process)
   if (!resident) {
@@ -535,9 +569,21 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
   // 16-byte chunks need 16-byte aligned rows: nx % 4 == 0 and aligned bases
   p.chunk16 = nx % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
               reinterpret_cast<uintptr_t>(force) % 16 == 0;
-  if (storage == ST_Q16)
-    return force ? launch_fluid_t<ST_Q16, true>(p, st) : launch_fluid_t<ST_Q16, false>(p, st);
-  return force ? launch_fluid_t<ST_F32, true>(p, st) : launch_fluid_t<ST_F32, false>(p, st);
+  if (storage == ST_Q16) {
+    KernelParams<ST_Q16> q;
+    static_cast<FluidParams&>(q) = p;
+    return force ? launch_fluid_t<ST_Q16, true>(q, st) : launch_fluid_t<ST_Q16, false>(q, st);
+  }
+  KernelParams<ST_F32> q;
+  static_cast<FluidParams&>(q) = p;
+  const size_t N = size_t(nx) * ny * nz;
+  for (int k = 0; k < 10; ++k) {
+    q.in_w[k] = static_cast<const uint32_t*>(in) + k * N;
+    q.out_w[k] = static_cast<uint32_t*>(out) + k * N;
+  }
+  for (int k = 0; k < 3; ++k)
+    q.f_w[k] = force ? reinterpret_cast<const uint32_t*>(force) + k * N : nullptr;
+  return force ? launch_fluid_t<ST_F32, true>(q, st) : launch_fluid_t<ST_F32, false>(q, st);
 }
 
 }  // namespace melbm
