@@ -89,10 +89,53 @@ int ensure_staging(melbm_t h, size_t bytes) {
 }
 
 void free_list(melbm_t h) {
+  dev_free(h, h->src_table, size_t(h->L) * 27 * 4);
+  dev_free(h, h->src_cells, size_t(h->S) * 4);
+  dev_free(h, h->src_pop, size_t(h->S) * 27 * 4);
+  h->src_table = h->src_cells = nullptr;
+  h->src_pop = nullptr;
+  h->S = 0;
   dev_free(h, h->list_cell, size_t(h->L) * 4);
   dev_free(h, h->list_word, size_t(h->L) * 4);
   h->list_cell = h->list_word = nullptr;
   h->L = 0;
+}
+
+// The source set of the boundary update (after the list): the cells whose
+// post-collision state a listed cell reads, compacted in ascending order, and
+// the 27 source slots of every listed cell.  Temporaries: mark[N], slot_of[N].
+int build_sources(melbm_t h) {
+  const size_t N = size_t(h->N);
+  uint8_t* mark = nullptr;
+  uint32_t* slot_of = nullptr;
+  int rc = dev_alloc(h, (void**)&mark, N);
+  if (rc) return rc;
+  cudaError_t e = launch_source_setup_mark(h->nx, h->ny, h->nz, h->list_cell, h->list_word, h->L,
+                                           mark, h->cl_counts, h->stream);
+  if (e == cudaSuccess)
+    e = launch_exclusive_scan(h->cl_counts, h->cl_offsets, source_flag_blocks(h->N),
+                              h->cl_total, h->stream);
+  uint32_t S = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&S, h->cl_total, 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && S) {
+    h->S = S;  // before the allocations, so that free_list accounts for them
+    if ((rc = dev_alloc(h, (void**)&slot_of, N * 4)) ||
+        (rc = dev_alloc(h, (void**)&h->src_cells, size_t(S) * 4)) ||
+        (rc = dev_alloc(h, (void**)&h->src_table, size_t(h->L) * 27 * 4)) ||
+        (rc = dev_alloc(h, (void**)&h->src_pop, size_t(S) * 27 * 4))) {
+      dev_free(h, mark, N);
+      dev_free(h, slot_of, slot_of ? N * 4 : 0);
+      return rc;
+    }
+    e = launch_source_setup_fill(h->nx, h->ny, h->nz, h->list_cell, h->list_word, h->L, mark,
+                                 h->cl_offsets, h->src_cells, slot_of, h->src_table, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  dev_free(h, mark, N);
+  if (slot_of) dev_free(h, slot_of, N * 4);
+  if (e != cudaSuccess) return cuda_fail(h, e, "build_sources");
+  return MELBM_OK;
 }
 
 // (Re)build types and the boundary list from the mask and the inflow/outflow flags.
@@ -123,6 +166,7 @@ int reclassify(melbm_t h) {
     h->L = total;
     MELBM_CUDA(h, launch_classify_scatter(h->nx, h->ny, h->nz, h->mask, h->type, h->cl_offsets,
                                           h->list_cell, h->list_word, h->stream));
+    if ((rc = build_sources(h))) return rc;
   }
   return MELBM_OK;
 }
@@ -136,7 +180,8 @@ cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out
                                h->seed, h->stream);
   if (e == cudaSuccess && h->L)
     e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
-                        h->list_word, h->L, h->inflow, t_out, h->seed, h->stream);
+                        h->list_word, h->L, h->src_cells, h->S, h->src_table, h->src_pop,
+                        h->inflow, t_out, h->seed, h->stream);
   if (e == cudaSuccess && h->outflow_on && h->type)
     e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream);
   return e;

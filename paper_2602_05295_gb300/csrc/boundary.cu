@@ -4,7 +4,10 @@
 //     halfway bounce-back for solid links, f_i(x) = f+_{opp(i)}(x) when x - c_i is
 //     solid (in place of the paper's additive triangle correction, which needs a
 //     mesh; recomputing from the input gives the post-streaming moments directly,
-//     with no atomics and no second rounding of the 16-bit state).
+//     with no atomics and no second rounding of the 16-bit state).  The
+//     post-collision populations of every source were evaluated once by phase
+//     A (sources.cu); this kernel gathers, per direction, the one it needs
+//     through the cell's 27 source slots.
 //   * INFLOW: reset to the equilibrium (rho_in, u_in, S = u_in u_in).
 // The outflow pass then copies the stored state of x = nx-2 onto x = nx-1.
 #include "melbm_device.cuh"
@@ -21,23 +24,12 @@ struct BoundaryParams {
   const uint32_t* cells;
   const uint32_t* words;
   int64_t count;
+  const uint32_t* table;  // [27][count] source slots
+  const float* pop;       // [27][S] post-collision populations f+_i / w_i - 1 of the sources
+  int64_t S;
   float in_rho, in_ux, in_uy, in_uz;
   uint32_t t_out, seed;
 };
-
-// f+_i / w_i - 1 from the Hermite moments: the coefficient of P_p P_q P_r is
-// mu_pqr divided by the D1Q3 norms (1, 1/3, 2/9) of each factor (P_2(c) = c^2 - 1/3).
-__device__ __forceinline__ float hermite_eval(const Mom17& A, int cx, int cy, int cz) {
-  const float fx = float(cx), fy = float(cy), fz = float(cz);
-  const float qx = fx * fx - (1.0f / 3.0f), qy = fy * fy - (1.0f / 3.0f),
-              qz = fz * fz - (1.0f / 3.0f);
-  return A.m000 + 3.0f * (A.m100 * fx + A.m010 * fy + A.m001 * fz) +
-         4.5f * (A.m200 * qx + A.m020 * qy + A.m002 * qz) +
-         9.0f * (A.m110 * fx * fy + A.m101 * fx * fz + A.m011 * fy * fz) +
-         13.5f * (A.m210 * qx * fy + A.m120 * fx * qy + A.m201 * qx * fz + A.m102 * fx * qz +
-                  A.m021 * qy * fz + A.m012 * fy * qz) +
-         27.0f * A.m111 * fx * fy * fz;
-}
 
 template <int STORAGE, bool FORCE>
 __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
@@ -63,31 +55,20 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   }
   float m000 = 0.f, m100 = 0.f, m010 = 0.f, m001 = 0.f, m200 = 0.f, m020 = 0.f, m002 = 0.f,
         m110 = 0.f, m101 = 0.f, m011 = 0.f;
-  // post-collision coefficients of the cell itself (used by every bounced link)
   float fx0 = 0.f, fy0 = 0.f, fz0 = 0.f;
   if (FORCE) {
     fx0 = P.force[n];
     fy0 = P.force[N + n];
     fz0 = P.force[2 * N + n];
   }
-  const Mom17 Aself = collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n), P.omega, fx0, fy0, fz0);
+#pragma unroll
   for (int i = 0; i < 27; ++i) {
     const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-    float g;  // (f_i / w_i - 1)
-    if ((word >> i) & 1u) {
-      g = hermite_eval(Aself, -cx, -cy, -cz);  // bounce-back: population opp(i) of x
-    } else {
-      const size_t src = size_t(wrapi(x - cx, nx)) +
-                         size_t(nx) * (size_t(wrapi(y - cy, ny)) + size_t(ny) * wrapi(z - cz, nz));
-      float fx = 0.f, fy = 0.f, fz = 0.f;
-      if (FORCE) {
-        fx = P.force[src];
-        fy = P.force[N + src];
-        fz = P.force[2 * N + src];
-      }
-      const Mom17 A = collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, src), P.omega, fx, fy, fz);
-      g = hermite_eval(A, cx, cy, cz);
-    }
+    // f_i / w_i - 1: population i pulled from x - c_i, or population opp(i) =
+    // 26 - i of x itself (bounce-back) when the link is solid -- the slot then holds x
+    const uint32_t slot = __ldg(P.table + int64_t(i) * P.count + k);
+    const int j = ((word >> i) & 1u) ? 26 - i : i;
+    const float g = __ldg(P.pop + int64_t(j) * P.S + slot);
     const float w = (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *
                     (cz ? (1.0f / 6.0f) : (2.0f / 3.0f));
     const float f = w * g;
@@ -109,9 +90,13 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
 
 cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
                             const float* force, float omega, const uint32_t* cells,
-                            const uint32_t* words, int64_t count, const float inflow[4],
+                            const uint32_t* words, int64_t count, const uint32_t* src_cells,
+                            int64_t S, const uint32_t* table, float* pop, const float inflow[4],
                             uint32_t t_out, uint32_t seed, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
+  cudaError_t e = launch_source_collide(storage, size_t(nx) * ny * nz, in, force, omega, src_cells,
+                                        S, pop, st);
+  if (e != cudaSuccess) return e;
   BoundaryParams p;
   p.nx = nx;
   p.ny = ny;
@@ -123,6 +108,9 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
   p.cells = cells;
   p.words = words;
   p.count = count;
+  p.table = table;
+  p.pop = pop;
+  p.S = S;
   p.in_rho = inflow[0];
   p.in_ux = inflow[1];
   p.in_uy = inflow[2];

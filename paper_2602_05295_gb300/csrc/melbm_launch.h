@@ -11,11 +11,31 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
                          const float* force, float omega, uint32_t t_out, uint32_t seed,
                          cudaStream_t st);
 
-// Boundary kernel over the list: bounce-back recompute and inflow reset, in -> out.
+// Boundary update over the list: phase A collides the S source cells and keeps
+// their 27 populations in pop[27][S] (sources.cu), then the boundary kernel
+// recomputes every listed cell (bounce-back through its 27 source slots in
+// table[27][count], inflow reset), in -> out.
 cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
                             const float* force, float omega, const uint32_t* cells,
-                            const uint32_t* words, int64_t count, const float inflow[4],
+                            const uint32_t* words, int64_t count, const uint32_t* src_cells,
+                            int64_t S, const uint32_t* table, float* pop, const float inflow[4],
                             uint32_t t_out, uint32_t seed, cudaStream_t st);
+
+// Source set of the boundary update (sources.cu).  Setup, after the list is
+// built: mark the sources (mark[N] bytes) and count them per block of
+// source_flag_blocks(N); after an exclusive scan of the counts, fill src_cells
+// (ascending), slot_of[N] and table[27][L].  Per step: phase A.
+int64_t source_flag_blocks(int64_t N);
+cudaError_t launch_source_setup_mark(int nx, int ny, int nz, const uint32_t* cells,
+                                     const uint32_t* words, int64_t L, uint8_t* mark,
+                                     uint32_t* block_counts, cudaStream_t st);
+cudaError_t launch_source_setup_fill(int nx, int ny, int nz, const uint32_t* cells,
+                                     const uint32_t* words, int64_t L, const uint8_t* mark,
+                                     const uint32_t* block_offsets, uint32_t* src_cells,
+                                     uint32_t* slot_of, uint32_t* table, cudaStream_t st);
+cudaError_t launch_source_collide(int storage, size_t N, const void* in, const float* force,
+                                  float omega, const uint32_t* src_cells, int64_t S, float* pop,
+                                  cudaStream_t st);
 
 // Outflow copy on the plane x = nx-1 (cells typed OUTFLOW), in place on buf.
 cudaError_t launch_outflow(int storage, int nx, int ny, int nz, void* buf, const uint8_t* type,
