@@ -253,10 +253,26 @@ def cpu_oracle_run(steps=2, warmup=1, planes=64):
         cur = oracle.step(cur, shape, wl.tau)
     el = time.perf_counter() - t
     cells = nx * ny * planes
-    return {"value": cells * steps / el / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{steps} FP64 oracle steps (after {warmup} warm-up) of a periodic "
-                      f"{nx}x{ny}x{planes} slab of the 256^3 turbulence field ({cells} cells)"}, el
+    out = {"value": cells * steps / el / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+           "kind": "oracle",
+           "sample": f"{steps} FP64 oracle steps (after {warmup} warm-up) of a periodic "
+                     f"{nx}x{ny}x{planes} slab of the 256^3 turbulence field ({cells} cells)"}
+    # the same oracle on one thread, on a thinner slab
+    threads = oracle.num_threads()
+    p1 = 4
+    m1 = oracle.initial_state_from_velocity(W.flat(u[:, :p1]))
+    oracle.set_threads(1)
+    try:
+        m1 = oracle.step(m1, (nx, ny, p1), wl.tau)
+        t1 = time.perf_counter()
+        oracle.step(m1, (nx, ny, p1), wl.tau)
+        el1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(threads)
+    out["single_thread"] = {"value": nx * ny * p1 / el1 / 1e6, "unit": "MLUPS", "cores": 1,
+                            "sample": f"1 FP64 oracle step (after 1 warm-up) of a periodic "
+                                      f"{nx}x{ny}x{p1} slab ({nx * ny * p1} cells)"}
+    return out, el
 
 
 def reference_arm(args):
