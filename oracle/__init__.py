@@ -75,6 +75,13 @@ def lib():
             L.orc_dither.argtypes = [U32, U32, U32, U32, U32, P]
             L.orc_encode.argtypes = [I, I, I, P, U32, U32, I, P]
             L.orc_decode.argtypes = [I64, P, P]
+            L.orc_encode_bits.argtypes = [I, I, I, P, U32, U32, I, I, I, P]
+            L.orc_decode_bits.argtypes = [I64, P, I, I, P]
+            L.orc_codec_constants_bits.argtypes = [I, I, I, P]
+            L.orc_mean_code_over_dither_bits.argtypes = [ctypes.c_float, I, I, I]
+            L.orc_mean_code_over_dither_bits.restype = D
+            L.orc_code_coordinate_bits.argtypes = [ctypes.c_float, I, I, I]
+            L.orc_code_coordinate_bits.restype = D
             L.orc_ranges.argtypes = [P, P]
             L.orc_codec_constants.argtypes = [I, P]
             L.orc_mean_code_over_dither.argtypes = [ctypes.c_float, I]
@@ -235,21 +242,26 @@ def dither(x, y, z, t, seed):
     return d
 
 
-def codec_constants(k):
-    """(qc, step, c, K, b) of component k's 16-bit grid (FP32 values)."""
+# Bit widths (b_rho_u, b_S) of the adaptive allocation (Sec. 6.1); (16, 16) is
+# the uniform 16-bit codec.
+BITS16 = (16, 16)
+
+
+def codec_constants(k, bits=BITS16):
+    """(qc, step, c, K, b) of component k's grid (FP32 values)."""
     out = np.empty(5)
-    lib().orc_codec_constants(int(k), _p(out))
+    lib().orc_codec_constants_bits(int(k), int(bits[0]), int(bits[1]), _p(out))
     return out
 
 
-def mean_code_over_dither(value32, k):
+def mean_code_over_dither(value32, k, bits=BITS16):
     """Expected code of an FP32 codec input over all dither values of component k."""
-    return lib().orc_mean_code_over_dither(float(value32), int(k))
+    return lib().orc_mean_code_over_dither_bits(float(value32), int(k), int(bits[0]), int(bits[1]))
 
 
-def code_coordinate(value32, k):
+def code_coordinate(value32, k, bits=BITS16):
     """Exact position of an FP32 codec input on the code axis (FP64)."""
-    return lib().orc_code_coordinate(float(value32), int(k))
+    return lib().orc_code_coordinate_bits(float(value32), int(k), int(bits[0]), int(bits[1]))
 
 
 def public_to_stored(m):
@@ -286,30 +298,31 @@ def stored_to_public(s):
     return out
 
 
-def encode(stored32, shape, t, seed, deterministic=False):
-    """FP32 stored variables (10, N), component 0 = rho - 1, -> uint16 codes (10, N)."""
+def encode(stored32, shape, t, seed, deterministic=False, bits=BITS16):
+    """FP32 stored variables (10, N), component 0 = rho - 1, -> codes (10, N) of
+    b_rho_u / b_S bits (uint16)."""
     nx, ny, nz = shape
     v = np.ascontiguousarray(stored32, np.float32)
     q = np.empty(v.shape, np.uint16)
-    lib().orc_encode(nx, ny, nz, _p(v), int(t) & 0xFFFFFFFF, int(seed) & 0xFFFFFFFF,
-                     int(deterministic), _p(q))
+    lib().orc_encode_bits(nx, ny, nz, _p(v), int(t) & 0xFFFFFFFF, int(seed) & 0xFFFFFFFF,
+                          int(deterministic), int(bits[0]), int(bits[1]), _p(q))
     return q
 
 
-def decode(q):
+def decode(q, bits=BITS16):
     q = np.ascontiguousarray(q, np.uint16)
     v = np.empty(q.shape, np.float64)
-    lib().orc_decode(q.shape[1], _p(q), _p(v))
+    lib().orc_decode_bits(q.shape[1], _p(q), int(bits[0]), int(bits[1]), _p(v))
     return v
 
 
-def q16_step(codes, shape, tau, t_out, seed, F=None, typ=None, inflow=None):
-    """One step of the 16-bit form: decode, FP64 step, FP32 re-encode with the
+def q16_step(codes, shape, tau, t_out, seed, F=None, typ=None, inflow=None, bits=BITS16):
+    """One step of the quantised form: decode, FP64 step, FP32 re-encode with the
     dither of time index ``t_out``.  Solid cells keep their codes; outflow cells
     take the codes of (nx-2, y, z)."""
-    pub = stored_to_public(decode(codes))
+    pub = stored_to_public(decode(codes, bits))
     new = step(pub, shape, tau, F=F, typ=typ, inflow=inflow)
-    q = encode(stored_for_codec(public_to_stored(new)), shape, t_out, seed)
+    q = encode(stored_for_codec(public_to_stored(new)), shape, t_out, seed, bits=bits)
     if typ is not None:
         solid = typ == SOLID
         q[:, solid] = codes[:, solid]

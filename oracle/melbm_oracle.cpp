@@ -458,35 +458,50 @@ const double QHI[10] = {1.5, 0.4, 0.4, 0.4, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1};
 // constants then only scales the (zero-mean) deviation from the centre, and the
 // floor of w + d is exact, so the rounding stays unbiased (Sec. 5.4 dithering).
 // All constants are the FP32 roundings of their FP64 values.
+// Bit widths of the adaptive allocation (Sec. 6.1, "b_rho_u / b_S"): rho and u
+// (components 0..3) take b_ru bits, rho S^neq (components 4..9) b_s bits; the
+// grid of component k has Q = 2^b - 1 steps.  16/16 is the default.
+struct Bits {
+  int ru = 16, s = 16;
+};
+inline double levels(int k, Bits bits) { return double((1u << (k < 4 ? bits.ru : bits.s)) - 1u); }
+
 struct QGroup {
   double lo, hi, centre;  // range and centre in the shifted variable m'
-  double qc;
+  double qc, Q;           // centre code and number of steps
 };
-inline QGroup qgroup(int k) {
+inline QGroup qgroup(int k, Bits bits) {
   QGroup g;
   const double shift = (k == 0) ? 1.0 : 0.0;
   g.lo = QLO[k] - shift;
   g.hi = QHI[k] - shift;
   g.centre = 0.0;
-  g.qc = std::floor((g.centre - g.lo) * 65535.0 / (g.hi - g.lo) + 0.5);
+  g.Q = levels(k, bits);
+  g.qc = std::floor((g.centre - g.lo) * g.Q / (g.hi - g.lo) + 0.5);
   return g;
 }
-inline float q_step(int k) { QGroup g = qgroup(k); return float((g.hi - g.lo) / 65535.0); }
-inline float q_K(int k) { QGroup g = qgroup(k); return float(65535.0 / (g.hi - g.lo)); }
-inline float q_b(int k) {
-  QGroup g = qgroup(k);
-  return float((g.centre - g.lo) * 65535.0 / (g.hi - g.lo) - g.qc);
+inline float q_step(int k, Bits bits) {
+  QGroup g = qgroup(k, bits);
+  return float((g.hi - g.lo) / g.Q);
 }
-inline float q_c(int k) {
-  QGroup g = qgroup(k);
-  return float(g.lo + g.qc * (g.hi - g.lo) / 65535.0);
+inline float q_K(int k, Bits bits) {
+  QGroup g = qgroup(k, bits);
+  return float(g.Q / (g.hi - g.lo));
+}
+inline float q_b(int k, Bits bits) {
+  QGroup g = qgroup(k, bits);
+  return float((g.centre - g.lo) * g.Q / (g.hi - g.lo) - g.qc);
+}
+inline float q_c(int k, Bits bits) {
+  QGroup g = qgroup(k, bits);
+  return float(g.lo + g.qc * (g.hi - g.lo) / g.Q);
 }
 
 // Encode the shifted value mp (rho - 1 for k = 0) with dither d.
-inline uint16_t encode_one(float mp, int k, float d) {
-  const QGroup g = qgroup(k);
-  float w = std::fma(mp, q_K(k), q_b(k));
-  const float wlo = float(-g.qc), whi = float(65535.0 - g.qc);
+inline uint16_t encode_one(float mp, int k, float d, Bits bits) {
+  const QGroup g = qgroup(k, bits);
+  float w = std::fma(mp, q_K(k, bits), q_b(k, bits));
+  const float wlo = float(-g.qc), whi = float(g.Q - g.qc);
   w = std::fmax(w, wlo);  // fmax/fmin return the other operand for NaN: NaN -> code 0
   w = std::fmin(w, whi);
   const double f = std::floor(double(w) + double(d));  // exact in double
@@ -495,10 +510,10 @@ inline uint16_t encode_one(float mp, int k, float d) {
 
 // Dequantisation: m = c + (q - qc) step, returned for the unshifted variable
 // (rho for k = 0), in FP64 from the FP32 grid constants.
-inline double decode_one(uint16_t q, int k) {
-  const QGroup g = qgroup(k);
+inline double decode_one(uint16_t q, int k, Bits bits) {
+  const QGroup g = qgroup(k, bits);
   const double shift = (k == 0) ? 1.0 : 0.0;
-  return shift + double(q_c(k)) + (double(q) - g.qc) * double(q_step(k));
+  return shift + double(q_c(k, bits)) + (double(q) - g.qc) * double(q_step(k, bits));
 }
 
 }  // namespace
@@ -748,12 +763,13 @@ void orc_dither(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t seed, f
 }
 
 // Encode stored variables (FP32, component-major 10 x N; component 0 is
-// rho - 1) into 16-bit codes.  deterministic != 0 uses d = 1/2 (round to nearest)
-// for every component.
-void orc_encode(int nx, int ny, int nz, const float* v, uint32_t t, uint32_t seed, int deterministic,
-                uint16_t* q) {
+// rho - 1) into codes of b_ru / b_s bits.  deterministic != 0 uses d = 1/2 (round
+// to nearest) for every component.
+void orc_encode_bits(int nx, int ny, int nz, const float* v, uint32_t t, uint32_t seed,
+                     int deterministic, int b_ru, int b_s, uint16_t* q) {
   Grid g{nx, ny, nz};
   const int64_t N = g.N();
+  const Bits bits{b_ru, b_s};
 #pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < N; ++n) {
     float d[10];
@@ -763,30 +779,38 @@ void orc_encode(int nx, int ny, int nz, const float* v, uint32_t t, uint32_t see
       const uint32_t x = uint32_t(n % nx), y = uint32_t((n / nx) % ny), z = uint32_t(n / (int64_t(nx) * ny));
       dither10(x, y, z, t, seed, d);
     }
-    for (int k = 0; k < 10; ++k) q[k * N + n] = encode_one(v[k * N + n], k, d[k]);
+    for (int k = 0; k < 10; ++k) q[k * N + n] = encode_one(v[k * N + n], k, d[k], bits);
   }
+}
+void orc_encode(int nx, int ny, int nz, const float* v, uint32_t t, uint32_t seed, int deterministic,
+                uint16_t* q) {
+  orc_encode_bits(nx, ny, nz, v, t, seed, deterministic, 16, 16, q);
 }
 
 // Mean code of the FP32 value mp (rho - 1 for k = 0) over every dither field
 // value of component k (the expectation of the stochastic rounding).
-double orc_mean_code_over_dither(float mp, int k) {
+double orc_mean_code_over_dither_bits(float mp, int k, int b_ru, int b_s) {
   const uint32_t n = 1u << dither_bits(k);
   double s = 0.0;
-  for (uint32_t f = 0; f < n; ++f) s += encode_one(mp, k, dither_of_field(k, f));
+  for (uint32_t f = 0; f < n; ++f) s += encode_one(mp, k, dither_of_field(k, f), Bits{b_ru, b_s});
   return s / double(n);
 }
+double orc_mean_code_over_dither(float mp, int k) { return orc_mean_code_over_dither_bits(mp, k, 16, 16); }
 
 // Exact code-space coordinate (m' - c)/step + qc of an FP32 value, in FP64.
-double orc_code_coordinate(float mp, int k) {
-  const QGroup g = qgroup(k);
-  return (double(mp) - (g.lo + g.qc * (g.hi - g.lo) / 65535.0)) * 65535.0 / (g.hi - g.lo) + g.qc;
+double orc_code_coordinate_bits(float mp, int k, int b_ru, int b_s) {
+  const QGroup g = qgroup(k, Bits{b_ru, b_s});
+  return (double(mp) - (g.lo + g.qc * (g.hi - g.lo) / g.Q)) * g.Q / (g.hi - g.lo) + g.qc;
 }
+double orc_code_coordinate(float mp, int k) { return orc_code_coordinate_bits(mp, k, 16, 16); }
 
-void orc_decode(int64_t N, const uint16_t* q, double* v) {
+void orc_decode_bits(int64_t N, const uint16_t* q, int b_ru, int b_s, double* v) {
+  const Bits bits{b_ru, b_s};
 #pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < N; ++n)
-    for (int k = 0; k < 10; ++k) v[k * N + n] = decode_one(q[k * N + n], k);
+    for (int k = 0; k < 10; ++k) v[k * N + n] = decode_one(q[k * N + n], k, bits);
 }
+void orc_decode(int64_t N, const uint16_t* q, double* v) { orc_decode_bits(N, q, 16, 16, v); }
 
 void orc_ranges(double* lo, double* hi) {
   for (int k = 0; k < 10; ++k) {
@@ -797,12 +821,14 @@ void orc_ranges(double* lo, double* hi) {
 
 // Grid constants of component k: centre code, FP32 step, FP32 value of the
 // centre code (shifted variable), K and b of the encoding.
-void orc_codec_constants(int k, double* out /*5*/) {
-  out[0] = qgroup(k).qc;
-  out[1] = q_step(k);
-  out[2] = q_c(k);
-  out[3] = q_K(k);
-  out[4] = q_b(k);
+void orc_codec_constants_bits(int k, int b_ru, int b_s, double* out /*5*/) {
+  const Bits bits{b_ru, b_s};
+  out[0] = qgroup(k, bits).qc;
+  out[1] = q_step(k, bits);
+  out[2] = q_c(k, bits);
+  out[3] = q_K(k, bits);
+  out[4] = q_b(k, bits);
 }
+void orc_codec_constants(int k, double* out /*5*/) { orc_codec_constants_bits(k, 16, 16, out); }
 
 }  // extern "C"

@@ -501,6 +501,76 @@ def test_stochastic_rounding_is_unbiased_over_the_dither(orc):
         assert abs(np.mean(d)) < 6e-5, (k, np.mean(d))
 
 
+# Adaptive bit allocation (Sec. 6.1): rho and u take b_rho_u bits, rho S^neq b_S
+# bits, each on the grid of Sec. 5.4 with 2^b - 1 steps.
+BIT_CONFIGS = [(16, 15), (15, 14), (14, 13), (13, 12), (12, 11)]
+
+
+@pytest.mark.parametrize("bits", BIT_CONFIGS)
+def test_codec_bits_grid_endpoints_and_round_trip(orc, bits):
+    """Dequantisation m_min + q (m_max - m_min)/(2^b - 1) for q = 0 .. 2^b - 1 with b
+    per group; every code survives decode -> FP32 -> deterministic encode, and the
+    centre code is the one nearest the centre of the values."""
+    lo, hi = orc.ranges()
+    Q = np.array([2 ** bits[0] - 1] * 4 + [2 ** bits[1] - 1] * 6, np.int64)
+    for k in (0, 1, 4):
+        qc, step, c, K, b = orc.codec_constants(k, bits)
+        centre = 1.0 if k == 0 else 0.0
+        assert qc == np.floor((centre - lo[k]) * Q[k] / (hi[k] - lo[k]) + 0.5)
+        assert abs(step - (hi[k] - lo[k]) / Q[k]) <= 1e-7 * step
+    n = int(Q.max()) + 1
+    codes = np.tile(np.arange(n, dtype=np.int64), (10, 1))
+    codes = np.minimum(codes, Q[:, None]).astype(np.uint16)
+    dec = orc.decode(codes, bits)
+    assert np.abs(dec[:, 0] - lo).max() < 1e-6 and np.abs(dec[np.arange(10), Q] - hi).max() < 1e-6
+    step = (hi - lo) / Q
+    d = np.diff(dec, axis=1)
+    for k in range(10):
+        assert np.abs(d[k, :Q[k]] - step[k]).max() < 1e-6 * step[k]
+    enc = orc.encode(orc.stored_for_codec(dec), (n, 1, 1), 0, 0, deterministic=True, bits=bits)
+    assert np.array_equal(enc, codes)
+
+
+@pytest.mark.parametrize("bits", BIT_CONFIGS)
+def test_codec_bits_error_bounds_saturation_and_unbiased_rounding(orc, bits):
+    rng = np.random.default_rng(12)
+    lo, hi = orc.ranges()
+    Q = np.array([2 ** bits[0] - 1] * 4 + [2 ** bits[1] - 1] * 6, np.float64)
+    step = (hi - lo) / Q
+    v = lo[:, None] + (hi - lo)[:, None] * rng.uniform(size=(10, 4096))
+    v32 = orc.stored_for_codec(v)
+    ref = v32.astype(np.float64)
+    ref[0] += 1.0
+    det = orc.decode(orc.encode(v32, (16, 16, 16), 0, 0, deterministic=True, bits=bits), bits)
+    sto = orc.decode(orc.encode(v32, (16, 16, 16), 5, 99, bits=bits), bits)
+    slack = 4e-3 * step[:, None]
+    assert np.all(np.abs(det - ref) <= 0.5 * step[:, None] + slack)
+    assert np.all(np.abs(sto - ref) < step[:, None] + slack)
+    out = np.zeros((10, 3), np.float32)
+    out[:, 0] = (lo - 1.0) - np.array([1.0] + [0.0] * 9)
+    out[:, 1] = (hi + 1.0) - np.array([1.0] + [0.0] * 9)
+    out[:, 2] = np.nan
+    q = orc.encode(out, (3, 1, 1), 0, 0, bits=bits)
+    assert np.all(q[:, 0] == 0) and np.all(q[:, 1] == Q) and np.all(q[:, 2] == 0)
+    # expected code over every dither value = the exact code coordinate
+    for k, spread in ((0, 0.01), (1, 0.05), (4, 0.005)):
+        for val in (spread * rng.standard_normal(50)).astype(np.float32):
+            w = orc.code_coordinate(val, k, bits) - orc.codec_constants(k, bits)[0]
+            bound = 1.0 / 8192 + float(np.spacing(np.float32(abs(w)))) / 2 + abs(w) * 2.0 ** -24
+            dev = orc.mean_code_over_dither(val, k, bits) - orc.code_coordinate(val, k, bits)
+            assert abs(dev) <= bound, (bits, k, val, dev)
+
+
+def test_codec_bits_16_16_is_the_uniform_codec(orc):
+    rng = np.random.default_rng(13)
+    lo, hi = orc.ranges()
+    v32 = orc.stored_for_codec(lo[:, None] + (hi - lo)[:, None] * rng.uniform(size=(10, 512)))
+    a = orc.encode(v32, (8, 8, 8), 3, 9)
+    b = orc.encode(v32, (8, 8, 8), 3, 9, bits=(16, 16))
+    assert np.array_equal(a, b)
+    assert np.array_equal(orc.decode(a), orc.decode(a, (16, 16)))
+
+
 def test_repeated_requantisation_conserves_mass_and_momentum(orc):
     """1000 decode/encode cycles of a field fluctuating about rho = 1, u = 0 (the
     round trip a stored state makes every step) leave the mean density and
