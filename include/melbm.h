@@ -184,6 +184,27 @@ MELBM_API int melbm_q16_decode(const uint32_t* words, int64_t N, float* stored, 
 MELBM_API int melbm_reduce_state_noalloc(const void* state, int storage, int64_t N,
                                          const uint8_t* type, double* out, void* cuda_stream);
 
+/* Adaptive bit allocation (Sec. 6.2.2, "b_rho_u / b_S"): rho and u are stored
+ * with bits_rho_u bits and rho S^neq with bits_S bits, each on the Sec. 5.4 grid
+ * m_min + q (m_max - m_min)/(2^b - 1) (the same centre-anchored FP32 evaluation
+ * and dither as the 16-bit codec), still two codes per 32-bit word.  Only for
+ * MELBM_Q16 handles; 8 <= bits <= 16 each (else MELBM_EINVAL); 16/16 is the
+ * default.  The current state is re-encoded (decoded on the old grids, encoded
+ * on the new ones with the dither of the current time index); synchronises.
+ * Every later step, set_state, get_moments and reduce use the new grids
+ * (reduce counts codes on 0 or 2^b - 1).  Checkpoints of
+ * melbm_forward_checkpointed and melbm_reduce_state_noalloc keep 16/16. */
+MELBM_API int melbm_set_bits(melbm_t h, int bits_rho_u, int bits_S);
+
+/* The codec of melbm_q16_encode / melbm_q16_decode with bit widths
+ * bits_rho_u / bits_S (8..16 each, else MELBM_EINVAL): codes 0 .. 2^b - 1 in the
+ * same word layout.  Device pointers; cuda_stream may be NULL. */
+MELBM_API int melbm_codec_encode(const float* stored, int nx, int ny, int nz, uint32_t t,
+                                 uint32_t seed, int deterministic, int bits_rho_u, int bits_S,
+                                 uint32_t* words, void* cuda_stream);
+MELBM_API int melbm_codec_decode(const uint32_t* words, int64_t N, int bits_rho_u, int bits_S,
+                                 float* stored, void* cuda_stream);
+
 /* Message of the last failure of h (or of the last handle-less call if h is
  * NULL).  Valid until the next call on the same handle. */
 MELBM_API const char* melbm_last_error(melbm_t h);

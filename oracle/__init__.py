@@ -242,7 +242,7 @@ def dither(x, y, z, t, seed):
     return d
 
 
-# Bit widths (b_rho_u, b_S) of the adaptive allocation (Sec. 6.1); (16, 16) is
+# Bit widths (b_rho_u, b_S) of the adaptive allocation (Sec. 6.2.2); (16, 16) is
 # the uniform 16-bit codec.
 BITS16 = (16, 16)
 

@@ -458,7 +458,7 @@ const double QHI[10] = {1.5, 0.4, 0.4, 0.4, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1};
 // constants then only scales the (zero-mean) deviation from the centre, and the
 // floor of w + d is exact, so the rounding stays unbiased (Sec. 5.4 dithering).
 // All constants are the FP32 roundings of their FP64 values.
-// Bit widths of the adaptive allocation (Sec. 6.1, "b_rho_u / b_S"): rho and u
+// Bit widths of the adaptive allocation (Sec. 6.2.2, "b_rho_u / b_S"): rho and u
 // (components 0..3) take b_ru bits, rho S^neq (components 4..9) b_s bits; the
 // grid of component k has Q = 2^b - 1 steps.  16/16 is the default.
 struct Bits {

@@ -6,7 +6,9 @@ For every workload: throughput (MLUPS over all cells, and over fluid cells where
 solids exist), device memory of the 16-bit and FP32 forms, and a check that needs
 no reference solution: the Taylor-Green decay rate (tgv32), total-mass drift
 (FP64 reductions), boundary-list size and solid fraction (channel512, large1000),
-gradient norms and timing of the checkpointed adjoint (adjoint128).
+gradient norms and timing of the checkpointed adjoint (adjoint128), and the
+error-vs-bits sweep of the adaptive bit allocation on the turbulence field
+(bits_sweep).
 Timing uses CUDA events on the simulator's stream after warm-up steps.
 """
 from __future__ import annotations
@@ -164,8 +166,44 @@ def run_adjoint128(steps):
             "grad_F_norm": float(F.grad.norm().item()), "memory_bytes": sim.memory_bytes()}
 
 
+def run_bits_sweep(steps):
+    """Adaptive bit allocation b_rho_u / b_S (Sec. 6.2.2) on the 256^3 turbulence
+    field: velocity error against the FP32-storage run after 100 steps (relative
+    l2 and max over the field), mass drift, throughput, and the packed-equivalent
+    bits per cell 4 b_rho_u + 6 b_S (the codes are kept in 16-bit halves)."""
+    wl = W.TURB256
+    rho, u = _state_from_velocity(W.flat(W.random_phase_field(wl.shape, 0.08)))
+    T = 100
+
+    def run(storage, bits=None):
+        sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602)
+        if bits:
+            sim.set_bits(*bits)
+        sim.set_state(rho, u)
+        M0, _ = sim.reduce()
+        sim.step(T)
+        M1, _ = sim.reduce()
+        _, uu, _ = sim.get_moments()
+        ms = _timed_steps(sim, steps)
+        sim.close()
+        return uu.double(), (M1 - M0) / M0, ms
+
+    uref, _, ms_f = run("f32")
+    out = [{"workload": "bits_sweep", "config": "fp32", "bits_per_cell": 320, "MLUPS": wl.cells / ms_f / 1e3}]
+    nref = torch.linalg.vector_norm(uref).item()
+    for bits in ((16, 16), (16, 15), (15, 14), (14, 13), (13, 12), (12, 11)):
+        uq, drift, ms = run("q16", bits)
+        d = uq - uref
+        out.append({"workload": "bits_sweep", "config": f"{bits[0]}/{bits[1]}",
+                    "bits_per_cell": 4 * bits[0] + 6 * bits[1], "steps": T,
+                    "u_rel_l2_vs_fp32": torch.linalg.vector_norm(d).item() / nref,
+                    "u_max_vs_fp32": d.abs().max().item() / uref.abs().max().item(),
+                    "mass_drift": drift, "MLUPS": wl.cells / ms / 1e3})
+    return out
+
+
 RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256, "channel512": run_channel512,
-           "large1000": run_large1000, "adjoint128": run_adjoint128}
+           "large1000": run_large1000, "adjoint128": run_adjoint128, "bits_sweep": run_bits_sweep}
 
 
 def main():

@@ -177,11 +177,11 @@ namespace melbm {
 cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out) {
   const float omega = 1.0f / h->tau;
   cudaError_t e = launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                               h->seed, h->stream);
+                               h->seed, h->grids, h->stream);
   if (e == cudaSuccess && h->L)
     e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
                         h->list_word, h->L, h->src_cells, h->S, h->src_table, h->src_pop,
-                        h->inflow, t_out, h->seed, h->stream);
+                        h->inflow, t_out, h->seed, h->grids, h->stream);
   if (e == cudaSuccess && h->outflow_on && h->type)
     e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream);
   return e;
@@ -222,7 +222,7 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
     return rc;
   }
   // rest state (rho = 1, u = 0, S = 0) at time index 0
-  cudaError_t e = launch_rest_state(storage, nx, ny, nz, h->buf[0], 0, h->stream);
+  cudaError_t e = launch_rest_state(storage, nx, ny, nz, h->buf[0], 0, h->grids, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     cuda_fail(h, e, "melbm_create: initialising the rest state");
@@ -284,7 +284,7 @@ int melbm_set_state(melbm_t h, const float* rho, const float* u, const float* S)
     ss = S ? st + 4 * N : nullptr;
   }
   MELBM_CUDA(h, launch_set_state(h->storage, h->nx, h->ny, h->nz, r, uu, ss, h->buf[h->cur], 0,
-                                 h->seed, 0, h->stream));
+                                 h->seed, 0, h->grids, h->stream));
   if (!dev) MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->t = 0;
   h->poisoned = false;
@@ -297,14 +297,15 @@ int melbm_get_moments(melbm_t h, float* rho, float* u, float* S) {
   const size_t N = size_t(h->N);
   const bool dev = (!rho || is_device_ptr(rho)) && (!u || is_device_ptr(u)) && (!S || is_device_ptr(S));
   if (dev) {
-    MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], rho, u, S, h->stream));
+    MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], rho, u, S, h->grids,
+                                     h->stream));
     return MELBM_OK;
   }
   int rc = ensure_staging(h, N * 40);
   if (rc) return rc;
   float* st = static_cast<float*>(h->staging);
   MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], st, st + N, st + 4 * N,
-                                   h->stream));
+                                   h->grids, h->stream));
   const cudaMemcpyKind k = cudaMemcpyDefault;
   if (rho) MELBM_CUDA(h, cudaMemcpyAsync(rho, st, N * 4, k, h->stream));
   if (u) MELBM_CUDA(h, cudaMemcpyAsync(u, st + N, N * 12, k, h->stream));
@@ -401,7 +402,7 @@ int melbm_step(melbm_t h, int n) {
 int melbm_reduce(melbm_t h, double* mass, double* ke) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_reduce: NULL handle");
   MELBM_CUDA(h, launch_reduce(h->storage, h->N, h->buf[h->cur], h->type, h->red_partials,
-                              h->red_out, h->stream));
+                              h->red_out, h->grids, h->stream));
   double out[3];
   MELBM_CUDA(h, cudaMemcpyAsync(out, h->red_out, sizeof out, cudaMemcpyDeviceToHost, h->stream));
   MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -458,9 +459,62 @@ int melbm_q16_encode(const float* stored, int nx, int ny, int nz, uint32_t t, ui
   if (!stored || !words) return fail(nullptr, MELBM_EINVAL, "melbm_q16_encode: NULL pointer");
   if (nx < 1 || ny < 1 || nz < 1 || int64_t(nx) * ny * nz >= (int64_t(1) << 31))
     return fail(nullptr, MELBM_EINVAL, "melbm_q16_encode: bad grid");
-  cudaError_t e = launch_q16_encode(stored, nx, ny, nz, t, seed, deterministic,
-                                    words, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_q16_encode(stored, nx, ny, nz, t, seed, deterministic, words,
+                                    make_qgrids(16, 16), static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "melbm_q16_encode");
+  return MELBM_OK;
+}
+
+int melbm_codec_encode(const float* stored, int nx, int ny, int nz, uint32_t t, uint32_t seed,
+                       int deterministic, int bits_rho_u, int bits_S, uint32_t* words,
+                       void* stream) {
+  if (!stored || !words) return fail(nullptr, MELBM_EINVAL, "melbm_codec_encode: NULL pointer");
+  if (nx < 1 || ny < 1 || nz < 1 || int64_t(nx) * ny * nz >= (int64_t(1) << 31))
+    return fail(nullptr, MELBM_EINVAL, "melbm_codec_encode: bad grid");
+  if (bits_rho_u < 8 || bits_rho_u > 16 || bits_S < 8 || bits_S > 16)
+    return fail(nullptr, MELBM_EINVAL, "melbm_codec_encode: bit widths %d/%d outside 8..16",
+                bits_rho_u, bits_S);
+  cudaError_t e = launch_q16_encode(stored, nx, ny, nz, t, seed, deterministic, words,
+                                    make_qgrids(bits_rho_u, bits_S),
+                                    static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "melbm_codec_encode");
+  return MELBM_OK;
+}
+
+int melbm_codec_decode(const uint32_t* words, int64_t N, int bits_rho_u, int bits_S, float* stored,
+                       void* stream) {
+  if (!stored || !words || N < 0 || N >= (int64_t(1) << 31))
+    return fail(nullptr, MELBM_EINVAL, "melbm_codec_decode: bad argument");
+  if (bits_rho_u < 8 || bits_rho_u > 16 || bits_S < 8 || bits_S > 16)
+    return fail(nullptr, MELBM_EINVAL, "melbm_codec_decode: bit widths %d/%d outside 8..16",
+                bits_rho_u, bits_S);
+  if (N == 0) return MELBM_OK;
+  cudaError_t e = launch_q16_decode(words, N, stored, make_qgrids(bits_rho_u, bits_S),
+                                    static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "melbm_codec_decode");
+  return MELBM_OK;
+}
+
+int melbm_set_bits(melbm_t h, int bits_rho_u, int bits_S) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_bits: NULL handle");
+  if (h->storage != MELBM_Q16)
+    return fail(h, MELBM_EINVAL, "melbm_set_bits: only the quantised storage has bit widths");
+  if (bits_rho_u < 8 || bits_rho_u > 16 || bits_S < 8 || bits_S > 16)
+    return fail(h, MELBM_EINVAL, "melbm_set_bits: bit widths %d/%d outside 8..16", bits_rho_u,
+                bits_S);
+  if (h->grids.bits_ru == bits_rho_u && h->grids.bits_s == bits_S) return MELBM_OK;
+  // re-encode the current state: decode on the old grids, encode on the new ones
+  // (dither of the current time index)
+  const size_t N = size_t(h->N);
+  int rc = ensure_staging(h, N * 40);
+  if (rc) return rc;
+  float* st = static_cast<float*>(h->staging);
+  MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], st, st + N, st + 4 * N,
+                                   h->grids, h->stream));
+  h->grids = make_qgrids(bits_rho_u, bits_S);
+  MELBM_CUDA(h, launch_set_state(h->storage, h->nx, h->ny, h->nz, st, st + N, st + 4 * N,
+                                 h->buf[h->cur], uint32_t(h->t), h->seed, 0, h->grids, h->stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return MELBM_OK;
 }
 
@@ -468,7 +522,8 @@ int melbm_q16_decode(const uint32_t* words, int64_t N, float* stored, void* stre
   if (!stored || !words || N < 0 || N >= (int64_t(1) << 31))
     return fail(nullptr, MELBM_EINVAL, "melbm_q16_decode: bad argument");
   if (N == 0) return MELBM_OK;
-  cudaError_t e = launch_q16_decode(words, N, stored, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_q16_decode(words, N, stored, make_qgrids(16, 16),
+                                    static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "melbm_q16_decode");
   return MELBM_OK;
 }

@@ -29,6 +29,7 @@ struct BoundaryParams {
   int64_t S;
   float in_rho, in_ux, in_uy, in_uz;
   uint32_t t_out, seed;
+  QGrids q;
 };
 
 template <int STORAGE, bool FORCE>
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
     s.uy = P.in_uy;
     s.uz = P.in_uz;
     s.nxx = s.nyy = s.nzz = s.nxy = s.nxz = s.nyz = 0.f;
-    store_stored<STORAGE>(P.out, N, n, s, x, y, z, P.t_out, P.seed);
+    store_stored<STORAGE>(P.out, N, n, s, x, y, z, P.t_out, P.seed, false, P.q);
     return;
   }
   float m000 = 0.f, m100 = 0.f, m010 = 0.f, m001 = 0.f, m200 = 0.f, m020 = 0.f, m002 = 0.f,
@@ -85,17 +86,17 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   }
   const Stored o = finish_moments<FORCE>(m000, m100, m010, m001, m200, m020, m002, m110, m101,
                                          m011, fx0, fy0, fz0);
-  store_stored<STORAGE>(P.out, N, n, o, x, y, z, P.t_out, P.seed);
+  store_stored<STORAGE>(P.out, N, n, o, x, y, z, P.t_out, P.seed, false, P.q);
 }
 
 cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
                             const float* force, float omega, const uint32_t* cells,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
                             int64_t S, const uint32_t* table, float* pop, const float inflow[4],
-                            uint32_t t_out, uint32_t seed, cudaStream_t st) {
+                            uint32_t t_out, uint32_t seed, const QGrids& q, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   cudaError_t e = launch_source_collide(storage, size_t(nx) * ny * nz, in, force, omega, src_cells,
-                                        S, pop, st);
+                                        S, pop, q, st);
   if (e != cudaSuccess) return e;
   BoundaryParams p;
   p.nx = nx;
@@ -117,6 +118,7 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
   p.in_uz = inflow[3];
   p.t_out = t_out;
   p.seed = seed;
+  p.q = q;
   const unsigned blocks = unsigned((count + 127) / 128);
   if (storage == ST_Q16) {
     if (force) boundary_kernel<ST_Q16, true><<<blocks, 128, 0, st>>>(p);

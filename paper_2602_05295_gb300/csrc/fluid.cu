@@ -35,6 +35,7 @@
 //   * the next pair's loads are issued before the current pair is processed.
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
@@ -87,12 +88,27 @@ struct FluidParams {
   int chunk16;  // FP32 storage: 16-byte aligned rows, so the halo gather copies chunks
 };
 
+template <int STORAGE, bool RT> struct KernelParams;
+// the grid constants of the RT kernel (nullptr for the others)
+template <class KP>
+__device__ __forceinline__ const QGrids* grids_of(const KP& p) {
+  if constexpr (std::is_same_v<KP, KernelParams<ST_Q16, true>>)
+    return &p.q;
+  else
+    return nullptr;
+}
+
 // Kernel parameters per storage: the FP32 kernel also gets per-word plane
-// pointers of in / out and of the force components.
-template <int STORAGE>
+// pointers of in / out and of the force components; the quantised kernel with
+// bit widths other than 16/16 (RT) gets the grid constants.
+template <int STORAGE, bool RT>
 struct KernelParams : FluidParams {};
 template <>
-struct KernelParams<ST_F32> : FluidParams {
+struct KernelParams<ST_Q16, true> : FluidParams {
+  QGrids q;
+};
+template <>
+struct KernelParams<ST_F32, false> : FluidParams {
   const uint32_t* in_w[10];
   uint32_t* out_w[10];
   const uint32_t* f_w[3];
@@ -140,6 +156,20 @@ __device__ __forceinline__ StoredT<float2> decode_pair(const RawPair<ST_Q16>& r)
   s.nyz = q_decode<2>(make_float2(q_hi_magic(r.a[4]), q_hi_magic(r.b[4])));
   return s;
 }
+__device__ __forceinline__ StoredT<float2> decode_pair(const RawPair<ST_Q16>& r, const QGrids& q) {
+  StoredT<float2> s;
+  s.drho = qg_decode(q.g[0], make_float2(q_lo_magic(r.a[0]), q_lo_magic(r.b[0])));
+  s.ux = qg_decode(q.g[1], make_float2(q_hi_magic(r.a[0]), q_hi_magic(r.b[0])));
+  s.uy = qg_decode(q.g[1], make_float2(q_lo_magic(r.a[1]), q_lo_magic(r.b[1])));
+  s.uz = qg_decode(q.g[1], make_float2(q_hi_magic(r.a[1]), q_hi_magic(r.b[1])));
+  s.nxx = qg_decode(q.g[2], make_float2(q_lo_magic(r.a[2]), q_lo_magic(r.b[2])));
+  s.nyy = qg_decode(q.g[2], make_float2(q_hi_magic(r.a[2]), q_hi_magic(r.b[2])));
+  s.nzz = qg_decode(q.g[2], make_float2(q_lo_magic(r.a[3]), q_lo_magic(r.b[3])));
+  s.nxy = qg_decode(q.g[2], make_float2(q_hi_magic(r.a[3]), q_hi_magic(r.b[3])));
+  s.nxz = qg_decode(q.g[2], make_float2(q_lo_magic(r.a[4]), q_lo_magic(r.b[4])));
+  s.nyz = qg_decode(q.g[2], make_float2(q_hi_magic(r.a[4]), q_hi_magic(r.b[4])));
+  return s;
+}
 __device__ __forceinline__ StoredT<float2> decode_pair(const RawPair<ST_F32>& r) {
   StoredT<float2> s;
   s.drho = make_float2(r.a[0], r.b[0]);
@@ -171,21 +201,31 @@ __device__ __forceinline__ void store_pair_f32(OutPlanes w, size_t na, size_t nb
   }
 }
 
+template <bool RT>
 __device__ __forceinline__ void store_pair_q16(void* buf, size_t N, size_t na, size_t nb,
                                                const StoredT<float2>& o, bool sa, bool sb, uint32_t x,
                                                uint32_t y, uint32_t za, uint32_t zb, uint32_t t,
-                                               uint32_t seed) {
+                                               uint32_t seed, const QGrids* q) {
   const DitherBits ha = pcg4d(x, y, za, t, seed);
   const DitherBits hb = pcg4d(x, y, zb, t, seed);
   float2 d[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k)
     d[k] = dither_value(make_float2(dither_magic(ha, k), dither_magic(hb, k)), k);
-  const uint2 e0 = q_encode_codes<0>(o.drho, d[0]), e1 = q_encode_codes<1>(o.ux, d[1]);
-  const uint2 e2 = q_encode_codes<1>(o.uy, d[2]), e3 = q_encode_codes<1>(o.uz, d[3]);
-  const uint2 e4 = q_encode_codes<2>(o.nxx, d[4]), e5 = q_encode_codes<2>(o.nyy, d[5]);
-  const uint2 e6 = q_encode_codes<2>(o.nzz, d[6]), e7 = q_encode_codes<2>(o.nxy, d[7]);
-  const uint2 e8 = q_encode_codes<2>(o.nxz, d[8]), e9 = q_encode_codes<2>(o.nyz, d[9]);
+  uint2 e0, e1, e2, e3, e4, e5, e6, e7, e8, e9;
+  if constexpr (RT) {
+    e0 = qg_encode_codes(q->g[0], o.drho, d[0]), e1 = qg_encode_codes(q->g[1], o.ux, d[1]);
+    e2 = qg_encode_codes(q->g[1], o.uy, d[2]), e3 = qg_encode_codes(q->g[1], o.uz, d[3]);
+    e4 = qg_encode_codes(q->g[2], o.nxx, d[4]), e5 = qg_encode_codes(q->g[2], o.nyy, d[5]);
+    e6 = qg_encode_codes(q->g[2], o.nzz, d[6]), e7 = qg_encode_codes(q->g[2], o.nxy, d[7]);
+    e8 = qg_encode_codes(q->g[2], o.nxz, d[8]), e9 = qg_encode_codes(q->g[2], o.nyz, d[9]);
+  } else {
+    e0 = q_encode_codes<0>(o.drho, d[0]), e1 = q_encode_codes<1>(o.ux, d[1]);
+    e2 = q_encode_codes<1>(o.uy, d[2]), e3 = q_encode_codes<1>(o.uz, d[3]);
+    e4 = q_encode_codes<2>(o.nxx, d[4]), e5 = q_encode_codes<2>(o.nyy, d[5]);
+    e6 = q_encode_codes<2>(o.nzz, d[6]), e7 = q_encode_codes<2>(o.nxy, d[7]);
+    e8 = q_encode_codes<2>(o.nxz, d[8]), e9 = q_encode_codes<2>(o.nyz, d[9]);
+  }
   uint32_t* p = static_cast<uint32_t*>(buf);
   if (sa) {
     p[na] = q_pack(e0.x, e1.x);
@@ -238,9 +278,13 @@ __device__ __forceinline__ float2 shfl_idx2(float2 v, int src) {
 
 // ----------------------------------------------------------------- kernel
 // The y-pass slices are indexed s = 3 p + r' (p: x-order, r': input z-order).
-template <int STORAGE, bool FORCE>
-__global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelParams<STORAGE> P) {
+template <int STORAGE, bool FORCE, bool RT>
+__global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelParams<STORAGE, RT> P) {
   using HS = HaloStage<STORAGE, FORCE>;
+  auto decode = [&](const RawPair<STORAGE>& r) {
+    if constexpr (STORAGE == ST_Q16 && RT) return decode_pair(r, P.q);
+    else return decode_pair(r);
+  };
   extern __shared__ float2 sm2[];
   float2* const hb = sm2 + 2 * SM_BUF;  // halo populations [buffer][row][slice][side]
   uint32_t* const stg = reinterpret_cast<uint32_t*>(hb + 2 * HALO_BUF);  // warp 0 staging
@@ -333,7 +377,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
       set_word<STORAGE>(hr, 0, w, d[(2 * w) * 32 * HS::CHUNK]);
       set_word<STORAGE>(hr, 1, w, d[(2 * w + 1) * 32 * HS::CHUNK]);
     }
-    const StoredT<float2> hs = decode_pair(hr);
+    const StoredT<float2> hs = decode(hr);
     float2 hfx = make_float2(0.f, 0.f), hfy = hfx, hfz = hfx;
     if (FORCE) {
       const float* sf = reinterpret_cast<const float*>(d) + 2 * HS::W * 32 * HS::CHUNK;
@@ -379,7 +423,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     const bool halo_next = halo_warp && zz + 2 <= z1;
     const bool halo_ahead = halo_warp && zz + 4 <= z1;
     if (halo_ahead) halo_issue(zz + 4, parity);
-    const StoredT<float2> s = decode_pair(raw);
+    const StoredT<float2> s = decode(raw);
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
     if (FORCE) {
       const size_t na = col + plane * wz(zz), nb = col + plane * wz(zz + 1);
@@ -498,9 +542,9 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
                                 M[4][0], M[1][1], M[2][1], ox, oy, oz);
       const int za = zz - 1, zb = zz;
       if constexpr (STORAGE == ST_Q16)
-        store_pair_q16(P.out, N, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
+        store_pair_q16<RT>(P.out, N, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
                        col_ok && zb < z1, uint32_t(xw), uint32_t(yw), uint32_t(za), uint32_t(zb),
-                       P.t_out, P.seed);
+                       P.t_out, P.seed, grids_of(P));
       else
         store_pair_f32(P.out_w, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
                        col_ok && zb < z1);
@@ -530,18 +574,18 @@ static int choose_zchunk(int64_t tiles_xy, int nz, int64_t resident_blocks) {
   return best;
 }
 
-template <int STORAGE, bool FORCE>
-static cudaError_t launch_fluid_t(KernelParams<STORAGE>& p, cudaStream_t st) {
+template <int STORAGE, bool FORCE, bool RT>
+static cudaError_t launch_fluid_t(KernelParams<STORAGE, RT>& p, cudaStream_t st) {
   const size_t smem = HaloStage<STORAGE, FORCE>::SMEM;
   static int resident = 0;  // blocks resident on the whole GPU (device 0 of the process)
   if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE>,
+    cudaError_t e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE, RT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     int dev = 0, sms = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_kernel<STORAGE, FORCE>,
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_kernel<STORAGE, FORCE, RT>,
                                                         FX * FY, smem);
     if (e != cudaSuccess) return e;
     resident = std::max(1, sms * per_sm);
@@ -549,13 +593,13 @@ static cudaError_t launch_fluid_t(KernelParams<STORAGE>& p, cudaStream_t st) {
   const int64_t tiles_xy = int64_t((p.nx + FX - 1) / FX) * ((p.ny + FYI - 1) / FYI);
   p.zc = choose_zchunk(tiles_xy, p.nz, resident);
   dim3 grid((p.nx + FX - 1) / FX, (p.ny + FYI - 1) / FYI, (p.nz + p.zc - 1) / p.zc);
-  fluid_kernel<STORAGE, FORCE><<<grid, dim3(FX, FY), smem, st>>>(p);
+  fluid_kernel<STORAGE, FORCE, RT><<<grid, dim3(FX, FY), smem, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, void* out,
                          const float* force, float omega, uint32_t t_out, uint32_t seed,
-                         cudaStream_t st) {
+                         const QGrids& grids, cudaStream_t st) {
   FluidParams p;
   p.nx = nx;
   p.ny = ny;
@@ -569,12 +613,20 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
   // 16-byte chunks need 16-byte aligned rows: nx % 4 == 0 and aligned bases
   p.chunk16 = nx % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
               reinterpret_cast<uintptr_t>(force) % 16 == 0;
-  if (storage == ST_Q16) {
-    KernelParams<ST_Q16> q;
+  if (storage == ST_Q16 && !qgrids_16(grids)) {
+    KernelParams<ST_Q16, true> q;
     static_cast<FluidParams&>(q) = p;
-    return force ? launch_fluid_t<ST_Q16, true>(q, st) : launch_fluid_t<ST_Q16, false>(q, st);
+    q.q = grids;
+    return force ? launch_fluid_t<ST_Q16, true, true>(q, st)
+                 : launch_fluid_t<ST_Q16, false, true>(q, st);
   }
-  KernelParams<ST_F32> q;
+  if (storage == ST_Q16) {
+    KernelParams<ST_Q16, false> q;
+    static_cast<FluidParams&>(q) = p;
+    return force ? launch_fluid_t<ST_Q16, true, false>(q, st)
+                 : launch_fluid_t<ST_Q16, false, false>(q, st);
+  }
+  KernelParams<ST_F32, false> q;
   static_cast<FluidParams&>(q) = p;
   const size_t N = size_t(nx) * ny * nz;
   for (int k = 0; k < 10; ++k) {
@@ -583,7 +635,8 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
   }
   for (int k = 0; k < 3; ++k)
     q.f_w[k] = force ? reinterpret_cast<const uint32_t*>(force) + k * N : nullptr;
-  return force ? launch_fluid_t<ST_F32, true>(q, st) : launch_fluid_t<ST_F32, false>(q, st);
+  return force ? launch_fluid_t<ST_F32, true, false>(q, st)
+               : launch_fluid_t<ST_F32, false, false>(q, st);
 }
 
 }  // namespace melbm

@@ -10,6 +10,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "melbm_launch.h"
+
 namespace melbm {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -149,6 +151,31 @@ __device__ __forceinline__ float2 q_decode(float2 magic_q) {
                     make_float2(QConst<G>::c, QConst<G>::c));
 }
 
+// The same maps with runtime grid constants (b-bit codes): the clamp to
+// [-qc, 2^b - 1 - qc] is explicit, since cvt's saturation is at 65535.
+__device__ __forceinline__ uint32_t qg_encode_bits(const QGrid& g, float m, float d) {
+  float w = __fmaf_rn(m, g.K, g.b);
+  w = fminf(fmaxf(w, g.wlo), g.whi);  // NaN -> wlo (code 0)
+  return __float_as_uint(__fadd_rd(__fadd_rd(w, d), g.magic));
+}
+__device__ __forceinline__ uint2 qg_encode_codes(const QGrid& g, float2 m, float2 d) {
+  float2 w = __ffma2_rn(m, make_float2(g.K, g.K), make_float2(g.b, g.b));
+  w.x = fminf(fmaxf(w.x, g.wlo), g.whi);
+  w.y = fminf(fmaxf(w.y, g.wlo), g.whi);
+  const float2 z = __fadd2_rd(__fadd2_rd(w, d), make_float2(g.qc, g.qc));
+  unsigned short qa, qb;
+  asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qa) : "f"(z.x));
+  asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qb) : "f"(z.y));
+  return make_uint2(qa, qb);
+}
+__device__ __forceinline__ float qg_decode(const QGrid& g, float magic_q) {
+  return __fmaf_rn(magic_q - g.magic, g.step, g.c);
+}
+__device__ __forceinline__ float2 qg_decode(const QGrid& g, float2 magic_q) {
+  const float2 f = __fadd2_rn(magic_q, make_float2(-g.magic, -g.magic));
+  return __ffma2_rn(f, make_float2(g.step, g.step), make_float2(g.c, g.c));
+}
+
 // Counter-based dither: pcg4d of Jarzynski & Olano, "Hash Functions for GPU
 // Rendering", JCGT 9(3) 2020, on (x, y, z, t ^ seed).  Components 0..7 take the
 // 12-bit fields [0,12) (even) and [12,24) (odd) of word k/2; components 8 and 9
@@ -260,6 +287,44 @@ __device__ __forceinline__ Stored load_stored<ST_Q16>(const void* buf, size_t N,
   return decode_words(w);
 }
 
+__device__ __forceinline__ Stored decode_words(const uint32_t w[5], const QGrids& q) {
+  Stored s;
+  s.drho = qg_decode(q.g[0], q_lo_magic(w[0]));
+  s.ux = qg_decode(q.g[1], q_hi_magic(w[0]));
+  s.uy = qg_decode(q.g[1], q_lo_magic(w[1]));
+  s.uz = qg_decode(q.g[1], q_hi_magic(w[1]));
+  s.nxx = qg_decode(q.g[2], q_lo_magic(w[2]));
+  s.nyy = qg_decode(q.g[2], q_hi_magic(w[2]));
+  s.nzz = qg_decode(q.g[2], q_lo_magic(w[3]));
+  s.nxy = qg_decode(q.g[2], q_hi_magic(w[3]));
+  s.nxz = qg_decode(q.g[2], q_lo_magic(w[4]));
+  s.nyz = qg_decode(q.g[2], q_hi_magic(w[4]));
+  return s;
+}
+
+// Load with the handle's grids (b-bit codes); FP32 storage ignores them.
+template <int STORAGE>
+__device__ __forceinline__ Stored load_stored(const void* buf, size_t N, size_t n, const QGrids& q) {
+  if constexpr (STORAGE == ST_F32) {
+    return load_stored<ST_F32>(buf, N, n);
+  } else {
+    const uint32_t* b = static_cast<const uint32_t*>(buf);
+    uint32_t w[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w[k] = __ldg(b + k * N + n);
+    return decode_words(w, q);
+  }
+}
+
+__device__ __forceinline__ void encode_words(const Stored& s, const Dither& d, uint32_t w[5],
+                                             const QGrids& q) {
+  w[0] = q_pack(qg_encode_bits(q.g[0], s.drho, d.d[0]), qg_encode_bits(q.g[1], s.ux, d.d[1]));
+  w[1] = q_pack(qg_encode_bits(q.g[1], s.uy, d.d[2]), qg_encode_bits(q.g[1], s.uz, d.d[3]));
+  w[2] = q_pack(qg_encode_bits(q.g[2], s.nxx, d.d[4]), qg_encode_bits(q.g[2], s.nyy, d.d[5]));
+  w[3] = q_pack(qg_encode_bits(q.g[2], s.nzz, d.d[6]), qg_encode_bits(q.g[2], s.nxy, d.d[7]));
+  w[4] = q_pack(qg_encode_bits(q.g[2], s.nxz, d.d[8]), qg_encode_bits(q.g[2], s.nyz, d.d[9]));
+}
+
 __device__ __forceinline__ void encode_words(const Stored& s, const Dither& d, uint32_t w[5]) {
   w[0] = q_pack(q_encode_bits<0>(s.drho, d.d[0]), q_encode_bits<1>(s.ux, d.d[1]));
   w[1] = q_pack(q_encode_bits<1>(s.uy, d.d[2]), q_encode_bits<1>(s.uz, d.d[3]));
@@ -308,6 +373,29 @@ __device__ __forceinline__ void store_stored<ST_Q16>(void* buf, size_t N, size_t
   uint32_t* b = static_cast<uint32_t*>(buf);
 #pragma unroll
   for (int k = 0; k < 5; ++k) b[k * N + n] = w[k];
+}
+
+// Store with the handle's grids (b-bit codes); FP32 storage ignores them.
+template <int STORAGE>
+__device__ __forceinline__ void store_stored(void* buf, size_t N, size_t n, const Stored& s,
+                                             uint32_t x, uint32_t y, uint32_t z, uint32_t t,
+                                             uint32_t seed, bool det, const QGrids& q) {
+  if constexpr (STORAGE == ST_F32) {
+    store_stored<ST_F32>(buf, N, n, s, x, y, z, t, seed, det);
+  } else {
+    Dither d;
+    if (det) {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) d.d[k] = 0.5f;
+    } else {
+      d = dither10(x, y, z, t, seed);
+    }
+    uint32_t w[5];
+    encode_words(s, d, w, q);
+    uint32_t* b = static_cast<uint32_t*>(buf);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) b[k * N + n] = w[k];
+  }
 }
 
 // ----------------------------------------------------------------- collision

@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "melbm_launch.h"
+
 namespace melbm {
 struct AdjointState;
 }
@@ -14,6 +16,7 @@ struct melbm_sim {
   int nx = 0, ny = 0, nz = 0;
   int64_t N = 0;
   int storage = 0;
+  melbm::QGrids grids = melbm::make_qgrids(16, 16);  // bit widths of the quantised form
   float tau = 0.f;
   uint32_t seed = 0;
   int64_t t = 0;

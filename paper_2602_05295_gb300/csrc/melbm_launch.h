@@ -6,10 +6,48 @@
 
 namespace melbm {
 
+// Grid constants of one codec group for b-bit codes (Sec. 5.4 with the adaptive
+// bit allocation of the quantization results: rho and u on b_rho_u bits, rho
+// S^neq on b_S bits).  The same FP32 roundings of FP64 expressions as the
+// compile-time 16-bit constants; qmax = 2^b - 1.
+struct QGrid {
+  float step, K, b, c, wlo, whi, magic, qc;
+  uint32_t qmax;
+};
+struct QGrids {
+  QGrid g[3];  // group 0 = rho - 1, 1 = velocity, 2 = rho S^neq
+  int bits_ru, bits_s;
+};
+inline QGrids make_qgrids(int bits_ru, int bits_s) {
+  const double lo[3] = {0.8 - 1.0, -0.4, -0.1}, hi[3] = {1.5 - 1.0, 0.4, 0.1};
+  QGrids r;
+  r.bits_ru = bits_ru;
+  r.bits_s = bits_s;
+  for (int G = 0; G < 3; ++G) {
+    const double Q = double((1u << (G < 2 ? bits_ru : bits_s)) - 1u);
+    const double t = (0.0 - lo[G]) * Q / (hi[G] - lo[G]);
+    const double qcd = double(int64_t(t + 0.5));  // floor(t + 1/2), t > 0
+    QGrid& g = r.g[G];
+    g.step = float((hi[G] - lo[G]) / Q);
+    g.K = float(Q / (hi[G] - lo[G]));
+    g.b = float(t - qcd);
+    g.c = float(lo[G] + qcd * (hi[G] - lo[G]) / Q);
+    g.wlo = float(-qcd);
+    g.whi = float(Q - qcd);
+    g.magic = float(8388608.0 + qcd);  // 2^23 + qc
+    g.qc = float(qcd);
+    g.qmax = uint32_t(Q);
+  }
+  return r;
+}
+inline bool qgrids_16(const QGrids& g) { return g.bits_ru == 16 && g.bits_s == 16; }
+
 // Fluid kernel over every cell: in -> out (storage layout of melbm_device.cuh).
+// q: the grids of the handle's bit widths (16/16 runs the kernel instantiation
+// with compile-time grid constants).
 cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, void* out,
                          const float* force, float omega, uint32_t t_out, uint32_t seed,
-                         cudaStream_t st);
+                         const QGrids& q, cudaStream_t st);
 
 // Boundary update over the list: phase A collides the S source cells and keeps
 // their 27 populations in pop[27][S] (sources.cu), then the boundary kernel
@@ -19,7 +57,7 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
                             const float* force, float omega, const uint32_t* cells,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
                             int64_t S, const uint32_t* table, float* pop, const float inflow[4],
-                            uint32_t t_out, uint32_t seed, cudaStream_t st);
+                            uint32_t t_out, uint32_t seed, const QGrids& q, cudaStream_t st);
 
 // Source set of the boundary update (sources.cu).  Setup, after the list is
 // built: mark the sources (mark[N] bytes) and count them per block of
@@ -35,7 +73,7 @@ cudaError_t launch_source_setup_fill(int nx, int ny, int nz, const uint32_t* cel
                                      uint32_t* slot_of, uint32_t* table, cudaStream_t st);
 cudaError_t launch_source_collide(int storage, size_t N, const void* in, const float* force,
                                   float omega, const uint32_t* src_cells, int64_t S, float* pop,
-                                  cudaStream_t st);
+                                  const QGrids& q, cudaStream_t st);
 
 // Outflow copy on the plane x = nx-1 (cells typed OUTFLOW), in place on buf.
 cudaError_t launch_outflow(int storage, int nx, int ny, int nz, void* buf, const uint8_t* type,
@@ -57,18 +95,20 @@ cudaError_t launch_classify_scatter(int nx, int ny, int nz, const uint8_t* mask,
 // a fixed order.  out[0] = mass, out[1] = kinetic energy, out[2] = saturated codes.
 int reduce_blocks();
 cudaError_t launch_reduce(int storage, int64_t N, const void* buf, const uint8_t* type,
-                          double* partials, double* out, cudaStream_t st);
+                          double* partials, double* out, const QGrids& q, cudaStream_t st);
 
 // State conversions (public FP32 <-> stored) and the codec on caller buffers.
 cudaError_t launch_set_state(int storage, int nx, int ny, int nz, const float* rho, const float* u,
                              const float* S, void* buf, uint32_t t, uint32_t seed, int det,
-                             cudaStream_t st);
+                             const QGrids& q, cudaStream_t st);
 cudaError_t launch_rest_state(int storage, int nx, int ny, int nz, void* buf, uint32_t seed,
-                              cudaStream_t st);
+                              const QGrids& q, cudaStream_t st);
 cudaError_t launch_get_moments(int storage, int64_t N, const void* buf, float* rho, float* u,
-                               float* S, cudaStream_t st);
+                               float* S, const QGrids& q, cudaStream_t st);
 cudaError_t launch_q16_encode(const float* stored, int nx, int ny, int nz, uint32_t t,
-                              uint32_t seed, int det, uint32_t* words, cudaStream_t st);
-cudaError_t launch_q16_decode(const uint32_t* words, int64_t N, float* stored, cudaStream_t st);
+                              uint32_t seed, int det, uint32_t* words, const QGrids& q,
+                              cudaStream_t st);
+cudaError_t launch_q16_decode(const uint32_t* words, int64_t N, float* stored, const QGrids& q,
+                              cudaStream_t st);
 
 }  // namespace melbm

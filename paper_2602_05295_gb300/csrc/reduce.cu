@@ -1,6 +1,6 @@
 // reduce.cu -- FP64 conservation diagnostics: total mass sum(rho) and kinetic
-// energy sum(rho |u|^2 / 2) over non-solid cells, plus (16-bit storage) the number
-// of non-solid codes sitting on a range limit (0 or 65535), which flags saturation
+// energy sum(rho |u|^2 / 2) over non-solid cells, plus (quantised storage) the
+// number of non-solid codes sitting on a range limit (0 or 2^b - 1), which flags saturation
 // without any atomic in the hot kernels.  Per-block partial sums, then one block
 // adds the partials in a fixed order, so the result is deterministic.
 #include "melbm_device.cuh"
@@ -18,20 +18,20 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-__device__ __forceinline__ uint32_t rail_count(uint32_t w) {
+__device__ __forceinline__ uint32_t rail_count(uint32_t w, uint32_t qmax_lo, uint32_t qmax_hi) {
   const uint32_t lo = w & 0xFFFFu, hi = w >> 16;
-  return (lo == 0u || lo == 0xFFFFu) + (hi == 0u || hi == 0xFFFFu);
+  return (lo == 0u || lo == qmax_lo) + (hi == 0u || hi == qmax_hi);
 }
 
 template <int STORAGE>
 __global__ void __launch_bounds__(RD_THREADS) reduce_partial_kernel(int64_t N, const void* buf,
                                                                    const uint8_t* type,
-                                                                   double* partials) {
+                                                                   double* partials, QGrids q) {
   double mass = 0.0, ke = 0.0, sat = 0.0;
   for (int64_t n = int64_t(blockIdx.x) * RD_THREADS + threadIdx.x; n < N;
        n += int64_t(gridDim.x) * RD_THREADS) {
     if (type && type[n] == T_SOLID) continue;
-    const Stored s = load_stored<STORAGE>(buf, size_t(N), size_t(n));
+    const Stored s = load_stored<STORAGE>(buf, size_t(N), size_t(n), q);
     const double rho = 1.0 + double(s.drho);
     const double u2 = double(s.ux) * s.ux + double(s.uy) * s.uy + double(s.uz) * s.uz;
     mass += rho;
@@ -40,7 +40,12 @@ __global__ void __launch_bounds__(RD_THREADS) reduce_partial_kernel(int64_t N, c
       const uint32_t* b = static_cast<const uint32_t*>(buf);
       uint32_t c = 0;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) c += rail_count(b[size_t(k) * N + n]);
+      for (int k = 0; k < 5; ++k) {
+        // word 0 = (rho, ux), 1 = (uy, uz), 2..4 = rho S^neq
+        const uint32_t qm_lo = q.g[k == 0 ? 0 : (k == 1 ? 1 : 2)].qmax;
+        const uint32_t qm_hi = q.g[k < 2 ? 1 : 2].qmax;
+        c += rail_count(b[size_t(k) * N + n], qm_lo, qm_hi);
+      }
       sat += double(c);
     }
   }
@@ -72,11 +77,11 @@ __global__ void reduce_final_kernel(const double* partials, int nblocks, double*
 }
 
 cudaError_t launch_reduce(int storage, int64_t N, const void* buf, const uint8_t* type,
-                          double* partials, double* out, cudaStream_t st) {
+                          double* partials, double* out, const QGrids& q, cudaStream_t st) {
   if (storage == ST_Q16)
-    reduce_partial_kernel<ST_Q16><<<RD_BLOCKS, RD_THREADS, 0, st>>>(N, buf, type, partials);
+    reduce_partial_kernel<ST_Q16><<<RD_BLOCKS, RD_THREADS, 0, st>>>(N, buf, type, partials, q);
   else
-    reduce_partial_kernel<ST_F32><<<RD_BLOCKS, RD_THREADS, 0, st>>>(N, buf, type, partials);
+    reduce_partial_kernel<ST_F32><<<RD_BLOCKS, RD_THREADS, 0, st>>>(N, buf, type, partials, q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reduce_final_kernel<<<1, 32, 0, st>>>(partials, RD_BLOCKS, out);

@@ -162,7 +162,7 @@ template <int STORAGE, bool FORCE>
 __global__ void __launch_bounds__(256) source_collide_kernel(const void* in, size_t N,
                                                              const float* force, float omega,
                                                              const uint32_t* src_cells, int64_t S,
-                                                             float* pop) {
+                                                             float* pop, QGrids q) {
   const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const uint32_t n = src_cells[s];
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) source_collide_kernel(const void* in, siz
     fy = __ldg(force + N + n);
     fz = __ldg(force + 2 * N + n);
   }
-  const Mom17 A = collide_moments<FORCE>(load_stored<STORAGE>(in, N, n), omega, fx, fy, fz);
+  const Mom17 A = collide_moments<FORCE>(load_stored<STORAGE>(in, N, n, q), omega, fx, fy, fz);
 #pragma unroll
   for (int i = 0; i < 27; ++i)
     pop[int64_t(i) * S + s] = hermite_eval(A, i % 3 - 1, (i / 3) % 3 - 1, i / 9 - 1);
@@ -180,15 +180,15 @@ __global__ void __launch_bounds__(256) source_collide_kernel(const void* in, siz
 
 cudaError_t launch_source_collide(int storage, size_t N, const void* in, const float* force,
                                   float omega, const uint32_t* src_cells, int64_t S, float* pop,
-                                  cudaStream_t st) {
+                                  const QGrids& q, cudaStream_t st) {
   if (S <= 0) return cudaSuccess;
   const unsigned blocks = unsigned((S + 255) / 256);
   if (storage == ST_Q16) {
-    if (force) source_collide_kernel<ST_Q16, true><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop);
-    else source_collide_kernel<ST_Q16, false><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop);
+    if (force) source_collide_kernel<ST_Q16, true><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
+    else source_collide_kernel<ST_Q16, false><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
   } else {
-    if (force) source_collide_kernel<ST_F32, true><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop);
-    else source_collide_kernel<ST_F32, false><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop);
+    if (force) source_collide_kernel<ST_F32, true><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
+    else source_collide_kernel<ST_F32, false><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
   }
   return cudaGetLastError();
 }

@@ -71,6 +71,9 @@ def lib():
         "melbm_backward": [P, P, P, P],
         "melbm_q16_encode": [P, I, I, I, U32, U32, I, P, P],
         "melbm_q16_decode": [P, I64, P, P],
+        "melbm_set_bits": [P, I, I],
+        "melbm_codec_encode": [P, I, I, I, U32, U32, I, I, I, P, P],
+        "melbm_codec_decode": [P, I64, I, I, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -211,6 +214,11 @@ class Simulator:
     def set_force(self, F):
         _check(lib().melbm_set_force(self._h, _ptr(F, 3 * self.N, name="F")), self._h)
 
+    def set_bits(self, bits_rho_u, bits_S):
+        """Bit widths b_rho_u / b_S of the quantised form (8..16 each); re-encodes
+        the current state."""
+        _check(lib().melbm_set_bits(self._h, int(bits_rho_u), int(bits_S)), self._h)
+
     def boundary_list(self):
         cnt = ctypes.c_int64()
         _check(lib().melbm_get_boundary_list(self._h, None, None, 0, ctypes.byref(cnt)), self._h)
@@ -277,6 +285,27 @@ def q16_decode(words, stream=None):
     out = torch.empty(10, N, dtype=torch.float32, device=words.device)
     _check(lib().melbm_q16_decode(_ptr(words, 5 * N, torch.int32), N, ctypes.c_void_p(out.data_ptr()),
                                   _stream_ptr(stream)))
+    return out
+
+
+def codec_encode(stored, shape, t, seed, bits, deterministic=False, stream=None):
+    """FP32 stored variables (10, N) -> int32 words (5, N) of b_rho_u / b_S-bit codes."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    words = torch.empty(5, N, dtype=torch.int32, device=stored.device)
+    _check(lib().melbm_codec_encode(_ptr(stored, 10 * N), nx, ny, nz,
+                                    ctypes.c_uint32(t & 0xFFFFFFFF),
+                                    ctypes.c_uint32(seed & 0xFFFFFFFF), int(deterministic),
+                                    int(bits[0]), int(bits[1]),
+                                    ctypes.c_void_p(words.data_ptr()), _stream_ptr(stream)))
+    return words
+
+
+def codec_decode(words, bits, stream=None):
+    N = words.shape[-1]
+    out = torch.empty(10, N, dtype=torch.float32, device=words.device)
+    _check(lib().melbm_codec_decode(_ptr(words, 5 * N, torch.int32), N, int(bits[0]), int(bits[1]),
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
 
 

@@ -501,7 +501,7 @@ def test_stochastic_rounding_is_unbiased_over_the_dither(orc):
         assert abs(np.mean(d)) < 6e-5, (k, np.mean(d))
 
 
-# Adaptive bit allocation (Sec. 6.1): rho and u take b_rho_u bits, rho S^neq b_S
+# Adaptive bit allocation (Sec. 6.2.2): rho and u take b_rho_u bits, rho S^neq b_S
 # bits, each on the grid of Sec. 5.4 with 2^b - 1 steps.
 BIT_CONFIGS = [(16, 15), (15, 14), (14, 13), (13, 12), (12, 11)]
 
