@@ -76,6 +76,8 @@ def lib():
             L.orc_encode.argtypes = [I, I, I, P, U32, U32, I, P]
             L.orc_decode.argtypes = [I64, P, P]
             L.orc_encode_bits.argtypes = [I, I, I, P, U32, U32, I, I, I, P]
+            L.orc_step_wall_f64.argtypes = [I, I, I, D, P, P, P, P, I, P, P, P]
+            L.orc_solid_force_f64.argtypes = [I, I, I, D, P, P, P, I, P, P, I, P]
             L.orc_decode_bits.argtypes = [I64, P, I, I, P]
             L.orc_codec_constants_bits.argtypes = [I, I, I, P]
             L.orc_mean_code_over_dither_bits.argtypes = [ctypes.c_float, I, I, I]
@@ -166,7 +168,20 @@ def _inflow_arr(inflow):
     return np.asarray(inflow, np.float64).reshape(4)
 
 
-def step(m, shape, tau, F=None, typ=None, inflow=None, n=1, literal_xyz=False):
+class Wall:
+    """Solid walls (Sec. 3.2): model 0 = halfway bounce-back, 1 = moment-based
+    reconstruction with rigid body motion; ``body`` = uint8 body id per cell (the
+    solid mask values, None: every solid is body 1); ``motion`` = {id: (V, Om, r0)}."""
+
+    def __init__(self, model=1, body=None, motion=None):
+        self.model = int(model)
+        self.body = None if body is None else np.ascontiguousarray(body, np.uint8)
+        self.table = np.zeros((256, 9))
+        for b, (V, Om, r0) in (motion or {}).items():
+            self.table[b] = np.concatenate([V, Om, r0])
+
+
+def step(m, shape, tau, F=None, typ=None, inflow=None, n=1, literal_xyz=False, wall=None):
     """n FP64 steps of the public state ``m`` (10, N) on the grid ``shape`` = (nx, ny, nz)."""
     nx, ny, nz = shape
     cur = _f64(m).copy()
@@ -175,10 +190,25 @@ def step(m, shape, tau, F=None, typ=None, inflow=None, n=1, literal_xyz=False):
     ta = None if typ is None else np.ascontiguousarray(typ, np.uint8)
     ia = _inflow_arr(inflow)
     for _ in range(n):
-        lib().orc_step_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(ta), _p(ia),
-                           int(literal_xyz), _p(out))
+        if wall is None:
+            lib().orc_step_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(ta), _p(ia),
+                               int(literal_xyz), _p(out))
+        else:
+            lib().orc_step_wall_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(ta), _p(ia),
+                                    wall.model, _p(wall.body), _p(wall.table), _p(out))
         cur, out = out, cur
     return cur
+
+
+def solid_force(m, shape, tau, typ, wall, F=None, body_id=0):
+    """(Fx, Fy, Fz, Tx, Ty, Tz) the next step transfers to body ``body_id`` (0: all
+    solids) by momentum exchange; torque about the body's r0."""
+    nx, ny, nz = shape
+    out = np.zeros(6)
+    lib().orc_solid_force_f64(nx, ny, nz, float(tau), _p(_f64(m)), _p(_f64(F)),
+                              _p(np.ascontiguousarray(typ, np.uint8)), wall.model,
+                              _p(wall.body), _p(wall.table), int(body_id), _p(out))
+    return out
 
 
 def step_complex(m, shape, tau, F=None, typ=None, inflow=None, literal_xyz=False):

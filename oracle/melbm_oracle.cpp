@@ -15,7 +15,9 @@
 //   * streaming:      pull form f_i(x) = f+_i(x - c_i)                 (Eq. streaming; Alg. 2)
 //   * moments:        rho, rho u (+F/2), rho S                          (Eq. rho_u_stress)
 //   * boundaries:     halfway bounce-back f_i(x) = f+_{opp(i)}(x) for solid
-//                     links, equilibrium inflow, zero-gradient outflow  (split-kernel design, Sec. 4.2)
+//                     links, equilibrium inflow, zero-gradient outflow  (split-kernel design, Sec. 4.2);
+//                     or the moment-based reconstruction at moving solid walls,
+//                     and the momentum-exchange force and torque  (Sec. 3.2, solid coupling)
 //   * codec:          range, normalisation, dithered rounding to 16 bits (Sec. 5.4)
 //
 // Readings of the paper that it takes (each is also listed in the design notes):
@@ -209,16 +211,67 @@ void load_force(const T* F, int64_t N, int64_t n, T out[3]) {
   for (int a = 0; a < 3; ++a) out[a] = F ? F[a * N + n] : T(0.0);
 }
 
+// Solid walls (Sec. 3.2, solid coupling).  model 0: halfway bounce-back.
+// model 1: the moment-based reconstruction: a link of fluid node x that meets a
+// solid at p (the halfway point x - c_i / 2) receives the population
+// h_i(rho^p, u^p, S^p) with rho^p = rho^x, u^p the velocity of the solid at p and
+// S^p = u^p u^p + (S^x - u^x u^x), (rho, u, S)^x the post-collision moments of x.
+// Solid cells belong to bodies (the mask value, 1..255); body b moves rigidly,
+// u^p = V_b + Om_b x (p - r0_b), from table[9 b .. 9 b + 8] = (V, Om, r0).
+struct WallSpec {
+  int model;
+  const uint8_t* body;   // N body ids (NULL: every solid is body 1)
+  const double* table;   // 256 x 9
+};
+
+inline void wall_point(const Grid& g, int64_t n, int i, double p[3]) {
+  const int x = int(n % g.nx), y = int((n / g.nx) % g.ny), z = int(n / (int64_t(g.nx) * g.ny));
+  p[0] = x - 0.5 * L.c[i][0];
+  p[1] = y - 0.5 * L.c[i][1];
+  p[2] = z - 0.5 * L.c[i][2];
+}
+
+inline void wall_velocity(const WallSpec& w, int body, const double p[3], double up[3]) {
+  const double* t = w.table + 9 * body;
+  const double r[3] = {p[0] - t[6], p[1] - t[7], p[2] - t[8]};
+  up[0] = t[0] + t[4] * r[2] - t[5] * r[1];
+  up[1] = t[1] + t[5] * r[0] - t[3] * r[2];
+  up[2] = t[2] + t[3] * r[1] - t[4] * r[0];
+}
+
+// (rho^p, u^p, S^p) of the moment-based reconstruction.
+template <class T>
+Mom<T> wall_moments(const Mom<T>& mx, const double up[3]) {
+  Mom<T> o;
+  o.rho = mx.rho;
+  for (int a = 0; a < 3; ++a) o.u[a] = up[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b)
+      o.S[sidx(a, b)] = up[a] * up[b] + (mx.S[sidx(a, b)] - mx.u[a] * mx.u[b]);
+  return o;
+}
+
+// The population that solid link i of cell n receives.
+template <class T>
+T wall_population(const Grid& g, const std::vector<Mom<T>>& mp, int64_t n, int64_t src, int i,
+                  const WallSpec* w, int literal_xyz) {
+  if (!w || w->model == 0) return reconstruct(opposite(i), mp[n], literal_xyz);  // bounce-back
+  double p[3], up[3];
+  wall_point(g, n, i, p);
+  wall_velocity(*w, w->body ? w->body[src] : 1, p, up);
+  return reconstruct(i, wall_moments(mp[n], up), literal_xyz);
+}
+
 // The update of one non-solid cell from the post-collision moments `mp`
-// (Alg. 2 streaming + moments, with bounce-back for solid links).
+// (Alg. 2 streaming + moments, with the wall population for solid links).
 template <class T>
 Mom<T> pull_and_moments(const Grid& g, const std::vector<Mom<T>>& mp, const uint8_t* type,
-                        const T* F, int64_t n, int literal_xyz) {
+                        const T* F, int64_t n, int literal_xyz, const WallSpec* w = nullptr) {
   T f[27];
   for (int i = 0; i < 27; ++i) {
     const int64_t src = g.pull_src(n, i);
     if (type && type[src] == SOLID)
-      f[i] = reconstruct(opposite(i), mp[n], literal_xyz);  // halfway bounce-back
+      f[i] = wall_population(g, mp, n, src, i, w, literal_xyz);
     else
       f[i] = reconstruct(i, mp[src], literal_xyz);
   }
@@ -241,7 +294,7 @@ Mom<T> inflow_state(const double* inflow) {
 // pulls and re-forms the moments; pass 3 applies the zero-gradient outflow copy.
 template <class T>
 void step_grid(const Grid& g, double tau, const T* m, const T* F, const uint8_t* type,
-               const double* inflow, T* out, int literal_xyz) {
+               const double* inflow, T* out, int literal_xyz, const WallSpec* w = nullptr) {
   const int64_t N = g.N();
   std::vector<Mom<T>> mp(N);
 #pragma omp parallel for schedule(static)
@@ -259,7 +312,7 @@ void step_grid(const Grid& g, double tau, const T* m, const T* F, const uint8_t*
     } else if (t == INFLOW) {
       store(out, N, n, inflow_state<T>(inflow));
     } else {
-      store(out, N, n, pull_and_moments(g, mp, type, F, n, literal_xyz));
+      store(out, N, n, pull_and_moments(g, mp, type, F, n, literal_xyz, w));
     }
   }
   if (type) {
@@ -610,6 +663,58 @@ int64_t orc_classify(int nx, int ny, int nz, const uint8_t* mask, int inflow, in
 void orc_step_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
                   const uint8_t* type, const double* inflow, int literal_xyz, double* out) {
   step_grid<double>(Grid{nx, ny, nz}, tau, m, F, type, inflow, out, literal_xyz);
+}
+
+// The step with the wall model of WallSpec (body ids and the 256 x 9 motion table).
+void orc_step_wall_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                       const uint8_t* type, const double* inflow, int model, const uint8_t* body,
+                       const double* table, double* out) {
+  const WallSpec w{model, body, table};
+  step_grid<double>(Grid{nx, ny, nz}, tau, m, F, type, inflow, out, 0, &w);
+}
+
+// Force and torque (about r0 of the body) that the next step transfers to the
+// solid cells of body `body_id` (0: every solid): momentum exchange over every
+// solid link i of every FLUID_BOUNDARY cell x, -c_i (f_in + f_out), with f_out =
+// h_opp(i)(x) the post-collision population leaving x towards the wall and f_in
+// the population the wall returns; torque sum (p - r0) x that, p the link's
+// halfway point.  FP64, fixed order.
+void orc_solid_force_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                         const uint8_t* type, int model, const uint8_t* body, const double* table,
+                         int body_id, double* out /*6*/) {
+  const Grid g{nx, ny, nz};
+  const int64_t N = g.N();
+  const WallSpec w{model, body, table};
+  std::vector<Mom<double>> mp(N);
+  for (int64_t n = 0; n < N; ++n) {
+    if (type[n] == SOLID) continue;
+    double Fx[3];
+    load_force(F, N, n, Fx);
+    mp[n] = collide(load(m, N, n), Fx, tau);
+  }
+  for (int k = 0; k < 6; ++k) out[k] = 0.0;
+  for (int64_t n = 0; n < N; ++n) {
+    if (type[n] != FLUID_BOUNDARY) continue;
+    for (int i = 0; i < 27; ++i) {
+      const int64_t src = g.pull_src(n, i);
+      if (type[src] != SOLID) continue;
+      const int b = body ? body[src] : 1;
+      if (body_id && b != body_id) continue;
+      const double f_out = reconstruct(opposite(i), mp[n], 0);
+      const double f_in = wall_population(g, mp, n, src, i, &w, 0);
+      double dF[3], p[3];
+      for (int a = 0; a < 3; ++a) dF[a] = -double(L.c[i][a]) * (f_in + f_out);
+      wall_point(g, n, i, p);
+      const double* t = table + 9 * (body_id ? body_id : b);
+      const double r[3] = {p[0] - t[6], p[1] - t[7], p[2] - t[8]};
+      out[0] += dF[0];
+      out[1] += dF[1];
+      out[2] += dF[2];
+      out[3] += r[1] * dF[2] - r[2] * dF[1];
+      out[4] += r[2] * dF[0] - r[0] * dF[2];
+      out[5] += r[0] * dF[1] - r[1] * dF[0];
+    }
+  }
 }
 
 // The same step on complex numbers (interleaved re/im), for complex-step derivatives.

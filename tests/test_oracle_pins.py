@@ -404,6 +404,108 @@ def test_multistep_adjoint_against_central_differences(orc):
         assert abs(fd - ad) < 1e-6 * abs(ad), (fd, ad)
 
 
+# ------------------------------------------------------------------ moving solid walls
+def _two_body_mask(shape, rng, dens=0.12):
+    """Random solid cells split into bodies 1 and 2 (the mask value is the body id)."""
+    nx, ny, nz = shape
+    body = (rng.uniform(size=nx * ny * nz) < dens).astype(np.uint8)
+    body[body > 0] = 1 + (rng.uniform(size=int(body.sum())) < 0.5)
+    return body
+
+
+def test_wall_momentum_exchange_balances_the_step(orc):
+    """Sec. 3.2: the force on the solid is the momentum its links exchange with the
+    fluid, sum -c_i (f_in + f_out).  For every state the step then changes the total
+    fluid momentum by the body force minus that force, exactly:
+    P(t+1) - P(t) = sum F - F_solid (both wall models, moving bodies, any state)."""
+    rng = np.random.default_rng(31)
+    shape = (9, 8, 7)
+    N = 9 * 8 * 7
+    body = _two_body_mask(shape, rng)
+    typ = orc.classify((body > 0).reshape(shape[::-1]))[0]
+    fluid = typ != orc.SOLID
+    u = 0.05 * rng.standard_normal((3, N))
+    m = np.zeros((10, N))
+    m[0] = 1 + 0.01 * rng.standard_normal(N)
+    m[1:4] = u
+    for k, (a, b) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        m[4 + k] = u[a] * u[b] + 0.003 * rng.standard_normal(N)
+    F = 1e-4 * rng.standard_normal((3, N))
+    motion = {1: ([0.02, -0.01, 0.0], [0.0, 0.0, 0.003], [4.0, 3.5, 3.0]),
+              2: ([-0.01, 0.0, 0.015], [0.002, -0.001, 0.0], [1.0, 2.0, 5.0])}
+    for model in (0, 1):
+        wall = orc.Wall(model, body, motion)
+        new = orc.step(m, shape, 0.6, F=F, typ=typ, wall=wall)
+        P0 = (m[0] * m[1:4])[:, fluid].sum(1)
+        P1 = (new[0] * new[1:4])[:, fluid].sum(1)
+        Fs = orc.solid_force(m, shape, 0.6, typ, wall, F=F)
+        assert np.abs(P1 - P0 - (F[:, fluid].sum(1) - Fs[:3])).max() < 1e-12, model
+        F1 = orc.solid_force(m, shape, 0.6, typ, wall, F=F, body_id=1)
+        F2 = orc.solid_force(m, shape, 0.6, typ, wall, F=F, body_id=2)
+        assert np.allclose(F1[:3] + F2[:3], Fs[:3], rtol=0, atol=1e-13)
+        # the same motion described about r0 + d (V + Om x d): the torque becomes
+        # T(r0 + d) = T(r0) - d x F
+        d = np.array([0.7, -1.3, 2.1])
+        V1 = np.add(motion[1][0], np.cross(motion[1][1], d))
+        m1 = {1: (V1, motion[1][1], list(np.add(motion[1][2], d))), 2: motion[2]}
+        F1s = orc.solid_force(m, shape, 0.6, typ, orc.Wall(model, body, m1), F=F, body_id=1)
+        assert np.allclose(F1s[3:], F1[3:] - np.cross(d, F1[:3]), rtol=0, atol=1e-12)
+
+
+def test_moment_wall_moving_with_the_flow_keeps_uniform_flow(orc):
+    """With the walls moving at the fluid's velocity U the reconstruction at p is
+    the fluid's own equilibrium, so (rho, U, U U) stays a fixed point; halfway
+    bounce-back (a wall at rest) does not keep it."""
+    rng = np.random.default_rng(32)
+    shape = (8, 7, 6)
+    N = 8 * 7 * 6
+    body = _two_body_mask(shape, rng)
+    typ = orc.classify((body > 0).reshape(shape[::-1]))[0]
+    fluid = typ != orc.SOLID
+    U = np.array([0.04, -0.02, 0.03])
+    m = np.zeros((10, N))
+    m[0] = 1.0
+    m[1:4] = U[:, None]
+    for k, (a, b) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        m[4 + k] = U[a] * U[b]
+    moving = orc.Wall(1, body, {1: (U, [0, 0, 0], [0, 0, 0]), 2: (U, [0, 0, 0], [3, 3, 3])})
+    new = orc.step(m, shape, 0.7, typ=typ, wall=moving)
+    assert np.abs(new[:, fluid] - m[:, fluid]).max() < 1e-14
+    bb = orc.step(m, shape, 0.7, typ=typ, wall=orc.Wall(0, body))
+    assert np.abs(bb[1:4, fluid] - m[1:4, fluid]).max() > 1e-3
+
+
+def test_moment_wall_couette_flow(orc):
+    """Plane Couette flow between body 1 (y = 0, at rest) and body 2 (y = ny - 1,
+    moving with U x): the steady profile is linear, and the force on each wall
+    equals the viscous momentum flux rho nu du/dy times the wall area."""
+    shape = (2, 14, 2)
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    y = (np.arange(N) // nx) % ny
+    body = np.zeros(N, np.uint8)
+    body[y == 0] = 1
+    body[y == ny - 1] = 2
+    typ = orc.classify((body > 0).reshape(shape[::-1]))[0]
+    U, tau = 0.05, 0.8
+    nu = (tau - 0.5) / 3
+    wall = orc.Wall(1, body, {1: ([0, 0, 0], [0, 0, 0], [0, 0, 0]), 2: ([U, 0, 0], [0, 0, 0], [0, 0, 0])})
+    m = np.zeros((10, N))
+    m[0] = 1.0
+    m = orc.step(m, shape, tau, typ=typ, wall=wall, n=6000)
+    rows = np.arange(1, ny - 1)
+    ux = np.array([m[1][y == r].mean() for r in rows])
+    rho = np.array([m[0][y == r].mean() for r in rows])
+    slope, icpt = np.polyfit(rows, ux, 1)
+    assert np.abs(ux - (slope * rows + icpt)).max() < 1e-7 * U
+    y0, y1 = -icpt / slope, (U - icpt) / slope  # where the profile meets the wall velocities
+    assert abs(y0 - 0.5) < 1.0 and abs(y1 - (ny - 1.5)) < 1.0, (y0, y1)
+    F2 = orc.solid_force(m, shape, tau, typ, wall, body_id=2)
+    F1 = orc.solid_force(m, shape, tau, typ, wall, body_id=1)
+    flux = rho.mean() * nu * slope * nx * nz
+    assert abs(F2[0] + flux) < 1e-3 * flux and abs(F1[0] - flux) < 1e-3 * flux, (F1[0], F2[0], flux)
+
+
 # ------------------------------------------------------------------ P8 codec
 def test_codec_paper_formula_endpoints_and_round_trip(orc):
     """Sec. 5.4: ranges, b = 16 bits, dequantisation m_min + q (m_max - m_min)/(2^b - 1).
