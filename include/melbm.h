@@ -184,6 +184,28 @@ MELBM_API int melbm_q16_decode(const uint32_t* words, int64_t N, float* stored, 
 MELBM_API int melbm_reduce_state_noalloc(const void* state, int storage, int64_t N,
                                          const uint8_t* type, double* out, void* cuda_stream);
 
+/* Solid walls (Sec. 3.2, solid coupling).  model 0 (default): halfway bounce-back,
+ * f_i(x) = f+_opp(i)(x) for a solid link.  model 1: moment-based reconstruction --
+ * the link receives the third-order Hermite population of (rho^p, u^p, S^p) with
+ * rho^p = rho of x, u^p the velocity of the solid at the link's halfway point p
+ * and S^p = u^p u^p + (S - u u) from the post-collision moments of x.  Solid cells
+ * belong to bodies: the value of melbm_set_solid's mask (1..255) is the body id.
+ * Body b moves rigidly: u^p = V + Omega x (p - r0), p in cell units with cell
+ * (x, y, z) at (x, y, z); melbm_set_body_motion sets (V, Omega, r0) (host
+ * pointers, NULL = zeros; bodies never set are at rest).  The geometry itself
+ * does not move.  melbm_forward_checkpointed requires model 0 (MELBM_EINVAL). */
+MELBM_API int melbm_set_wall_model(melbm_t h, int model);
+MELBM_API int melbm_set_body_motion(melbm_t h, int body, const float* V, const float* Omega,
+                                    const float* r0);
+
+/* Force and torque (out[0..2], out[3..5], host, FP64) that the next step
+ * transfers to the solid cells of body `body` (0: every solid; torques then each
+ * about their own body's r0), by momentum exchange: every solid link i of a
+ * FLUID_BOUNDARY cell adds -c_i (f_in + f_out), f_out = f+_opp(i)(x) and f_in
+ * the population the wall returns; the torque adds (p - r0) x that.  Sums in a
+ * fixed order (deterministic); synchronises.  Zero without solids. */
+MELBM_API int melbm_solid_force(melbm_t h, int body, double* out);
+
 /* Adaptive bit allocation (Sec. 6.2.2, "b_rho_u / b_S"): rho and u are stored
  * with bits_rho_u bits and rho S^neq with bits_S bits, each on the Sec. 5.4 grid
  * m_min + q (m_max - m_min)/(2^b - 1) (the same centre-anchored FP32 evaluation

@@ -181,7 +181,8 @@ cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out
   if (e == cudaSuccess && h->L)
     e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
                         h->list_word, h->L, h->src_cells, h->S, h->src_table, h->src_pop,
-                        h->inflow, t_out, h->seed, h->grids, h->stream);
+                        h->inflow, t_out, h->seed, h->grids, h->wall_model, h->mask, h->bodies,
+                        h->stream);
   if (e == cudaSuccess && h->outflow_on && h->type)
     e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream);
   return e;
@@ -249,6 +250,9 @@ int melbm_destroy(melbm_t h) {
   dev_free(h, h->staging, 0);
   dev_free(h, h->red_partials, 0);
   dev_free(h, h->red_out, 0);
+  dev_free(h, h->bodies, 256 * 9 * 4);
+  dev_free(h, h->sf_partials, size_t(solid_force_blocks()) * 6 * 8);
+  dev_free(h, h->sf_out, 6 * 8);
   delete h;
   return MELBM_OK;
 }
@@ -492,6 +496,60 @@ int melbm_codec_decode(const uint32_t* words, int64_t N, int bits_rho_u, int bit
   cudaError_t e = launch_q16_decode(words, N, stored, make_qgrids(bits_rho_u, bits_S),
                                     static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "melbm_codec_decode");
+  return MELBM_OK;
+}
+
+int melbm_set_wall_model(melbm_t h, int model) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_wall_model: NULL handle");
+  if (model != 0 && model != 1) return fail(h, MELBM_EINVAL, "melbm_set_wall_model: model %d unknown", model);
+  if (!h->bodies) {
+    int rc = dev_alloc(h, (void**)&h->bodies, 256 * 9 * 4);
+    if (rc) return rc;
+    MELBM_CUDA(h, cudaMemcpyAsync(h->bodies, h->bodies_host, 256 * 9 * 4, cudaMemcpyHostToDevice,
+                                  h->stream));
+    MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  h->wall_model = model;
+  return MELBM_OK;
+}
+
+int melbm_set_body_motion(melbm_t h, int body, const float* V, const float* Omega, const float* r0) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_body_motion: NULL handle");
+  if (body < 1 || body > 255) return fail(h, MELBM_EINVAL, "melbm_set_body_motion: body %d outside 1..255", body);
+  float* t = h->bodies_host + 9 * body;
+  for (int a = 0; a < 3; ++a) {
+    t[a] = V ? V[a] : 0.f;
+    t[3 + a] = Omega ? Omega[a] : 0.f;
+    t[6 + a] = r0 ? r0[a] : 0.f;
+  }
+  if (!h->bodies) {
+    int rc = dev_alloc(h, (void**)&h->bodies, 256 * 9 * 4);
+    if (rc) return rc;
+  }
+  MELBM_CUDA(h, cudaMemcpyAsync(h->bodies, h->bodies_host, 256 * 9 * 4, cudaMemcpyHostToDevice,
+                                h->stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MELBM_OK;
+}
+
+int melbm_solid_force(melbm_t h, int body, double* out) {
+  if (!h || !out) return fail(h, MELBM_EINVAL, "melbm_solid_force: NULL argument");
+  if (body < 0 || body > 255) return fail(h, MELBM_EINVAL, "melbm_solid_force: body %d outside 0..255", body);
+  for (int k = 0; k < 6; ++k) out[k] = 0.0;
+  if (!h->L || !h->mask) return MELBM_OK;
+  int rc;
+  if (!h->bodies && (rc = melbm_set_wall_model(h, h->wall_model))) return rc;
+  if (!h->sf_partials) {
+    if ((rc = dev_alloc(h, (void**)&h->sf_partials, size_t(solid_force_blocks()) * 6 * 8)) ||
+        (rc = dev_alloc(h, (void**)&h->sf_out, 6 * 8)))
+      return rc;
+  }
+  MELBM_CUDA(h, launch_solid_force(h->storage, h->nx, h->ny, h->nz, h->buf[h->cur], h->force,
+                                   1.0f / h->tau, h->list_cell, h->list_word, h->L, h->grids,
+                                   h->wall_model, h->mask, h->bodies, body, h->sf_partials,
+                                   h->sf_out, h->stream));
+  MELBM_CUDA(h, cudaMemcpyAsync(out, h->sf_out, 6 * 8, cudaMemcpyDeviceToHost, h->stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return MELBM_OK;
 }
 

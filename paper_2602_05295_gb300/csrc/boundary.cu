@@ -8,6 +8,11 @@
 //     post-collision populations of every source were evaluated once by phase
 //     A (sources.cu); this kernel gathers, per direction, the one it needs
 //     through the cell's 27 source slots.
+//     With the moment-based wall model (Sec. 3.2, solid coupling) a solid link
+//     instead receives the Hermite population of (rho, u^p, S^p) at the link's
+//     halfway point p, u^p the rigid velocity of the body the solid cell
+//     belongs to (its mask value) and S^p = u^p u^p + (S - u u) from the cell's
+//     own post-collision moments.
 //   * INFLOW: reset to the equilibrium (rho_in, u_in, S = u_in u_in).
 // The outflow pass then copies the stored state of x = nx-2 onto x = nx-1.
 #include "melbm_device.cuh"
@@ -27,12 +32,15 @@ struct BoundaryParams {
   const uint32_t* table;  // [27][count] source slots
   const float* pop;       // [27][S] post-collision populations f+_i / w_i - 1 of the sources
   int64_t S;
+  int wall_model;          // 0 halfway bounce-back, 1 moment-based reconstruction
+  const uint8_t* mask;     // body id of every cell (wall model 1)
+  const float* bodies;     // 256 x 9: V, Om, r0 of each body (wall model 1)
   float in_rho, in_ux, in_uy, in_uz;
   uint32_t t_out, seed;
   QGrids q;
 };
 
-template <int STORAGE, bool FORCE>
+template <int STORAGE, bool FORCE, bool MOVING>
 __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= P.count) return;
@@ -62,14 +70,26 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
     fy0 = P.force[N + n];
     fz0 = P.force[2 * N + n];
   }
+  Mom17 Aself;
+  if constexpr (MOVING)
+    Aself = collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n, P.q), P.omega, fx0, fy0, fz0);
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
     const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-    // f_i / w_i - 1: population i pulled from x - c_i, or population opp(i) =
-    // 26 - i of x itself (bounce-back) when the link is solid -- the slot then holds x
-    const uint32_t slot = __ldg(P.table + int64_t(i) * P.count + k);
-    const int j = ((word >> i) & 1u) ? 26 - i : i;
-    const float g = __ldg(P.pop + int64_t(j) * P.S + slot);
+    // f_i / w_i - 1: population i pulled from x - c_i, or, for a solid link,
+    // population opp(i) = 26 - i of x itself (bounce-back; the slot then holds x)
+    // or the population of the moving wall
+    float g;
+    if (MOVING && ((word >> i) & 1u)) {
+      float up[3];
+      body_velocity(P.bodies, P.mask[pull_source(x, y, z, nx, ny, nz, i)], x - 0.5f * cx,
+                    y - 0.5f * cy, z - 0.5f * cz, up);
+      g = hermite_eval(wall_moments(Aself, up[0], up[1], up[2]), cx, cy, cz);
+    } else {
+      const uint32_t slot = __ldg(P.table + int64_t(i) * P.count + k);
+      const int j = ((word >> i) & 1u) ? 26 - i : i;
+      g = __ldg(P.pop + int64_t(j) * P.S + slot);
+    }
     const float w = (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *
                     (cz ? (1.0f / 6.0f) : (2.0f / 3.0f));
     const float f = w * g;
@@ -93,7 +113,8 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
                             const float* force, float omega, const uint32_t* cells,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
                             int64_t S, const uint32_t* table, float* pop, const float inflow[4],
-                            uint32_t t_out, uint32_t seed, const QGrids& q, cudaStream_t st) {
+                            uint32_t t_out, uint32_t seed, const QGrids& q, int wall_model,
+                            const uint8_t* mask, const float* bodies, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   cudaError_t e = launch_source_collide(storage, size_t(nx) * ny * nz, in, force, omega, src_cells,
                                         S, pop, q, st);
@@ -119,13 +140,27 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
   p.t_out = t_out;
   p.seed = seed;
   p.q = q;
+  p.wall_model = wall_model;
+  p.mask = mask;
+  p.bodies = bodies;
   const unsigned blocks = unsigned((count + 127) / 128);
+  const bool mv = wall_model == 1;
   if (storage == ST_Q16) {
-    if (force) boundary_kernel<ST_Q16, true><<<blocks, 128, 0, st>>>(p);
-    else boundary_kernel<ST_Q16, false><<<blocks, 128, 0, st>>>(p);
+    if (force) {
+      if (mv) boundary_kernel<ST_Q16, true, true><<<blocks, 128, 0, st>>>(p);
+      else boundary_kernel<ST_Q16, true, false><<<blocks, 128, 0, st>>>(p);
+    } else {
+      if (mv) boundary_kernel<ST_Q16, false, true><<<blocks, 128, 0, st>>>(p);
+      else boundary_kernel<ST_Q16, false, false><<<blocks, 128, 0, st>>>(p);
+    }
   } else {
-    if (force) boundary_kernel<ST_F32, true><<<blocks, 128, 0, st>>>(p);
-    else boundary_kernel<ST_F32, false><<<blocks, 128, 0, st>>>(p);
+    if (force) {
+      if (mv) boundary_kernel<ST_F32, true, true><<<blocks, 128, 0, st>>>(p);
+      else boundary_kernel<ST_F32, true, false><<<blocks, 128, 0, st>>>(p);
+    } else {
+      if (mv) boundary_kernel<ST_F32, false, true><<<blocks, 128, 0, st>>>(p);
+      else boundary_kernel<ST_F32, false, false><<<blocks, 128, 0, st>>>(p);
+    }
   }
   return cudaGetLastError();
 }

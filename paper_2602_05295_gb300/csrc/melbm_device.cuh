@@ -478,6 +478,86 @@ __device__ __forceinline__ Mom17T<T> collide_moments(const StoredT<T>& s, float 
   return A;
 }
 
+// f+_i / w_i - 1 from the Hermite moments: the coefficient of P_p P_q P_r is
+// mu_pqr divided by the D1Q3 norms (1, 1/3, 2/9) of each factor (P_2(c) = c^2 - 1/3).
+__device__ __forceinline__ float hermite_eval(const Mom17& A, int cx, int cy, int cz) {
+  const float fx = float(cx), fy = float(cy), fz = float(cz);
+  const float qx = fx * fx - (1.0f / 3.0f), qy = fy * fy - (1.0f / 3.0f),
+              qz = fz * fz - (1.0f / 3.0f);
+  return A.m000 + 3.0f * (A.m100 * fx + A.m010 * fy + A.m001 * fz) +
+         4.5f * (A.m200 * qx + A.m020 * qy + A.m002 * qz) +
+         9.0f * (A.m110 * fx * fy + A.m101 * fx * fz + A.m011 * fy * fz) +
+         13.5f * (A.m210 * qx * fy + A.m120 * fx * qy + A.m201 * qx * fz + A.m102 * fx * qz +
+                  A.m021 * qy * fz + A.m012 * fy * qz) +
+         27.0f * A.m111 * fx * fy * fz;
+}
+
+// Hermite moments of the wall state of the moment-based reconstruction (Sec.
+// 3.2): rho^p = rho of the cell, u^p the wall velocity, and the non-equilibrium
+// stress rho (S - u u) of the cell's post-collision moments A kept, i.e.
+// S^p = u^p u^p + (S - u u); third moments from the same closure as the collision.
+__device__ __forceinline__ Mom17 wall_moments(const Mom17& A, float upx, float upy, float upz) {
+  const float rho = 1.0f + A.m000;
+  const float inv = __frcp_rn(rho);
+  const float exx = A.m200 - A.m100 * A.m100 * inv, eyy = A.m020 - A.m010 * A.m010 * inv,
+              ezz = A.m002 - A.m001 * A.m001 * inv;
+  const float exy = A.m110 - A.m100 * A.m010 * inv, exz = A.m101 - A.m100 * A.m001 * inv,
+              eyz = A.m011 - A.m010 * A.m001 * inv;
+  const float rux = rho * upx, ruy = rho * upy, ruz = rho * upz;
+  Mom17 W;
+  W.m000 = A.m000;
+  W.m100 = rux;
+  W.m010 = ruy;
+  W.m001 = ruz;
+  W.m200 = __fmaf_rn(rux, upx, exx);
+  W.m020 = __fmaf_rn(ruy, upy, eyy);
+  W.m002 = __fmaf_rn(ruz, upz, ezz);
+  W.m110 = __fmaf_rn(rux, upy, exy);
+  W.m101 = __fmaf_rn(rux, upz, exz);
+  W.m011 = __fmaf_rn(ruy, upz, eyz);
+  W.m210 = __fmaf_rn(upy, W.m200, 2.0f * upx * exy);
+  W.m120 = __fmaf_rn(upx, W.m020, 2.0f * upy * exy);
+  W.m201 = __fmaf_rn(upz, W.m200, 2.0f * upx * exz);
+  W.m102 = __fmaf_rn(upx, W.m002, 2.0f * upz * exz);
+  W.m021 = __fmaf_rn(upz, W.m020, 2.0f * upy * eyz);
+  W.m012 = __fmaf_rn(upy, W.m002, 2.0f * upz * eyz);
+  W.m111 = __fmaf_rn(rux * upy, upz, exy * upz + exz * upy + eyz * upx);
+  return W;
+}
+
+// Velocity of body b at point p: V + Om x (p - r0), table[9 b ..] = (V, Om, r0).
+__device__ __forceinline__ void body_velocity(const float* table, int b, float px, float py,
+                                              float pz, float* up) {
+  const float* t = table + 9 * b;
+  const float rx = px - t[6], ry = py - t[7], rz = pz - t[8];
+  up[0] = t[0] + t[4] * rz - t[5] * ry;
+  up[1] = t[1] + t[5] * rx - t[3] * rz;
+  up[2] = t[2] + t[3] * ry - t[4] * rx;
+}
+
+// Linear index of the neighbour x - c_i (periodic, one-step wrap).
+__device__ __forceinline__ uint32_t pull_source(int x, int y, int z, int nx, int ny, int nz, int i) {
+  const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+  int sx = x - cx, sy = y - cy, sz = z - cz;
+  sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+  sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+  sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
+  return uint32_t(sx) + uint32_t(nx) * (uint32_t(sy) + uint32_t(ny) * uint32_t(sz));
+}
+
+__device__ __forceinline__ void cell_xyz(uint32_t n, int nx, int ny, int* x, int* y, int* z) {
+  *x = int(n % uint32_t(nx));
+  *y = int((n / uint32_t(nx)) % uint32_t(ny));
+  *z = int(n / (uint32_t(nx) * uint32_t(ny)));
+}
+
+// Lattice weight of direction i = (cx+1) + 3 (cy+1) + 9 (cz+1).
+__device__ __forceinline__ float lattice_weight(int cx, int cy, int cz) {
+  return (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *
+         (cz ? (1.0f / 6.0f) : (2.0f / 3.0f));
+}
+
+
 // ----------------------------------------------------------------- 1D lattice pass
 // One axis of the separable stream: D3Q27 is the tensor product of three D1Q3
 // lattices (c in {-1, 0, 1}, weights 1/6, 2/3, 1/6).  Along one axis the local

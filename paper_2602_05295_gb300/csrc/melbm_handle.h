@@ -41,6 +41,13 @@ struct melbm_sim {
   int inflow_on = 0;
   float inflow[4] = {1.f, 0.f, 0.f, 0.f};
   int outflow_on = 0;
+  // solid walls: model (0 halfway bounce-back, 1 moment-based reconstruction) and
+  // the rigid motion (V, Om, r0) of each body id, host copy and device copy
+  int wall_model = 0;
+  float bodies_host[256 * 9] = {};
+  float* bodies = nullptr;
+  double* sf_partials = nullptr;
+  double* sf_out = nullptr;
   // force, staging, reductions
   float* force = nullptr;
   void* staging = nullptr;

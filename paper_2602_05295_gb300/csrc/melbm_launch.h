@@ -57,7 +57,18 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
                             const float* force, float omega, const uint32_t* cells,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
                             int64_t S, const uint32_t* table, float* pop, const float inflow[4],
-                            uint32_t t_out, uint32_t seed, const QGrids& q, cudaStream_t st);
+                            uint32_t t_out, uint32_t seed, const QGrids& q, int wall_model,
+                            const uint8_t* mask, const float* bodies, cudaStream_t st);
+
+// Force and torque (about r0 of the body) the next step transfers to the solid
+// cells of body `body` (0: every solid) by momentum exchange over the solid
+// links of the listed cells; 6 doubles into out (device), fixed-order sums.
+int solid_force_blocks();
+cudaError_t launch_solid_force(int storage, int nx, int ny, int nz, const void* in,
+                               const float* force, float omega, const uint32_t* cells,
+                               const uint32_t* words, int64_t count, const QGrids& q,
+                               int wall_model, const uint8_t* mask, const float* bodies, int body,
+                               double* partials, double* out, cudaStream_t st);
 
 // Source set of the boundary update (sources.cu).  Setup, after the list is
 // built: mark the sources (mark[N] bytes) and count them per block of

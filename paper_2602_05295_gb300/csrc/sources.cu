@@ -19,22 +19,6 @@ constexpr int SRC_CHUNK = SRC_THREADS * SRC_ROUNDS;  // flags per block, consecu
 
 int64_t source_flag_blocks(int64_t N) { return (N + SRC_CHUNK - 1) / SRC_CHUNK; }
 
-// Linear index of the neighbour x - c_i (periodic, one-step wrap).
-__device__ __forceinline__ uint32_t pull_source(int x, int y, int z, int nx, int ny, int nz, int i) {
-  const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-  int sx = x - cx, sy = y - cy, sz = z - cz;
-  sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-  sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-  sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
-  return uint32_t(sx) + uint32_t(nx) * (uint32_t(sy) + uint32_t(ny) * uint32_t(sz));
-}
-
-__device__ __forceinline__ void cell_xyz(uint32_t n, int nx, int ny, int* x, int* y, int* z) {
-  *x = int(n % uint32_t(nx));
-  *y = int((n / uint32_t(nx)) % uint32_t(ny));
-  *z = int(n / (uint32_t(nx) * uint32_t(ny)));
-}
-
 __global__ void mark_sources_kernel(int nx, int ny, int nz, const uint32_t* cells,
                                     const uint32_t* words, int64_t L, uint8_t* mark) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -142,20 +126,6 @@ cudaError_t launch_source_setup_fill(int nx, int ny, int nz, const uint32_t* cel
 }
 
 // ----------------------------------------------------------------- phase A
-// f+_i / w_i - 1 from the Hermite moments: the coefficient of P_p P_q P_r is
-// mu_pqr divided by the D1Q3 norms (1, 1/3, 2/9) of each factor (P_2(c) = c^2 - 1/3).
-__device__ __forceinline__ float hermite_eval(const Mom17& A, int cx, int cy, int cz) {
-  const float fx = float(cx), fy = float(cy), fz = float(cz);
-  const float qx = fx * fx - (1.0f / 3.0f), qy = fy * fy - (1.0f / 3.0f),
-              qz = fz * fz - (1.0f / 3.0f);
-  return A.m000 + 3.0f * (A.m100 * fx + A.m010 * fy + A.m001 * fz) +
-         4.5f * (A.m200 * qx + A.m020 * qy + A.m002 * qz) +
-         9.0f * (A.m110 * fx * fy + A.m101 * fx * fz + A.m011 * fy * fz) +
-         13.5f * (A.m210 * qx * fy + A.m120 * fx * qy + A.m201 * qx * fz + A.m102 * fx * qz +
-                  A.m021 * qy * fz + A.m012 * fy * qz) +
-         27.0f * A.m111 * fx * fy * fz;
-}
-
 // pop[i S + s] = f+_i / w_i - 1 at source cell src_cells[s] (App. A with its
 // force, then the Hermite population of direction i).
 template <int STORAGE, bool FORCE>

@@ -14,6 +14,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 import torch
 
 from . import build as _build
@@ -72,6 +74,9 @@ def lib():
         "melbm_q16_encode": [P, I, I, I, U32, U32, I, P, P],
         "melbm_q16_decode": [P, I64, P, P],
         "melbm_set_bits": [P, I, I],
+        "melbm_set_wall_model": [P, I],
+        "melbm_set_body_motion": [P, I, P, P, P],
+        "melbm_solid_force": [P, I, P],
         "melbm_codec_encode": [P, I, I, I, U32, U32, I, I, I, P, P],
         "melbm_codec_decode": [P, I64, I, I, P, P],
     }
@@ -213,6 +218,22 @@ class Simulator:
 
     def set_force(self, F):
         _check(lib().melbm_set_force(self._h, _ptr(F, 3 * self.N, name="F")), self._h)
+
+    def set_wall_model(self, model):
+        """0: halfway bounce-back; 1: moment-based reconstruction at moving walls."""
+        _check(lib().melbm_set_wall_model(self._h, int(model)), self._h)
+
+    def set_body_motion(self, body, V=(0, 0, 0), Omega=(0, 0, 0), r0=(0, 0, 0)):
+        """Rigid motion of body ``body`` (the solid mask value, 1..255)."""
+        arr = [(ctypes.c_float * 3)(*map(float, v)) for v in (V, Omega, r0)]
+        _check(lib().melbm_set_body_motion(self._h, int(body), *[ctypes.cast(a, ctypes.c_void_p) for a in arr]),
+               self._h)
+
+    def solid_force(self, body=0):
+        """(Fx, Fy, Fz, Tx, Ty, Tz) the next step transfers to body ``body`` (0: all)."""
+        out = (ctypes.c_double * 6)()
+        _check(lib().melbm_solid_force(self._h, int(body), ctypes.cast(out, ctypes.c_void_p)), self._h)
+        return np.array(list(out))
 
     def set_bits(self, bits_rho_u, bits_S):
         """Bit widths b_rho_u / b_S of the quantised form (8..16 each); re-encodes
