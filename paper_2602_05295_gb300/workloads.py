@@ -161,6 +161,24 @@ def sphere_pack(shape, count=300, rmin=4.0, rmax=20.0, seed=SEED + 3, max_tries=
     return m, spheres
 
 
+def sphere_bodies(shape, spheres, max_bodies=254):
+    """Body ids for a sphere pack (the solid mask values): sphere k < max_bodies is
+    body k + 1, the channel walls and any further spheres are body 255."""
+    nx, ny, nz = shape
+    m = channel_walls(shape) * np.uint8(255)
+    for k, (cx, cy, cz, r) in enumerate(spheres):
+        x0, x1 = max(int(np.floor(cx - r)), 0), min(int(np.ceil(cx + r)) + 1, nx)
+        y0, y1 = max(int(np.floor(cy - r)), 0), min(int(np.ceil(cy + r)) + 1, ny)
+        z0, z1 = max(int(np.floor(cz - r)), 0), min(int(np.ceil(cz + r)) + 1, nz)
+        xs = np.arange(x0, x1)[None, None, :]
+        ys = np.arange(y0, y1)[None, :, None]
+        zs = np.arange(z0, z1)[:, None, None]
+        inside = (xs - cx) ** 2 + (ys - cy) ** 2 + (zs - cz) ** 2 <= r * r
+        sub = m[z0:z1, y0:y1, x0:x1]
+        sub[inside] = np.uint8(k + 1 if k < max_bodies else 255)
+    return m
+
+
 def procedural_obstacle(shape, count=40, hmin=10.0, hmax=60.0, seed=SEED + 4,
                         region=((100, 600), (100, 300), (75, 325))):
     """Union of seeded boxes and ellipsoids (probability 1/2 each) with half-extents
