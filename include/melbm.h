@@ -58,7 +58,7 @@ typedef enum melbm_status {
 } melbm_status;
 
 enum { MELBM_D3Q27 = 27 };
-enum { MELBM_F32 = 0, MELBM_Q16 = 1 };
+enum { MELBM_F32 = 0, MELBM_Q16 = 1, MELBM_MIXED = 2 };
 /* cell types, priority SOLID > INFLOW > OUTFLOW > FLUID_BOUNDARY > FLUID */
 enum { MELBM_FLUID = 0, MELBM_FLUID_BOUNDARY = 1, MELBM_INFLOW = 2, MELBM_OUTFLOW = 3,
        MELBM_SOLID = 4 };
@@ -67,7 +67,15 @@ enum { MELBM_FLUID = 0, MELBM_FLUID_BOUNDARY = 1, MELBM_INFLOW = 2, MELBM_OUTFLO
  * relaxation time (nu = (tau - 1/2)/3); storage is MELBM_F32 (40 B/cell per
  * buffer) or MELBM_Q16 (20 B/cell per buffer, Sec. 5.4).  Allocates two state
  * buffers on the current device, initialised to rest (rho = 1, u = 0, S = 0).
- * N must be below 2^31.  *out receives the handle (NULL on failure). */
+ * MELBM_MIXED is the paper's own mixed-precision scheme with solids (Sec. 5.4,
+ * "Atomic accumulation with mixed precision"; kept for comparison): the
+ * post-collision moments in 16 bits (20 B/cell) and the post-streaming raw moments
+ * in FP32 (40 B/cell); a step is the fluid pass, the solid correction with
+ * atomicAdd (halfway bounce-back), the outflow copy and the collision with
+ * re-quantisation.  It supports solids, inflow and outflow, but not forces, bit
+ * widths, the moving-wall model, solid forces, raw state or the adjoint
+ * (MELBM_EINVAL).  N must be below 2^31.  *out receives the handle (NULL on
+ * failure). */
 MELBM_API int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, melbm_t* out);
 
 /* Free every device and host resource of the handle.  NULL is accepted. */

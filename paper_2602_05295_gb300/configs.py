@@ -198,6 +198,32 @@ def run_adjoint128(steps):
             "grad_F_norm": float(F.grad.norm().item()), "memory_bytes": sim.memory_bytes()}
 
 
+def run_mixed_vs_recompute(steps):
+    """The paper's mixed-precision scheme (16-bit post-collision + FP32
+    post-streaming, atomic solid correction, re-quantisation pass) against this
+    library's recompute design (16-bit post-streaming ping-pong, boundary list
+    recomputed from the input) on the periodic 256^3 turbulence and on the
+    512x256x256 sphere channel: throughput and device memory."""
+    out = []
+    wl = W.TURB256
+    rho, u = _state_from_velocity(W.flat(W.random_phase_field(wl.shape, 0.08)))
+    for storage in ("q16", "mixed"):
+        sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602)
+        sim.set_state(rho, u)
+        ms = _timed_steps(sim, steps)
+        out.append({"workload": "mixed_vs_recompute", "case": wl.name, "storage": storage,
+                    "ms_per_step": ms, "MLUPS": wl.cells / ms / 1e3, "memory_bytes": sim.memory_bytes()})
+        sim.close()
+    wl = W.CHANNEL512
+    mask, _ = W.sphere_pack(wl.shape)
+    for storage in ("q16", "mixed"):
+        rec = _channel(wl, mask, 0.05, steps, storage=storage)
+        out.append({"workload": "mixed_vs_recompute", "case": wl.name, "storage": storage,
+                    "ms_per_step": rec["ms_per_step"], "MLUPS": rec["MLUPS"],
+                    "memory_bytes": rec["memory_bytes"]})
+    return out
+
+
 def run_bits_sweep(steps):
     """Adaptive bit allocation b_rho_u / b_S (Sec. 6.2.2) on the 256^3 turbulence
     field: velocity error against the FP32-storage run after 100 steps (relative
@@ -235,7 +261,8 @@ def run_bits_sweep(steps):
 
 
 RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256, "channel512": run_channel512,
-           "channel512_moving": run_channel512_moving, "large1000": run_large1000, "adjoint128": run_adjoint128, "bits_sweep": run_bits_sweep}
+           "channel512_moving": run_channel512_moving, "large1000": run_large1000, "adjoint128": run_adjoint128, "bits_sweep": run_bits_sweep,
+           "mixed_vs_recompute": run_mixed_vs_recompute}
 
 
 def main():

@@ -73,8 +73,23 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Bytes of the state a raw-state call moves (0: the mixed scheme has none).
 size_t state_bytes(const melbm_sim* h) {
+  if (h->storage == MELBM_MIXED) return 0;
   return size_t(h->N) * (h->storage == MELBM_Q16 ? 20 : 40);
+}
+
+// Bytes of buffer k: the ping-pong pair, or Q (16-bit post-collision) and P
+// (FP32 post-streaming) of the mixed scheme.
+size_t buf_bytes(const melbm_sim* h, int k) {
+  if (h->storage == MELBM_MIXED) return size_t(h->N) * (k == 0 ? 20 : 40);
+  return state_bytes(h);
+}
+
+float* mixed_p(const melbm_sim* h) { return static_cast<float*>(h->buf[1]); }
+
+int mixed_unsupported(melbm_t h, const char* what) {
+  return fail(h, MELBM_EINVAL, "%s: not available with MELBM_MIXED storage", what);
 }
 
 int ensure_staging(melbm_t h, size_t bytes) {
@@ -203,7 +218,7 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
     return fail(nullptr, MELBM_EINVAL, "melbm_create: %lld cells exceed 2^31 - 1", (long long)N);
   if (!(tau > 0.5f) || !(tau < 1e6f))
     return fail(nullptr, MELBM_EINVAL, "melbm_create: tau = %g must exceed 1/2", double(tau));
-  if (storage != MELBM_F32 && storage != MELBM_Q16)
+  if (storage != MELBM_F32 && storage != MELBM_Q16 && storage != MELBM_MIXED)
     return fail(nullptr, MELBM_EINVAL, "melbm_create: storage %d unknown", storage);
   melbm_sim* h = new (std::nothrow) melbm_sim;
   if (!h) return fail(nullptr, MELBM_ENOMEM, "melbm_create: host allocation failed");
@@ -213,9 +228,9 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
   h->N = N;
   h->tau = tau;
   h->storage = storage;
-  const size_t sb = state_bytes(h);
   int rc;
-  if ((rc = dev_alloc(h, &h->buf[0], sb)) || (rc = dev_alloc(h, &h->buf[1], sb)) ||
+  if ((rc = dev_alloc(h, &h->buf[0], buf_bytes(h, 0))) ||
+      (rc = dev_alloc(h, &h->buf[1], buf_bytes(h, 1))) ||
       (rc = dev_alloc(h, (void**)&h->red_partials, size_t(reduce_blocks()) * 3 * 8)) ||
       (rc = dev_alloc(h, (void**)&h->red_out, 3 * 8))) {
     g_err = h->err;
@@ -223,7 +238,15 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
     return rc;
   }
   // rest state (rho = 1, u = 0, S = 0) at time index 0
-  cudaError_t e = launch_rest_state(storage, nx, ny, nz, h->buf[0], 0, h->grids, h->stream);
+  cudaError_t e;
+  if (storage == MELBM_MIXED) {
+    e = cudaMemsetAsync(h->buf[1], 0, buf_bytes(h, 1), h->stream);
+    if (e == cudaSuccess)
+      e = launch_mixed_collide_quantize(nx, ny, nz, mixed_p(h), h->buf[0], 1.0f / tau, 0, 0,
+                                        h->stream);
+  } else {
+    e = launch_rest_state(storage, nx, ny, nz, h->buf[0], 0, h->grids, h->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     cuda_fail(h, e, "melbm_create: initialising the rest state");
@@ -238,8 +261,8 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
 int melbm_destroy(melbm_t h) {
   if (!h) return MELBM_OK;
   if (h->adj) adjoint_free(h->adj);
-  dev_free(h, h->buf[0], state_bytes(h));
-  dev_free(h, h->buf[1], state_bytes(h));
+  dev_free(h, h->buf[0], buf_bytes(h, 0));
+  dev_free(h, h->buf[1], buf_bytes(h, 1));
   dev_free(h, h->mask, size_t(h->N));
   dev_free(h, h->type, size_t(h->N));
   free_list(h);
@@ -287,8 +310,14 @@ int melbm_set_state(melbm_t h, const float* rho, const float* u, const float* S)
     uu = st + N;
     ss = S ? st + 4 * N : nullptr;
   }
-  MELBM_CUDA(h, launch_set_state(h->storage, h->nx, h->ny, h->nz, r, uu, ss, h->buf[h->cur], 0,
-                                 h->seed, 0, h->grids, h->stream));
+  if (h->storage == MELBM_MIXED) {
+    MELBM_CUDA(h, launch_mixed_set_state(h->N, r, uu, ss, mixed_p(h), h->stream));
+    MELBM_CUDA(h, launch_mixed_collide_quantize(h->nx, h->ny, h->nz, mixed_p(h), h->buf[0],
+                                                1.0f / h->tau, 0, h->seed, h->stream));
+  } else {
+    MELBM_CUDA(h, launch_set_state(h->storage, h->nx, h->ny, h->nz, r, uu, ss, h->buf[h->cur], 0,
+                                   h->seed, 0, h->grids, h->stream));
+  }
   if (!dev) MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->t = 0;
   h->poisoned = false;
@@ -300,6 +329,10 @@ int melbm_get_moments(melbm_t h, float* rho, float* u, float* S) {
   if (!rho && !u && !S) return fail(h, MELBM_EINVAL, "melbm_get_moments: no output");
   const size_t N = size_t(h->N);
   const bool dev = (!rho || is_device_ptr(rho)) && (!u || is_device_ptr(u)) && (!S || is_device_ptr(S));
+  if (dev && h->storage == MELBM_MIXED) {
+    MELBM_CUDA(h, launch_mixed_get_moments(h->N, mixed_p(h), rho, u, S, h->stream));
+    return MELBM_OK;
+  }
   if (dev) {
     MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], rho, u, S, h->grids,
                                      h->stream));
@@ -308,8 +341,11 @@ int melbm_get_moments(melbm_t h, float* rho, float* u, float* S) {
   int rc = ensure_staging(h, N * 40);
   if (rc) return rc;
   float* st = static_cast<float*>(h->staging);
-  MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], st, st + N, st + 4 * N,
-                                   h->grids, h->stream));
+  if (h->storage == MELBM_MIXED)
+    MELBM_CUDA(h, launch_mixed_get_moments(h->N, mixed_p(h), st, st + N, st + 4 * N, h->stream));
+  else
+    MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], st, st + N, st + 4 * N,
+                                     h->grids, h->stream));
   const cudaMemcpyKind k = cudaMemcpyDefault;
   if (rho) MELBM_CUDA(h, cudaMemcpyAsync(rho, st, N * 4, k, h->stream));
   if (u) MELBM_CUDA(h, cudaMemcpyAsync(u, st + N, N * 12, k, h->stream));
@@ -379,6 +415,7 @@ int melbm_get_types(melbm_t h, uint8_t* types) {
 
 int melbm_set_force(melbm_t h, const float* F) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_force: NULL handle");
+  if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_set_force");
   if (!F) {
     dev_free(h, h->force, size_t(h->N) * 12);
     h->force = nullptr;
@@ -396,8 +433,19 @@ int melbm_step(melbm_t h, int n) {
   if (h->poisoned) return fail(h, MELBM_ESTATE, "melbm_step: an earlier CUDA failure left the state undefined; call melbm_set_state");
   for (int s = 0; s < n; ++s) {
     const uint32_t t_out = uint32_t(h->t + 1);
-    MELBM_CUDA(h, forward_step(h, h->buf[h->cur], h->buf[1 - h->cur], t_out));
-    h->cur = 1 - h->cur;
+    if (h->storage == MELBM_MIXED) {
+      MELBM_CUDA(h, launch_fluid_mixed(h->nx, h->ny, h->nz, h->buf[0], mixed_p(h), h->stream));
+      if (h->L)
+        MELBM_CUDA(h, launch_mixed_correct(h->nx, h->ny, h->nz, h->buf[0], mixed_p(h), h->list_cell,
+                                           h->list_word, h->L, h->inflow, h->stream));
+      if (h->outflow_on && h->type)
+        MELBM_CUDA(h, launch_outflow(MELBM_F32, h->nx, h->ny, h->nz, mixed_p(h), h->type, h->stream));
+      MELBM_CUDA(h, launch_mixed_collide_quantize(h->nx, h->ny, h->nz, mixed_p(h), h->buf[0],
+                                                  1.0f / h->tau, t_out, h->seed, h->stream));
+    } else {
+      MELBM_CUDA(h, forward_step(h, h->buf[h->cur], h->buf[1 - h->cur], t_out));
+      h->cur = 1 - h->cur;
+    }
     h->t += 1;
   }
   return MELBM_OK;
@@ -405,8 +453,9 @@ int melbm_step(melbm_t h, int n) {
 
 int melbm_reduce(melbm_t h, double* mass, double* ke) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_reduce: NULL handle");
-  MELBM_CUDA(h, launch_reduce(h->storage, h->N, h->buf[h->cur], h->type, h->red_partials,
-                              h->red_out, h->grids, h->stream));
+  const void* state = h->storage == MELBM_MIXED ? h->buf[1] : h->buf[h->cur];
+  MELBM_CUDA(h, launch_reduce(h->storage, h->N, state, h->type, h->red_partials, h->red_out,
+                              h->grids, h->stream));
   double out[3];
   MELBM_CUDA(h, cudaMemcpyAsync(out, h->red_out, sizeof out, cudaMemcpyDeviceToHost, h->stream));
   MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -437,6 +486,7 @@ int melbm_state_bytes(melbm_t h, int64_t* bytes) {
 
 int melbm_get_raw_state(melbm_t h, void* dst, int64_t bytes) {
   if (!h || !dst) return fail(h, MELBM_EINVAL, "melbm_get_raw_state: NULL argument");
+  if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_get_raw_state");
   if (bytes != int64_t(state_bytes(h)))
     return fail(h, MELBM_EINVAL, "melbm_get_raw_state: bytes %lld != %lld", (long long)bytes,
                 (long long)state_bytes(h));
@@ -447,6 +497,7 @@ int melbm_get_raw_state(melbm_t h, void* dst, int64_t bytes) {
 
 int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int64_t time_index) {
   if (!h || !src) return fail(h, MELBM_EINVAL, "melbm_set_raw_state: NULL argument");
+  if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_set_raw_state");
   if (bytes != int64_t(state_bytes(h)))
     return fail(h, MELBM_EINVAL, "melbm_set_raw_state: bytes %lld != %lld", (long long)bytes,
                 (long long)state_bytes(h));
@@ -501,6 +552,7 @@ int melbm_codec_decode(const uint32_t* words, int64_t N, int bits_rho_u, int bit
 
 int melbm_set_wall_model(melbm_t h, int model) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_wall_model: NULL handle");
+  if (h->storage == MELBM_MIXED && model != 0) return mixed_unsupported(h, "melbm_set_wall_model");
   if (model != 0 && model != 1) return fail(h, MELBM_EINVAL, "melbm_set_wall_model: model %d unknown", model);
   if (!h->bodies) {
     int rc = dev_alloc(h, (void**)&h->bodies, 256 * 9 * 4);
@@ -535,6 +587,7 @@ int melbm_set_body_motion(melbm_t h, int body, const float* V, const float* Omeg
 int melbm_solid_force(melbm_t h, int body, double* out) {
   if (!h || !out) return fail(h, MELBM_EINVAL, "melbm_solid_force: NULL argument");
   if (body < 0 || body > 255) return fail(h, MELBM_EINVAL, "melbm_solid_force: body %d outside 0..255", body);
+  if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_solid_force");
   for (int k = 0; k < 6; ++k) out[k] = 0.0;
   if (!h->L || !h->mask) return MELBM_OK;
   int rc;

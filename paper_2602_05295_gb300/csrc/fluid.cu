@@ -108,6 +108,10 @@ struct KernelParams<ST_Q16, true> : FluidParams {
   QGrids q;
 };
 template <>
+struct KernelParams<ST_MIXED, false> : FluidParams {
+  uint32_t* out_w[10];  // the raw FP32 post-streaming moment planes
+};
+template <>
 struct KernelParams<ST_F32, false> : FluidParams {
   const uint32_t* in_w[10];
   uint32_t* out_w[10];
@@ -280,9 +284,11 @@ __device__ __forceinline__ float2 shfl_idx2(float2 v, int src) {
 // The y-pass slices are indexed s = 3 p + r' (p: x-order, r': input z-order).
 template <int STORAGE, bool FORCE, bool RT>
 __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelParams<STORAGE, RT> P) {
-  using HS = HaloStage<STORAGE, FORCE>;
-  auto decode = [&](const RawPair<STORAGE>& r) {
-    if constexpr (STORAGE == ST_Q16 && RT) return decode_pair(r, P.q);
+  // the input side reads 16-bit codes in the mixed scheme (post-collision moments)
+  constexpr int IN = STORAGE == ST_MIXED ? ST_Q16 : STORAGE;
+  using HS = HaloStage<IN, FORCE>;
+  auto decode = [&](const RawPair<IN>& r) {
+    if constexpr (IN == ST_Q16 && RT) return decode_pair(r, P.q);
     else return decode_pair(r);
   };
   extern __shared__ float2 sm2[];
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     };
 #pragma unroll
     for (int w = 0; w < HS::W; ++w) {
-      if constexpr (STORAGE == ST_Q16) {
+      if constexpr (IN == ST_Q16) {
         copy(2 * w, src + w * N, na);
         copy(2 * w + 1, src + w * N, nb);
       } else {
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     if (FORCE) {
 #pragma unroll
       for (int w = 0; w < 3; ++w) {
-        if constexpr (STORAGE == ST_Q16) {
+        if constexpr (IN == ST_Q16) {
           copy(2 * HS::W + 2 * w, fsrc + w * N, na);
           copy(2 * HS::W + 2 * w + 1, fsrc + w * N, nb);
         } else {
@@ -371,11 +377,11 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
   // {phi+ of column x0-1, phi- of column x0+32}.
   auto halo_finish = [&](int b, int hbuf) {
     const uint32_t* d = stg + b * HS::BUF_WORDS + lane * HS::CHUNK + (chunk16 ? int(hcol & 3) : 0);
-    RawPair<STORAGE> hr;
+    RawPair<IN> hr;
 #pragma unroll
     for (int w = 0; w < HS::W; ++w) {
-      set_word<STORAGE>(hr, 0, w, d[(2 * w) * 32 * HS::CHUNK]);
-      set_word<STORAGE>(hr, 1, w, d[(2 * w + 1) * 32 * HS::CHUNK]);
+      set_word<IN>(hr, 0, w, d[(2 * w) * 32 * HS::CHUNK]);
+      set_word<IN>(hr, 1, w, d[(2 * w + 1) * 32 * HS::CHUNK]);
     }
     const StoredT<float2> hs = decode(hr);
     float2 hfx = make_float2(0.f, 0.f), hfy = hfx, hfz = hfx;
@@ -399,8 +405,8 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     }
   };
 
-  RawPair<STORAGE> raw;
-  if constexpr (STORAGE == ST_Q16)
+  RawPair<IN> raw;
+  if constexpr (IN == ST_Q16)
     load_pair(raw, P.in, N, col + plane * wz(z0 - 1), col + plane * wz(z0));
   else
     load_pair(raw, P.in_w, col + plane * wz(z0 - 1), col + plane * wz(z0));
@@ -427,7 +433,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
     if (FORCE) {
       const size_t na = col + plane * wz(zz), nb = col + plane * wz(zz + 1);
-      if constexpr (STORAGE == ST_Q16) {
+      if constexpr (IN == ST_Q16) {
         fx = make_float2(__ldg(P.force + na), __ldg(P.force + nb));
         fy = make_float2(__ldg(P.force + N + na), __ldg(P.force + N + nb));
         fz = make_float2(__ldg(P.force + 2 * N + na), __ldg(P.force + 2 * N + nb));
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     }
     if (zz + 2 <= z1)  // prefetch the next pair
     {
-      if constexpr (STORAGE == ST_Q16)
+      if constexpr (IN == ST_Q16)
         load_pair(raw, P.in, N, col + plane * wz(zz + 2), col + plane * wz(zz + 3));
       else
         load_pair(raw, P.in_w, col + plane * wz(zz + 2), col + plane * wz(zz + 3));
@@ -537,10 +543,20 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
         oz = make_float2(fprev[2], fz.x);
       }
       // slices: 0:(0,0) 1:(1,0) 2:(0,1) 3:(2,0) 4:(1,1) 5:(0,2)
+      const int za = zz - 1, zb = zz;
+      if constexpr (STORAGE == ST_MIXED) {
+        // the raw post-streaming sums rho - 1, sum c f, sum (c c - 1/3) f
+        StoredT<float2> r;
+        r.drho = M[0][0], r.ux = M[1][0], r.uy = M[2][0], r.uz = M[0][1];
+        r.nxx = M[3][0], r.nyy = M[5][0], r.nzz = M[0][2];
+        r.nxy = M[4][0], r.nxz = M[1][1], r.nyz = M[2][1];
+        store_pair_f32(P.out_w, col + plane * za, col + plane * (zb < nz ? zb : 0), r, col_ok,
+                       col_ok && zb < z1);
+        continue;
+      }
       const StoredT<float2> o =
           finish_moments<FORCE>(M[0][0], M[1][0], M[2][0], M[0][1], M[3][0], M[5][0], M[0][2],
                                 M[4][0], M[1][1], M[2][1], ox, oy, oz);
-      const int za = zz - 1, zb = zz;
       if constexpr (STORAGE == ST_Q16)
         store_pair_q16<RT>(P.out, N, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
                        col_ok && zb < z1, uint32_t(xw), uint32_t(yw), uint32_t(za), uint32_t(zb),
@@ -576,7 +592,7 @@ static int choose_zchunk(int64_t tiles_xy, int nz, int64_t resident_blocks) {
 
 template <int STORAGE, bool FORCE, bool RT>
 static cudaError_t launch_fluid_t(KernelParams<STORAGE, RT>& p, cudaStream_t st) {
-  const size_t smem = HaloStage<STORAGE, FORCE>::SMEM;
+  const size_t smem = HaloStage<STORAGE == ST_MIXED ? ST_Q16 : STORAGE, FORCE>::SMEM;
   static int resident = 0;  // blocks resident on the whole GPU (device 0 of the process)
   if (!resident) {
     cudaError_t e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE, RT>,
@@ -637,6 +653,29 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
     q.f_w[k] = force ? reinterpret_cast<const uint32_t*>(force) + k * N : nullptr;
   return force ? launch_fluid_t<ST_F32, true, false>(q, st)
                : launch_fluid_t<ST_F32, false, false>(q, st);
+}
+
+// The fluid pass of the mixed-precision scheme: 16-bit post-collision moments
+// (stored variables rho - 1, u+, rho (S+ - u+ u+)) in, raw FP32 post-streaming
+// sums out.  The stored stress is already traceless, so the collision with
+// omega = 0 only rebuilds the Hermite moments.
+cudaError_t launch_fluid_mixed(int nx, int ny, int nz, const void* q_in, float* p_out,
+                               cudaStream_t st) {
+  KernelParams<ST_MIXED, false> k;
+  FluidParams& p = k;
+  p.nx = nx;
+  p.ny = ny;
+  p.nz = nz;
+  p.in = q_in;
+  p.out = p_out;
+  p.force = nullptr;
+  p.omega = 0.0f;
+  p.t_out = 0;
+  p.seed = 0;
+  p.chunk16 = 0;
+  const size_t N = size_t(nx) * ny * nz;
+  for (int w = 0; w < 10; ++w) k.out_w[w] = reinterpret_cast<uint32_t*>(p_out) + w * N;
+  return launch_fluid_t<ST_MIXED, false, false>(k, st);
 }
 
 }  // namespace melbm

@@ -17,7 +17,7 @@ namespace melbm {
 constexpr unsigned FULL = 0xffffffffu;
 
 enum : uint8_t { T_FLUID = 0, T_FLUID_BOUNDARY = 1, T_INFLOW = 2, T_OUTFLOW = 3, T_SOLID = 4 };
-enum { ST_F32 = 0, ST_Q16 = 1 };
+enum { ST_F32 = 0, ST_Q16 = 1, ST_MIXED = 2 };  // MIXED: 16-bit post-collision + FP32 post-streaming
 
 // ----------------------------------------------------------------- scalar / pair math
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }

@@ -49,6 +49,21 @@ cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, vo
                          const float* force, float omega, uint32_t t_out, uint32_t seed,
                          const QGrids& q, cudaStream_t st);
 
+// The mixed-precision scheme (mixed.cu): fluid pass Q -> P (fluid.cu), solid
+// correction with atomicAdd into P, collision + quantisation P -> Q, and the
+// public-state conversions of P.
+cudaError_t launch_fluid_mixed(int nx, int ny, int nz, const void* q_in, float* p_out,
+                               cudaStream_t st);
+cudaError_t launch_mixed_correct(int nx, int ny, int nz, const void* q, float* p,
+                                 const uint32_t* cells, const uint32_t* words, int64_t count,
+                                 const float inflow[4], cudaStream_t st);
+cudaError_t launch_mixed_collide_quantize(int nx, int ny, int nz, const float* p, void* q,
+                                          float omega, uint32_t t, uint32_t seed, cudaStream_t st);
+cudaError_t launch_mixed_set_state(int64_t N, const float* rho, const float* u, const float* S,
+                                   float* p, cudaStream_t st);
+cudaError_t launch_mixed_get_moments(int64_t N, const float* p, float* rho, float* u, float* S,
+                                     cudaStream_t st);
+
 // Boundary update over the list: phase A collides the S source cells and keeps
 // their 27 populations in pop[27][S] (sources.cu), then the boundary kernel
 // recomputes every listed cell (bounce-back through its 27 source slots in

@@ -31,9 +31,17 @@ __global__ void __launch_bounds__(RD_THREADS) reduce_partial_kernel(int64_t N, c
   for (int64_t n = int64_t(blockIdx.x) * RD_THREADS + threadIdx.x; n < N;
        n += int64_t(gridDim.x) * RD_THREADS) {
     if (type && type[n] == T_SOLID) continue;
-    const Stored s = load_stored<STORAGE>(buf, size_t(N), size_t(n), q);
-    const double rho = 1.0 + double(s.drho);
-    const double u2 = double(s.ux) * s.ux + double(s.uy) * s.uy + double(s.uz) * s.uz;
+    double rho, u2;
+    if constexpr (STORAGE == ST_MIXED) {  // raw post-streaming sums rho - 1, rho u
+      const float* p = static_cast<const float*>(buf);
+      rho = 1.0 + double(p[n]);
+      const double jx = p[N + n], jy = p[2 * N + n], jz = p[3 * N + n];
+      u2 = (jx * jx + jy * jy + jz * jz) / (rho * rho);
+    } else {
+      const Stored s = load_stored<STORAGE>(buf, size_t(N), size_t(n), q);
+      rho = 1.0 + double(s.drho);
+      u2 = double(s.ux) * s.ux + double(s.uy) * s.uy + double(s.uz) * s.uz;
+    }
     mass += rho;
     ke += 0.5 * rho * u2;
     if (STORAGE == ST_Q16) {
@@ -80,6 +88,8 @@ cudaError_t launch_reduce(int storage, int64_t N, const void* buf, const uint8_t
                           double* partials, double* out, const QGrids& q, cudaStream_t st) {
   if (storage == ST_Q16)
     reduce_partial_kernel<ST_Q16><<<RD_BLOCKS, RD_THREADS, 0, st>>>(N, buf, type, partials, q);
+  else if (storage == ST_MIXED)
+    reduce_partial_kernel<ST_MIXED><<<RD_BLOCKS, RD_THREADS, 0, st>>>(N, buf, type, partials, q);
   else
     reduce_partial_kernel<ST_F32><<<RD_BLOCKS, RD_THREADS, 0, st>>>(N, buf, type, partials, q);
   cudaError_t e = cudaGetLastError();

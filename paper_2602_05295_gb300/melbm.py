@@ -21,9 +21,9 @@ import torch
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, WSATURATED = 0, 1, 2, 3, 4, 5
-F32, Q16 = 0, 1
+F32, Q16, MIXED = 0, 1, 2
 FLUID, FLUID_BOUNDARY, INFLOW, OUTFLOW, SOLID = 0, 1, 2, 3, 4
-_STORAGE = {"f32": F32, "q16": Q16}
+_STORAGE = {"f32": F32, "q16": Q16, "mixed": MIXED}
 
 _lib = None
 
@@ -135,7 +135,8 @@ def _stream_ptr(stream):
 class Simulator:
     """One moment-encoded LBM simulation on the current CUDA device.
 
-    ``storage`` is ``"f32"`` or ``"q16"`` (the paper's 16-bit form).  Work is
+    ``storage`` is ``"f32"``, ``"q16"`` (the paper's 16-bit form) or ``"mixed"``
+    (the paper's mixed-precision scheme with solids, kept for comparison).  Work is
     enqueued on ``stream`` (default: torch's current stream at construction)."""
 
     def __init__(self, shape, tau, storage="q16", stream=None, seed=0):
