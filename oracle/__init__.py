@@ -77,6 +77,8 @@ def lib():
             L.orc_decode.argtypes = [I64, P, P]
             L.orc_encode_bits.argtypes = [I, I, I, P, U32, U32, I, I, I, P]
             L.orc_step_wall_f64.argtypes = [I, I, I, D, P, P, P, P, I, P, P, P]
+            L.orc_step19_f64.argtypes = [I, I, I, D, P, P, P]
+            L.orc_reconstruct19.argtypes = [P, P, P, P]
             L.orc_solid_force_f64.argtypes = [I, I, I, D, P, P, P, I, P, P, I, P]
             L.orc_decode_bits.argtypes = [I64, P, I, I, P]
             L.orc_codec_constants_bits.argtypes = [I, I, I, P]
@@ -198,6 +200,27 @@ def step(m, shape, tau, F=None, typ=None, inflow=None, n=1, literal_xyz=False, w
                                     wall.model, _p(wall.body), _p(wall.table), _p(out))
         cur, out = out, cur
     return cur
+
+
+def step19(m, shape, tau, F=None, n=1):
+    """n FP64 periodic D3Q19 steps of the public state ``m`` (10, N)."""
+    nx, ny, nz = shape
+    cur = _f64(m).copy()
+    out = np.empty_like(cur)
+    Fa = _f64(F)
+    for _ in range(n):
+        lib().orc_step19_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(out))
+        cur, out = out, cur
+    return cur
+
+
+def reconstruct19(m10):
+    """(f[19], c[19, 3], w[19]) of the D3Q19 reconstruction of one moment set."""
+    f = np.empty(19)
+    c = np.empty((19, 3), np.int32)
+    w = np.empty(19)
+    lib().orc_reconstruct19(_p(np.ascontiguousarray(m10, np.float64)), _p(f), _p(c), _p(w))
+    return f, c, w
 
 
 def solid_force(m, shape, tau, typ, wall, F=None, body_id=0):

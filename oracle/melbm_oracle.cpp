@@ -19,6 +19,9 @@
 //                     or the moment-based reconstruction at moving solid walls,
 //                     and the momentum-exchange force and torque  (Sec. 3.2, solid coupling)
 //   * codec:          range, normalisation, dithered rounding to 16 bits (Sec. 5.4)
+//   * D3Q19:          the same moments and collision on the 19-velocity lattice
+//                     (Table 1's D3Q19 scene), periodic, with the third-order
+//                     reconstruction projected on what that lattice carries
 //
 // Readings of the paper that it takes (each is also listed in the design notes):
 //   * the xyz third-order Hermite term carries 1/c_s^6 (the other six triples
@@ -322,6 +325,110 @@ void step_grid(const Grid& g, double tau, const T* m, const T* F, const uint8_t*
       const int64_t s = n - 1;  // (nx-2, y, z): the outflow plane is x = nx-1
       store(out, N, n, load(out, N, s));
     }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// D3Q19 (Sec. 6.3, Table 1 "Yeahright (D3Q19)"): the 19 velocities with
+// |c|^2 <= 2, weights 1/3, 1/18, 1/36, c_s^2 = 1/3.  The collision (App. A) and
+// the moments (Eq. rho_u_stress) are the same.  The paper does not give the
+// reconstruction on this lattice; the reading taken is the orthogonal projection
+// of Eq. three_order_f on the polynomials the lattice carries: H3_xyz vanishes on
+// every D3Q19 velocity, and H3_aab and H3_bgg (the two triples with the same
+// single index b) are not orthogonal there, while their sum and difference are,
+// with lattice norms 2 c_s^6 and 6 c_s^6.  So
+//   f_i = rho w_i [1 + c.u/cs2 + H2:S/(2 cs2^2)
+//           + sum_b ((T_aab + T_bgg) (H3_aab + H3_bgg) / (2 cs2^3)
+//                  + (T_aab - T_bgg) (H3_aab - H3_bgg) / (6 cs2^3))],
+// which reproduces rho, rho u, rho S and the six rho T_aab exactly.
+// Direction index: the D3Q27 index i with |c_i|^2 <= 2, in ascending order.
+// ----------------------------------------------------------------------------
+struct Lattice19 {
+  int c[19][3];
+  double w[19];
+  int opp[19];
+  Lattice19() {
+    int k = 0;
+    for (int i = 0; i < 27; ++i) {
+      const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+      if (cx * cx + cy * cy + cz * cz > 2) continue;
+      c[k][0] = cx;
+      c[k][1] = cy;
+      c[k][2] = cz;
+      const int n2 = cx * cx + cy * cy + cz * cz;
+      w[k] = n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+      ++k;
+    }
+    for (int a = 0; a < 19; ++a)
+      for (int b = 0; b < 19; ++b)
+        if (c[b][0] == -c[a][0] && c[b][1] == -c[a][1] && c[b][2] == -c[a][2]) opp[a] = b;
+  }
+};
+const Lattice19 L19;
+
+// The three pairs of triples sharing the single index b: (a a b, b g g).
+const int PAIRS19[3][2][3] = {{{0, 0, 1}, {1, 2, 2}},   // b = y: xxy, yzz
+                              {{0, 1, 1}, {0, 2, 2}},   // b = x: xyy, xzz
+                              {{0, 0, 2}, {1, 1, 2}}};  // b = z: xxz, yyz
+
+template <class T>
+T reconstruct19(int i, const Mom<T>& m) {
+  const int* c = L19.c[i];
+  T cu = 0.0;
+  for (int a = 0; a < 3; ++a) cu += double(c[a]) * m.u[a];
+  T h2 = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) h2 += H2(a, b, c) * m.S[sidx(a, b)];
+  T h3 = 0.0;
+  for (int p = 0; p < 3; ++p) {
+    const int* t1 = PAIRS19[p][0];
+    const int* t2 = PAIRS19[p][1];
+    const T T1 = Tabg(m, t1[0], t1[1], t1[2]), T2 = Tabg(m, t2[0], t2[1], t2[2]);
+    const double H1 = H3(t1[0], t1[1], t1[2], c), Hb = H3(t2[0], t2[1], t2[2], c);
+    h3 += (T1 + T2) * (H1 + Hb) / (2.0 * CS2 * CS2 * CS2) +
+          (T1 - T2) * (H1 - Hb) / (6.0 * CS2 * CS2 * CS2);
+  }
+  return m.rho * L19.w[i] * (1.0 + cu / CS2 + h2 / (2.0 * CS2 * CS2) + h3);
+}
+
+template <class T>
+Mom<T> moments19(const T* f, const T F[3]) {
+  Mom<T> o;
+  T rho = 0.0, J[3] = {0.0, 0.0, 0.0}, P[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i < 19; ++i) {
+    rho += f[i];
+    for (int a = 0; a < 3; ++a) J[a] += double(L19.c[i][a]) * f[i];
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b) P[sidx(a, b)] += H2(a, b, L19.c[i]) * f[i];
+  }
+  o.rho = rho;
+  for (int a = 0; a < 3; ++a) o.u[a] = (J[a] + 0.5 * F[a]) / rho;
+  for (int k = 0; k < 6; ++k) o.S[k] = P[k] / rho;
+  return o;
+}
+
+// One periodic D3Q19 step: collide every cell, pull the 19 populations, moments.
+void step_grid19(const Grid& g, double tau, const double* m, const double* F, double* out) {
+  const int64_t N = g.N();
+  std::vector<Mom<double>> mp(N);
+#pragma omp parallel for schedule(static)
+  for (int64_t n = 0; n < N; ++n) {
+    double Fx[3];
+    load_force(F, N, n, Fx);
+    mp[n] = collide(load(m, N, n), Fx, tau);
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t n = 0; n < N; ++n) {
+    const int x = int(n % g.nx), y = int((n / g.nx) % g.ny), z = int(n / (int64_t(g.nx) * g.ny));
+    double f[19];
+    for (int i = 0; i < 19; ++i) {
+      const int sx = (x - L19.c[i][0] + g.nx) % g.nx, sy = (y - L19.c[i][1] + g.ny) % g.ny,
+                sz = (z - L19.c[i][2] + g.nz) % g.nz;
+      f[i] = reconstruct19(i, mp[g.idx(sx, sy, sz)]);
+    }
+    double Fx[3];
+    load_force(F, N, n, Fx);
+    store(out, N, n, moments19(f, Fx));
   }
 }
 
@@ -663,6 +770,26 @@ int64_t orc_classify(int nx, int ny, int nz, const uint8_t* mask, int inflow, in
 void orc_step_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
                   const uint8_t* type, const double* inflow, int literal_xyz, double* out) {
   step_grid<double>(Grid{nx, ny, nz}, tau, m, F, type, inflow, out, literal_xyz);
+}
+
+// One periodic D3Q19 step (public state, component-major 10 x N).
+void orc_step19_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                    double* out) {
+  step_grid19(Grid{nx, ny, nz}, tau, m, F, out);
+}
+
+// D3Q19 populations of one moment set (rho, u[3], S[6]) and its 19 velocities
+// and weights (for the moment-identity pins).
+void orc_reconstruct19(const double* m10, double* f19, int* c57, double* w19) {
+  Mom<double> m;
+  m.rho = m10[0];
+  for (int a = 0; a < 3; ++a) m.u[a] = m10[1 + a];
+  for (int k = 0; k < 6; ++k) m.S[k] = m10[4 + k];
+  for (int i = 0; i < 19; ++i) {
+    f19[i] = reconstruct19(i, m);
+    for (int a = 0; a < 3; ++a) c57[3 * i + a] = L19.c[i][a];
+    w19[i] = L19.w[i];
+  }
 }
 
 // The step with the wall model of WallSpec (body ids and the 256 x 9 motion table).

@@ -776,3 +776,115 @@ def test_q16_emulation_tracks_fp64(orc):
     du = np.abs(pub[1:4] - ref[1:4]).max() / np.abs(ref[1:4]).max()
     assert du < 2e-3, du
     assert abs(pub[0].sum() - M0) / M0 < 1e-6
+
+
+# ------------------------------------------------------------------ D3Q19
+TRIPLES19 = [(0, 0, 1), (1, 2, 2), (0, 1, 1), (0, 2, 2), (0, 0, 2), (1, 1, 2)]
+
+
+def _h3(c, a, b, g):
+    c = c.astype(float)
+    return (c[:, a] * c[:, b] * c[:, g]
+            - CS2 * (c[:, a] * (b == g) + c[:, b] * (a == g) + c[:, g] * (a == b)))
+
+
+def _T(m, a, b, g):
+    S, u = m[4:], m[1:4]
+    return (sget(S, a, b) * u[g] + sget(S, a, g) * u[b] + sget(S, b, g) * u[a]
+            - 2 * u[a] * u[b] * u[g])
+
+
+def test_d3q19_lattice_is_the_textbook_lattice(orc):
+    """19 velocities |c|^2 <= 2, weights 1/3, 1/18, 1/36; summed over c_z they give
+    App. D's D2Q9 weights; isotropic to 4th order with c_s^2 = 1/3."""
+    _, c, w = orc.reconstruct19(np.array([1.0, 0, 0, 0, 0, 0, 0, 0, 0, 0]))
+    n2 = (c ** 2).sum(1)
+    assert len(c) == 19 and len({tuple(v) for v in c}) == 19 and n2.max() == 2
+    assert np.all(w[n2 == 0] == 1 / 3) and np.all(w[n2 == 1] == 1 / 18) and np.all(w[n2 == 2] == 1 / 36)
+    g = GOLD["d2q9"]
+    for cx, cy, num, den in zip(g["cx"], g["cy"], g["w_num"], g["w_den"]):
+        sel = (c[:, 0] == cx) & (c[:, 1] == cy)
+        assert abs(w[sel].sum() - num / den) < 1e-15
+    for a, b in itertools.product(range(3), repeat=2):
+        assert abs((w * c[:, a] * c[:, b]).sum() - CS2 * (a == b)) < 1e-15
+    assert abs((w * c[:, 0] ** 2 * c[:, 1] ** 2).sum() - CS2 ** 2) < 1e-15
+    assert abs((w * c[:, 0] ** 4).sum() - 3 * CS2 ** 2) < 1e-15
+    # the xyz Hermite polynomial vanishes on every D3Q19 velocity
+    assert np.all(_h3(c, 0, 1, 2) == 0)
+
+
+def test_d3q19_reconstruction_is_the_unique_moment_matching_polynomial(orc):
+    """f / w lies in the span of {1, H1, H2, H3_aab for the six triples with a
+    repeated index} and reproduces rho, rho u, rho S and rho T_aab: 16 linear
+    conditions with a non-singular Gram matrix on the lattice, so f is fixed by
+    them alone (independently of how the projection is written)."""
+    rng = np.random.default_rng(31)
+    _, c, w = orc.reconstruct19(np.zeros(10) + [1, 0, 0, 0, 0, 0, 0, 0, 0, 0])
+    cf = c.astype(float)
+    basis = [np.ones(19)] + [cf[:, a] for a in range(3)]
+    basis += [cf[:, a] * cf[:, b] - CS2 * (a == b) for a, b in PAIRS]
+    basis += [_h3(c, *t) for t in TRIPLES19]
+    B = np.array(basis).T  # (19, 16)
+    G = B.T @ (w[:, None] * B)
+    assert np.linalg.matrix_rank(G) == 16
+    for m in random_cells(24, rng):
+        f, _, _ = orc.reconstruct19(m)
+        coef, *_ = np.linalg.lstsq(B, f / w, rcond=None)
+        assert np.abs(B @ coef - f / w).max() < 1e-13
+        rho = m[0]
+        assert abs(f.sum() - rho) < 1e-14
+        assert np.abs(cf.T @ f - rho * m[1:4]).max() < 1e-14
+        for k, (a, b) in enumerate(PAIRS):
+            assert abs(((cf[:, a] * cf[:, b] - CS2 * (a == b)) * f).sum() - rho * m[4 + k]) < 1e-14
+        for t in TRIPLES19:
+            assert abs((_h3(c, *t) * f).sum() - rho * _T(m, *t)) < 1e-14, t
+        assert abs((_h3(c, 0, 1, 2) * f).sum()) < 1e-15
+
+
+def test_d3q19_step_conserves_mass_and_gains_the_force(orc):
+    rng = np.random.default_rng(32)
+    shape = (6, 5, 4)
+    m = random_state(shape, rng)
+    F = 1e-4 * rng.standard_normal((3, 120))
+    P0 = (m[0] * m[1:4]).sum(1)
+    out = orc.step19(m, shape, 0.55, F=F, n=9)
+    assert abs(out[0].sum() - m[0].sum()) / m[0].sum() < 1e-13
+    assert np.abs((out[0] * out[1:4]).sum(1) - P0 - 9 * F.sum(1)).max() < 1e-13
+
+
+def test_d3q19_uniform_flow_is_fixed_point_and_symmetries(orc):
+    U = np.array([0.1, -0.05, 0.07])
+    m = eq_state(1.02, np.repeat(U[:, None], 64, 1))
+    assert np.abs(orc.step19(m, (4, 4, 4), 0.52, n=3) - m).max() < 2e-15
+    n = 5
+    rng = np.random.default_rng(33)
+    m = random_state((n, n, n), rng, du=0.08, ds=0.01)
+    F = 1e-3 * rng.standard_normal((3, n ** 3))
+    pad = lambda v: np.concatenate([np.zeros((1, n ** 3)), v, np.zeros((6, n ** 3))])
+    a = orc.step19(_perm_state(m, n), (n, n, n), 0.57, F=_perm_state(pad(F), n)[1:4])
+    b = _perm_state(orc.step19(m, (n, n, n), 0.57, F=F), n)
+    assert np.abs(a - b).max() < 1e-15
+    a = orc.step19(_mirror_x(m, n), (n, n, n), 0.57, F=_mirror_x(pad(F), n)[1:4])
+    b = _mirror_x(orc.step19(m, (n, n, n), 0.57, F=F), n)
+    assert np.abs(a - b).max() < 1e-15
+
+
+def test_d3q19_taylor_green_decay_rate(orc):
+    """Same workload as the D3Q27 pin: the shear viscosity nu = c_s^2 (tau - 1/2)
+    does not depend on the velocity set."""
+    wl = W.TGV32
+    u, k = W.taylor_green(wl.shape, 0.05)
+    cur = eq_state(1.0, W.flat(u))
+    nx, ny, nz = wl.shape
+    x = np.arange(nx)[None, None, :]
+    y = np.arange(ny)[None, :, None]
+    mode = (np.sin(k * x) * np.cos(k * y) * np.ones((nz, 1, 1))).ravel()
+    amps, ts = [], []
+    for t in range(0, 101, 10):
+        if t:
+            cur = orc.step19(cur, wl.shape, wl.tau, n=10)
+        if t >= 20:
+            amps.append((cur[1] * mode).sum() / (mode * mode).sum())
+            ts.append(t)
+    nu_fit = -np.polyfit(ts, np.log(amps), 1)[0] / (2 * k * k)
+    assert abs(nu_fit / (CS2 * (wl.tau - 0.5)) - 1) < 0.01, nu_fit
