@@ -57,13 +57,13 @@ typedef enum melbm_status {
   MELBM_WSATURATED = 5   /* warning: some 16-bit codes sit on the range limits */
 } melbm_status;
 
-enum { MELBM_D3Q27 = 27 };
+enum { MELBM_D3Q27 = 27, MELBM_D3Q19 = 19 };
 enum { MELBM_F32 = 0, MELBM_Q16 = 1, MELBM_MIXED = 2 };
 /* cell types, priority SOLID > INFLOW > OUTFLOW > FLUID_BOUNDARY > FLUID */
 enum { MELBM_FLUID = 0, MELBM_FLUID_BOUNDARY = 1, MELBM_INFLOW = 2, MELBM_OUTFLOW = 3,
        MELBM_SOLID = 4 };
 
-/* Create a simulation (Sec. 4.2).  lattice must be MELBM_D3Q27; tau > 1/2 is the
+/* Create a simulation (Sec. 4.2).  lattice is MELBM_D3Q27 or MELBM_D3Q19; tau > 1/2 is the
  * relaxation time (nu = (tau - 1/2)/3); storage is MELBM_F32 (40 B/cell per
  * buffer) or MELBM_Q16 (20 B/cell per buffer, Sec. 5.4).  Allocates two state
  * buffers on the current device, initialised to rest (rho = 1, u = 0, S = 0).
@@ -75,7 +75,16 @@ enum { MELBM_FLUID = 0, MELBM_FLUID_BOUNDARY = 1, MELBM_INFLOW = 2, MELBM_OUTFLO
  * re-quantisation.  It supports solids, inflow and outflow, but not forces, bit
  * widths, the moving-wall model, solid forces, raw state or the adjoint
  * (MELBM_EINVAL).  N must be below 2^31.  *out receives the handle (NULL on
- * failure). */
+ * failure).
+ * MELBM_D3Q19 (the 19-velocity lattice of Table 1's D3Q19 scene) keeps the same
+ * ten stored moments, collision and storage forms; its post-collision populations
+ * are the third-order Hermite expansion projected on the polynomials that lattice
+ * carries (the xyz term vanishes on it; each pair of triples T_aab, T_bgg enters
+ * through its sum and difference), which reproduces rho, rho u, rho S and the six
+ * rho T_aab.  A D3Q19 handle is periodic in all three directions, with or without
+ * a body force, in MELBM_F32 or MELBM_Q16 storage (any bit widths); solids,
+ * inflow, outflow, the moving-wall model, solid forces, the adjoint and
+ * MELBM_MIXED are refused with MELBM_EINVAL. */
 MELBM_API int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, melbm_t* out);
 
 /* Free every device and host resource of the handle.  NULL is accepted. */

@@ -78,6 +78,7 @@ def lib():
             L.orc_encode_bits.argtypes = [I, I, I, P, U32, U32, I, I, I, P]
             L.orc_step_wall_f64.argtypes = [I, I, I, D, P, P, P, P, I, P, P, P]
             L.orc_step19_f64.argtypes = [I, I, I, D, P, P, P]
+            L.orc_step19_cells_f64.argtypes = [I, I, I, D, P, P, P, I64, P]
             L.orc_reconstruct19.argtypes = [P, P, P, P]
             L.orc_solid_force_f64.argtypes = [I, I, I, D, P, P, P, I, P, P, I, P]
             L.orc_decode_bits.argtypes = [I64, P, I, I, P]
@@ -212,6 +213,16 @@ def step19(m, shape, tau, F=None, n=1):
         lib().orc_step19_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(out))
         cur, out = out, cur
     return cur
+
+
+def step19_cells(m, shape, tau, cells, F=None):
+    """The periodic D3Q19 update of the listed cells: (10, len(cells))."""
+    nx, ny, nz = shape
+    ma = _f64(m)
+    ca = np.ascontiguousarray(cells, np.int64)
+    out = np.empty((len(ca), 10))
+    lib().orc_step19_cells_f64(nx, ny, nz, float(tau), _p(ma), _p(_f64(F)), _p(ca), len(ca), _p(out))
+    return out.T.copy()
 
 
 def reconstruct19(m10):
@@ -369,12 +380,15 @@ def decode(q, bits=BITS16):
     return v
 
 
-def q16_step(codes, shape, tau, t_out, seed, F=None, typ=None, inflow=None, bits=BITS16):
+def q16_step(codes, shape, tau, t_out, seed, F=None, typ=None, inflow=None, bits=BITS16, lattice=27):
     """One step of the quantised form: decode, FP64 step, FP32 re-encode with the
     dither of time index ``t_out``.  Solid cells keep their codes; outflow cells
-    take the codes of (nx-2, y, z)."""
+    take the codes of (nx-2, y, z).  ``lattice=19``: the periodic D3Q19 step."""
     pub = stored_to_public(decode(codes, bits))
-    new = step(pub, shape, tau, F=F, typ=typ, inflow=inflow)
+    if lattice == 19:
+        new = step19(pub, shape, tau, F=F)
+    else:
+        new = step(pub, shape, tau, F=F, typ=typ, inflow=inflow)
     q = encode(stored_for_codec(public_to_stored(new)), shape, t_out, seed, bits=bits)
     if typ is not None:
         solid = typ == SOLID

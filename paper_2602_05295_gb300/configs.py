@@ -86,6 +86,27 @@ def run_turbulence256(steps):
     return out
 
 
+def run_turbulence256_d3q19(steps):
+    """The 256^3 turbulence workload on the D3Q19 lattice (same stored moments and
+    storage forms; the 19-velocity reconstruction), beside the D3Q27 figures of
+    run_turbulence256."""
+    wl = W.TURB256
+    rho, u = _state_from_velocity(W.flat(W.random_phase_field(wl.shape, 0.08)))
+    out = []
+    for storage in ("q16", "f32"):
+        sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602, lattice=19)
+        sim.set_state(rho, u)
+        M0, E0 = sim.reduce()
+        ms = _timed_steps(sim, steps)
+        M1, E1 = sim.reduce()
+        out.append({"workload": wl.name + "_d3q19", "storage": storage, "cells": wl.cells,
+                    "ms_per_step": ms, "MLUPS": wl.cells / ms / 1e3,
+                    "memory_bytes": sim.memory_bytes(), "steps_run": steps + 3,
+                    "mass_drift": (M1 - M0) / M0, "ke_ratio": E1 / E0})
+        sim.close()
+    return out
+
+
 def _channel(wl, mask, inflow_u, steps, storage="q16"):
     sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602)
     N = wl.cells
@@ -260,7 +281,8 @@ def run_bits_sweep(steps):
     return out
 
 
-RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256, "channel512": run_channel512,
+RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256,
+           "turbulence256_d3q19": run_turbulence256_d3q19, "channel512": run_channel512,
            "channel512_moving": run_channel512_moving, "large1000": run_large1000, "adjoint128": run_adjoint128, "bits_sweep": run_bits_sweep,
            "mixed_vs_recompute": run_mixed_vs_recompute}
 

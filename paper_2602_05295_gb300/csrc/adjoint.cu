@@ -382,6 +382,8 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
   if (nsteps < 1 || K < 1) return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: nsteps and K must be >= 1");
   if (h->storage != MELBM_F32)
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: requires MELBM_F32 storage");
+  if (h->lattice != MELBM_D3Q27)
+    return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: requires the D3Q27 lattice");
   if (h->wall_model != 0)
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: the adjoint covers halfway bounce-back walls only");
   const size_t N = size_t(h->N);

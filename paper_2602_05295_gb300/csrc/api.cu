@@ -92,6 +92,10 @@ int mixed_unsupported(melbm_t h, const char* what) {
   return fail(h, MELBM_EINVAL, "%s: not available with MELBM_MIXED storage", what);
 }
 
+int q19_unsupported(melbm_t h, const char* what) {
+  return fail(h, MELBM_EINVAL, "%s: D3Q19 handles are periodic (no solids, inflow, outflow, walls)", what);
+}
+
 int ensure_staging(melbm_t h, size_t bytes) {
   if (h->staging_bytes >= bytes) return MELBM_OK;
   dev_free(h, h->staging, h->staging_bytes);
@@ -191,6 +195,9 @@ int reclassify(melbm_t h) {
 namespace melbm {
 cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out) {
   const float omega = 1.0f / h->tau;
+  if (h->lattice == MELBM_D3Q19)
+    return launch_fluid19(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out, h->seed,
+                          h->grids, h->stream);
   cudaError_t e = launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
                                h->seed, h->grids, h->stream);
   if (e == cudaSuccess && h->L)
@@ -209,8 +216,8 @@ extern "C" {
 int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, melbm_t* out) {
   if (!out) return fail(nullptr, MELBM_EINVAL, "melbm_create: out is NULL");
   *out = nullptr;
-  if (lattice != MELBM_D3Q27)
-    return fail(nullptr, MELBM_EINVAL, "melbm_create: lattice %d unsupported (only 27)", lattice);
+  if (lattice != MELBM_D3Q27 && lattice != MELBM_D3Q19)
+    return fail(nullptr, MELBM_EINVAL, "melbm_create: lattice %d unsupported (27 or 19)", lattice);
   if (nx < 1 || ny < 1 || nz < 1)
     return fail(nullptr, MELBM_EINVAL, "melbm_create: bad grid %d x %d x %d", nx, ny, nz);
   const int64_t N = int64_t(nx) * ny * nz;
@@ -220,6 +227,8 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
     return fail(nullptr, MELBM_EINVAL, "melbm_create: tau = %g must exceed 1/2", double(tau));
   if (storage != MELBM_F32 && storage != MELBM_Q16 && storage != MELBM_MIXED)
     return fail(nullptr, MELBM_EINVAL, "melbm_create: storage %d unknown", storage);
+  if (lattice == MELBM_D3Q19 && storage == MELBM_MIXED)
+    return fail(nullptr, MELBM_EINVAL, "melbm_create: MELBM_MIXED storage is D3Q27 only");
   melbm_sim* h = new (std::nothrow) melbm_sim;
   if (!h) return fail(nullptr, MELBM_ENOMEM, "melbm_create: host allocation failed");
   h->nx = nx;
@@ -228,6 +237,7 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
   h->N = N;
   h->tau = tau;
   h->storage = storage;
+  h->lattice = lattice;
   int rc;
   if ((rc = dev_alloc(h, &h->buf[0], buf_bytes(h, 0))) ||
       (rc = dev_alloc(h, &h->buf[1], buf_bytes(h, 1))) ||
@@ -357,6 +367,7 @@ int melbm_get_moments(melbm_t h, float* rho, float* u, float* S) {
 int melbm_set_solid(melbm_t h, const uint8_t* mask) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_solid: NULL handle");
   if (mask && !is_device_ptr(mask)) return fail(h, MELBM_EINVAL, "melbm_set_solid: mask must be a device pointer");
+  if (mask && h->lattice == MELBM_D3Q19) return q19_unsupported(h, "melbm_set_solid");
   if (!mask) {
     dev_free(h, h->mask, size_t(h->N));
     h->mask = nullptr;
@@ -370,6 +381,7 @@ int melbm_set_solid(melbm_t h, const uint8_t* mask) {
 
 int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float uz) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_inflow: NULL handle");
+  if (h->lattice == MELBM_D3Q19) return q19_unsupported(h, "melbm_set_inflow");
   if (face != 0) return fail(h, MELBM_EINVAL, "melbm_set_inflow: only face 0 (x = 0) is supported");
   if (!(rho > 0.f)) return fail(h, MELBM_EINVAL, "melbm_set_inflow: rho must be positive");
   h->inflow_on = 1;
@@ -382,6 +394,7 @@ int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float u
 
 int melbm_set_outflow(melbm_t h, int face) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_outflow: NULL handle");
+  if (h->lattice == MELBM_D3Q19) return q19_unsupported(h, "melbm_set_outflow");
   if (face != 1) return fail(h, MELBM_EINVAL, "melbm_set_outflow: only face 1 (x = nx-1) is supported");
   h->outflow_on = 1;
   return reclassify(h);
@@ -553,6 +566,7 @@ int melbm_codec_decode(const uint32_t* words, int64_t N, int bits_rho_u, int bit
 int melbm_set_wall_model(melbm_t h, int model) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_wall_model: NULL handle");
   if (h->storage == MELBM_MIXED && model != 0) return mixed_unsupported(h, "melbm_set_wall_model");
+  if (h->lattice == MELBM_D3Q19 && model != 0) return q19_unsupported(h, "melbm_set_wall_model");
   if (model != 0 && model != 1) return fail(h, MELBM_EINVAL, "melbm_set_wall_model: model %d unknown", model);
   if (!h->bodies) {
     int rc = dev_alloc(h, (void**)&h->bodies, 256 * 9 * 4);
@@ -588,6 +602,7 @@ int melbm_solid_force(melbm_t h, int body, double* out) {
   if (!h || !out) return fail(h, MELBM_EINVAL, "melbm_solid_force: NULL argument");
   if (body < 0 || body > 255) return fail(h, MELBM_EINVAL, "melbm_solid_force: body %d outside 0..255", body);
   if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_solid_force");
+  if (h->lattice == MELBM_D3Q19) return q19_unsupported(h, "melbm_solid_force");
   for (int k = 0; k < 6; ++k) out[k] = 0.0;
   if (!h->L || !h->mask) return MELBM_OK;
   int rc;

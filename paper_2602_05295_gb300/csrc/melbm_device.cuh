@@ -478,6 +478,40 @@ __device__ __forceinline__ Mom17T<T> collide_moments(const StoredT<T>& s, float 
   return A;
 }
 
+// D3Q19 (the 19-velocity set of Table 1's D3Q19 scene, |c|^2 <= 2): the
+// post-collision populations are the third-order Hermite expansion projected on
+// what that lattice carries (the xyz term vanishes there, and each pair
+// H_aab, H_bgg enters through its orthogonal sum and difference), which
+// reproduces rho, rho u, rho S and the six rho T_aab.  Extended by zero to the
+// eight corners they are a function on the D3Q27 cube, whose tensor moments
+// mu_pqr (rest state removed: mu_000 = rho - 1, mu_222 + 1/27) are those of
+// Mom17T with mu_111 = 0 plus the ten below; each follows from the populations'
+// vanishing at the corners, so c_a^2 c_b c_g and c_x^2 c_y^2 c_z^2 have zero sum,
+// and from the even part of the edge populations for sum c_a^2 c_b^2 f:
+//   mu_aabb = -mu_gg / 6,  mu_aabg = -mu_bg / 3,
+//   mu_aabbg = -(mu_aag + mu_bbg) / 3 - mu_g / 9,
+//   mu_xxyyzz = -mu_000 / 27 - (mu_xx + mu_yy + mu_zz) / 18.
+template <class T>
+struct Closure19T {
+  T m220, m202, m022, m211, m121, m112, m221, m212, m122, m222;
+};
+template <class T>
+__device__ __forceinline__ Closure19T<T> closure19(const Mom17T<T>& A) {
+  Closure19T<T> E;
+  E.m220 = vmulc(A.m002, -1.0f / 6.0f);
+  E.m202 = vmulc(A.m020, -1.0f / 6.0f);
+  E.m022 = vmulc(A.m200, -1.0f / 6.0f);
+  E.m211 = vmulc(A.m011, -1.0f / 3.0f);
+  E.m121 = vmulc(A.m101, -1.0f / 3.0f);
+  E.m112 = vmulc(A.m110, -1.0f / 3.0f);
+  E.m221 = vfmac(A.m001, -1.0f / 9.0f, vmulc(vadd(A.m201, A.m021), -1.0f / 3.0f));
+  E.m212 = vfmac(A.m010, -1.0f / 9.0f, vmulc(vadd(A.m210, A.m012), -1.0f / 3.0f));
+  E.m122 = vfmac(A.m100, -1.0f / 9.0f, vmulc(vadd(A.m120, A.m102), -1.0f / 3.0f));
+  E.m222 = vfmac(A.m000, -1.0f / 27.0f,
+                 vmulc(vadd(vadd(A.m200, A.m020), A.m002), -1.0f / 18.0f));
+  return E;
+}
+
 // f+_i / w_i - 1 from the Hermite moments: the coefficient of P_p P_q P_r is
 // mu_pqr divided by the D1Q3 norms (1, 1/3, 2/9) of each factor (P_2(c) = c^2 - 1/3).
 __device__ __forceinline__ float hermite_eval(const Mom17& A, int cx, int cy, int cz) {

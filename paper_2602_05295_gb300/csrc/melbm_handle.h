@@ -16,6 +16,7 @@ struct melbm_sim {
   int nx = 0, ny = 0, nz = 0;
   int64_t N = 0;
   int storage = 0;
+  int lattice = 27;  // 27 or 19 (periodic only)
   melbm::QGrids grids = melbm::make_qgrids(16, 16);  // bit widths of the quantised form
   float tau = 0.f;
   uint32_t seed = 0;

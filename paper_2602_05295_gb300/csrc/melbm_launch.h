@@ -48,6 +48,10 @@ inline bool qgrids_16(const QGrids& g) { return g.bits_ru == 16 && g.bits_s == 1
 cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, void* out,
                          const float* force, float omega, uint32_t t_out, uint32_t seed,
                          const QGrids& q, cudaStream_t st);
+// The same on the D3Q19 lattice (fluid19.cu; F32 or Q16 storage, periodic).
+cudaError_t launch_fluid19(int storage, int nx, int ny, int nz, const void* in, void* out,
+                           const float* force, float omega, uint32_t t_out, uint32_t seed,
+                           const QGrids& q, cudaStream_t st);
 
 // The mixed-precision scheme (mixed.cu): fluid pass Q -> P (fluid.cu), solid
 // correction with atomicAdd into P, collision + quantisation P -> Q, and the

@@ -136,17 +136,20 @@ class Simulator:
     """One moment-encoded LBM simulation on the current CUDA device.
 
     ``storage`` is ``"f32"``, ``"q16"`` (the paper's 16-bit form) or ``"mixed"``
-    (the paper's mixed-precision scheme with solids, kept for comparison).  Work is
-    enqueued on ``stream`` (default: torch's current stream at construction)."""
+    (the paper's mixed-precision scheme with solids, kept for comparison).
+    ``lattice`` is 27 (D3Q27) or 19 (D3Q19: periodic, with or without a force,
+    ``"f32"`` or ``"q16"``).  Work is enqueued on ``stream`` (default: torch's
+    current stream at construction)."""
 
-    def __init__(self, shape, tau, storage="q16", stream=None, seed=0):
+    def __init__(self, shape, tau, storage="q16", stream=None, seed=0, lattice=27):
         nx, ny, nz = (int(v) for v in shape)
         self.shape = (nx, ny, nz)
         self.N = nx * ny * nz
         self.tau = float(tau)
         self.storage = storage
+        self.lattice = int(lattice)
         h = ctypes.c_void_p()
-        _check(lib().melbm_create(nx, ny, nz, 27, ctypes.c_float(tau), _STORAGE[storage],
+        _check(lib().melbm_create(nx, ny, nz, self.lattice, ctypes.c_float(tau), _STORAGE[storage],
                                   ctypes.byref(h)))
         self._h = h
         self.stream = stream if stream is not None else torch.cuda.current_stream()

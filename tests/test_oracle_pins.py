@@ -888,3 +888,13 @@ def test_d3q19_taylor_green_decay_rate(orc):
             ts.append(t)
     nu_fit = -np.polyfit(ts, np.log(amps), 1)[0] / (2 * k * k)
     assert abs(nu_fit / (CS2 * (wl.tau - 0.5)) - 1) < 0.01, nu_fit
+
+
+def test_d3q19_sampled_cells_agree_with_full_step(orc):
+    rng = np.random.default_rng(34)
+    shape = (7, 5, 6)
+    m = random_state(shape, rng)
+    F = 1e-4 * rng.standard_normal((3, 210))
+    full = orc.step19(m, shape, 0.6, F=F)
+    cells = np.array([0, 1, 6, 7, 34, 35, 100, 209])
+    assert np.abs(orc.step19_cells(m, shape, 0.6, cells, F=F) - full[:, cells]).max() < 1e-15
