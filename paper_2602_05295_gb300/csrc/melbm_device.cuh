@@ -618,9 +618,10 @@ __device__ __forceinline__ PhiT<T> phi3(T mu0, T mu1, T mu2) {
   return r;
 }
 // Projection after streaming: pl = phi_+ pulled from the minus side, z = own
-// phi_0, mr = phi_- pulled from the plus side.
+// phi_0, mr = phi_- pulled from the plus side.  m0 is summed as (pl + mr) + z so
+// that m2 reuses pl + mr.
 template <class T>
-__device__ __forceinline__ T proj0(T pl, T z, T mr) { return vadd(vadd(pl, z), mr); }
+__device__ __forceinline__ T proj0(T pl, T z, T mr) { return vadd(vadd(pl, mr), z); }
 template <class T>
 __device__ __forceinline__ T proj1(T pl, T mr) { return vsub(pl, mr); }
 template <class T>
