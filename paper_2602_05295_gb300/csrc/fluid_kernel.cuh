@@ -651,21 +651,28 @@ inline int choose_zchunk(int64_t tiles_xy, int nz, int64_t resident_blocks) {
 template <int STORAGE, bool FORCE, bool RT, bool Q19 = false>
 cudaError_t launch_fluid_t(KernelParams<STORAGE, RT>& p, cudaStream_t st) {
   const size_t smem = HaloStage<STORAGE == ST_MIXED ? ST_Q16 : STORAGE, FORCE, Q19>::SMEM;
-  static int resident = 0;  // blocks resident on the whole GPU (device 0 of the process)
-  if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE, RT, Q19>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    int dev = 0, sms = 0, per_sm = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  // per device: the shared-memory opt-in of this instantiation and the number of
+  // its blocks resident on the whole GPU (set once; a racing first call writes
+  // the same values)
+  constexpr int MAX_DEV = 64;
+  static int resident[MAX_DEV] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
+  if (!resident[dev]) {
+    int sms = 0, per_sm = 0;
+    e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE, RT, Q19>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_kernel<STORAGE, FORCE, RT, Q19>,
                                                         FX * FY, smem);
     if (e != cudaSuccess) return e;
-    resident = std::max(1, sms * per_sm);
+    resident[dev] = std::max(1, sms * per_sm);
   }
   const int64_t tiles_xy = int64_t((p.nx + FX - 1) / FX) * ((p.ny + FYI - 1) / FYI);
-  p.zc = choose_zchunk(tiles_xy, p.nz, resident);
+  p.zc = choose_zchunk(tiles_xy, p.nz, resident[dev]);
   dim3 grid((p.nx + FX - 1) / FX, (p.ny + FYI - 1) / FYI, (p.nz + p.zc - 1) / p.zc);
   fluid_kernel<STORAGE, FORCE, RT, Q19><<<grid, dim3(FX, FY), smem, st>>>(p);
   return cudaGetLastError();
