@@ -2,18 +2,22 @@
 // 16-bit checkpointing (the paper has no adjoint; inverse design motivates it,
 // Sec. 1).  One forward step is  m' = Fin(Stream(Coll(m, F)), F)  per cell, with
 // bounce-back, inflow and outflow applied by the boundary kernels.  Its
-// vector-Jacobian product is taken in two per-cell kernels:
-//   1. fin_vjp:  lambda_M = (dFin/dM)^T lambda'   (and dL/dF from the F/2 of
-//      Eq. rho_u_stress), zero for solid, inflow and outflow cells;
-//   2. stream_collide_vjp, in gather form: the source cell y collects, from each
-//      destination y + c_i that pulled population i from it, the adjoint of that
-//      population, lambda_f_i = (dM/df_i)^T lambda_M(y + c_i), maps it back onto
-//      its 17 Hermite moments with df_i/dmu (the transpose of the pull of
-//      Eq. streaming), adds the bounce-back terms f_i(y) = f+_opp(i)(y) of its own
-//      solid links, and applies (dColl/dm)^T (App. A transposed by hand).
+// vector-Jacobian product is taken by one fused kernel and one list kernel:
+//   1. adj_stream_kernel, over every cell: lambda_M = (dFin/dM)^T lambda' (and
+//      dL/dF from the F/2 of Eq. rho_u_stress), zero for solid, inflow and
+//      outflow cells; then the transpose of the separable pull stream of the
+//      fluid kernel (Eq. streaming), back onto the 17 Hermite moments of each
+//      source cell, with three transposed 1D passes (z in registers, y through
+//      shared memory, x by shuffles); then (dColl/dm)^T (App. A transposed by
+//      hand);
+//   2. adj_boundary_kernel, over the listed FLUID_BOUNDARY cells: the bounce-back
+//      terms f_i(x) = f+_opp(i)(x) of their own solid links, through the same
+//      (dColl/dm)^T, added (the map is linear in the moment adjoints).
 // The forward states of each segment are recomputed in FP32 from a 16-bit
 // checkpoint (deterministic rounding) taken every K steps; the initial state is
 // rebuilt exactly from u0.
+#include <algorithm>
+#include <cstdint>
 #include <new>
 
 #include "../../include/melbm.h"
@@ -33,7 +37,6 @@ struct AdjointState {
   float* seg = nullptr;       // (K + 1) x 10N FP32 states of one segment
   float* lam = nullptr;       // 10N adjoint of the stored variables
   float* lam2 = nullptr;      // 10N
-  float* lamM = nullptr;      // 10N adjoint of the streamed moments
   float* gF = nullptr;        // 3N accumulated dL/dF
 };
 
@@ -44,7 +47,6 @@ void adjoint_free(AdjointState* a) {
   cudaFree(a->seg);
   cudaFree(a->lam);
   cudaFree(a->lam2);
-  cudaFree(a->lamM);
   cudaFree(a->gF);
   delete a;
 }
@@ -52,16 +54,6 @@ void adjoint_free(AdjointState* a) {
 namespace {
 
 constexpr int AT = 256;
-
-__device__ __forceinline__ void cell_xyz(size_t n, int nx, int ny, int& x, int& y, int& z) {
-  x = int(n % size_t(nx));
-  y = int((n / size_t(nx)) % size_t(ny));
-  z = int(n / (size_t(nx) * size_t(ny)));
-}
-
-__device__ __forceinline__ size_t cell_index(int x, int y, int z, int nx, int ny, int nz) {
-  return size_t(wrapi(x, nx)) + size_t(nx) * (size_t(wrapi(y, ny)) + size_t(ny) * wrapi(z, nz));
-}
 
 __device__ __forceinline__ Stored load_f32(const float* b, size_t N, size_t n) {
   return load_stored<ST_F32>(b, N, n);
@@ -127,25 +119,20 @@ __global__ void outflow_vjp_kernel(float* lam, const uint8_t* type, int nx, int 
 
 // ------------------------------------------------------------------ Fin^T
 // Forward: drho' = M000, J = M1 + F/2, inv = 1/(1 + M000), u' = J inv,
-// n'_ab = M_ab - J_a J_b inv.  The streamed moments are recovered from the output.
-template <bool FORCE>
-__global__ void fin_vjp_kernel(const float* mnext, const float* F, const uint8_t* type,
-                               const float* lam, float* lamM, float* gF, int64_t N_) {
-  const size_t N = size_t(N_), n = size_t(blockIdx.x) * AT + threadIdx.x;
-  if (n >= N) return;
-  const uint8_t t = type ? type[n] : T_FLUID;
-  if (t == T_SOLID || t == T_INFLOW || t == T_OUTFLOW) {
-    for (int k = 0; k < 10; ++k) lamM[k * N + n] = 0.f;
-    return;
-  }
-  const Stored o = load_f32(mnext, N, n);
+// n'_ab = M_ab - J_a J_b inv.  The streamed moments are recovered from the output
+// o.  lam: the adjoint of the stored output variables; lamM: that of the ten
+// streamed moments (M000, M100, M010, M001, M200, M020, M002, M110, M101, M011);
+// lJ: the adjoint of J, of which F/2 takes half.
+__device__ __forceinline__ void fin_vjp_cell(const Stored& o, const float lam[10], float lamM[10],
+                                             float lJ[3]) {
   const float rho = 1.0f + o.drho, inv = 1.0f / rho;
   const float J[3] = {o.ux * rho, o.uy * rho, o.uz * rho};
-  const float lu[3] = {lam[N + n], lam[2 * N + n], lam[3 * N + n]};
-  const float ln[6] = {lam[4 * N + n], lam[5 * N + n], lam[6 * N + n],
-                       lam[7 * N + n], lam[8 * N + n], lam[9 * N + n]};
+  const float* lu = lam + 1;
+  const float* ln = lam + 4;
   const int A[6] = {0, 1, 2, 0, 0, 1}, B[6] = {0, 1, 2, 1, 2, 2};
-  float lJ[3] = {lu[0], lu[1], lu[2]};
+  lJ[0] = lu[0];
+  lJ[1] = lu[1];
+  lJ[2] = lu[2];
   float linv = 0.f;
   for (int a = 0; a < 3; ++a) linv += lu[a] * J[a];
   for (int k = 0; k < 6; ++k) {
@@ -154,13 +141,15 @@ __global__ void fin_vjp_kernel(const float* mnext, const float* F, const uint8_t
     linv -= ln[k] * J[A[k]] * J[B[k]];
   }
   for (int a = 0; a < 3; ++a) lJ[a] *= inv;
-  lamM[n] = lam[n] - linv * inv * inv;  // M000
-  lamM[N + n] = lJ[0];
-  lamM[2 * N + n] = lJ[1];
-  lamM[3 * N + n] = lJ[2];
-  for (int k = 0; k < 6; ++k) lamM[(4 + k) * N + n] = ln[k];
-  if (FORCE)
-    for (int a = 0; a < 3; ++a) gF[a * N + n] += 0.5f * lJ[a];
+  lamM[0] = lam[0] - linv * inv * inv;
+  lamM[1] = lJ[0];
+  lamM[2] = lJ[1];
+  lamM[3] = lJ[2];
+  for (int k = 0; k < 6; ++k) lamM[4 + k] = ln[k];
+}
+
+__device__ __forceinline__ bool special_type(uint8_t t) {
+  return t == T_SOLID || t == T_INFLOW || t == T_OUTFLOW;  // output not from the stream
 }
 
 // ------------------------------------------------------------------ Coll^T
@@ -299,52 +288,305 @@ __device__ __forceinline__ void add_population_adjoint(int cx, int cy, int cz, f
   lmu[16] += 27.0f * g * px * py * pz;
 }
 
-// lambda_f_i at a destination cell: (dM/df_i)^T lambda_M with
-// M = (sum f, sum c f, sum (c c - delta/3) f).
-__device__ __forceinline__ float population_lambda(const float* lamM, size_t N, size_t d, int cx,
-                                                   int cy, int cz) {
-  const float fx = float(cx), fy = float(cy), fz = float(cz);
-  return lamM[d] + fx * lamM[N + d] + fy * lamM[2 * N + d] + fz * lamM[3 * N + d] +
-         (fx * fx - (1.0f / 3.0f)) * lamM[4 * N + d] + (fy * fy - (1.0f / 3.0f)) * lamM[5 * N + d] +
-         (fz * fz - (1.0f / 3.0f)) * lamM[6 * N + d] + fx * fy * lamM[7 * N + d] +
-         fx * fz * lamM[8 * N + d] + fy * fz * lamM[9 * N + d];
+// ------------------------------------------------------------------ stream^T
+// The pull stream followed by the moment sums is the separable map of the fluid
+// kernel: per axis, (mu0, mu1, mu2) -> phi = (phi+, phi0, phi-) with
+// s = mu0/6 + mu2/2, phi0 = mu0 - 2 s, phi+- = s +- mu1/2; pull phi+ from the
+// minus side and phi- from the plus side; project m0 = pl + z + mr, m1 = pl - mr,
+// m2 = (2/3)(pl + mr) - z/3.  Its transpose, per axis and in reverse order
+// (z, then y, then x), is the same three-point stencil read the other way:
+//   proj^T: lpl = l0 + l1 + (2/3) l2,  lmr = l0 - l1 + (2/3) l2,  lz = l0 - l2/3;
+//   push:   lphi+(x) = lpl(x + 1), lphi-(x) = lmr(x - 1), lphi0 = lz;
+//   phi^T:  ls = lphi+ + lphi- - 2 lphi0, lmu0 = lphi0 + ls/6, lmu1 = (lphi+ - lphi-)/2,
+//           lmu2 = ls/2.
+// Carried adjoints mirror the forward's moment counts: 10 -> 18 (z) -> 24 (y) -> 17 (x).
+struct LamT {
+  float p, z, m;  // lpl, lz, lmr of one cell, before the push
+};
+__device__ __forceinline__ LamT proj_t(float l0, float l1, float l2) {
+  const float a = fmaf(l2, 2.0f / 3.0f, l0);
+  LamT r;
+  r.p = a + l1;
+  r.m = a - l1;
+  r.z = fmaf(l2, -1.0f / 3.0f, l0);
+  return r;
+}
+// lp = lphi+ (the plus neighbour's lpl), lz = own lz, lm = lphi- (the minus
+// neighbour's lmr) -> (lmu0, lmu1, lmu2)
+__device__ __forceinline__ void phi_t(float lp, float lz, float lm, float& l0, float& l1, float& l2) {
+  const float ls = fmaf(lz, -2.0f, lp + lm);
+  l1 = 0.5f * (lp - lm);
+  l0 = fmaf(ls, 1.0f / 6.0f, lz);
+  l2 = 0.5f * ls;
 }
 
+constexpr int AFX = 32;             // lanes: columns x0 .. x0+31, lanes 0 and 31 halo
+constexpr int AFY = 16;             // warps: rows y0 .. y0+15, warps 0 and 15 halo
+constexpr int AIX = AFX - 2, AIY = AFY - 2;
+constexpr int ANS = 9;              // y-pass slices (d, r)
+constexpr int ASM = 2 * ANS * AFY * AFX;  // floats per buffer (lpl and lmr)
+constexpr size_t ADJ_SMEM = size_t(2) * ASM * sizeof(float);
+
+struct AdjStreamParams {
+  int nx, ny, nz, zc;
+  const float* lam_next;  // adjoint of the output state (10N, stored variables)
+  const float* m_next;    // output state (10N)
+  const float* m_t;       // input state (10N)
+  const float* force;     // 3N or null
+  const uint8_t* type;    // N or null
+  float* lam_out;         // adjoint of the input state (10N)
+  float* gF;              // 3N, accumulated
+  float omega;
+};
+
+// One thread per (x, y) column marching in z: fin^T and the z^T projection at
+// plane zz, the rest of z^T, y^T (shared memory), x^T (shuffles) and Coll^T
+// for the plane zz - 1.  Periodic in all directions; cells whose output does
+// not come from the stream contribute no adjoint (special_type), and solid cells
+// get none; the bounce-back terms of listed cells are added by adj_boundary_kernel.
+template <bool FORCE, bool TYPED>
+__global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams P) {
+  extern __shared__ float asm_[];
+  const int lane = threadIdx.x, row = threadIdx.y;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const size_t N = size_t(nx) * ny * nz, plane = size_t(nx) * ny;
+  const int x = int(blockIdx.x) * AIX - 1 + lane, y = int(blockIdx.y) * AIY - 1 + row;
+  const size_t col = size_t(wrapi(x, nx)) + size_t(nx) * wrapi(y, ny);
+  const bool mid_row = row >= 1 && row <= AFY - 2;
+  const bool own = mid_row && lane >= 1 && lane <= AFX - 2 && x < nx && y < ny;
+  const int z0 = int(blockIdx.z) * P.zc, z1 = min(z0 + P.zc, nz);
+  // z-march state per (d, e) slice: lz of plane zz-1, lmr of planes zz-1 and zz-2
+  float zl[6], m1[6], m2[6];
+  for (int k = 0; k < 6; ++k) zl[k] = m1[k] = m2[k] = 0.f;
+  float gprev[3] = {0.f, 0.f, 0.f};  // F/2 share of fin^T at plane zz-1
+  // plane zz's lambda' and output state are loaded one iteration ahead
+  float Lnext[10], Mnext[10];
+  bool skip_next = false;
+  auto load_plane = [&](int zp) {
+    const size_t n = col + plane * size_t(wrapi(zp, nz));
+    skip_next = TYPED && special_type(P.type[n]);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+      Lnext[k] = __ldg(P.lam_next + k * N + n);
+      Mnext[k] = __ldg(P.m_next + k * N + n);
+    }
+  };
+  load_plane(z0 - 1);
+  int parity = 0;
+  for (int zz = z0 - 1; zz <= z1; ++zz, parity ^= 1) {
+    const int zo = zz - 1;  // the plane finished in this iteration
+    const bool out_plane = zo >= z0;
+    // the input state (and force, gradient) of plane zo, used after the passes
+    const bool do_out = out_plane && own;
+    float mt[10], fo[3] = {0.f, 0.f, 0.f}, go[3] = {0.f, 0.f, 0.f};
+    bool solid_out = false;
+    const size_t no = col + plane * size_t(zo < 0 ? 0 : zo);
+    if (do_out) {
+      solid_out = TYPED && P.type[no] == T_SOLID;
+#pragma unroll
+      for (int k = 0; k < 10; ++k) mt[k] = __ldg(P.m_t + k * N + no);
+      if (FORCE)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          fo[a] = __ldg(P.force + a * N + no);
+          go[a] = P.gF[a * N + no];
+        }
+    }
+    // ---- fin^T at plane zz, then proj^T along z of the six (d, e) slices
+    float lam[10], mn[10];
+    const bool skip = skip_next;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+      lam[k] = Lnext[k];
+      mn[k] = Mnext[k];
+    }
+    if (zz + 1 <= z1) load_plane(zz + 1);
+    float lM[10];
+    float lJ[3] = {0.f, 0.f, 0.f};
+    if (skip) {
+      for (int k = 0; k < 10; ++k) lM[k] = 0.f;
+    } else {
+      Stored o;
+      o.drho = mn[0];
+      o.ux = mn[1];
+      o.uy = mn[2];
+      o.uz = mn[3];
+      o.nxx = mn[4];
+      o.nyy = mn[5];
+      o.nzz = mn[6];
+      o.nxy = mn[7];
+      o.nxz = mn[8];
+      o.nyz = mn[9];
+      fin_vjp_cell(o, lam, lM, lJ);
+    }
+    // slices (d, e) = (0,0) (1,0) (0,1) (2,0) (1,1) (0,2), inputs over f
+    const LamT t[6] = {proj_t(lM[0], lM[3], lM[6]), proj_t(lM[1], lM[8], 0.f),
+                       proj_t(lM[2], lM[9], 0.f),   proj_t(lM[4], 0.f, 0.f),
+                       proj_t(lM[7], 0.f, 0.f),     proj_t(lM[5], 0.f, 0.f)};
+    float Z[6][3];  // lZ[(d, e)][r] of plane zo
+    for (int k = 0; k < 6; ++k) {
+      phi_t(t[k].p, zl[k], m2[k], Z[k][0], Z[k][1], Z[k][2]);
+      m2[k] = m1[k];
+      m1[k] = t[k].m;
+      zl[k] = t[k].z;
+    }
+    const float gcur[3] = {gprev[0], gprev[1], gprev[2]};
+    gprev[0] = 0.5f * lJ[0];
+    gprev[1] = 0.5f * lJ[1];
+    gprev[2] = 0.5f * lJ[2];
+    if (!out_plane) continue;  // block-uniform
+    // ---- y^T on slices (d, r): inputs over e
+    float* sp = asm_ + parity * ASM;
+    // lZ by (d, e): index of (d, e) in the six slices, -1 = absent
+    const int DE[3][3] = {{0, 2, 5}, {1, 4, -1}, {3, -1, -1}};
+    float yz[ANS];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float e0 = Z[DE[d][0]][r];
+        const float e1 = DE[d][1] >= 0 ? Z[DE[d][1]][r] : 0.f;
+        const float e2 = DE[d][2] >= 0 ? Z[DE[d][2]][r] : 0.f;
+        const LamT u = proj_t(e0, e1, e2);
+        const int s_ = 3 * d + r;
+        sp[(s_ * AFY + row) * AFX + lane] = u.p;
+        sp[((ANS + s_) * AFY + row) * AFX + lane] = u.m;
+        yz[s_] = u.z;
+      }
+    __syncthreads();
+    if (!mid_row) continue;
+    float Y[3][3][3];  // lY[d][q][r]
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int s_ = 3 * d + r;
+        const float lp = sp[(s_ * AFY + row + 1) * AFX + lane];         // lpl of y + 1
+        const float lm = sp[((ANS + s_) * AFY + row - 1) * AFX + lane];  // lmr of y - 1
+        phi_t(lp, yz[s_], lm, Y[d][0][r], Y[d][1][r], Y[d][2][r]);
+      }
+    // ---- x^T on slices (q, r): inputs over d, exchanged by shuffles
+    float X[3][3][3];  // lmu[p][q][r]
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (q == 2 && r == 2) continue;  // no Hermite moment has q = r = 2
+        const LamT u = proj_t(Y[0][q][r], Y[1][q][r], Y[2][q][r]);
+        const float lp = __shfl_down_sync(FULL, u.p, 1);  // lpl of x + 1
+        const float lm = __shfl_up_sync(FULL, u.m, 1);    // lmr of x - 1
+        phi_t(lp, u.z, lm, X[0][q][r], X[1][q][r], X[2][q][r]);
+      }
+    if (!own) continue;
+    // ---- Coll^T at plane zo
+    if (solid_out) {
+      for (int k = 0; k < 10; ++k) P.lam_out[k * N + no] = 0.f;
+      continue;
+    }
+    // Mom17 order: 000 100 010 001 200 020 002 110 101 011 210 120 201 102 021 012 111
+    const float lmu[17] = {X[0][0][0], X[1][0][0], X[0][1][0], X[0][0][1], X[2][0][0],
+                           X[0][2][0], X[0][0][2], X[1][1][0], X[1][0][1], X[0][1][1],
+                           X[2][1][0], X[1][2][0], X[2][0][1], X[1][0][2], X[0][2][1],
+                           X[0][1][2], X[1][1][1]};
+    float lf[3] = {0.f, 0.f, 0.f};
+    Stored st;
+    st.drho = mt[0];
+    st.ux = mt[1];
+    st.uy = mt[2];
+    st.uz = mt[3];
+    st.nxx = mt[4];
+    st.nyy = mt[5];
+    st.nzz = mt[6];
+    st.nxy = mt[7];
+    st.nxz = mt[8];
+    st.nyz = mt[9];
+    float lin[10];
+    collide_vjp<FORCE>(st, P.omega, fo, lmu, lin, lf);
+    for (int k = 0; k < 10; ++k) P.lam_out[k * N + no] = lin[k];
+    if (FORCE)
+      for (int a = 0; a < 3; ++a) P.gF[a * N + no] = go[a] + (lf[a] + gcur[a]);
+  }
+}
+
+// Bounce-back terms of the listed FLUID_BOUNDARY cells: a solid link i of cell x
+// took f_i(x) = f+_opp(i)(x), so lambda_f_i(x) flows back onto x's own Hermite
+// moments; Coll^T is linear in them, so its image is added to lam_out.
 template <bool FORCE>
-__global__ void stream_collide_vjp_kernel(const float* m, const float* F, const uint8_t* type,
-                                          const float* lamM, float* lam_out, float* gF, float omega,
-                                          int nx, int ny, int nz) {
-  const size_t N = size_t(nx) * ny * nz, n = size_t(blockIdx.x) * AT + threadIdx.x;
-  if (n >= N) return;
-  const uint8_t t = type ? type[n] : T_FLUID;
-  if (t == T_SOLID) {
-    for (int k = 0; k < 10; ++k) lam_out[k * N + n] = 0.f;
-    return;
-  }
-  int x, y, z;
-  cell_xyz(n, nx, ny, x, y, z);
+__global__ void adj_boundary_kernel(const float* lam_next, const float* m_next, const float* m_t,
+                                    const float* F, const uint32_t* cells, const uint32_t* words,
+                                    int64_t count, float* lam_out, float* gF, float omega, int64_t N_) {
+  const int64_t k = int64_t(blockIdx.x) * AT + threadIdx.x;
+  if (k >= count) return;
+  const uint32_t word = words[k];
+  const uint32_t links = word & 0x7FFFFFFu;
+  if ((word >> 27) != T_FLUID_BOUNDARY || !links) return;
+  const size_t N = size_t(N_), n = cells[k];
+  float lam[10], lM[10], lJ[3];
+  for (int c = 0; c < 10; ++c) lam[c] = lam_next[c * N + n];
+  fin_vjp_cell(load_stored<ST_F32>(m_next, N, n), lam, lM, lJ);
   float lmu[17];
-  for (int k = 0; k < 17; ++k) lmu[k] = 0.f;
+  for (int c = 0; c < 17; ++c) lmu[c] = 0.f;
   for (int i = 0; i < 27; ++i) {
+    if (!((links >> i) & 1u)) continue;
     const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-    // destination y + c_i pulled population i from this (non-solid) cell
-    const size_t d = cell_index(x + cx, y + cy, z + cz, nx, ny, nz);
-    add_population_adjoint(cx, cy, cz, population_lambda(lamM, N, d, cx, cy, cz), lmu);
-    // own solid link i (source x - c_i solid): f_i(x) = f+_opp(i)(x)
-    if (t == T_FLUID_BOUNDARY && type[cell_index(x - cx, y - cy, z - cz, nx, ny, nz)] == T_SOLID)
-      add_population_adjoint(-cx, -cy, -cz, population_lambda(lamM, N, n, cx, cy, cz), lmu);
+    const float fx = float(cx), fy = float(cy), fz = float(cz);
+    const float lf = lM[0] + fx * lM[1] + fy * lM[2] + fz * lM[3] +
+                     (fx * fx - (1.0f / 3.0f)) * lM[4] + (fy * fy - (1.0f / 3.0f)) * lM[5] +
+                     (fz * fz - (1.0f / 3.0f)) * lM[6] + fx * fy * lM[7] + fx * fz * lM[8] +
+                     fy * fz * lM[9];
+    add_population_adjoint(-cx, -cy, -cz, lf, lmu);
   }
-  float f[3] = {0.f, 0.f, 0.f}, lf[3] = {0.f, 0.f, 0.f};
+  float f[3] = {0.f, 0.f, 0.f}, lff[3] = {0.f, 0.f, 0.f};
   if (FORCE)
     for (int a = 0; a < 3; ++a) f[a] = F[a * N + n];
   float lin[10];
-  collide_vjp<FORCE>(load_f32(m, N, n), omega, f, lmu, lin, lf);
-  for (int k = 0; k < 10; ++k) lam_out[k * N + n] = lin[k];
+  collide_vjp<FORCE>(load_stored<ST_F32>(m_t, N, n), omega, f, lmu, lin, lff);
+  for (int c = 0; c < 10; ++c) lam_out[c * N + n] += lin[c];
   if (FORCE)
-    for (int a = 0; a < 3; ++a) gF[a * N + n] += lf[a];
+    for (int a = 0; a < 3; ++a) gF[a * N + n] += lff[a];
 }
 
 unsigned blocks_for(int64_t N) { return unsigned((N + AT - 1) / AT); }
+
+template <bool FORCE, bool TYPED>
+cudaError_t launch_adj_stream_t(AdjStreamParams& p, cudaStream_t st) {
+  constexpr int MAX_DEV = 64;
+  static int sms[MAX_DEV] = {};  // per device, once: SM count and the shared-memory opt-in
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
+  if (!sms[dev]) {
+    int n = 0;
+    e = cudaFuncSetAttribute(adj_stream_kernel<FORCE, TYPED>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(ADJ_SMEM));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    sms[dev] = n > 0 ? n : 1;
+  }
+  // z-chunk: minimise waves (one block per SM) times the planes a block marches
+  const int64_t tiles = int64_t((p.nx + AIX - 1) / AIX) * ((p.ny + AIY - 1) / AIY);
+  int best = 1;
+  int64_t best_cost = INT64_MAX;
+  for (int zc = std::min(p.nz, 128); zc >= 1; --zc) {
+    const int64_t blocks = tiles * ((p.nz + zc - 1) / zc);
+    const int64_t cost = (blocks + sms[dev] - 1) / sms[dev] * (zc + 2);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = zc;
+    }
+  }
+  p.zc = best;
+  const dim3 grid((p.nx + AIX - 1) / AIX, (p.ny + AIY - 1) / AIY, (p.nz + best - 1) / best);
+  adj_stream_kernel<FORCE, TYPED><<<grid, dim3(AFX, AFY), ADJ_SMEM, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_stream(AdjStreamParams& p, cudaStream_t st) {
+  if (p.force)
+    return p.type ? launch_adj_stream_t<true, true>(p, st) : launch_adj_stream_t<true, false>(p, st);
+  return p.type ? launch_adj_stream_t<false, true>(p, st) : launch_adj_stream_t<false, false>(p, st);
+}
 
 }  // namespace
 }  // namespace melbm
@@ -391,7 +633,7 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
   const int nck = (nsteps - 1) / K;  // checkpoints at t = K, 2K, ... < nsteps
   if (!a || a->N != h->N || a->K != K || a->nck < nck) {
     if (a) {
-      h->mem_bytes -= a->N * 4 * (3 + 10 * (a->K + 1) + 33) + a->N * 20 * int64_t(a->nck);
+      h->mem_bytes -= a->N * 4 * (3 + 10 * (a->K + 1) + 23) + a->N * 20 * int64_t(a->nck);
       adjoint_free(a);
     }
     a = new (std::nothrow) AdjointState;
@@ -406,7 +648,6 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
     if (e == cudaSuccess) e = cudaMalloc(&a->seg, N * 40 * size_t(K + 1));
     if (e == cudaSuccess) e = cudaMalloc(&a->lam, N * 40);
     if (e == cudaSuccess) e = cudaMalloc(&a->lam2, N * 40);
-    if (e == cudaSuccess) e = cudaMalloc(&a->lamM, N * 40);
     if (e == cudaSuccess) e = cudaMalloc(&a->gF, N * 12);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -414,7 +655,7 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
       h->adj = nullptr;
       return adj_fail(h, MELBM_ENOMEM, "melbm_forward_checkpointed: device allocation failed");
     }
-    h->mem_bytes += a->N * 4 * (3 + 10 * (K + 1) + 33) + a->N * 20 * int64_t(nck);
+    h->mem_bytes += a->N * 4 * (3 + 10 * (K + 1) + 23) + a->N * 20 * int64_t(nck);
   }
   a->ready = false;
   a->nsteps = nsteps;
@@ -475,16 +716,30 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
                                                                              h->ny, h->nz);
         ADJ_CUDA(h, cudaGetLastError());
       }
-      if (h->force) {
-        fin_vjp_kernel<true><<<nb, AT, 0, st>>>(m_next, h->force, h->type, lam, a->lamM, a->gF, h->N);
-        stream_collide_vjp_kernel<true><<<nb, AT, 0, st>>>(m_t, h->force, h->type, a->lamM, lam2,
-                                                           a->gF, omega, h->nx, h->ny, h->nz);
-      } else {
-        fin_vjp_kernel<false><<<nb, AT, 0, st>>>(m_next, nullptr, h->type, lam, a->lamM, a->gF, h->N);
-        stream_collide_vjp_kernel<false><<<nb, AT, 0, st>>>(m_t, nullptr, h->type, a->lamM, lam2,
-                                                            a->gF, omega, h->nx, h->ny, h->nz);
+      AdjStreamParams ap;
+      ap.nx = h->nx;
+      ap.ny = h->ny;
+      ap.nz = h->nz;
+      ap.zc = 0;
+      ap.lam_next = lam;
+      ap.m_next = m_next;
+      ap.m_t = m_t;
+      ap.force = h->force;
+      ap.type = h->type;
+      ap.lam_out = lam2;
+      ap.gF = a->gF;
+      ap.omega = omega;
+      ADJ_CUDA(h, launch_adj_stream(ap, st));
+      if (h->L) {
+        const unsigned lb = blocks_for(h->L);
+        if (h->force)
+          adj_boundary_kernel<true><<<lb, AT, 0, st>>>(lam, m_next, m_t, h->force, h->list_cell,
+                                                       h->list_word, h->L, lam2, a->gF, omega, h->N);
+        else
+          adj_boundary_kernel<false><<<lb, AT, 0, st>>>(lam, m_next, m_t, nullptr, h->list_cell,
+                                                        h->list_word, h->L, lam2, a->gF, omega, h->N);
+        ADJ_CUDA(h, cudaGetLastError());
       }
-      ADJ_CUDA(h, cudaGetLastError());
       float* tmp = lam;
       lam = lam2;
       lam2 = tmp;

@@ -30,7 +30,8 @@ def gpu_grad(M, shape, tau, u0, F, g, nsteps, K, mask=None, inflow=None, outflow
         sim.set_inflow(inflow[0], inflow[1:])
     if outflow:
         sim.set_outflow()
-    sim.set_force(cuda(F))
+    if F is not None:
+        sim.set_force(cuda(F))
     sim.forward_checkpointed(cuda(u0), nsteps, K)
     gu, gF = sim.backward(cuda(g), dL_dF=torch.empty(3, sim.N, device="cuda"))
     torch.cuda.synchronize()
@@ -54,6 +55,19 @@ def test_adjoint_matches_oracle_periodic_with_force(M, orc):
     ou, oF = orc.adjoint(u0, F, shape, 0.55, 6, lambda m: g, K=6)
     assert rel(gu, ou) < 1e-4, rel(gu, ou)
     assert rel(gF, oF) < 1e-4, rel(gF, oF)
+
+
+@pytest.mark.parametrize("shape", [(37, 29, 9), (4, 3, 5), (64, 15, 33)])
+def test_adjoint_matches_oracle_periodic_without_force(M, orc, shape):
+    """No body force (the force-free kernel); ragged tiles, grids smaller than one
+    tile in every direction, several z-chunks."""
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(40)
+    u0 = 0.05 * rng.standard_normal((3, N))
+    g = rng.standard_normal((10, N))
+    gu, _ = gpu_grad(M, shape, 0.58, u0, None, g, 4, 4)
+    ou, _ = orc.adjoint(u0, np.zeros((3, N)), shape, 0.58, 4, lambda m: g, K=4)
+    assert rel(gu, ou) < 1e-4, rel(gu, ou)
 
 
 def test_adjoint_matches_oracle_with_bounce_back_inflow_outflow(M, orc):
