@@ -246,19 +246,37 @@ __device__ __forceinline__ void store_pair_q16(void* buf, size_t N, size_t na, s
     e8 = q_encode_codes<2>(o.nxz, d[8]), e9 = q_encode_codes<2>(o.nyz, d[9]);
   }
   uint32_t* p = static_cast<uint32_t*>(buf);
-  if (sa) {
-    p[na] = q_pack(e0.x, e1.x);
-    p[N + na] = q_pack(e2.x, e3.x);
-    p[2 * N + na] = q_pack(e4.x, e5.x);
-    p[3 * N + na] = q_pack(e6.x, e7.x);
-    p[4 * N + na] = q_pack(e8.x, e9.x);
-  }
-  if (sb) {
-    p[nb] = q_pack(e0.y, e1.y);
-    p[N + nb] = q_pack(e2.y, e3.y);
-    p[2 * N + nb] = q_pack(e4.y, e5.y);
-    p[3 * N + nb] = q_pack(e6.y, e7.y);
-    p[4 * N + nb] = q_pack(e8.y, e9.y);
+  if constexpr (RT) {
+    const uint32_t qr = q->g[1].qmax, qs = q->g[2].qmax;
+    if (sa) {
+      p[na] = qg_clamp_word(q_pack(e0.x, e1.x), qr);
+      p[N + na] = qg_clamp_word(q_pack(e2.x, e3.x), qr);
+      p[2 * N + na] = qg_clamp_word(q_pack(e4.x, e5.x), qs);
+      p[3 * N + na] = qg_clamp_word(q_pack(e6.x, e7.x), qs);
+      p[4 * N + na] = qg_clamp_word(q_pack(e8.x, e9.x), qs);
+    }
+    if (sb) {
+      p[nb] = qg_clamp_word(q_pack(e0.y, e1.y), qr);
+      p[N + nb] = qg_clamp_word(q_pack(e2.y, e3.y), qr);
+      p[2 * N + nb] = qg_clamp_word(q_pack(e4.y, e5.y), qs);
+      p[3 * N + nb] = qg_clamp_word(q_pack(e6.y, e7.y), qs);
+      p[4 * N + nb] = qg_clamp_word(q_pack(e8.y, e9.y), qs);
+    }
+  } else {
+    if (sa) {
+      p[na] = q_pack(e0.x, e1.x);
+      p[N + na] = q_pack(e2.x, e3.x);
+      p[2 * N + na] = q_pack(e4.x, e5.x);
+      p[3 * N + na] = q_pack(e6.x, e7.x);
+      p[4 * N + na] = q_pack(e8.x, e9.x);
+    }
+    if (sb) {
+      p[nb] = q_pack(e0.y, e1.y);
+      p[N + nb] = q_pack(e2.y, e3.y);
+      p[2 * N + nb] = q_pack(e4.y, e5.y);
+      p[3 * N + nb] = q_pack(e6.y, e7.y);
+      p[4 * N + nb] = q_pack(e8.y, e9.y);
+    }
   }
 }
 

@@ -158,15 +158,21 @@ __device__ __forceinline__ uint32_t qg_encode_bits(const QGrid& g, float m, floa
   w = fminf(fmaxf(w, g.wlo), g.whi);  // NaN -> wlo (code 0)
   return __float_as_uint(__fadd_rd(__fadd_rd(w, d), g.magic));
 }
+// Pair form without the upper clamp: cvt.rmi.u16 saturates below at 0 (NaN -> 0),
+// which is the lower clamp; the codes above 2^b - 1 are cut by qg_clamp_word on
+// the packed word.  Both give the codes of the clamped form for every input: w
+// below -qc or above 2^b - 1 - qc floors to a code at or beyond the same end.
 __device__ __forceinline__ uint2 qg_encode_codes(const QGrid& g, float2 m, float2 d) {
-  float2 w = __ffma2_rn(m, make_float2(g.K, g.K), make_float2(g.b, g.b));
-  w.x = fminf(fmaxf(w.x, g.wlo), g.whi);
-  w.y = fminf(fmaxf(w.y, g.wlo), g.whi);
+  const float2 w = __ffma2_rn(m, make_float2(g.K, g.K), make_float2(g.b, g.b));
   const float2 z = __fadd2_rd(__fadd2_rd(w, d), make_float2(g.qc, g.qc));
   unsigned short qa, qb;
   asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qa) : "f"(z.x));
   asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qb) : "f"(z.y));
   return make_uint2(qa, qb);
+}
+// Both codes of a word share one group's 2^b - 1 (rho and u use b_rho_u).
+__device__ __forceinline__ uint32_t qg_clamp_word(uint32_t w, uint32_t qmax) {
+  return __vminu2(w, qmax * 0x10001u);
 }
 __device__ __forceinline__ float qg_decode(const QGrid& g, float magic_q) {
   return __fmaf_rn(magic_q - g.magic, g.step, g.c);
