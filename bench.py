@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % of HBM peak, 16-bit vs FP32 moment storage on 1 GB300 at stated error"
-BYTES_PER_CELL = {"q16": 40, "f32": 80}  # algorithmic: state read once + written once
+BYTES_PER_CELL = {"q16": 40, "f32": 80, "q16_d3q19": 40}  # state read once + written once
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -146,9 +146,9 @@ def turbulence_inputs():
     return wl, W.flat(u).astype(np.float32)
 
 
-def time_storage(torch, melbm, wl, u_np, storage, steps, warmup, clocks=None):
+def time_storage(torch, melbm, wl, u_np, storage, steps, warmup, clocks=None, lattice=27):
     N = wl.cells
-    sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602)
+    sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602, lattice=lattice)
     u = torch.from_numpy(u_np).cuda()
     rho = torch.ones(N, dtype=torch.float32, device="cuda")
     sim.set_state(rho, u)
@@ -374,6 +374,11 @@ def main():
     q_total = max_over_ranks(torch, q_total)
     f_total, f_kern, f_mem = time_storage(torch, melbm, wl, u_np, "f32", args.steps, args.warmup)
     f_total = max_over_ranks(torch, f_total)
+    # the same workload on the D3Q19 lattice (16-bit), a shorter run
+    d_steps = max(3, min(args.steps, 200))
+    d_total, d_kern, _ = time_storage(torch, melbm, wl, u_np, "q16", d_steps, args.warmup,
+                                      lattice=19)
+    d_total = max_over_ranks(torch, d_total)
 
     clk = clocks.summary()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -385,7 +390,8 @@ def main():
         out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                "frac": achieved / peak, "frac_of_nominal_8000": achieved / 8000.0,
                "traffic": rec.get("bytes_per_launch_256cube"), "peak_source": peak_src,
-               "kernel": f"fluid_kernel<{storage}>", "kernel_ms": avg_s * 1e3,
+               "kernel": "fluid_kernel<q16, D3Q19>" if storage == "q16_d3q19"
+               else f"fluid_kernel<{storage}>", "kernel_ms": avg_s * 1e3,
                "algorithmic_bytes_per_launch": BYTES_PER_CELL[storage] * N}
         inst, mhz = rec.get("warp_inst_per_launch_256cube"), clk.get("sm_mhz")
         if inst and mhz:
@@ -409,6 +415,9 @@ def main():
         "roofline": roof("q16", q_kern),
         "fp32_storage": {"value": f_value, "unit": "MLUPS", "ms_per_step": f_total / args.steps,
                          "roofline": roof("f32", f_kern)},
+        "d3q19_q16": {"value": job_mlups(N, d_steps, world, d_total), "unit": "MLUPS",
+                      "steps": d_steps, "ms_per_step": d_total / d_steps,
+                      "roofline": roof("q16_d3q19", d_kern)},
         "memory_bytes": {"q16": q_mem, "f32": f_mem},
         "gpu_launches": args.steps,
         "clocks": clk,
