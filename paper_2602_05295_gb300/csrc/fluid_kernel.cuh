@@ -62,6 +62,11 @@ namespace melbm {
 #ifndef MELBM_FLUID_MINB
 #define MELBM_FLUID_MINB 1
 #endif
+// 32-bit words per staged halo entry of the 16-bit kernel (1: the word alone
+// through L1; 4: its 16-byte aligned chunk, L2 only)
+#ifndef MELBM_Q16_HALO_CHUNK
+#define MELBM_Q16_HALO_CHUNK 1
+#endif
 // z-loop unroll factor, an expression of the kernel's STORAGE and FORCE parameters
 #ifndef MELBM_FLUID_ZUNROLL
 #define MELBM_FLUID_ZUNROLL (STORAGE == ST_F32 && !FORCE ? 2 : 1)
@@ -86,7 +91,7 @@ static_assert(ZCHUNK % 2 == 0, "planes are processed in pairs");
 template <int STORAGE, bool FORCE, bool Q19 = false>
 struct HaloStage {
   static constexpr int W = STORAGE == ST_Q16 ? 5 : 10;     // stored 32-bit words per cell
-  static constexpr int CHUNK = STORAGE == ST_Q16 ? 1 : 4;  // 4: a 16-byte aligned chunk
+  static constexpr int CHUNK = STORAGE == ST_Q16 ? MELBM_Q16_HALO_CHUNK : 4;  // 4: 16-byte chunk
   static constexpr int ENTRIES = 2 * W + (FORCE ? 6 : 0);
   static constexpr int BUF_WORDS = ENTRIES * 32 * CHUNK;
   static constexpr size_t SMEM =
