@@ -77,7 +77,7 @@ def lib():
             L.orc_decode.argtypes = [I64, P, P]
             L.orc_encode_bits.argtypes = [I, I, I, P, U32, U32, I, I, I, P]
             L.orc_step_wall_f64.argtypes = [I, I, I, D, P, P, P, P, I, P, P, P]
-            L.orc_step19_f64.argtypes = [I, I, I, D, P, P, P]
+            L.orc_step19_f64.argtypes = [I, I, I, D, P, P, P, P, P]
             L.orc_step19_cells_f64.argtypes = [I, I, I, D, P, P, P, I64, P]
             L.orc_reconstruct19.argtypes = [P, P, P, P]
             L.orc_solid_force_f64.argtypes = [I, I, I, D, P, P, P, I, P, P, I, P]
@@ -203,14 +203,17 @@ def step(m, shape, tau, F=None, typ=None, inflow=None, n=1, literal_xyz=False, w
     return cur
 
 
-def step19(m, shape, tau, F=None, n=1):
-    """n FP64 periodic D3Q19 steps of the public state ``m`` (10, N)."""
+def step19(m, shape, tau, F=None, n=1, typ=None, inflow=None):
+    """n FP64 D3Q19 steps of the public state ``m`` (10, N); ``typ``/``inflow`` as
+    for ``step`` (None: periodic)."""
     nx, ny, nz = shape
     cur = _f64(m).copy()
     out = np.empty_like(cur)
     Fa = _f64(F)
+    ta = None if typ is None else np.ascontiguousarray(typ, np.uint8)
+    ia = None if inflow is None else np.ascontiguousarray(inflow, np.float64)
     for _ in range(n):
-        lib().orc_step19_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(out))
+        lib().orc_step19_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(ta), _p(ia), _p(out))
         cur, out = out, cur
     return cur
 
@@ -386,7 +389,7 @@ def q16_step(codes, shape, tau, t_out, seed, F=None, typ=None, inflow=None, bits
     take the codes of (nx-2, y, z).  ``lattice=19``: the periodic D3Q19 step."""
     pub = stored_to_public(decode(codes, bits))
     if lattice == 19:
-        new = step19(pub, shape, tau, F=F)
+        new = step19(pub, shape, tau, F=F, typ=typ, inflow=inflow)
     else:
         new = step(pub, shape, tau, F=F, typ=typ, inflow=inflow)
     q = encode(stored_for_codec(public_to_stored(new)), shape, t_out, seed, bits=bits)

@@ -407,28 +407,53 @@ Mom<T> moments19(const T* f, const T F[3]) {
   return o;
 }
 
-// One periodic D3Q19 step: collide every cell, pull the 19 populations, moments.
-void step_grid19(const Grid& g, double tau, const double* m, const double* F, double* out) {
+// One D3Q19 step: collide every non-solid cell, pull the 19 populations (halfway
+// bounce-back f_i(x) = f+_opp(i)(x) where x - c_i is solid), re-form the moments;
+// inflow cells take the inflow equilibrium, solid cells keep their value and the
+// outflow plane copies x = nx-2 (the same split-design boundaries as D3Q27).
+Mom<double> pull_and_moments19(const Grid& g, const std::vector<Mom<double>>& mp,
+                               const uint8_t* type, const double* F, int64_t n) {
+  const int x = int(n % g.nx), y = int((n / g.nx) % g.ny), z = int(n / (int64_t(g.nx) * g.ny));
+  double f[19];
+  for (int i = 0; i < 19; ++i) {
+    const int sx = (x - L19.c[i][0] + g.nx) % g.nx, sy = (y - L19.c[i][1] + g.ny) % g.ny,
+              sz = (z - L19.c[i][2] + g.nz) % g.nz;
+    const int64_t src = g.idx(sx, sy, sz);
+    if (type && type[src] == SOLID)
+      f[i] = reconstruct19(L19.opp[i], mp[n]);
+    else
+      f[i] = reconstruct19(i, mp[src]);
+  }
+  double Fx[3];
+  load_force(F, g.N(), n, Fx);
+  return moments19(f, Fx);
+}
+
+void step_grid19(const Grid& g, double tau, const double* m, const double* F, const uint8_t* type,
+                 const double* inflow, double* out) {
   const int64_t N = g.N();
   std::vector<Mom<double>> mp(N);
 #pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < N; ++n) {
+    if (type && type[n] == SOLID) continue;
     double Fx[3];
     load_force(F, N, n, Fx);
     mp[n] = collide(load(m, N, n), Fx, tau);
   }
 #pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < N; ++n) {
-    const int x = int(n % g.nx), y = int((n / g.nx) % g.ny), z = int(n / (int64_t(g.nx) * g.ny));
-    double f[19];
-    for (int i = 0; i < 19; ++i) {
-      const int sx = (x - L19.c[i][0] + g.nx) % g.nx, sy = (y - L19.c[i][1] + g.ny) % g.ny,
-                sz = (z - L19.c[i][2] + g.nz) % g.nz;
-      f[i] = reconstruct19(i, mp[g.idx(sx, sy, sz)]);
-    }
-    double Fx[3];
-    load_force(F, N, n, Fx);
-    store(out, N, n, moments19(f, Fx));
+    const uint8_t t = type ? type[n] : FLUID;
+    if (t == SOLID)
+      store(out, N, n, load(m, N, n));
+    else if (t == INFLOW)
+      store(out, N, n, inflow_state<double>(inflow));
+    else
+      store(out, N, n, pull_and_moments19(g, mp, type, F, n));
+  }
+  if (type) {
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n)
+      if (type[n] == OUTFLOW) store(out, N, n, load(out, N, n - 1));
   }
 }
 
@@ -772,10 +797,11 @@ void orc_step_f64(int nx, int ny, int nz, double tau, const double* m, const dou
   step_grid<double>(Grid{nx, ny, nz}, tau, m, F, type, inflow, out, literal_xyz);
 }
 
-// One periodic D3Q19 step (public state, component-major 10 x N).
+// One D3Q19 step (public state, component-major 10 x N; type and inflow as for
+// the D3Q27 step, or NULL for a periodic box).
 void orc_step19_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
-                    double* out) {
-  step_grid19(Grid{nx, ny, nz}, tau, m, F, out);
+                    const uint8_t* type, const double* inflow, double* out) {
+  step_grid19(Grid{nx, ny, nz}, tau, m, F, type, inflow, out);
 }
 
 // The periodic D3Q19 update of the listed cells only (each collides the 19 cells

@@ -898,3 +898,64 @@ def test_d3q19_sampled_cells_agree_with_full_step(orc):
     full = orc.step19(m, shape, 0.6, F=F)
     cells = np.array([0, 1, 6, 7, 34, 35, 100, 209])
     assert np.abs(orc.step19_cells(m, shape, 0.6, cells, F=F) - full[:, cells]).max() < 1e-15
+
+
+def test_d3q19_closed_box_bounce_back_conserves_mass(orc):
+    shape = (7, 6, 5)
+    rng = np.random.default_rng(35)
+    mask = W.channel_walls(shape)
+    mask[:, :, 0] = 1
+    mask[:, :, -1] = 1
+    mask[2, 2, 3] = 1
+    typ, _, _, _ = orc.classify(mask)
+    m = random_state(shape, rng)
+    fl = typ != orc.SOLID
+    M0 = m[0][fl].sum()
+    out = orc.step19(m, shape, 0.6, typ=typ, n=15)
+    assert abs(out[0][fl].sum() - M0) / M0 < 1e-13
+    assert np.array_equal(out[:, ~fl], m[:, ~fl])
+
+
+def test_d3q19_poiseuille_profile_with_bounce_back(orc):
+    """The same body-force channel as the D3Q27 pin: halfway bounce-back on the
+    19-velocity lattice puts the walls at y = 0.5 and ny - 1.5 as well."""
+    ny = 34
+    shape = (1, ny, 1)
+    mask = np.zeros((1, ny, 1), np.uint8)
+    mask[0, 0, 0] = mask[0, ny - 1, 0] = 1
+    typ, _, _, _ = orc.classify(mask)
+    tau = 0.8
+    nu = CS2 * (tau - 0.5)
+    umax = 0.01
+    Fx = 8 * nu * umax / (ny - 2.0) ** 2
+    F = np.zeros((3, ny))
+    F[0] = Fx
+    F[:, typ == orc.SOLID] = 0
+    m = orc.step19(eq_state(1.0, np.zeros((3, ny))), shape, tau, F=F, typ=typ, n=12000)
+    y = np.arange(ny)
+    want = Fx / (2 * nu) * (y - 0.5) * (ny - 1.5 - y)
+    fl = typ != orc.SOLID
+    err = np.sqrt(((m[1][fl] - want[fl]) ** 2).sum() / (want[fl] ** 2).sum())
+    assert err < 0.02, err
+    assert np.abs(m[2:4][:, fl]).max() < 1e-12
+
+
+def test_d3q19_inflow_outflow_cells(orc):
+    """Inflow cells take the inflow equilibrium, the outflow plane copies x = nx-2,
+    solid cells keep their value."""
+    shape = (9, 6, 5)
+    rng = np.random.default_rng(36)
+    mask = W.channel_walls(shape)
+    typ, _, _, _ = orc.classify(mask, True, True)
+    m = random_state(shape, rng)
+    inflow = [1.01, 0.03, -0.01, 0.02]
+    out = orc.step19(m, shape, 0.6, typ=typ, inflow=inflow)
+    nx = shape[0]
+    i_in = np.nonzero(typ == orc.INFLOW)[0]
+    assert len(i_in) and np.allclose(out[0, i_in], 1.01) and np.allclose(out[1, i_in], 0.03)
+    assert np.allclose(out[4, i_in], 0.03 ** 2) and np.allclose(out[7, i_in], 0.03 * -0.01)
+    i_out = np.nonzero(typ == orc.OUTFLOW)[0]
+    assert len(i_out) and np.all(i_out % nx == nx - 1)
+    assert np.array_equal(out[:, i_out], out[:, i_out - 1])
+    sol = typ == orc.SOLID
+    assert np.array_equal(out[:, sol], m[:, sol])
