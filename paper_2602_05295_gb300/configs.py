@@ -107,8 +107,8 @@ def run_turbulence256_d3q19(steps):
     return out
 
 
-def _channel(wl, mask, inflow_u, steps, storage="q16"):
-    sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602)
+def _channel(wl, mask, inflow_u, steps, storage="q16", lattice=27):
+    sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602, lattice=lattice)
     N = wl.cells
     u = np.zeros((3, N), np.float32)
     u[0] = inflow_u
@@ -128,7 +128,8 @@ def _channel(wl, mask, inflow_u, steps, storage="q16"):
     M0, _ = sim.reduce()
     ms = _timed_steps(sim, steps)
     M1, E1 = sim.reduce()
-    rec = {"workload": wl.name, "storage": storage, "cells": N, "fluid_cells": fluid,
+    rec = {"workload": wl.name + ("_d3q19" if lattice == 19 else ""), "storage": storage,
+           "cells": N, "fluid_cells": fluid,
            "solid_fraction": 1.0 - fluid / N, "boundary_list": int(cells.numel()),
            "classify_ms": classify_ms, "ms_per_step": ms, "MLUPS": N / ms / 1e3,
            "fluid_MLUPS": fluid / ms / 1e3, "memory_bytes": sim.memory_bytes(),
@@ -141,6 +142,16 @@ def run_channel512(steps):
     wl = W.CHANNEL512
     mask, spheres = W.sphere_pack(wl.shape)
     rec = _channel(wl, mask, 0.05, steps)
+    rec["spheres"] = int(len(spheres))
+    return rec
+
+
+def run_channel512_d3q19(steps):
+    """The sphere channel on the D3Q19 lattice (the paper runs one scene with solids
+    on D3Q19): halfway bounce-back over its 19 directions."""
+    wl = W.CHANNEL512
+    mask, spheres = W.sphere_pack(wl.shape)
+    rec = _channel(wl, mask, 0.05, steps, lattice=19)
     rec["spheres"] = int(len(spheres))
     return rec
 
@@ -283,6 +294,7 @@ def run_bits_sweep(steps):
 
 RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256,
            "turbulence256_d3q19": run_turbulence256_d3q19, "channel512": run_channel512,
+           "channel512_d3q19": run_channel512_d3q19,
            "channel512_moving": run_channel512_moving, "large1000": run_large1000, "adjoint128": run_adjoint128, "bits_sweep": run_bits_sweep,
            "mixed_vs_recompute": run_mixed_vs_recompute}
 

@@ -93,7 +93,7 @@ int mixed_unsupported(melbm_t h, const char* what) {
 }
 
 int q19_unsupported(melbm_t h, const char* what) {
-  return fail(h, MELBM_EINVAL, "%s: D3Q19 handles are periodic (no solids, inflow, outflow, walls)", what);
+  return fail(h, MELBM_EINVAL, "%s: D3Q19 handles take halfway bounce-back walls only", what);
 }
 
 int ensure_staging(melbm_t h, size_t bytes) {
@@ -195,16 +195,17 @@ int reclassify(melbm_t h) {
 namespace melbm {
 cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out) {
   const float omega = 1.0f / h->tau;
-  if (h->lattice == MELBM_D3Q19)
-    return launch_fluid19(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out, h->seed,
-                          h->grids, h->stream);
-  cudaError_t e = launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                               h->seed, h->grids, h->stream);
+  cudaError_t e =
+      h->lattice == MELBM_D3Q19
+          ? launch_fluid19(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
+                           h->seed, h->grids, h->stream)
+          : launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
+                         h->seed, h->grids, h->stream);
   if (e == cudaSuccess && h->L)
     e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
                         h->list_word, h->L, h->src_cells, h->S, h->src_table, h->src_pop,
                         h->inflow, t_out, h->seed, h->grids, h->wall_model, h->mask, h->bodies,
-                        h->stream);
+                        h->lattice, h->stream);
   if (e == cudaSuccess && h->outflow_on && h->type)
     e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream);
   return e;
@@ -367,7 +368,6 @@ int melbm_get_moments(melbm_t h, float* rho, float* u, float* S) {
 int melbm_set_solid(melbm_t h, const uint8_t* mask) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_solid: NULL handle");
   if (mask && !is_device_ptr(mask)) return fail(h, MELBM_EINVAL, "melbm_set_solid: mask must be a device pointer");
-  if (mask && h->lattice == MELBM_D3Q19) return q19_unsupported(h, "melbm_set_solid");
   if (!mask) {
     dev_free(h, h->mask, size_t(h->N));
     h->mask = nullptr;
@@ -381,7 +381,6 @@ int melbm_set_solid(melbm_t h, const uint8_t* mask) {
 
 int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float uz) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_inflow: NULL handle");
-  if (h->lattice == MELBM_D3Q19) return q19_unsupported(h, "melbm_set_inflow");
   if (face != 0) return fail(h, MELBM_EINVAL, "melbm_set_inflow: only face 0 (x = 0) is supported");
   if (!(rho > 0.f)) return fail(h, MELBM_EINVAL, "melbm_set_inflow: rho must be positive");
   h->inflow_on = 1;
@@ -394,7 +393,6 @@ int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float u
 
 int melbm_set_outflow(melbm_t h, int face) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_outflow: NULL handle");
-  if (h->lattice == MELBM_D3Q19) return q19_unsupported(h, "melbm_set_outflow");
   if (face != 1) return fail(h, MELBM_EINVAL, "melbm_set_outflow: only face 1 (x = nx-1) is supported");
   h->outflow_on = 1;
   return reclassify(h);

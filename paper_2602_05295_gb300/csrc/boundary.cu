@@ -15,6 +15,8 @@
 //     own post-collision moments.
 //   * INFLOW: reset to the equilibrium (rho_in, u_in, S = u_in u_in).
 // The outflow pass then copies the stored state of x = nx-2 onto x = nx-1.
+// On the D3Q19 lattice the same update runs over its 19 directions and weights
+// (halfway bounce-back only).
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
 
@@ -40,7 +42,7 @@ struct BoundaryParams {
   QGrids q;
 };
 
-template <int STORAGE, bool FORCE, bool MOVING>
+template <int STORAGE, bool FORCE, bool MOVING, bool Q19 = false>
 __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= P.count) return;
@@ -76,6 +78,7 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
     const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    if (Q19 && !in_d3q19(cx, cy, cz)) continue;  // D3Q19: no corner populations
     // f_i / w_i - 1: population i pulled from x - c_i, or, for a solid link,
     // population opp(i) = 26 - i of x itself (bounce-back; the slot then holds x)
     // or the population of the moving wall
@@ -90,8 +93,9 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
       const int j = ((word >> i) & 1u) ? 26 - i : i;
       g = __ldg(P.pop + int64_t(j) * P.S + slot);
     }
-    const float w = (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *
-                    (cz ? (1.0f / 6.0f) : (2.0f / 3.0f));
+    const float w = Q19 ? lattice_weight19(cx, cy, cz)
+                        : (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *
+                              (cz ? (1.0f / 6.0f) : (2.0f / 3.0f));
     const float f = w * g;
     m000 += f;
     m100 += cx * f;
@@ -114,10 +118,12 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
                             int64_t S, const uint32_t* table, float* pop, const float inflow[4],
                             uint32_t t_out, uint32_t seed, const QGrids& q, int wall_model,
-                            const uint8_t* mask, const float* bodies, cudaStream_t st) {
+                            const uint8_t* mask, const float* bodies, int lattice,
+                            cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
+  if (lattice == 19 && wall_model != 0) return cudaErrorInvalidValue;
   cudaError_t e = launch_source_collide(storage, size_t(nx) * ny * nz, in, force, omega, src_cells,
-                                        S, pop, q, st);
+                                        S, pop, q, lattice, st);
   if (e != cudaSuccess) return e;
   BoundaryParams p;
   p.nx = nx;
@@ -145,6 +151,16 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
   p.bodies = bodies;
   const unsigned blocks = unsigned((count + 127) / 128);
   const bool mv = wall_model == 1;
+  if (lattice == 19) {
+    if (storage == ST_Q16) {
+      if (force) boundary_kernel<ST_Q16, true, false, true><<<blocks, 128, 0, st>>>(p);
+      else boundary_kernel<ST_Q16, false, false, true><<<blocks, 128, 0, st>>>(p);
+    } else {
+      if (force) boundary_kernel<ST_F32, true, false, true><<<blocks, 128, 0, st>>>(p);
+      else boundary_kernel<ST_F32, false, false, true><<<blocks, 128, 0, st>>>(p);
+    }
+    return cudaGetLastError();
+  }
   if (storage == ST_Q16) {
     if (force) {
       if (mv) boundary_kernel<ST_Q16, true, true><<<blocks, 128, 0, st>>>(p);

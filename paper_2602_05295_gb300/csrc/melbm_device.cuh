@@ -532,6 +532,34 @@ __device__ __forceinline__ float hermite_eval(const Mom17& A, int cx, int cy, in
          27.0f * A.m111 * fx * fy * fz;
 }
 
+// f+_i / w19_i - 1 on the D3Q19 lattice (|c|^2 <= 2, weights 1/3, 1/18, 1/36):
+// the same zeroth to second order terms, and the third order projected on what
+// the lattice carries -- for each pair of triples (a a b, b g g) with moments
+// (A, B) and Hermite polynomials (h1, h2) = (P2(c_a) c_b, c_b P2(c_g)),
+//   (A + B)(h1 + h2)/(2 c_s^6) + (A - B)(h1 - h2)/(6 c_s^6) = A (18 h1 + 9 h2) + B (9 h1 + 18 h2),
+// and no xyz term.
+__device__ __forceinline__ float hermite_eval19(const Mom17& A, int cx, int cy, int cz) {
+  const float fx = float(cx), fy = float(cy), fz = float(cz);
+  const float qx = fx * fx - (1.0f / 3.0f), qy = fy * fy - (1.0f / 3.0f),
+              qz = fz * fz - (1.0f / 3.0f);
+  const float hy1 = qx * fy, hy2 = fy * qz;  // xxy, yzz
+  const float hx1 = fx * qy, hx2 = fx * qz;  // xyy, xzz
+  const float hz1 = qx * fz, hz2 = qy * fz;  // xxz, yyz
+  return A.m000 + 3.0f * (A.m100 * fx + A.m010 * fy + A.m001 * fz) +
+         4.5f * (A.m200 * qx + A.m020 * qy + A.m002 * qz) +
+         9.0f * (A.m110 * fx * fy + A.m101 * fx * fz + A.m011 * fy * fz) +
+         A.m210 * (18.0f * hy1 + 9.0f * hy2) + A.m012 * (9.0f * hy1 + 18.0f * hy2) +
+         A.m120 * (18.0f * hx1 + 9.0f * hx2) + A.m102 * (9.0f * hx1 + 18.0f * hx2) +
+         A.m201 * (18.0f * hz1 + 9.0f * hz2) + A.m021 * (9.0f * hz1 + 18.0f * hz2);
+}
+__device__ __forceinline__ constexpr bool in_d3q19(int cx, int cy, int cz) {
+  return cx * cx + cy * cy + cz * cz <= 2;
+}
+__device__ __forceinline__ float lattice_weight19(int cx, int cy, int cz) {
+  const int n2 = cx * cx + cy * cy + cz * cz;
+  return n2 == 0 ? (1.0f / 3.0f) : (n2 == 1 ? (1.0f / 18.0f) : (1.0f / 36.0f));
+}
+
 // Hermite moments of the wall state of the moment-based reconstruction (Sec.
 // 3.2): rho^p = rho of the cell, u^p the wall velocity, and the non-equilibrium
 // stress rho (S - u u) of the cell's post-collision moments A kept, i.e.

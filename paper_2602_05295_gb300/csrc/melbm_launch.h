@@ -77,7 +77,7 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
                             int64_t S, const uint32_t* table, float* pop, const float inflow[4],
                             uint32_t t_out, uint32_t seed, const QGrids& q, int wall_model,
-                            const uint8_t* mask, const float* bodies, cudaStream_t st);
+                            const uint8_t* mask, const float* bodies, int lattice, cudaStream_t st);
 
 // Force and torque (about r0 of the body) the next step transfers to the solid
 // cells of body `body` (0: every solid) by momentum exchange over the solid
@@ -103,7 +103,7 @@ cudaError_t launch_source_setup_fill(int nx, int ny, int nz, const uint32_t* cel
                                      uint32_t* slot_of, uint32_t* table, cudaStream_t st);
 cudaError_t launch_source_collide(int storage, size_t N, const void* in, const float* force,
                                   float omega, const uint32_t* src_cells, int64_t S, float* pop,
-                                  const QGrids& q, cudaStream_t st);
+                                  const QGrids& q, int lattice, cudaStream_t st);
 
 // Outflow copy on the plane x = nx-1 (cells typed OUTFLOW), in place on buf.
 cudaError_t launch_outflow(int storage, int nx, int ny, int nz, void* buf, const uint8_t* type,

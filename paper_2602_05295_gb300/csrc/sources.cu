@@ -127,8 +127,9 @@ cudaError_t launch_source_setup_fill(int nx, int ny, int nz, const uint32_t* cel
 
 // ----------------------------------------------------------------- phase A
 // pop[i S + s] = f+_i / w_i - 1 at source cell src_cells[s] (App. A with its
-// force, then the Hermite population of direction i).
-template <int STORAGE, bool FORCE>
+// force, then the Hermite population of direction i).  D3Q19 (Q19): the 19
+// directions with |c|^2 <= 2 and their own weights; the corner rows stay unused.
+template <int STORAGE, bool FORCE, bool Q19>
 __global__ void __launch_bounds__(256) source_collide_kernel(const void* in, size_t N,
                                                              const float* force, float omega,
                                                              const uint32_t* src_cells, int64_t S,
@@ -144,22 +145,35 @@ __global__ void __launch_bounds__(256) source_collide_kernel(const void* in, siz
   }
   const Mom17 A = collide_moments<FORCE>(load_stored<STORAGE>(in, N, n, q), omega, fx, fy, fz);
 #pragma unroll
-  for (int i = 0; i < 27; ++i)
-    pop[int64_t(i) * S + s] = hermite_eval(A, i % 3 - 1, (i / 3) % 3 - 1, i / 9 - 1);
+  for (int i = 0; i < 27; ++i) {
+    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    if (Q19 && !in_d3q19(cx, cy, cz)) continue;
+    pop[int64_t(i) * S + s] = Q19 ? hermite_eval19(A, cx, cy, cz) : hermite_eval(A, cx, cy, cz);
+  }
+}
+
+template <bool Q19>
+static void launch_source_collide_t(int storage, size_t N, const void* in, const float* force,
+                                    float omega, const uint32_t* src_cells, int64_t S, float* pop,
+                                    const QGrids& q, cudaStream_t st) {
+  const unsigned blocks = unsigned((S + 255) / 256);
+  if (storage == ST_Q16) {
+    if (force) source_collide_kernel<ST_Q16, true, Q19><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
+    else source_collide_kernel<ST_Q16, false, Q19><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
+  } else {
+    if (force) source_collide_kernel<ST_F32, true, Q19><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
+    else source_collide_kernel<ST_F32, false, Q19><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
+  }
 }
 
 cudaError_t launch_source_collide(int storage, size_t N, const void* in, const float* force,
                                   float omega, const uint32_t* src_cells, int64_t S, float* pop,
-                                  const QGrids& q, cudaStream_t st) {
+                                  const QGrids& q, int lattice, cudaStream_t st) {
   if (S <= 0) return cudaSuccess;
-  const unsigned blocks = unsigned((S + 255) / 256);
-  if (storage == ST_Q16) {
-    if (force) source_collide_kernel<ST_Q16, true><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
-    else source_collide_kernel<ST_Q16, false><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
-  } else {
-    if (force) source_collide_kernel<ST_F32, true><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
-    else source_collide_kernel<ST_F32, false><<<blocks, 256, 0, st>>>(in, N, force, omega, src_cells, S, pop, q);
-  }
+  if (lattice == 19)
+    launch_source_collide_t<true>(storage, N, in, force, omega, src_cells, S, pop, q, st);
+  else
+    launch_source_collide_t<false>(storage, N, in, force, omega, src_cells, S, pop, q, st);
   return cudaGetLastError();
 }
 
