@@ -78,7 +78,7 @@ def lib():
             L.orc_encode_bits.argtypes = [I, I, I, P, U32, U32, I, I, I, P]
             L.orc_step_wall_f64.argtypes = [I, I, I, D, P, P, P, P, I, P, P, P]
             L.orc_step19_f64.argtypes = [I, I, I, D, P, P, P, P, P]
-            L.orc_step19_cells_f64.argtypes = [I, I, I, D, P, P, P, I64, P]
+            L.orc_step19_cells_f64.argtypes = [I, I, I, D, P, P, P, P, P, I64, P]
             L.orc_reconstruct19.argtypes = [P, P, P, P]
             L.orc_solid_force_f64.argtypes = [I, I, I, D, P, P, P, I, P, P, I, P]
             L.orc_decode_bits.argtypes = [I64, P, I, I, P]
@@ -218,13 +218,16 @@ def step19(m, shape, tau, F=None, n=1, typ=None, inflow=None):
     return cur
 
 
-def step19_cells(m, shape, tau, cells, F=None):
-    """The periodic D3Q19 update of the listed cells: (10, len(cells))."""
+def step19_cells(m, shape, tau, cells, F=None, typ=None, inflow=None):
+    """The D3Q19 update of the listed cells: (10, len(cells))."""
     nx, ny, nz = shape
     ma = _f64(m)
     ca = np.ascontiguousarray(cells, np.int64)
+    ta = None if typ is None else np.ascontiguousarray(typ, np.uint8)
+    ia = None if inflow is None else np.ascontiguousarray(inflow, np.float64)
     out = np.empty((len(ca), 10))
-    lib().orc_step19_cells_f64(nx, ny, nz, float(tau), _p(ma), _p(_f64(F)), _p(ca), len(ca), _p(out))
+    lib().orc_step19_cells_f64(nx, ny, nz, float(tau), _p(ma), _p(_f64(F)), _p(ta), _p(ia), _p(ca),
+                               len(ca), _p(out))
     return out.T.copy()
 
 

@@ -804,28 +804,46 @@ void orc_step19_f64(int nx, int ny, int nz, double tau, const double* m, const d
   step_grid19(Grid{nx, ny, nz}, tau, m, F, type, inflow, out);
 }
 
-// The periodic D3Q19 update of the listed cells only (each collides the 19 cells
-// it pulls from); out is [ncells][10].
+// The D3Q19 update of the listed cells only (each collides the cells it pulls
+// from; type / inflow as for the full step, or NULL); out is [ncells][10].
 void orc_step19_cells_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
-                          const int64_t* cells, int64_t ncells, double* out) {
+                          const uint8_t* type, const double* inflow, const int64_t* cells,
+                          int64_t ncells, double* out) {
   Grid g{nx, ny, nz};
   const int64_t N = g.N();
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t k = 0; k < ncells; ++k) {
-    const int64_t n = cells[k];
-    const int x = int(n % nx), y = int((n / nx) % ny), z = int(n / (int64_t(nx) * ny));
-    double f[19];
-    for (int i = 0; i < 19; ++i) {
-      const int sx = (x - L19.c[i][0] + nx) % nx, sy = (y - L19.c[i][1] + ny) % ny,
-                sz = (z - L19.c[i][2] + nz) % nz;
-      const int64_t src = g.idx(sx, sy, sz);
-      double Fx[3];
-      load_force(F, N, src, Fx);
-      f[i] = reconstruct19(i, collide(load(m, N, src), Fx, tau));
+    int64_t n = cells[k];
+    uint8_t t = type ? type[n] : FLUID;
+    if (t == OUTFLOW) {
+      n = n - 1;
+      t = type[n];
     }
-    double Fx[3];
-    load_force(F, N, n, Fx);
-    store(out + 10 * k, 1, 0, moments19(f, Fx));
+    Mom<double> r;
+    if (t == SOLID) {
+      r = load(m, N, n);
+    } else if (t == INFLOW) {
+      r = inflow_state<double>(inflow);
+    } else {
+      const int x = int(n % nx), y = int((n / nx) % ny), z = int(n / (int64_t(nx) * ny));
+      double Fn[3];
+      load_force(F, N, n, Fn);
+      double f[19];
+      for (int i = 0; i < 19; ++i) {
+        const int sx = (x - L19.c[i][0] + nx) % nx, sy = (y - L19.c[i][1] + ny) % ny,
+                  sz = (z - L19.c[i][2] + nz) % nz;
+        const int64_t src = g.idx(sx, sy, sz);
+        if (type && type[src] == SOLID) {
+          f[i] = reconstruct19(L19.opp[i], collide(load(m, N, n), Fn, tau));
+        } else {
+          double Fx[3];
+          load_force(F, N, src, Fx);
+          f[i] = reconstruct19(i, collide(load(m, N, src), Fx, tau));
+        }
+      }
+      r = moments19(f, Fn);
+    }
+    store(out + 10 * k, 1, 0, r);
   }
 }
 

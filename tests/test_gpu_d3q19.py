@@ -231,6 +231,39 @@ def test_d3q19_q16_channel_one_step_codes_match_emulation(M, orc):
     assert (d > 0).mean() < 0.02
 
 
+def test_d3q19_channel512_sampled_one_step(M, orc):
+    """The full-size sphere channel on D3Q19 (16-bit): one GPU step against the
+    oracle's D3Q19 update of sampled listed, inflow, outflow and fluid cells."""
+    wl = W.CHANNEL512
+    mask, _ = W.sphere_pack(wl.shape)
+    N = wl.cells
+    rng = np.random.default_rng(28)
+    u = np.zeros((3, N), np.float32)
+    u[0] = 0.05
+    u += (0.01 * rng.standard_normal((3, N))).astype(np.float32)
+    sim = M.Simulator(wl.shape, wl.tau, "q16", seed=8, lattice=19)
+    sim.set_state(to_gpu(np.ones(N, np.float32)), to_gpu(u))
+    sim.set_solid(to_gpu(mask.ravel(), torch.uint8))
+    sim.set_inflow(1.0, (0.05, 0.0, 0.0))
+    sim.set_outflow()
+    typ = sim.types().cpu().numpy()
+    listed, _ = sim.boundary_list()
+    listed = listed.cpu().numpy().astype(np.int64)
+    sim.step(2)
+    g_in = read(sim)
+    sim.step(1)
+    g_out = read(sim)
+    cells = np.unique(np.concatenate([
+        rng.choice(listed, 3000, replace=False), rng.integers(0, N, 2000),
+        np.nonzero(typ == orc.INFLOW)[0][:300], np.nonzero(typ == orc.OUTFLOW)[0][:300]]))
+    cells = cells[typ[cells] != orc.SOLID]
+    ref = orc.step19_cells(g_in, wl.shape, wl.tau, cells, typ=typ, inflow=[1.0, 0.05, 0.0, 0.0])
+    got = g_out[:, cells]
+    du = np.abs(got[1:4] - ref[1:4]).max()
+    drho = np.abs(got[0] - ref[0]).max()
+    assert du <= 0.8 / 65535 * 1.01 and drho <= 0.7 / 65535 * 1.01, (du, drho)
+
+
 def test_d3q19_refuses_what_it_does_not_cover(M):
     shape = (16, 8, 8)
     N = 16 * 8 * 8

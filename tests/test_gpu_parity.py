@@ -199,6 +199,47 @@ def test_classification_of_config_channel512_bit_exact(M, orc):
     assert np.array_equal(sim.types().cpu().numpy(), t)
 
 
+@pytest.mark.parametrize("storage", ["f32", "q16"])
+def test_channel512_sampled_one_step(M, orc, storage):
+    """At the full 512 x 256 x 256 sphere-channel size (the configuration the
+    channel workload times), one GPU step agrees with the oracle's update of
+    sampled cells -- listed boundary cells, inflow and outflow cells and plain
+    fluid cells -- computed from the GPU's own input state."""
+    wl = W.CHANNEL512
+    mask, _ = W.sphere_pack(wl.shape)
+    N = wl.cells
+    rng = np.random.default_rng(27)
+    u = np.zeros((3, N), np.float32)
+    u[0] = 0.05
+    u += (0.01 * rng.standard_normal((3, N))).astype(np.float32)
+    sim = M.Simulator(wl.shape, wl.tau, storage, seed=8)
+    sim.set_state(to_gpu(np.ones(N, np.float32)), to_gpu(u))
+    sim.set_solid(to_gpu(mask.ravel(), torch.uint8))
+    sim.set_inflow(1.0, (0.05, 0.0, 0.0))
+    sim.set_outflow()
+    typ = sim.types().cpu().numpy()
+    listed, _ = sim.boundary_list()
+    listed = listed.cpu().numpy().astype(np.int64)
+    sim.step(2)
+    g_in = read(sim)
+    sim.step(1)
+    g_out = read(sim)
+    nx = wl.shape[0]
+    cells = np.unique(np.concatenate([
+        rng.choice(listed, 3000, replace=False), rng.integers(0, N, 2000),
+        np.nonzero(typ == orc.INFLOW)[0][:300], np.nonzero(typ == orc.OUTFLOW)[0][:300]]))
+    cells = cells[typ[cells] != orc.SOLID]
+    ref = orc.step_cells(g_in, wl.shape, wl.tau, cells, typ=typ, inflow=[1.0, 0.05, 0.0, 0.0])
+    got = g_out[:, cells]
+    du = np.abs(got[1:4] - ref[1:4]).max()
+    drho = np.abs(got[0] - ref[0]).max()
+    if storage == "f32":
+        assert du < 5e-7 and drho < 5e-7, (du, drho)
+    else:
+        assert du <= 0.8 / 65535 * 1.01 and drho <= 0.7 / 65535 * 1.01, (du, drho)
+    assert np.all(cells % nx < nx)
+
+
 # ------------------------------------------------------------------ boundaries
 def _channel_case(shape=(48, 26, 22)):
     nx, ny, nz = shape

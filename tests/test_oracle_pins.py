@@ -959,3 +959,18 @@ def test_d3q19_inflow_outflow_cells(orc):
     assert np.array_equal(out[:, i_out], out[:, i_out - 1])
     sol = typ == orc.SOLID
     assert np.array_equal(out[:, sol], m[:, sol])
+
+
+def test_d3q19_sampled_cells_agree_with_full_step_with_boundaries(orc):
+    shape = (9, 7, 6)
+    rng = np.random.default_rng(37)
+    mask = W.channel_walls(shape)
+    mask[3, 3, 4] = 1
+    typ, _, _, _ = orc.classify(mask, True, True)
+    m = random_state(shape, rng)
+    F = 1e-4 * rng.standard_normal((3, m.shape[1]))
+    inflow = [1.0, 0.04, 0.0, 0.01]
+    full = orc.step19(m, shape, 0.6, F=F, typ=typ, inflow=inflow)
+    cells = np.arange(m.shape[1])
+    got = orc.step19_cells(m, shape, 0.6, cells, F=F, typ=typ, inflow=inflow)
+    assert np.abs(got - full).max() < 1e-15
