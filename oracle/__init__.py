@@ -79,6 +79,8 @@ def lib():
             L.orc_step_wall_f64.argtypes = [I, I, I, D, P, P, P, P, I, P, P, P]
             L.orc_step19_f64.argtypes = [I, I, I, D, P, P, P, P, P]
             L.orc_step19_cells_f64.argtypes = [I, I, I, D, P, P, P, P, P, I64, P]
+            L.orc_step19_wall_f64.argtypes = [I, I, I, D, P, P, P, P, I, P, P, P]
+            L.orc_solid_force19_f64.argtypes = [I, I, I, D, P, P, P, I, P, P, I, P]
             L.orc_reconstruct19.argtypes = [P, P, P, P]
             L.orc_solid_force_f64.argtypes = [I, I, I, D, P, P, P, I, P, P, I, P]
             L.orc_decode_bits.argtypes = [I64, P, I, I, P]
@@ -203,9 +205,9 @@ def step(m, shape, tau, F=None, typ=None, inflow=None, n=1, literal_xyz=False, w
     return cur
 
 
-def step19(m, shape, tau, F=None, n=1, typ=None, inflow=None):
-    """n FP64 D3Q19 steps of the public state ``m`` (10, N); ``typ``/``inflow`` as
-    for ``step`` (None: periodic)."""
+def step19(m, shape, tau, F=None, n=1, typ=None, inflow=None, wall=None):
+    """n FP64 D3Q19 steps of the public state ``m`` (10, N); ``typ``/``inflow``/
+    ``wall`` as for ``step`` (None: periodic)."""
     nx, ny, nz = shape
     cur = _f64(m).copy()
     out = np.empty_like(cur)
@@ -213,7 +215,11 @@ def step19(m, shape, tau, F=None, n=1, typ=None, inflow=None):
     ta = None if typ is None else np.ascontiguousarray(typ, np.uint8)
     ia = None if inflow is None else np.ascontiguousarray(inflow, np.float64)
     for _ in range(n):
-        lib().orc_step19_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(ta), _p(ia), _p(out))
+        if wall is None:
+            lib().orc_step19_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(ta), _p(ia), _p(out))
+        else:
+            lib().orc_step19_wall_f64(nx, ny, nz, float(tau), _p(cur), _p(Fa), _p(ta), _p(ia),
+                                      wall.model, _p(wall.body), _p(wall.table), _p(out))
         cur, out = out, cur
     return cur
 
@@ -240,14 +246,14 @@ def reconstruct19(m10):
     return f, c, w
 
 
-def solid_force(m, shape, tau, typ, wall, F=None, body_id=0):
+def solid_force(m, shape, tau, typ, wall, F=None, body_id=0, lattice=27):
     """(Fx, Fy, Fz, Tx, Ty, Tz) the next step transfers to body ``body_id`` (0: all
     solids) by momentum exchange; torque about the body's r0."""
     nx, ny, nz = shape
     out = np.zeros(6)
-    lib().orc_solid_force_f64(nx, ny, nz, float(tau), _p(_f64(m)), _p(_f64(F)),
-                              _p(np.ascontiguousarray(typ, np.uint8)), wall.model,
-                              _p(wall.body), _p(wall.table), int(body_id), _p(out))
+    fn = lib().orc_solid_force19_f64 if lattice == 19 else lib().orc_solid_force_f64
+    fn(nx, ny, nz, float(tau), _p(_f64(m)), _p(_f64(F)), _p(np.ascontiguousarray(typ, np.uint8)),
+       wall.model, _p(wall.body), _p(wall.table), int(body_id), _p(out))
     return out
 
 

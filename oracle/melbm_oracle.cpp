@@ -407,12 +407,27 @@ Mom<T> moments19(const T* f, const T F[3]) {
   return o;
 }
 
+// The population solid link i of cell n receives on the D3Q19 lattice: halfway
+// bounce-back, or the D3Q19 reconstruction of the wall state (rho^p, u^p, S^p) at
+// the link's halfway point (the same solid coupling as on D3Q27).
+double wall_population19(const Grid& g, const std::vector<Mom<double>>& mp, int64_t n,
+                         int64_t src, int i, const WallSpec* w) {
+  if (!w || w->model == 0) return reconstruct19(L19.opp[i], mp[n]);
+  const int x = int(n % g.nx), y = int((n / g.nx) % g.ny), z = int(n / (int64_t(g.nx) * g.ny));
+  const double p[3] = {x - 0.5 * L19.c[i][0], y - 0.5 * L19.c[i][1], z - 0.5 * L19.c[i][2]};
+  double up[3];
+  wall_velocity(*w, w->body ? w->body[src] : 1, p, up);
+  return reconstruct19(i, wall_moments(mp[n], up));
+}
+
 // One D3Q19 step: collide every non-solid cell, pull the 19 populations (halfway
-// bounce-back f_i(x) = f+_opp(i)(x) where x - c_i is solid), re-form the moments;
-// inflow cells take the inflow equilibrium, solid cells keep their value and the
-// outflow plane copies x = nx-2 (the same split-design boundaries as D3Q27).
+// bounce-back f_i(x) = f+_opp(i)(x) where x - c_i is solid, or the moving-wall
+// population), re-form the moments; inflow cells take the inflow equilibrium,
+// solid cells keep their value and the outflow plane copies x = nx-2 (the same
+// split-design boundaries as D3Q27).
 Mom<double> pull_and_moments19(const Grid& g, const std::vector<Mom<double>>& mp,
-                               const uint8_t* type, const double* F, int64_t n) {
+                               const uint8_t* type, const double* F, int64_t n,
+                               const WallSpec* w = nullptr) {
   const int x = int(n % g.nx), y = int((n / g.nx) % g.ny), z = int(n / (int64_t(g.nx) * g.ny));
   double f[19];
   for (int i = 0; i < 19; ++i) {
@@ -420,7 +435,7 @@ Mom<double> pull_and_moments19(const Grid& g, const std::vector<Mom<double>>& mp
               sz = (z - L19.c[i][2] + g.nz) % g.nz;
     const int64_t src = g.idx(sx, sy, sz);
     if (type && type[src] == SOLID)
-      f[i] = reconstruct19(L19.opp[i], mp[n]);
+      f[i] = wall_population19(g, mp, n, src, i, w);
     else
       f[i] = reconstruct19(i, mp[src]);
   }
@@ -430,7 +445,7 @@ Mom<double> pull_and_moments19(const Grid& g, const std::vector<Mom<double>>& mp
 }
 
 void step_grid19(const Grid& g, double tau, const double* m, const double* F, const uint8_t* type,
-                 const double* inflow, double* out) {
+                 const double* inflow, double* out, const WallSpec* w = nullptr) {
   const int64_t N = g.N();
   std::vector<Mom<double>> mp(N);
 #pragma omp parallel for schedule(static)
@@ -448,7 +463,7 @@ void step_grid19(const Grid& g, double tau, const double* m, const double* F, co
     else if (t == INFLOW)
       store(out, N, n, inflow_state<double>(inflow));
     else
-      store(out, N, n, pull_and_moments19(g, mp, type, F, n));
+      store(out, N, n, pull_and_moments19(g, mp, type, F, n, w));
   }
   if (type) {
 #pragma omp parallel for schedule(static)
@@ -844,6 +859,56 @@ void orc_step19_cells_f64(int nx, int ny, int nz, double tau, const double* m, c
       r = moments19(f, Fn);
     }
     store(out + 10 * k, 1, 0, r);
+  }
+}
+
+// The D3Q19 step with the wall model of WallSpec.
+void orc_step19_wall_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                         const uint8_t* type, const double* inflow, int model,
+                         const uint8_t* body, const double* table, double* out) {
+  const WallSpec w{model, body, table};
+  step_grid19(Grid{nx, ny, nz}, tau, m, F, type, inflow, out, &w);
+}
+
+// Force and torque on body `body_id` (0: every solid) by momentum exchange over
+// the 19-velocity links, as orc_solid_force_f64 does over 27.
+void orc_solid_force19_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                           const uint8_t* type, int model, const uint8_t* body,
+                           const double* table, int body_id, double* out /*6*/) {
+  const Grid g{nx, ny, nz};
+  const int64_t N = g.N();
+  const WallSpec w{model, body, table};
+  std::vector<Mom<double>> mp(N);
+  for (int64_t n = 0; n < N; ++n) {
+    if (type[n] == SOLID) continue;
+    double Fx[3];
+    load_force(F, N, n, Fx);
+    mp[n] = collide(load(m, N, n), Fx, tau);
+  }
+  for (int k = 0; k < 6; ++k) out[k] = 0.0;
+  for (int64_t n = 0; n < N; ++n) {
+    if (type[n] != FLUID_BOUNDARY) continue;
+    const int x = int(n % nx), y = int((n / nx) % ny), z = int(n / (int64_t(nx) * ny));
+    for (int i = 0; i < 19; ++i) {
+      const int64_t src = g.idx((x - L19.c[i][0] + nx) % nx, (y - L19.c[i][1] + ny) % ny,
+                                (z - L19.c[i][2] + nz) % nz);
+      if (type[src] != SOLID) continue;
+      const int b = body ? body[src] : 1;
+      if (body_id && b != body_id) continue;
+      const double f_out = reconstruct19(L19.opp[i], mp[n]);
+      const double f_in = wall_population19(g, mp, n, src, i, &w);
+      const double p[3] = {x - 0.5 * L19.c[i][0], y - 0.5 * L19.c[i][1], z - 0.5 * L19.c[i][2]};
+      double dF[3];
+      for (int a = 0; a < 3; ++a) dF[a] = -double(L19.c[i][a]) * (f_in + f_out);
+      const double* t = table + 9 * (body_id ? body_id : b);
+      const double r[3] = {p[0] - t[6], p[1] - t[7], p[2] - t[8]};
+      out[0] += dF[0];
+      out[1] += dF[1];
+      out[2] += dF[2];
+      out[3] += r[1] * dF[2] - r[2] * dF[1];
+      out[4] += r[2] * dF[0] - r[0] * dF[2];
+      out[5] += r[0] * dF[1] - r[1] * dF[0];
+    }
   }
 }
 

@@ -974,3 +974,52 @@ def test_d3q19_sampled_cells_agree_with_full_step_with_boundaries(orc):
     cells = np.arange(m.shape[1])
     got = orc.step19_cells(m, shape, 0.6, cells, F=F, typ=typ, inflow=inflow)
     assert np.abs(got - full).max() < 1e-15
+
+
+def test_d3q19_wall_momentum_exchange_balances_the_step(orc):
+    """The momentum-exchange identity on the 19-velocity lattice:
+    P(t+1) - P(t) = sum F - F_solid for both wall models with moving bodies."""
+    rng = np.random.default_rng(38)
+    shape = (9, 8, 7)
+    N = 9 * 8 * 7
+    body = _two_body_mask(shape, rng)
+    typ = orc.classify((body > 0).reshape(shape[::-1]))[0]
+    fluid = typ != orc.SOLID
+    u = 0.05 * rng.standard_normal((3, N))
+    m = np.zeros((10, N))
+    m[0] = 1 + 0.01 * rng.standard_normal(N)
+    m[1:4] = u
+    for k, (a, b) in enumerate(PAIRS):
+        m[4 + k] = u[a] * u[b] + 0.003 * rng.standard_normal(N)
+    F = 1e-4 * rng.standard_normal((3, N))
+    motion = {1: ([0.02, -0.01, 0.0], [0.0, 0.0, 0.003], [4.0, 3.5, 3.0]),
+              2: ([-0.01, 0.0, 0.015], [0.002, -0.001, 0.0], [1.0, 2.0, 5.0])}
+    for model in (0, 1):
+        wall = orc.Wall(model, body, motion)
+        new = orc.step19(m, shape, 0.6, F=F, typ=typ, wall=wall)
+        P0 = (m[0] * m[1:4])[:, fluid].sum(1)
+        P1 = (new[0] * new[1:4])[:, fluid].sum(1)
+        Fs = orc.solid_force(m, shape, 0.6, typ, wall, F=F, lattice=19)
+        assert np.abs(P1 - P0 - (F[:, fluid].sum(1) - Fs[:3])).max() < 1e-12, model
+        F1 = orc.solid_force(m, shape, 0.6, typ, wall, F=F, body_id=1, lattice=19)
+        F2 = orc.solid_force(m, shape, 0.6, typ, wall, F=F, body_id=2, lattice=19)
+        assert np.allclose(F1[:3] + F2[:3], Fs[:3], rtol=0, atol=1e-13)
+    # model 0 through the wall path equals the plain bounce-back step
+    bb = orc.step19(m, shape, 0.6, F=F, typ=typ)
+    assert np.abs(orc.step19(m, shape, 0.6, F=F, typ=typ, wall=orc.Wall(0, body)) - bb).max() == 0
+
+
+def test_d3q19_moment_wall_moving_with_the_flow_keeps_uniform_flow(orc):
+    rng = np.random.default_rng(39)
+    shape = (8, 7, 6)
+    N = 8 * 7 * 6
+    body = _two_body_mask(shape, rng)
+    typ = orc.classify((body > 0).reshape(shape[::-1]))[0]
+    fluid = typ != orc.SOLID
+    U = np.array([0.04, -0.02, 0.03])
+    m = eq_state(1.0, np.repeat(U[:, None], N, 1))
+    moving = orc.Wall(1, body, {1: (U, [0, 0, 0], [0, 0, 0]), 2: (U, [0, 0, 0], [3, 3, 3])})
+    new = orc.step19(m, shape, 0.7, typ=typ, wall=moving)
+    assert np.abs(new[:, fluid] - m[:, fluid]).max() < 1e-14
+    bb = orc.step19(m, shape, 0.7, typ=typ, wall=orc.Wall(0, body))
+    assert np.abs(bb[1:4, fluid] - m[1:4, fluid]).max() > 1e-3
