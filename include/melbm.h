@@ -82,10 +82,10 @@ enum { MELBM_FLUID = 0, MELBM_FLUID_BOUNDARY = 1, MELBM_INFLOW = 2, MELBM_OUTFLO
  * carries (the xyz term vanishes on it; each pair of triples T_aab, T_bgg enters
  * through its sum and difference), which reproduces rho, rho u, rho S and the six
  * rho T_aab.  A D3Q19 handle takes the same boundaries over its 19 directions
- * (halfway bounce-back at solid cells, inflow, outflow), with or without a body
- * force, in MELBM_F32 or MELBM_Q16 storage (any bit widths); the moving-wall
- * model, solid forces, the adjoint and MELBM_MIXED are refused with
- * MELBM_EINVAL. */
+ * (halfway bounce-back or the moving-wall model at solid cells, with their
+ * momentum-exchange force and torque; inflow; outflow), with or without a body
+ * force, in MELBM_F32 or MELBM_Q16 storage (any bit widths); the adjoint and
+ * MELBM_MIXED are refused with MELBM_EINVAL. */
 MELBM_API int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, melbm_t* out);
 
 /* Free every device and host resource of the handle.  NULL is accepted. */

@@ -92,10 +92,6 @@ int mixed_unsupported(melbm_t h, const char* what) {
   return fail(h, MELBM_EINVAL, "%s: not available with MELBM_MIXED storage", what);
 }
 
-int q19_unsupported(melbm_t h, const char* what) {
-  return fail(h, MELBM_EINVAL, "%s: D3Q19 handles take halfway bounce-back walls only", what);
-}
-
 int ensure_staging(melbm_t h, size_t bytes) {
   if (h->staging_bytes >= bytes) return MELBM_OK;
   dev_free(h, h->staging, h->staging_bytes);
@@ -564,7 +560,6 @@ int melbm_codec_decode(const uint32_t* words, int64_t N, int bits_rho_u, int bit
 int melbm_set_wall_model(melbm_t h, int model) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_wall_model: NULL handle");
   if (h->storage == MELBM_MIXED && model != 0) return mixed_unsupported(h, "melbm_set_wall_model");
-  if (h->lattice == MELBM_D3Q19 && model != 0) return q19_unsupported(h, "melbm_set_wall_model");
   if (model != 0 && model != 1) return fail(h, MELBM_EINVAL, "melbm_set_wall_model: model %d unknown", model);
   if (!h->bodies) {
     int rc = dev_alloc(h, (void**)&h->bodies, 256 * 9 * 4);
@@ -600,7 +595,6 @@ int melbm_solid_force(melbm_t h, int body, double* out) {
   if (!h || !out) return fail(h, MELBM_EINVAL, "melbm_solid_force: NULL argument");
   if (body < 0 || body > 255) return fail(h, MELBM_EINVAL, "melbm_solid_force: body %d outside 0..255", body);
   if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_solid_force");
-  if (h->lattice == MELBM_D3Q19) return q19_unsupported(h, "melbm_solid_force");
   for (int k = 0; k < 6; ++k) out[k] = 0.0;
   if (!h->L || !h->mask) return MELBM_OK;
   int rc;
@@ -613,7 +607,7 @@ int melbm_solid_force(melbm_t h, int body, double* out) {
   MELBM_CUDA(h, launch_solid_force(h->storage, h->nx, h->ny, h->nz, h->buf[h->cur], h->force,
                                    1.0f / h->tau, h->list_cell, h->list_word, h->L, h->grids,
                                    h->wall_model, h->mask, h->bodies, body, h->sf_partials,
-                                   h->sf_out, h->stream));
+                                   h->sf_out, h->lattice, h->stream));
   MELBM_CUDA(h, cudaMemcpyAsync(out, h->sf_out, 6 * 8, cudaMemcpyDeviceToHost, h->stream));
   MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return MELBM_OK;

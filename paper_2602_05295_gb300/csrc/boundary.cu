@@ -15,8 +15,8 @@
 //     own post-collision moments.
 //   * INFLOW: reset to the equilibrium (rho_in, u_in, S = u_in u_in).
 // The outflow pass then copies the stored state of x = nx-2 onto x = nx-1.
-// On the D3Q19 lattice the same update runs over its 19 directions and weights
-// (halfway bounce-back only).
+// On the D3Q19 lattice the same update runs over its 19 directions and weights,
+// with the D3Q19 populations (hermite_eval19) for the moving-wall model.
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
 
@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
       float up[3];
       body_velocity(P.bodies, P.mask[pull_source(x, y, z, nx, ny, nz, i)], x - 0.5f * cx,
                     y - 0.5f * cy, z - 0.5f * cz, up);
-      g = hermite_eval(wall_moments(Aself, up[0], up[1], up[2]), cx, cy, cz);
+      const Mom17 Wm = wall_moments(Aself, up[0], up[1], up[2]);
+      g = Q19 ? hermite_eval19(Wm, cx, cy, cz) : hermite_eval(Wm, cx, cy, cz);
     } else {
       const uint32_t slot = __ldg(P.table + int64_t(i) * P.count + k);
       const int j = ((word >> i) & 1u) ? 26 - i : i;
@@ -121,7 +122,6 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
                             const uint8_t* mask, const float* bodies, int lattice,
                             cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  if (lattice == 19 && wall_model != 0) return cudaErrorInvalidValue;
   cudaError_t e = launch_source_collide(storage, size_t(nx) * ny * nz, in, force, omega, src_cells,
                                         S, pop, q, lattice, st);
   if (e != cudaSuccess) return e;
@@ -153,11 +153,21 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
   const bool mv = wall_model == 1;
   if (lattice == 19) {
     if (storage == ST_Q16) {
-      if (force) boundary_kernel<ST_Q16, true, false, true><<<blocks, 128, 0, st>>>(p);
-      else boundary_kernel<ST_Q16, false, false, true><<<blocks, 128, 0, st>>>(p);
+      if (force) {
+        if (mv) boundary_kernel<ST_Q16, true, true, true><<<blocks, 128, 0, st>>>(p);
+        else boundary_kernel<ST_Q16, true, false, true><<<blocks, 128, 0, st>>>(p);
+      } else {
+        if (mv) boundary_kernel<ST_Q16, false, true, true><<<blocks, 128, 0, st>>>(p);
+        else boundary_kernel<ST_Q16, false, false, true><<<blocks, 128, 0, st>>>(p);
+      }
     } else {
-      if (force) boundary_kernel<ST_F32, true, false, true><<<blocks, 128, 0, st>>>(p);
-      else boundary_kernel<ST_F32, false, false, true><<<blocks, 128, 0, st>>>(p);
+      if (force) {
+        if (mv) boundary_kernel<ST_F32, true, true, true><<<blocks, 128, 0, st>>>(p);
+        else boundary_kernel<ST_F32, true, false, true><<<blocks, 128, 0, st>>>(p);
+      } else {
+        if (mv) boundary_kernel<ST_F32, false, true, true><<<blocks, 128, 0, st>>>(p);
+        else boundary_kernel<ST_F32, false, false, true><<<blocks, 128, 0, st>>>(p);
+      }
     }
     return cudaGetLastError();
   }

@@ -87,7 +87,7 @@ cudaError_t launch_solid_force(int storage, int nx, int ny, int nz, const void* 
                                const float* force, float omega, const uint32_t* cells,
                                const uint32_t* words, int64_t count, const QGrids& q,
                                int wall_model, const uint8_t* mask, const float* bodies, int body,
-                               double* partials, double* out, cudaStream_t st);
+                               double* partials, double* out, int lattice, cudaStream_t st);
 
 // Source set of the boundary update (sources.cu).  Setup, after the list is
 // built: mark the sources (mark[N] bytes) and count them per block of

@@ -7,6 +7,7 @@
 // moving wall for the moment-based model).  The torque about the body's r0 adds
 // (p - r0) x that, p the link's halfway point.  Accumulated in FP64 per thread,
 // then per block, then by one block over the block partials in a fixed order.
+// On D3Q19 the links, weights and populations are those of the 19-velocity lattice.
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
 
@@ -33,7 +34,7 @@ struct SolidForceParams {
   double* partials;
 };
 
-template <int STORAGE, bool FORCE>
+template <int STORAGE, bool FORCE, bool Q19>
 __global__ void __launch_bounds__(SF_THREADS) solid_force_kernel(SolidForceParams P) {
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const size_t N = size_t(nx) * ny * nz;
@@ -56,16 +57,21 @@ __global__ void __launch_bounds__(SF_THREADS) solid_force_kernel(SolidForceParam
     for (int i = 0; i < 27; ++i) {
       if (!((links >> i) & 1u)) continue;
       const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+      if (Q19 && !in_d3q19(cx, cy, cz)) continue;  // D3Q19 has no corner links
       const int b = P.mask[pull_source(x, y, z, nx, ny, nz, i)];
       if (P.body && b != P.body) continue;
-      const float w = lattice_weight(cx, cy, cz);  // = w of opp(i)
+      // the weight of i = that of opp(i)
+      const float w = Q19 ? lattice_weight19(cx, cy, cz) : lattice_weight(cx, cy, cz);
       const float px = x - 0.5f * cx, py = y - 0.5f * cy, pz = z - 0.5f * cz;
-      const double f_out = double(w) * (1.0 + double(hermite_eval(A, -cx, -cy, -cz)));
+      const float g_out = Q19 ? hermite_eval19(A, -cx, -cy, -cz) : hermite_eval(A, -cx, -cy, -cz);
+      const double f_out = double(w) * (1.0 + double(g_out));
       double f_in = f_out;
       if (P.wall_model == 1) {
         float up[3];
         body_velocity(P.bodies, b, px, py, pz, up);
-        f_in = double(w) * (1.0 + double(hermite_eval(wall_moments(A, up[0], up[1], up[2]), cx, cy, cz)));
+        const Mom17 Wm = wall_moments(A, up[0], up[1], up[2]);
+        const float g_in = Q19 ? hermite_eval19(Wm, cx, cy, cz) : hermite_eval(Wm, cx, cy, cz);
+        f_in = double(w) * (1.0 + double(g_in));
       }
       const double s = f_in + f_out;
       const double dF[3] = {-cx * s, -cy * s, -cz * s};
@@ -107,7 +113,7 @@ cudaError_t launch_solid_force(int storage, int nx, int ny, int nz, const void* 
                                const float* force, float omega, const uint32_t* cells,
                                const uint32_t* words, int64_t count, const QGrids& q,
                                int wall_model, const uint8_t* mask, const float* bodies, int body,
-                               double* partials, double* out, cudaStream_t st) {
+                               double* partials, double* out, int lattice, cudaStream_t st) {
   SolidForceParams p;
   p.nx = nx;
   p.ny = ny;
@@ -124,12 +130,20 @@ cudaError_t launch_solid_force(int storage, int nx, int ny, int nz, const void* 
   p.bodies = bodies;
   p.body = body;
   p.partials = partials;
-  if (storage == ST_Q16) {
-    if (force) solid_force_kernel<ST_Q16, true><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
-    else solid_force_kernel<ST_Q16, false><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
+  if (lattice == 19) {
+    if (storage == ST_Q16) {
+      if (force) solid_force_kernel<ST_Q16, true, true><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
+      else solid_force_kernel<ST_Q16, false, true><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
+    } else {
+      if (force) solid_force_kernel<ST_F32, true, true><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
+      else solid_force_kernel<ST_F32, false, true><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
+    }
+  } else if (storage == ST_Q16) {
+    if (force) solid_force_kernel<ST_Q16, true, false><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
+    else solid_force_kernel<ST_Q16, false, false><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
   } else {
-    if (force) solid_force_kernel<ST_F32, true><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
-    else solid_force_kernel<ST_F32, false><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
+    if (force) solid_force_kernel<ST_F32, true, false><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
+    else solid_force_kernel<ST_F32, false, false><<<SF_BLOCKS, SF_THREADS, 0, st>>>(p);
   }
   solid_force_final_kernel<<<1, 32, 0, st>>>(partials, SF_BLOCKS, out);
   return cudaGetLastError();

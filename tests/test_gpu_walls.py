@@ -1,5 +1,6 @@
 """Solid coupling on the GPU (Sec. 3.2): the moment-based reconstruction at moving
-walls and the momentum-exchange force and torque, against the FP64 oracle.
+walls and the momentum-exchange force and torque, against the FP64 oracle, on the
+D3Q27 and the D3Q19 lattice.
 
 Geometry: channel walls in y and z (body 2, at rest) and a box obstacle (body 1)
 that translates and rotates (its geometry stays; only the wall velocity u^p at
@@ -50,8 +51,8 @@ def state(shape, seed=4):
     return m
 
 
-def make(M, shape, tau, storage, m, body, model=1):
-    sim = M.Simulator(shape, tau, storage, seed=3)
+def make(M, shape, tau, storage, m, body, model=1, lattice=27):
+    sim = M.Simulator(shape, tau, storage, seed=3, lattice=lattice)
     sim.set_state(to_gpu(m[0]), to_gpu(m[1:4]), to_gpu(m[4:10]))
     sim.set_solid(to_gpu(body, torch.uint8))
     sim.set_wall_model(model)
@@ -65,33 +66,40 @@ def read(sim):
     return np.concatenate([rho.cpu().numpy()[None], u.cpu().numpy(), S.cpu().numpy()]).astype(np.float64)
 
 
+def ostep(orc, lattice):
+    return orc.step19 if lattice == 19 else orc.step
+
+
+@pytest.mark.parametrize("lattice", [27, 19])
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("q16", 2e-3)])
-def test_moving_walls_track_the_oracle(M, orc, storage, tol):
+def test_moving_walls_track_the_oracle(M, orc, storage, tol, lattice):
     shape = (40, 20, 16)
     body = geometry(shape)
     m = state(shape)
-    sim = make(M, shape, 0.6, storage, m, body)
+    sim = make(M, shape, 0.6, storage, m, body, lattice=lattice)
     g0 = read(sim)
     typ = sim.types().cpu().numpy()
     fluid = typ != orc.SOLID
-    ref = orc.step(g0, shape, 0.6, typ=typ, wall=orc.Wall(1, body, MOTION), n=100)
+    step = ostep(orc, lattice)
+    ref = step(g0, shape, 0.6, typ=typ, wall=orc.Wall(1, body, MOTION), n=100)
     sim.step(100)
     g = read(sim)
     e_rho = np.abs(g[0] - ref[0])[fluid].max()
     e_u = np.abs(g[1:4] - ref[1:4])[:, fluid].max() / np.abs(ref[1:4])[:, fluid].max()
     assert e_u < tol and e_rho < tol, (e_rho, e_u)
     # the obstacle drags the fluid: the walls moved it away from the rest state
-    bb = orc.step(g0, shape, 0.6, typ=typ, wall=orc.Wall(0, body), n=100)
+    bb = step(g0, shape, 0.6, typ=typ, wall=orc.Wall(0, body), n=100)
     assert np.abs(bb[1:4] - ref[1:4])[:, fluid].max() > 10 * tol
 
 
+@pytest.mark.parametrize("lattice", [27, 19])
 @pytest.mark.parametrize("model", [0, 1])
-def test_solid_force_and_torque_match_the_oracle(M, orc, model):
+def test_solid_force_and_torque_match_the_oracle(M, orc, model, lattice):
     shape = (40, 20, 16)
     body = geometry(shape)
     m = state(shape, seed=5)
     F = 1e-5 * np.random.default_rng(6).standard_normal((3, m.shape[1]))
-    sim = make(M, shape, 0.6, "f32", m, body, model)
+    sim = make(M, shape, 0.6, "f32", m, body, model, lattice=lattice)
     sim.set_force(to_gpu(F))
     sim.step(10)
     g = read(sim)
@@ -102,18 +110,19 @@ def test_solid_force_and_torque_match_the_oracle(M, orc, model):
     # (x up to ~20 cells of lever arm for the torque)
     for b in (0, 1, 2):
         got = sim.solid_force(b)
-        ref = orc.solid_force(g, shape, 0.6, typ, wall, F=F, body_id=b)
+        ref = orc.solid_force(g, shape, 0.6, typ, wall, F=F, body_id=b, lattice=lattice)
         assert np.abs(got[:3] - ref[:3]).max() < 1e-5 * np.abs(ref[:3]).max() + 5e-5, (model, b, got, ref)
         assert np.abs(got[3:] - ref[3:]).max() < 1e-5 * np.abs(ref[3:]).max() + 1e-3, (model, b, got, ref)
 
 
-def test_momentum_exchange_identity_on_the_gpu(M, orc):
+@pytest.mark.parametrize("lattice", [27, 19])
+def test_momentum_exchange_identity_on_the_gpu(M, orc, lattice):
     """P(t+1) - P(t) = sum F - F_solid, with the FP32 state's rounding as the only error."""
     shape = (40, 20, 16)
     body = geometry(shape)
     m = state(shape, seed=7)
     F = 1e-5 * np.random.default_rng(8).standard_normal((3, m.shape[1]))
-    sim = make(M, shape, 0.6, "f32", m, body)
+    sim = make(M, shape, 0.6, "f32", m, body, lattice=lattice)
     sim.set_force(to_gpu(F))
     typ = sim.types().cpu().numpy()
     fluid = typ != orc.SOLID
@@ -126,7 +135,8 @@ def test_momentum_exchange_identity_on_the_gpu(M, orc):
     assert np.abs(dP - expect).max() < 1e-3 * np.abs(Fs[:3]).max(), (dP, expect)
 
 
-def test_comoving_walls_keep_uniform_flow(M):
+@pytest.mark.parametrize("lattice", [27, 19])
+def test_comoving_walls_keep_uniform_flow(M, lattice):
     shape = (40, 20, 16)
     body = geometry(shape)
     N = body.size
@@ -136,7 +146,7 @@ def test_comoving_walls_keep_uniform_flow(M):
     m[1:4] = U[:, None]
     for k, (a, b) in enumerate(PAIRS):
         m[4 + k] = U[a] * U[b]
-    sim = M.Simulator(shape, 0.6, "f32")
+    sim = M.Simulator(shape, 0.6, "f32", lattice=lattice)
     sim.set_state(to_gpu(m[0]), to_gpu(m[1:4]), to_gpu(m[4:10]))
     sim.set_solid(to_gpu(body, torch.uint8))
     sim.set_wall_model(1)
