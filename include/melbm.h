@@ -84,8 +84,9 @@ enum { MELBM_FLUID = 0, MELBM_FLUID_BOUNDARY = 1, MELBM_INFLOW = 2, MELBM_OUTFLO
  * rho T_aab.  A D3Q19 handle takes the same boundaries over its 19 directions
  * (halfway bounce-back or the moving-wall model at solid cells, with their
  * momentum-exchange force and torque; inflow; outflow), with or without a body
- * force, in MELBM_F32 or MELBM_Q16 storage (any bit widths); the adjoint and
- * MELBM_MIXED are refused with MELBM_EINVAL. */
+ * force, in MELBM_F32 or MELBM_Q16 storage (any bit widths), and the mixed
+ * scheme (MELBM_MIXED) with its 19-velocity correction; the adjoint is refused
+ * with MELBM_EINVAL. */
 MELBM_API int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, melbm_t* out);
 
 /* Free every device and host resource of the handle.  NULL is accepted. */

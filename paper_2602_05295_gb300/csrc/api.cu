@@ -224,8 +224,6 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
     return fail(nullptr, MELBM_EINVAL, "melbm_create: tau = %g must exceed 1/2", double(tau));
   if (storage != MELBM_F32 && storage != MELBM_Q16 && storage != MELBM_MIXED)
     return fail(nullptr, MELBM_EINVAL, "melbm_create: storage %d unknown", storage);
-  if (lattice == MELBM_D3Q19 && storage == MELBM_MIXED)
-    return fail(nullptr, MELBM_EINVAL, "melbm_create: MELBM_MIXED storage is D3Q27 only");
   melbm_sim* h = new (std::nothrow) melbm_sim;
   if (!h) return fail(nullptr, MELBM_ENOMEM, "melbm_create: host allocation failed");
   h->nx = nx;
@@ -441,10 +439,13 @@ int melbm_step(melbm_t h, int n) {
   for (int s = 0; s < n; ++s) {
     const uint32_t t_out = uint32_t(h->t + 1);
     if (h->storage == MELBM_MIXED) {
-      MELBM_CUDA(h, launch_fluid_mixed(h->nx, h->ny, h->nz, h->buf[0], mixed_p(h), h->stream));
+      if (h->lattice == MELBM_D3Q19)
+        MELBM_CUDA(h, launch_fluid_mixed19(h->nx, h->ny, h->nz, h->buf[0], mixed_p(h), h->stream));
+      else
+        MELBM_CUDA(h, launch_fluid_mixed(h->nx, h->ny, h->nz, h->buf[0], mixed_p(h), h->stream));
       if (h->L)
         MELBM_CUDA(h, launch_mixed_correct(h->nx, h->ny, h->nz, h->buf[0], mixed_p(h), h->list_cell,
-                                           h->list_word, h->L, h->inflow, h->stream));
+                                           h->list_word, h->L, h->inflow, h->lattice, h->stream));
       if (h->outflow_on && h->type)
         MELBM_CUDA(h, launch_outflow(MELBM_F32, h->nx, h->ny, h->nz, mixed_p(h), h->type, h->stream));
       MELBM_CUDA(h, launch_mixed_collide_quantize(h->nx, h->ny, h->nz, mixed_p(h), h->buf[0],

@@ -1,6 +1,6 @@
-// fluid19.cu -- launcher of the fluid kernel on the D3Q19 lattice (periodic, with
-// or without a body force, FP32 or 16-bit storage): the kernel of
-// fluid_kernel.cuh with Q19 = true.
+// fluid19.cu -- launchers of the fluid kernel on the D3Q19 lattice (with or
+// without a body force, FP32 or 16-bit storage, and the fluid pass of the
+// mixed-precision scheme): the kernel of fluid_kernel.cuh with Q19 = true.
 #include "fluid_kernel.cuh"
 
 namespace melbm {
@@ -45,6 +45,27 @@ cudaError_t launch_fluid19(int storage, int nx, int ny, int nz, const void* in, 
     q.f_w[k] = force ? reinterpret_cast<const uint32_t*>(force) + k * N : nullptr;
   return force ? launch_fluid_t<ST_F32, true, false, true>(q, st)
                : launch_fluid_t<ST_F32, false, false, true>(q, st);
+}
+
+// The fluid pass of the mixed-precision scheme on D3Q19 (16-bit post-collision
+// moments in, raw FP32 post-streaming sums out; see launch_fluid_mixed).
+cudaError_t launch_fluid_mixed19(int nx, int ny, int nz, const void* q_in, float* p_out,
+                                 cudaStream_t st) {
+  KernelParams<ST_MIXED, false> k;
+  FluidParams& p = k;
+  p.nx = nx;
+  p.ny = ny;
+  p.nz = nz;
+  p.in = q_in;
+  p.out = p_out;
+  p.force = nullptr;
+  p.omega = 0.0f;
+  p.t_out = 0;
+  p.seed = 0;
+  p.chunk16 = 0;
+  const size_t N = size_t(nx) * ny * nz;
+  for (int w = 0; w < 10; ++w) k.out_w[w] = reinterpret_cast<uint32_t*>(p_out) + w * N;
+  return launch_fluid_t<ST_MIXED, false, false, true>(k, st);
 }
 
 }  // namespace melbm

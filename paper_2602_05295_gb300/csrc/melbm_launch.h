@@ -58,9 +58,11 @@ cudaError_t launch_fluid19(int storage, int nx, int ny, int nz, const void* in, 
 // public-state conversions of P.
 cudaError_t launch_fluid_mixed(int nx, int ny, int nz, const void* q_in, float* p_out,
                                cudaStream_t st);
+cudaError_t launch_fluid_mixed19(int nx, int ny, int nz, const void* q_in, float* p_out,
+                                 cudaStream_t st);
 cudaError_t launch_mixed_correct(int nx, int ny, int nz, const void* q, float* p,
                                  const uint32_t* cells, const uint32_t* words, int64_t count,
-                                 const float inflow[4], cudaStream_t st);
+                                 const float inflow[4], int lattice, cudaStream_t st);
 cudaError_t launch_mixed_collide_quantize(int nx, int ny, int nz, const float* p, void* q,
                                           float omega, uint32_t t, uint32_t seed, cudaStream_t st);
 cudaError_t launch_mixed_set_state(int64_t N, const float* rho, const float* u, const float* S,

@@ -12,7 +12,8 @@
 //      to the inflow equilibrium;
 //   3. the outflow copy on P;
 //   4. buffer copy: P -> moments -> collision (App. A) -> quantise -> Q.
-// The public state is P (post-streaming, as in the other modes).
+// The public state is P (post-streaming, as in the other modes).  On D3Q19 the
+// fluid pass and the correction use the 19-velocity populations.
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
 
@@ -24,6 +25,7 @@ __device__ __forceinline__ Mom17 post_collision_moments(const void* q, size_t N,
   return collide_moments<false>(load_stored<ST_Q16>(q, N, n), 0.0f, 0.f, 0.f, 0.f);
 }
 
+template <bool Q19>
 __global__ void mixed_correct_kernel(int nx, int ny, int nz, const void* q, float* p,
                                      const uint32_t* cells, const uint32_t* words, int64_t count,
                                      float in_rho, float in_ux, float in_uy, float in_uz) {
@@ -48,9 +50,13 @@ __global__ void mixed_correct_kernel(int nx, int ny, int nz, const void* q, floa
   for (int i = 0; i < 27; ++i) {
     if (!((word >> i) & 1u)) continue;
     const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    if (Q19 && !in_d3q19(cx, cy, cz)) continue;  // D3Q19 has no corner links
     const Mom17 src = post_collision_moments(q, N, pull_source(x, y, z, nx, ny, nz, i));
-    const float df = lattice_weight(cx, cy, cz) *
-                     (hermite_eval(self, -cx, -cy, -cz) - hermite_eval(src, cx, cy, cz));
+    const float df =
+        Q19 ? lattice_weight19(cx, cy, cz) *
+                  (hermite_eval19(self, -cx, -cy, -cz) - hermite_eval19(src, cx, cy, cz))
+            : lattice_weight(cx, cy, cz) *
+                  (hermite_eval(self, -cx, -cy, -cz) - hermite_eval(src, cx, cy, cz));
     d[0] += df;
     d[1] += cx * df;
     d[2] += cy * df;
@@ -131,10 +137,15 @@ __global__ void mixed_get_moments_kernel(int64_t N_, const float* p, float* rho,
 
 cudaError_t launch_mixed_correct(int nx, int ny, int nz, const void* q, float* p,
                                  const uint32_t* cells, const uint32_t* words, int64_t count,
-                                 const float inflow[4], cudaStream_t st) {
+                                 const float inflow[4], int lattice, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  mixed_correct_kernel<<<unsigned((count + 127) / 128), 128, 0, st>>>(
-      nx, ny, nz, q, p, cells, words, count, inflow[0], inflow[1], inflow[2], inflow[3]);
+  const unsigned blocks = unsigned((count + 127) / 128);
+  if (lattice == 19)
+    mixed_correct_kernel<true><<<blocks, 128, 0, st>>>(nx, ny, nz, q, p, cells, words, count,
+                                                       inflow[0], inflow[1], inflow[2], inflow[3]);
+  else
+    mixed_correct_kernel<false><<<blocks, 128, 0, st>>>(nx, ny, nz, q, p, cells, words, count,
+                                                        inflow[0], inflow[1], inflow[2], inflow[3]);
   return cudaGetLastError();
 }
 

@@ -268,8 +268,6 @@ def test_d3q19_refuses_what_it_does_not_cover(M):
     shape = (16, 8, 8)
     N = 16 * 8 * 8
     with pytest.raises(M.MelbmError):
-        M.Simulator(shape, 0.6, "mixed", lattice=19)
-    with pytest.raises(M.MelbmError):
         M.Simulator(shape, 0.6, "f32", lattice=15)
     sim = M.Simulator(shape, 0.6, "f32", lattice=19)
     with pytest.raises(M.MelbmError):

@@ -42,24 +42,30 @@ def read(sim):
     return np.concatenate([rho.cpu().numpy()[None], u.cpu().numpy(), S.cpu().numpy()]).astype(np.float64)
 
 
-def test_mixed_periodic_tracks_fp64_and_conserves_mass(M, orc):
+def ostep(orc, lattice):
+    return orc.step19 if lattice == 19 else orc.step
+
+
+@pytest.mark.parametrize("lattice", [27, 19])
+def test_mixed_periodic_tracks_fp64_and_conserves_mass(M, orc, lattice):
     shape = (64, 48, 40)
     u = W.random_phase_field(shape, 0.08, kmax=8, seed=6)
     m = eq_state(1.0, W.flat(u))
-    sim = M.Simulator(shape, 0.52, "mixed", seed=11)
+    sim = M.Simulator(shape, 0.52, "mixed", seed=11, lattice=lattice)
     sim.set_state(to_gpu(m[0]), to_gpu(m[1:4]), to_gpu(m[4:10]))
     g0 = read(sim)
     M0, _ = sim.reduce()
     sim.step(100)
     g = read(sim)
-    ref = orc.step(g0, shape, 0.52, n=100)
+    ref = ostep(orc, lattice)(g0, shape, 0.52, n=100)
     e_u = np.abs(g[1:4] - ref[1:4]).max() / np.abs(ref[1:4]).max()
     assert e_u < 2e-3, e_u
     M1, _ = sim.reduce()
     assert abs(M1 - M0) / M0 < 1e-6, (M0, M1)
 
 
-def test_mixed_channel_with_atomic_solid_correction_tracks_fp64(M, orc):
+@pytest.mark.parametrize("lattice", [27, 19])
+def test_mixed_channel_with_atomic_solid_correction_tracks_fp64(M, orc, lattice):
     shape = (48, 26, 22)
     nx, ny, nz = shape
     mask = W.channel_walls(shape)
@@ -71,7 +77,7 @@ def test_mixed_channel_with_atomic_solid_correction_tracks_fp64(M, orc):
     u = np.zeros((3, N))
     u[0] = 0.05
     m = eq_state(np.ones(N), u)
-    sim = M.Simulator(shape, 0.55, "mixed", seed=9)
+    sim = M.Simulator(shape, 0.55, "mixed", seed=9, lattice=lattice)
     sim.set_state(to_gpu(m[0]), to_gpu(m[1:4]), to_gpu(m[4:10]))
     sim.set_solid(to_gpu(mask.ravel(), torch.uint8))
     sim.set_inflow(1.0, (0.05, 0.0, 0.0))
@@ -79,12 +85,12 @@ def test_mixed_channel_with_atomic_solid_correction_tracks_fp64(M, orc):
     g0 = read(sim)
     sim.step(100)
     g = read(sim)
-    ref = orc.step(g0, shape, 0.55, typ=typ, inflow=[1.0, 0.05, 0.0, 0.0], n=100)
+    ref = ostep(orc, lattice)(g0, shape, 0.55, typ=typ, inflow=[1.0, 0.05, 0.0, 0.0], n=100)
     keep = typ != orc.SOLID
     e_u = np.abs(g[1:4][:, keep] - ref[1:4][:, keep]).max() / np.abs(ref[1:4][:, keep]).max()
     assert e_u < 2e-3, e_u
     # the same channel in the recompute design agrees with it to the same order
-    q = M.Simulator(shape, 0.55, "q16", seed=9)
+    q = M.Simulator(shape, 0.55, "q16", seed=9, lattice=lattice)
     q.set_state(to_gpu(m[0]), to_gpu(m[1:4]), to_gpu(m[4:10]))
     q.set_solid(to_gpu(mask.ravel(), torch.uint8))
     q.set_inflow(1.0, (0.05, 0.0, 0.0))
