@@ -235,7 +235,7 @@ def run_mixed_vs_recompute(steps):
     post-streaming, atomic solid correction, re-quantisation pass) against this
     library's recompute design (16-bit post-streaming ping-pong, boundary list
     recomputed from the input) on the periodic 256^3 turbulence and on the
-    512x256x256 sphere channel: throughput and device memory."""
+    512x256x256 sphere channel (D3Q27 and D3Q19): throughput and device memory."""
     out = []
     wl = W.TURB256
     rho, u = _state_from_velocity(W.flat(W.random_phase_field(wl.shape, 0.08)))
@@ -248,11 +248,12 @@ def run_mixed_vs_recompute(steps):
         sim.close()
     wl = W.CHANNEL512
     mask, _ = W.sphere_pack(wl.shape)
-    for storage in ("q16", "mixed"):
-        rec = _channel(wl, mask, 0.05, steps, storage=storage)
-        out.append({"workload": "mixed_vs_recompute", "case": wl.name, "storage": storage,
-                    "ms_per_step": rec["ms_per_step"], "MLUPS": rec["MLUPS"],
-                    "memory_bytes": rec["memory_bytes"]})
+    for lattice in (27, 19):
+        for storage in ("q16", "mixed"):
+            rec = _channel(wl, mask, 0.05, steps, storage=storage, lattice=lattice)
+            out.append({"workload": "mixed_vs_recompute", "case": rec["workload"],
+                        "storage": storage, "ms_per_step": rec["ms_per_step"],
+                        "MLUPS": rec["MLUPS"], "memory_bytes": rec["memory_bytes"]})
     return out
 
 
