@@ -84,9 +84,8 @@ enum { MELBM_FLUID = 0, MELBM_FLUID_BOUNDARY = 1, MELBM_INFLOW = 2, MELBM_OUTFLO
  * rho T_aab.  A D3Q19 handle takes the same boundaries over its 19 directions
  * (halfway bounce-back or the moving-wall model at solid cells, with their
  * momentum-exchange force and torque; inflow; outflow), with or without a body
- * force, in MELBM_F32 or MELBM_Q16 storage (any bit widths), and the mixed
- * scheme (MELBM_MIXED) with its 19-velocity correction; the adjoint is refused
- * with MELBM_EINVAL. */
+ * force, in MELBM_F32 or MELBM_Q16 storage (any bit widths), the mixed scheme
+ * (MELBM_MIXED) with its 19-velocity correction, and the adjoint. */
 MELBM_API int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, melbm_t* out);
 
 /* Free every device and host resource of the handle.  NULL is accepted. */
@@ -168,7 +167,8 @@ MELBM_API int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int
  * melbm_backward: given dL/d(rho, u, S) of the final state (10N device floats,
  * component-major as melbm_get_moments), writes dL/du0[3N] and dL/dF[3N]
  * (device; dL_dF may be NULL) by the hand-written discrete adjoint, recomputing
- * each segment in FP32 from its checkpoint.  Requires MELBM_F32 storage. */
+ * each segment in FP32 from its checkpoint.  Requires MELBM_F32 storage and
+ * halfway bounce-back walls (wall model 0); either lattice. */
 MELBM_API int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps, int K);
 MELBM_API int melbm_backward(melbm_t h, const float* dL_dm_final, float* dL_du0, float* dL_dF);
 

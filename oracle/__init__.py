@@ -442,10 +442,11 @@ def amplification_matrix(rho0, U, tau, kvecs, h=1e-30):
 
 
 # ---------------------------------------------------------------- adjoint
-def forward_loss(u0, F, shape, tau, nsteps, loss_fn, typ=None, inflow=None):
+def forward_loss(u0, F, shape, tau, nsteps, loss_fn, typ=None, inflow=None, lattice=27):
     """Initial state (1, u0, u0 u0) -> n FP64 steps -> loss_fn(final state)."""
     m = initial_state_from_velocity(u0)
-    m = step(m, shape, tau, F=F, typ=typ, inflow=inflow, n=nsteps)
+    stepper = step19 if lattice == 19 else step
+    m = stepper(m, shape, tau, F=F, typ=typ, inflow=inflow, n=nsteps)
     return loss_fn(m), m
 
 

@@ -288,6 +288,32 @@ __device__ __forceinline__ void add_population_adjoint(int cx, int cy, int cz, f
   lmu[16] += 27.0f * g * px * py * pz;
 }
 
+// The same for a D3Q19 population, f_i = w19_i (1 + hermite_eval19): the third
+// order through the projected pairs, no xyz term.
+__device__ __forceinline__ void add_population_adjoint19(int cx, int cy, int cz, float lf,
+                                                         float lmu[17]) {
+  const float g = lattice_weight19(cx, cy, cz) * lf;
+  const float px = float(cx), py = float(cy), pz = float(cz);
+  const float qx = px * px - (1.0f / 3.0f), qy = py * py - (1.0f / 3.0f), qz = pz * pz - (1.0f / 3.0f);
+  lmu[0] += g;
+  lmu[1] += 3.0f * g * px;
+  lmu[2] += 3.0f * g * py;
+  lmu[3] += 3.0f * g * pz;
+  lmu[4] += 4.5f * g * qx;
+  lmu[5] += 4.5f * g * qy;
+  lmu[6] += 4.5f * g * qz;
+  lmu[7] += 9.0f * g * px * py;
+  lmu[8] += 9.0f * g * px * pz;
+  lmu[9] += 9.0f * g * py * pz;
+  const float hy1 = qx * py, hy2 = py * qz, hx1 = px * qy, hx2 = px * qz, hz1 = qx * pz, hz2 = qy * pz;
+  lmu[10] += g * (18.0f * hy1 + 9.0f * hy2);  // xxy
+  lmu[15] += g * (9.0f * hy1 + 18.0f * hy2);  // yzz
+  lmu[11] += g * (18.0f * hx1 + 9.0f * hx2);  // xyy
+  lmu[13] += g * (9.0f * hx1 + 18.0f * hx2);  // xzz
+  lmu[12] += g * (18.0f * hz1 + 9.0f * hz2);  // xxz
+  lmu[14] += g * (9.0f * hz1 + 18.0f * hz2);  // yyz
+}
+
 // ------------------------------------------------------------------ stream^T
 // The pull stream followed by the moment sums is the separable map of the fluid
 // kernel: per axis, (mu0, mu1, mu2) -> phi = (phi+, phi0, phi-) with
@@ -299,7 +325,9 @@ __device__ __forceinline__ void add_population_adjoint(int cx, int cy, int cz, f
 //   push:   lphi+(x) = lpl(x + 1), lphi-(x) = lmr(x - 1), lphi0 = lz;
 //   phi^T:  ls = lphi+ + lphi- - 2 lphi0, lmu0 = lphi0 + ls/6, lmu1 = (lphi+ - lphi-)/2,
 //           lmu2 = ls/2.
-// Carried adjoints mirror the forward's moment counts: 10 -> 18 (z) -> 24 (y) -> 17 (x).
+// Carried adjoints mirror the forward's moment counts: 10 -> 18 (z) -> 24 (y) -> 17 (x);
+// on D3Q19 the x pass yields all 27 tensor moments, folded back onto the 17 through
+// the transposed closure.
 struct LamT {
   float p, z, m;  // lpl, lz, lmr of one cell, before the push
 };
@@ -344,7 +372,7 @@ struct AdjStreamParams {
 // for the plane zz - 1.  Periodic in all directions; cells whose output does
 // not come from the stream contribute no adjoint (special_type), and solid cells
 // get none; the bounce-back terms of listed cells are added by adj_boundary_kernel.
-template <bool FORCE, bool TYPED>
+template <bool FORCE, bool TYPED, bool Q19>
 __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams P) {
   extern __shared__ float asm_[];
   const int lane = threadIdx.x, row = threadIdx.y;
@@ -471,7 +499,7 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams
     for (int q = 0; q < 3; ++q)
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        if (q == 2 && r == 2) continue;  // no Hermite moment has q = r = 2
+        if (!Q19 && q == 2 && r == 2) continue;  // no D3Q27 Hermite moment has q = r = 2
         const LamT u = proj_t(Y[0][q][r], Y[1][q][r], Y[2][q][r]);
         const float lp = __shfl_down_sync(FULL, u.p, 1);  // lpl of x + 1
         const float lm = __shfl_up_sync(FULL, u.m, 1);    // lmr of x - 1
@@ -484,10 +512,34 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams
       continue;
     }
     // Mom17 order: 000 100 010 001 200 020 002 110 101 011 210 120 201 102 021 012 111
-    const float lmu[17] = {X[0][0][0], X[1][0][0], X[0][1][0], X[0][0][1], X[2][0][0],
-                           X[0][2][0], X[0][0][2], X[1][1][0], X[1][0][1], X[0][1][1],
-                           X[2][1][0], X[1][2][0], X[2][0][1], X[1][0][2], X[0][2][1],
-                           X[0][1][2], X[1][1][1]};
+    float lmu[17] = {X[0][0][0], X[1][0][0], X[0][1][0], X[0][0][1], X[2][0][0],
+                     X[0][2][0], X[0][0][2], X[1][1][0], X[1][0][1], X[0][1][1],
+                     X[2][1][0], X[1][2][0], X[2][0][1], X[1][0][2], X[0][2][1],
+                     X[0][1][2], X[1][1][1]};
+    if constexpr (Q19) {
+      // D3Q19: mu_111 = 0, and the ten further tensor moments are the linear
+      // closure of the others (closure19), whose transpose adds their adjoints
+      lmu[16] = 0.f;
+      const float l220 = X[2][2][0], l202 = X[2][0][2], l022 = X[0][2][2];
+      const float l211 = X[2][1][1], l121 = X[1][2][1], l112 = X[1][1][2];
+      const float l221 = X[2][2][1], l212 = X[2][1][2], l122 = X[1][2][2], l222 = X[2][2][2];
+      lmu[6] -= l220 * (1.0f / 6.0f) + l222 * (1.0f / 18.0f);
+      lmu[5] -= l202 * (1.0f / 6.0f) + l222 * (1.0f / 18.0f);
+      lmu[4] -= l022 * (1.0f / 6.0f) + l222 * (1.0f / 18.0f);
+      lmu[9] -= l211 * (1.0f / 3.0f);
+      lmu[8] -= l121 * (1.0f / 3.0f);
+      lmu[7] -= l112 * (1.0f / 3.0f);
+      lmu[12] -= l221 * (1.0f / 3.0f);
+      lmu[14] -= l221 * (1.0f / 3.0f);
+      lmu[3] -= l221 * (1.0f / 9.0f);
+      lmu[10] -= l212 * (1.0f / 3.0f);
+      lmu[15] -= l212 * (1.0f / 3.0f);
+      lmu[2] -= l212 * (1.0f / 9.0f);
+      lmu[11] -= l122 * (1.0f / 3.0f);
+      lmu[13] -= l122 * (1.0f / 3.0f);
+      lmu[1] -= l122 * (1.0f / 9.0f);
+      lmu[0] -= l222 * (1.0f / 27.0f);
+    }
     float lf[3] = {0.f, 0.f, 0.f};
     Stored st;
     st.drho = mt[0];
@@ -511,7 +563,7 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams
 // Bounce-back terms of the listed FLUID_BOUNDARY cells: a solid link i of cell x
 // took f_i(x) = f+_opp(i)(x), so lambda_f_i(x) flows back onto x's own Hermite
 // moments; Coll^T is linear in them, so its image is added to lam_out.
-template <bool FORCE>
+template <bool FORCE, bool Q19>
 __global__ void adj_boundary_kernel(const float* lam_next, const float* m_next, const float* m_t,
                                     const float* F, const uint32_t* cells, const uint32_t* words,
                                     int64_t count, float* lam_out, float* gF, float omega, int64_t N_) {
@@ -529,12 +581,16 @@ __global__ void adj_boundary_kernel(const float* lam_next, const float* m_next, 
   for (int i = 0; i < 27; ++i) {
     if (!((links >> i) & 1u)) continue;
     const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    if (Q19 && !in_d3q19(cx, cy, cz)) continue;
     const float fx = float(cx), fy = float(cy), fz = float(cz);
     const float lf = lM[0] + fx * lM[1] + fy * lM[2] + fz * lM[3] +
                      (fx * fx - (1.0f / 3.0f)) * lM[4] + (fy * fy - (1.0f / 3.0f)) * lM[5] +
                      (fz * fz - (1.0f / 3.0f)) * lM[6] + fx * fy * lM[7] + fx * fz * lM[8] +
                      fy * fz * lM[9];
-    add_population_adjoint(-cx, -cy, -cz, lf, lmu);
+    if (Q19)
+      add_population_adjoint19(-cx, -cy, -cz, lf, lmu);
+    else
+      add_population_adjoint(-cx, -cy, -cz, lf, lmu);
   }
   float f[3] = {0.f, 0.f, 0.f}, lff[3] = {0.f, 0.f, 0.f};
   if (FORCE)
@@ -548,7 +604,7 @@ __global__ void adj_boundary_kernel(const float* lam_next, const float* m_next, 
 
 unsigned blocks_for(int64_t N) { return unsigned((N + AT - 1) / AT); }
 
-template <bool FORCE, bool TYPED>
+template <bool FORCE, bool TYPED, bool Q19>
 cudaError_t launch_adj_stream_t(AdjStreamParams& p, cudaStream_t st) {
   constexpr int MAX_DEV = 64;
   static int sms[MAX_DEV] = {};  // per device, once: SM count and the shared-memory opt-in
@@ -558,7 +614,7 @@ cudaError_t launch_adj_stream_t(AdjStreamParams& p, cudaStream_t st) {
   if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
   if (!sms[dev]) {
     int n = 0;
-    e = cudaFuncSetAttribute(adj_stream_kernel<FORCE, TYPED>,
+    e = cudaFuncSetAttribute(adj_stream_kernel<FORCE, TYPED, Q19>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(ADJ_SMEM));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -578,14 +634,21 @@ cudaError_t launch_adj_stream_t(AdjStreamParams& p, cudaStream_t st) {
   }
   p.zc = best;
   const dim3 grid((p.nx + AIX - 1) / AIX, (p.ny + AIY - 1) / AIY, (p.nz + best - 1) / best);
-  adj_stream_kernel<FORCE, TYPED><<<grid, dim3(AFX, AFY), ADJ_SMEM, st>>>(p);
+  adj_stream_kernel<FORCE, TYPED, Q19><<<grid, dim3(AFX, AFY), ADJ_SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_stream(AdjStreamParams& p, cudaStream_t st) {
+template <bool Q19>
+cudaError_t launch_adj_stream_l(AdjStreamParams& p, cudaStream_t st) {
   if (p.force)
-    return p.type ? launch_adj_stream_t<true, true>(p, st) : launch_adj_stream_t<true, false>(p, st);
-  return p.type ? launch_adj_stream_t<false, true>(p, st) : launch_adj_stream_t<false, false>(p, st);
+    return p.type ? launch_adj_stream_t<true, true, Q19>(p, st)
+                  : launch_adj_stream_t<true, false, Q19>(p, st);
+  return p.type ? launch_adj_stream_t<false, true, Q19>(p, st)
+                : launch_adj_stream_t<false, false, Q19>(p, st);
+}
+
+cudaError_t launch_adj_stream(AdjStreamParams& p, int lattice, cudaStream_t st) {
+  return lattice == 19 ? launch_adj_stream_l<true>(p, st) : launch_adj_stream_l<false>(p, st);
 }
 
 }  // namespace
@@ -624,8 +687,6 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
   if (nsteps < 1 || K < 1) return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: nsteps and K must be >= 1");
   if (h->storage != MELBM_F32)
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: requires MELBM_F32 storage");
-  if (h->lattice != MELBM_D3Q27)
-    return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: requires the D3Q27 lattice");
   if (h->wall_model != 0)
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: the adjoint covers halfway bounce-back walls only");
   const size_t N = size_t(h->N);
@@ -729,15 +790,22 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
       ap.lam_out = lam2;
       ap.gF = a->gF;
       ap.omega = omega;
-      ADJ_CUDA(h, launch_adj_stream(ap, st));
+      ADJ_CUDA(h, launch_adj_stream(ap, h->lattice, st));
       if (h->L) {
         const unsigned lb = blocks_for(h->L);
-        if (h->force)
-          adj_boundary_kernel<true><<<lb, AT, 0, st>>>(lam, m_next, m_t, h->force, h->list_cell,
-                                                       h->list_word, h->L, lam2, a->gF, omega, h->N);
+        const bool q19 = h->lattice == MELBM_D3Q19;
+        if (h->force && q19)
+          adj_boundary_kernel<true, true><<<lb, AT, 0, st>>>(lam, m_next, m_t, h->force, h->list_cell,
+                                                             h->list_word, h->L, lam2, a->gF, omega, h->N);
+        else if (h->force)
+          adj_boundary_kernel<true, false><<<lb, AT, 0, st>>>(lam, m_next, m_t, h->force, h->list_cell,
+                                                              h->list_word, h->L, lam2, a->gF, omega, h->N);
+        else if (q19)
+          adj_boundary_kernel<false, true><<<lb, AT, 0, st>>>(lam, m_next, m_t, nullptr, h->list_cell,
+                                                              h->list_word, h->L, lam2, a->gF, omega, h->N);
         else
-          adj_boundary_kernel<false><<<lb, AT, 0, st>>>(lam, m_next, m_t, nullptr, h->list_cell,
-                                                        h->list_word, h->L, lam2, a->gF, omega, h->N);
+          adj_boundary_kernel<false, false><<<lb, AT, 0, st>>>(lam, m_next, m_t, nullptr, h->list_cell,
+                                                               h->list_word, h->L, lam2, a->gF, omega, h->N);
         ADJ_CUDA(h, cudaGetLastError());
       }
       float* tmp = lam;

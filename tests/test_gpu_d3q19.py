@@ -264,15 +264,16 @@ def test_d3q19_channel512_sampled_one_step(M, orc):
     assert du <= 0.8 / 65535 * 1.01 and drho <= 0.7 / 65535 * 1.01, (du, drho)
 
 
-def test_d3q19_refuses_what_it_does_not_cover(M):
+def test_d3q19_refusals_and_recovery(M):
     shape = (16, 8, 8)
     N = 16 * 8 * 8
     with pytest.raises(M.MelbmError):
         M.Simulator(shape, 0.6, "f32", lattice=15)
     sim = M.Simulator(shape, 0.6, "f32", lattice=19)
-    with pytest.raises(M.MelbmError):
+    sim.set_wall_model(1)
+    with pytest.raises(M.MelbmError):  # the adjoint covers halfway bounce-back only
         sim.forward_checkpointed(torch.zeros(3, N, device="cuda"), 4, 2)
-    # what it does cover still runs after the refusals
+    sim.set_wall_model(0)
     sim.set_solid(torch.zeros(N, dtype=torch.uint8, device="cuda"))
     sim.step(2)
     assert sim.time_index == 2
