@@ -1,8 +1,8 @@
 /* melbm.h -- C ABI of the GB300 moment-encoded lattice Boltzmann library.
  *
- * The library advances a D3Q27 moment-encoded (HOME-LBM) fluid in which every
- * cell stores only its ten low-order moments (rho, u, S) instead of the 27
- * populations (arXiv 2602.05295, Sec. 3.2).  One step (Sec. 4.2, Alg. 2 and the
+ * The library advances a D3Q27 (or D3Q19) moment-encoded (HOME-LBM) fluid in
+ * which every cell stores only its ten low-order moments (rho, u, S) instead of
+ * the 27 (19) populations (arXiv 2602.05295, Sec. 3.2).  One step (Sec. 4.2, Alg. 2 and the
  * split-kernel design) is:
  *   1. a branch-free fluid kernel over all cells: load the moments, collide in
  *      moment space (App. A), rebuild the post-collision populations by the
@@ -23,7 +23,8 @@
  *   S is the per-mass Hermite second moment, S = sum (c c - c_s^2 I) f / rho,
  *   whose equilibrium value is u u.  rho and u are the post-streaming values at
  *   integer time (the physical velocity, which includes F/2).
- *   Lattice directions i = (cx+1) + 3 (cy+1) + 9 (cz+1), opposite = 26 - i.
+ *   Lattice directions i = (cx+1) + 3 (cy+1) + 9 (cz+1), opposite = 26 - i (the
+ *   same numbering on D3Q19, whose directions are those with |c|^2 <= 2).
  *   Every call returns an int status (melbm_status); on failure the handle keeps
  *   a message for melbm_last_error().  No C++ exception crosses the ABI.
  *   Unless stated otherwise pointers are CUDA device pointers on the current

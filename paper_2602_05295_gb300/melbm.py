@@ -137,9 +137,9 @@ class Simulator:
 
     ``storage`` is ``"f32"``, ``"q16"`` (the paper's 16-bit form) or ``"mixed"``
     (the paper's mixed-precision scheme with solids, kept for comparison).
-    ``lattice`` is 27 (D3Q27) or 19 (D3Q19: periodic, with or without a force,
-    ``"f32"`` or ``"q16"``).  Work is enqueued on ``stream`` (default: torch's
-    current stream at construction)."""
+    ``lattice`` is 27 (D3Q27) or 19 (D3Q19: the same storage forms, boundaries,
+    walls and adjoint over the 19 velocities).  Work is enqueued on ``stream``
+    (default: torch's current stream at construction)."""
 
     def __init__(self, shape, tau, storage="q16", stream=None, seed=0, lattice=27):
         nx, ny, nz = (int(v) for v in shape)
