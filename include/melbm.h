@@ -31,6 +31,9 @@
  *   device, owned by the caller, contiguous, not aliased with library memory.
  *   Work is enqueued on the handle's stream (melbm_set_stream); calls that
  *   return host values synchronise that stream.
+ *   Testing hook: with MELBM_FAIL_ALLOC_AFTER=k in the environment, every device
+ *   allocation of the process after the first k fails with MELBM_ENOMEM (the
+ *   handle stays usable).  melbm_step and melbm_set_solid open NVTX ranges.
  */
 #ifndef MELBM_H
 #define MELBM_H

@@ -1,11 +1,15 @@
 // api.cu -- the extern "C" entry points declared in include/melbm.h: handle
 // life cycle, argument checks, host/device pointer handling and the step loop
 // (fluid kernel -> boundary kernel -> outflow copy, Sec. 4.2).
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/melbm.h"
 #include "melbm_device.cuh"
@@ -42,10 +46,34 @@ int cuda_fail(melbm_t h, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);        \
   } while (0)
 
+// Failure injection on the host: with MELBM_FAIL_ALLOC_AFTER = k in the
+// environment, the device allocations of this process after the first k fail
+// as if the device were out of memory (read once, at the first allocation).
+bool injected_alloc_failure() {
+  static const long limit = [] {
+    const char* v = std::getenv("MELBM_FAIL_ALLOC_AFTER");
+    return v && *v ? std::strtol(v, nullptr, 10) : -1L;
+  }();
+  static std::atomic<long> count{0};
+  return limit >= 0 && count.fetch_add(1) >= limit;
+}
+
+// An NVTX range over the scope (seen by profilers that are attached; a no-op
+// otherwise).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
 int dev_alloc(melbm_t h, void** p, size_t bytes) {
   if (bytes == 0) {
     *p = nullptr;
     return MELBM_OK;
+  }
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return fail(h, MELBM_ENOMEM, "device allocation of %zu bytes failed (MELBM_FAIL_ALLOC_AFTER)",
+                bytes);
   }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
@@ -361,6 +389,7 @@ int melbm_get_moments(melbm_t h, float* rho, float* u, float* S) {
 
 int melbm_set_solid(melbm_t h, const uint8_t* mask) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_solid: NULL handle");
+  const Range range("melbm_set_solid");
   if (mask && !is_device_ptr(mask)) return fail(h, MELBM_EINVAL, "melbm_set_solid: mask must be a device pointer");
   if (!mask) {
     dev_free(h, h->mask, size_t(h->N));
@@ -434,6 +463,7 @@ int melbm_set_force(melbm_t h, const float* F) {
 
 int melbm_step(melbm_t h, int n) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_step: NULL handle");
+  const Range range("melbm_step");
   if (n < 0) return fail(h, MELBM_EINVAL, "melbm_step: n = %d < 0", n);
   if (h->poisoned) return fail(h, MELBM_ESTATE, "melbm_step: an earlier CUDA failure left the state undefined; call melbm_set_state");
   for (int s = 0; s < n; ++s) {

@@ -64,3 +64,26 @@ def test_product_does_not_touch_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "melbm_oracle" not in src, f
+
+
+_FAIL_ALLOC_SCRIPT = r"""
+import ctypes, sys
+sys.path.insert(0, {root!r})
+from paper_2602_05295_gb300 import melbm as M
+L = M.lib()
+h = ctypes.c_void_p()
+rc = L.melbm_create(8, 8, 8, 27, ctypes.c_float(0.6), 1, ctypes.byref(h))
+print(rc, L.melbm_last_error(None).decode())
+"""
+
+
+def test_injected_allocation_failure_is_reported_without_a_device(L):
+    """MELBM_FAIL_ALLOC_AFTER=0 makes the first device allocation fail on the host
+    side: melbm_create returns MELBM_ENOMEM with the reason, and frees what it had."""
+    import sys
+    env = dict(os.environ, MELBM_FAIL_ALLOC_AFTER="0")
+    r = subprocess.run([sys.executable, "-c", _FAIL_ALLOC_SCRIPT.format(root=ROOT)], env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    code, msg = r.stdout.strip().split(" ", 1)
+    assert int(code) == 2 and "MELBM_FAIL_ALLOC_AFTER" in msg, r.stdout

@@ -386,3 +386,37 @@ def test_q16_mass_drift_over_1000_steps(M):
     M1, E1 = sim.reduce()
     assert abs(M1 - M0) / M0 < 1e-6, (M0, M1)
     assert 0 < E1 < E0
+
+
+_ALLOC_SCRIPT = r"""
+import sys
+sys.path.insert(0, {root!r})
+import torch
+from paper_2602_05295_gb300 import melbm as M
+sim = M.Simulator((16, 8, 8), 0.6, "q16")       # its allocations come first
+try:
+    sim.set_force(torch.zeros(3, 1024, device="cuda"))
+    print("no failure")
+except M.MelbmError as e:
+    print("failed", e.code)
+sim.step(3)                                        # the handle still works
+rho, _, _ = sim.get_moments()
+print("steps", sim.time_index, float(rho.mean()))
+"""
+
+
+def test_injected_allocation_failure_leaves_the_handle_usable(M):
+    """MELBM_FAIL_ALLOC_AFTER=4 lets melbm_create take its four allocations and
+    fails the next (the force field): MELBM_ENOMEM, and the simulation keeps
+    running without the force."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MELBM_FAIL_ALLOC_AFTER="4")
+    r = subprocess.run([sys.executable, "-c", _ALLOC_SCRIPT.format(root=root)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.strip().splitlines()
+    assert lines[0] == "failed 2", r.stdout
+    assert lines[1].startswith("steps 3") and abs(float(lines[1].split()[2]) - 1.0) < 1e-6
