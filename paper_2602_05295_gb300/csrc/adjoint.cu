@@ -202,7 +202,11 @@ __device__ void collide_vjp(const Stored& s, float omega, const float f[3], cons
     le[kab] += 2.0f * l * U[a];
   }
   {  // mu111 = rU_x U_y U_z + e_xy U_z + e_xz U_y + e_yz U_x
+#ifdef MELBM_HERMITE_XYZ_LITERAL
+    const float l = 0.5f * lmu[16];  // mu111 is halved under the literal xyz factor
+#else
     const float l = lmu[16];
+#endif
     lrU[0] += l * U[1] * U[2];
     lU[1] += l * (rU[0] * U[2] + e[4]);
     lU[2] += l * (rU[0] * U[1] + e[3]);

@@ -409,7 +409,9 @@ __device__ __forceinline__ void store_stored(void* buf, size_t N, size_t n, cons
 // the post-collision populations, with P_0 = 1, P_1 = c, P_2 = c^2 - 1/3 and the
 // rest populations w_i removed (mu_000 = rho - 1):
 //   mu_a = rho u_a, mu_aa = rho S_aa, mu_ab = rho S_ab, mu_aab = rho T_aab,
-//   mu_xyz = rho T_xyz   (Eq. three_order_f: f+ is the third-order Hermite
+//   mu_xyz = rho T_xyz (half of it when built with MELBM_HERMITE_XYZ_LITERAL,
+//   the printed 1/(2 c_s^6) on the xyz term, kept as an ablation of that reading)
+//   (Eq. three_order_f: f+ is the third-order Hermite
 // expansion with exactly these moments, T_abg = S_ab u_g + S_ag u_b + S_bg u_a - 2 u_a u_b u_g).
 template <class T>
 struct Mom17T {
@@ -481,6 +483,9 @@ __device__ __forceinline__ Mom17T<T> collide_moments(const StoredT<T>& s, float 
   A.m012 = vfma(uy, A.m002, vmul(uz2, eyz));  // yzz
   // rho T_xyz = rho ux uy uz + rho (E_xy uz + E_xz uy + E_yz ux)
   A.m111 = vfma(vmul(rux, uy), uz, vfma(exy, uz, vfma(exz, uy, vmul(eyz, ux))));
+#ifdef MELBM_HERMITE_XYZ_LITERAL
+  A.m111 = vmulc(A.m111, 0.5f);  // the printed 1/(2 c_s^6) on xyz halves its moment
+#endif
   return A;
 }
 
@@ -590,6 +595,9 @@ __device__ __forceinline__ Mom17 wall_moments(const Mom17& A, float upx, float u
   W.m021 = __fmaf_rn(upz, W.m020, 2.0f * upy * eyz);
   W.m012 = __fmaf_rn(upy, W.m002, 2.0f * upz * eyz);
   W.m111 = __fmaf_rn(rux * upy, upz, exy * upz + exz * upy + eyz * upx);
+#ifdef MELBM_HERMITE_XYZ_LITERAL
+  W.m111 *= 0.5f;
+#endif
   return W;
 }
 

@@ -420,3 +420,38 @@ def test_injected_allocation_failure_leaves_the_handle_usable(M):
     lines = r.stdout.strip().splitlines()
     assert lines[0] == "failed 2", r.stdout
     assert lines[1].startswith("steps 3") and abs(float(lines[1].split()[2]) - 1.0) < 1e-6
+
+
+def test_literal_xyz_ablation_build_matches_the_oracle_switch(M, orc, tmp_path):
+    """Reading C1 as a build switch: a library built with MELBM_HERMITE_XYZ_LITERAL
+    (the printed 1/(2 c_s^6) on the xyz term) follows the oracle's literal_xyz
+    step, and differs from the default reading by far more than FP32 rounding."""
+    import ctypes
+    from paper_2602_05295_gb300 import build as B
+    path = B.build(extra_flags=["-DMELBM_HERMITE_XYZ_LITERAL"], lib_path=str(tmp_path / "lib.so"))
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    L.melbm_create.argtypes = [ctypes.c_int] * 4 + [ctypes.c_float, ctypes.c_int, ctypes.POINTER(P)]
+    L.melbm_set_state.argtypes = [P, P, P, P]
+    L.melbm_step.argtypes = [P, ctypes.c_int]
+    L.melbm_get_moments.argtypes = [P, P, P, P]
+    L.melbm_destroy.argtypes = [P]
+    shape = (37, 23, 19)
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(61)
+    m = eq_state(1.0 + 0.01 * rng.standard_normal(N), 0.08 * rng.standard_normal((3, N)))
+    m[4:] += 0.01 * rng.standard_normal((6, N))
+    h = P()
+    assert L.melbm_create(*shape, 27, ctypes.c_float(0.57), 0, ctypes.byref(h)) == 0
+    d = [to_gpu(m[0]), to_gpu(m[1:4]), to_gpu(m[4:])]
+    assert L.melbm_set_state(h, *(P(t.data_ptr()) for t in d)) == 0
+    assert L.melbm_step(h, 5) == 0
+    out = [torch.empty(k, N, device="cuda") for k in (1, 3, 6)]
+    assert L.melbm_get_moments(h, *(P(t.data_ptr()) for t in out)) == 0
+    torch.cuda.synchronize()
+    L.melbm_destroy(h)
+    g = np.concatenate([t.cpu().numpy() for t in out]).astype(np.float64)
+    lit = orc.step(m, shape, 0.57, n=5, literal_xyz=True)
+    std = orc.step(m, shape, 0.57, n=5)
+    assert max(errors(g, lit)) < 1e-5, errors(g, lit)
+    assert max(errors(std, lit)) > 100 * 1e-5
