@@ -182,7 +182,7 @@ int build_sources(melbm_t h) {
 }
 
 // (Re)build types and the boundary list from the mask and the inflow/outflow flags.
-int reclassify(melbm_t h) {
+int reclassify_lists(melbm_t h) {
   free_list(h);
   if (!h->mask && !h->inflow_on && !h->outflow_on) {
     dev_free(h, h->type, size_t(h->N));
@@ -212,6 +212,20 @@ int reclassify(melbm_t h) {
     if ((rc = build_sources(h))) return rc;
   }
   return MELBM_OK;
+}
+
+// A failed setup leaves no partial lists behind, and the handle refuses to step
+// (its boundaries are undefined) until a later setup succeeds.
+int reclassify(melbm_t h) {
+  const int rc = reclassify_lists(h);
+  if (rc != MELBM_OK) free_list(h);
+  h->boundary_error = rc != MELBM_OK;
+  return rc;
+}
+
+int boundary_refusal(melbm_t h, const char* what) {
+  return fail(h, MELBM_ESTATE, "%s: the last boundary setup failed; set the solids, inflow or "
+              "outflow again", what);
 }
 
 }  // namespace
@@ -466,6 +480,7 @@ int melbm_step(melbm_t h, int n) {
   const Range range("melbm_step");
   if (n < 0) return fail(h, MELBM_EINVAL, "melbm_step: n = %d < 0", n);
   if (h->poisoned) return fail(h, MELBM_ESTATE, "melbm_step: an earlier CUDA failure left the state undefined; call melbm_set_state");
+  if (h->boundary_error) return boundary_refusal(h, "melbm_step");
   for (int s = 0; s < n; ++s) {
     const uint32_t t_out = uint32_t(h->t + 1);
     if (h->storage == MELBM_MIXED) {
@@ -626,6 +641,7 @@ int melbm_solid_force(melbm_t h, int body, double* out) {
   if (!h || !out) return fail(h, MELBM_EINVAL, "melbm_solid_force: NULL argument");
   if (body < 0 || body > 255) return fail(h, MELBM_EINVAL, "melbm_solid_force: body %d outside 0..255", body);
   if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_solid_force");
+  if (h->boundary_error) return boundary_refusal(h, "melbm_solid_force");
   for (int k = 0; k < 6; ++k) out[k] = 0.0;
   if (!h->L || !h->mask) return MELBM_OK;
   int rc;

@@ -57,6 +57,7 @@ struct melbm_sim {
   double* red_out = nullptr;
   int64_t mem_bytes = 0;
   bool poisoned = false;
+  bool boundary_error = false;  // the last boundary setup failed: lists are empty
   std::string err;
   melbm::AdjointState* adj = nullptr;  // checkpoints of melbm_forward_checkpointed
 };

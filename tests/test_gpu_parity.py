@@ -455,3 +455,44 @@ def test_literal_xyz_ablation_build_matches_the_oracle_switch(M, orc, tmp_path):
     std = orc.step(m, shape, 0.57, n=5)
     assert max(errors(g, lit)) < 1e-5, errors(g, lit)
     assert max(errors(std, lit)) > 100 * 1e-5
+
+
+_BOUNDARY_FAIL_SCRIPT = r"""
+import sys
+sys.path.insert(0, {root!r})
+import numpy as np, torch
+from paper_2602_05295_gb300 import melbm as M, workloads as W
+shape = (24, 16, 12)
+sim = M.Simulator(shape, 0.6, "q16")
+mask = torch.from_numpy(W.channel_walls(shape).ravel()).cuda()
+try:
+    sim.set_solid(mask)
+    print("no failure")
+except M.MelbmError as e:
+    print("set_solid", e.code)
+for call in (lambda: sim.step(1), lambda: sim.solid_force(0)):
+    try:
+        call()
+        print("ran")
+    except M.MelbmError as e:
+        print("refused", e.code)
+print("time", sim.time_index)
+"""
+
+
+@pytest.mark.parametrize("after", [10, 12, 14, 15])
+def test_failed_boundary_setup_leaves_no_partial_lists(M, after):
+    """A device allocation failing inside melbm_set_solid (the type array, the
+    list, the source set; MELBM_FAIL_ALLOC_AFTER) is reported as MELBM_ENOMEM, and
+    the handle then refuses to step or to sum solid forces (MELBM_ESTATE) instead
+    of running with partial boundary tables."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MELBM_FAIL_ALLOC_AFTER=str(after))
+    r = subprocess.run([sys.executable, "-c", _BOUNDARY_FAIL_SCRIPT.format(root=root)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.strip().splitlines()
+    assert lines == ["set_solid 2", "refused 4", "refused 4", "time 0"], r.stdout
