@@ -120,7 +120,10 @@ MELBM_API int melbm_get_moments(melbm_t h, float* rho, float* u, float* S);
  * Runs the classification and compaction kernels (analogue of the surface
  * marking of Sec. 4.2): every cell gets a type and a 27-bit mask whose bit i is
  * set iff x - c_i is SOLID (periodic wrap); INFLOW and FLUID_BOUNDARY cells are
- * listed in ascending n.  Synchronises to read the list length. */
+ * listed in ascending n.  Synchronises to read the list length.  If the setup
+ * fails (MELBM_ENOMEM, MELBM_ECUDA) the lists are freed and melbm_step,
+ * melbm_solid_force and the adjoint return MELBM_ESTATE until a later
+ * melbm_set_solid / melbm_set_inflow / melbm_set_outflow succeeds. */
 MELBM_API int melbm_set_solid(melbm_t h, const uint8_t* mask);
 
 /* Equilibrium inflow on face 0 (x = 0): INFLOW cells are reset every step to
