@@ -42,6 +42,18 @@ struct BoundaryParams {
   QGrids q;
 };
 
+// Bits i of the 19 directions with |c|^2 <= 2.
+constexpr uint32_t d3q19_links() {
+  uint32_t m = 0;
+  for (int i = 0; i < 27; ++i) {
+    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    if (cx * cx + cy * cy + cz * cz <= 2) m |= 1u << i;
+  }
+  return m;
+}
+constexpr uint32_t D3Q19_LINKS = d3q19_links();
+static_assert(D3Q19_LINKS == 0x2EBFEBAu, "19 directions");
+
 template <int STORAGE, bool FORCE, bool MOVING, bool Q19 = false>
 __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -75,25 +87,7 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   Mom17 Aself;
   if constexpr (MOVING)
     Aself = collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n, P.q), P.omega, fx0, fy0, fz0);
-#pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-    if (Q19 && !in_d3q19(cx, cy, cz)) continue;  // D3Q19: no corner populations
-    // f_i / w_i - 1: population i pulled from x - c_i, or, for a solid link,
-    // population opp(i) = 26 - i of x itself (bounce-back; the slot then holds x)
-    // or the population of the moving wall
-    float g;
-    if (MOVING && ((word >> i) & 1u)) {
-      float up[3];
-      body_velocity(P.bodies, P.mask[pull_source(x, y, z, nx, ny, nz, i)], x - 0.5f * cx,
-                    y - 0.5f * cy, z - 0.5f * cz, up);
-      const Mom17 Wm = wall_moments(Aself, up[0], up[1], up[2]);
-      g = Q19 ? hermite_eval19(Wm, cx, cy, cz) : hermite_eval(Wm, cx, cy, cz);
-    } else {
-      const uint32_t slot = __ldg(P.table + int64_t(i) * P.count + k);
-      const int j = ((word >> i) & 1u) ? 26 - i : i;
-      g = __ldg(P.pop + int64_t(j) * P.S + slot);
-    }
+  auto accumulate = [&](int cx, int cy, int cz, float g) {
     const float w = Q19 ? lattice_weight19(cx, cy, cz)
                         : (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *
                               (cz ? (1.0f / 6.0f) : (2.0f / 3.0f));
@@ -108,6 +102,35 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
     m110 += float(cx * cy) * f;
     m101 += float(cx * cz) * f;
     m011 += float(cy * cz) * f;
+  };
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    if (Q19 && !in_d3q19(cx, cy, cz)) continue;  // D3Q19: no corner populations
+    const bool solid = (word >> i) & 1u;
+    if (MOVING && solid) continue;  // the moving-wall links follow below
+    // f_i / w_i - 1: population i pulled from x - c_i, or, for a solid link,
+    // population opp(i) = 26 - i of x itself (bounce-back; the slot then holds x)
+    const uint32_t slot = __ldg(P.table + int64_t(i) * P.count + k);
+    const int j = solid ? 26 - i : i;
+    accumulate(cx, cy, cz, __ldg(P.pop + int64_t(j) * P.S + slot));
+  }
+  if constexpr (MOVING) {
+    // the population of the moving wall for each solid link, each thread over
+    // its own links (a warp then runs as many iterations as its busiest cell,
+    // not one per direction that any of its cells has)
+    uint32_t links = word & 0x7FFFFFFu;
+    if (Q19) links &= D3Q19_LINKS;
+    while (links) {
+      const int i = __ffs(links) - 1;
+      links &= links - 1u;
+      const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+      float up[3];
+      body_velocity(P.bodies, P.mask[pull_source(x, y, z, nx, ny, nz, i)], x - 0.5f * cx,
+                    y - 0.5f * cy, z - 0.5f * cz, up);
+      const Mom17 Wm = wall_moments(Aself, up[0], up[1], up[2]);
+      accumulate(cx, cy, cz, Q19 ? hermite_eval19(Wm, cx, cy, cz) : hermite_eval(Wm, cx, cy, cz));
+    }
   }
   const Stored o = finish_moments<FORCE>(m000, m100, m010, m001, m200, m020, m002, m110, m101,
                                          m011, fx0, fy0, fz0);

@@ -13,6 +13,7 @@
 
 namespace melbm {
 
+constexpr uint32_t D3Q19_LINK_BITS = 0x2EBFEBAu;  // bits i with |c_i|^2 <= 2
 constexpr int SF_THREADS = 256;
 constexpr int SF_BLOCKS = 608;  // 4 per SM on a 152-SM part
 
@@ -54,10 +55,12 @@ __global__ void __launch_bounds__(SF_THREADS) solid_force_kernel(SolidForceParam
       fz = P.force[2 * N + n];
     }
     const Mom17 A = collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n, P.q), P.omega, fx, fy, fz);
-    for (int i = 0; i < 27; ++i) {
-      if (!((links >> i) & 1u)) continue;
+    // each thread over its own solid links (D3Q19 has no corner links)
+    uint32_t lk = Q19 ? (links & D3Q19_LINK_BITS) : links;
+    while (lk) {
+      const int i = __ffs(lk) - 1;
+      lk &= lk - 1u;
       const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-      if (Q19 && !in_d3q19(cx, cy, cz)) continue;  // D3Q19 has no corner links
       const int b = P.mask[pull_source(x, y, z, nx, ny, nz, i)];
       if (P.body && b != P.body) continue;
       // the weight of i = that of opp(i)
