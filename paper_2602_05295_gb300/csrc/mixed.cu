@@ -47,10 +47,12 @@ __global__ void mixed_correct_kernel(int nx, int ny, int nz, const void* q, floa
   cell_xyz(n, nx, ny, &x, &y, &z);
   const Mom17 self = post_collision_moments(q, N, n);
   float d[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int i = 0; i < 27; ++i) {
-    if (!((word >> i) & 1u)) continue;
+  // each thread over its own solid links (D3Q19: the 19 directions with |c|^2 <= 2)
+  uint32_t links = word & (Q19 ? 0x2EBFEBAu : 0x7FFFFFFu);
+  while (links) {
+    const int i = __ffs(links) - 1;
+    links &= links - 1u;
     const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-    if (Q19 && !in_d3q19(cx, cy, cz)) continue;  // D3Q19 has no corner links
     const Mom17 src = post_collision_moments(q, N, pull_source(x, y, z, nx, ny, nz, i));
     const float df =
         Q19 ? lattice_weight19(cx, cy, cz) *
