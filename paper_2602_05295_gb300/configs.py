@@ -198,7 +198,7 @@ def run_large1000(steps):
     return rec
 
 
-def run_adjoint128(steps):
+def run_adjoint128(steps, K=20):
     from .autograd import MELBMFunction, kinetic_energy_in_region
     wl = W.ADJOINT128
     N = wl.cells
@@ -216,18 +216,27 @@ def run_adjoint128(steps):
         a, b, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), \
             torch.cuda.Event(enable_timing=True)
         a.record()
-        m = MELBMFunction.apply(u0, F, sim, wl.steps, 20)
+        m = MELBMFunction.apply(u0, F, sim, wl.steps, K)
         L = kinetic_energy_in_region(m, region)
         b.record()
         L.backward()
         c.record()
         torch.cuda.synchronize()
         times.append((a.elapsed_time(b), b.elapsed_time(c)))
-    return {"workload": wl.name, "storage": "f32 + 16-bit checkpoints (K=20)", "cells": N,
+    storage = (f"f32 + 16-bit checkpoints (K={K})" if K < wl.steps
+               else "f32, every state kept (no recompute)")
+    return {"workload": wl.name + ("" if K < wl.steps else "_keep_all"), "storage": storage,
+            "cells": N,
             "steps": wl.steps, "loss": float(L.item()), "forward_ms": times[1][0],
             "backward_ms": times[1][1], "first_call_forward_ms": times[0][0],
             "first_call_backward_ms": times[0][1], "grad_u0_norm": float(u0.grad.norm().item()),
             "grad_F_norm": float(F.grad.norm().item()), "memory_bytes": sim.memory_bytes()}
+
+
+def run_adjoint128_keep_all(steps):
+    """The same gradient with K = 200: one segment, every FP32 state kept on the
+    device (200 x 84 MB), so the backward pass runs no recompute."""
+    return run_adjoint128(steps, K=W.ADJOINT128.steps)
 
 
 def run_mixed_vs_recompute(steps):
@@ -296,7 +305,8 @@ def run_bits_sweep(steps):
 RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256,
            "turbulence256_d3q19": run_turbulence256_d3q19, "channel512": run_channel512,
            "channel512_d3q19": run_channel512_d3q19,
-           "channel512_moving": run_channel512_moving, "large1000": run_large1000, "adjoint128": run_adjoint128, "bits_sweep": run_bits_sweep,
+           "channel512_moving": run_channel512_moving, "large1000": run_large1000, "adjoint128": run_adjoint128,
+           "adjoint128_keep_all": run_adjoint128_keep_all, "bits_sweep": run_bits_sweep,
            "mixed_vs_recompute": run_mixed_vs_recompute}
 
 

@@ -32,6 +32,7 @@ struct AdjointState {
   int nsteps = 0, K = 0, nck = 0;
   int64_t N = 0;
   bool ready = false;
+  bool seg_filled = false;    // nsteps <= K: the forward pass kept every state in seg
   float* u0 = nullptr;        // 3N
   uint32_t* ckpt = nullptr;   // nck x 5N (16-bit states at t = K, 2K, ...)
   float* seg = nullptr;       // (K + 1) x 10N FP32 states of one segment
@@ -725,8 +726,24 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
     h->mem_bytes += a->N * 4 * (3 + 10 * (K + 1) + 23) + a->N * 20 * int64_t(nck);
   }
   a->ready = false;
+  a->seg_filled = false;
   a->nsteps = nsteps;
   ADJ_CUDA(h, cudaMemcpyAsync(a->u0, u0, N * 12, cudaMemcpyDeviceToDevice, h->stream));
+  if (nsteps <= K) {
+    // one segment: its states stay in seg, so the backward pass needs no recompute
+    // (the same kernels on the same inputs: the states it would recompute)
+    init_from_u0_kernel<<<blocks_for(h->N), AT, 0, h->stream>>>(a->u0, a->seg, h->N);
+    ADJ_CUDA(h, cudaGetLastError());
+    for (int t = 0; t < nsteps; ++t)
+      ADJ_CUDA(h, forward_step(h, a->seg + size_t(t) * 10 * N, a->seg + size_t(t + 1) * 10 * N,
+                               uint32_t(t + 1)));
+    ADJ_CUDA(h, cudaMemcpyAsync(h->buf[h->cur], a->seg + size_t(nsteps) * 10 * N, N * 40,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    h->t = nsteps;
+    a->seg_filled = true;
+    a->ready = true;
+    return MELBM_OK;
+  }
   init_from_u0_kernel<<<blocks_for(h->N), AT, 0, h->stream>>>(a->u0, static_cast<float*>(h->buf[h->cur]), h->N);
   ADJ_CUDA(h, cudaGetLastError());
   h->t = 0;
@@ -768,14 +785,16 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int s = sg * K, e = (s + K < nsteps) ? s + K : nsteps;
     float* seg0 = a->seg;
-    if (sg == 0)
-      init_from_u0_kernel<<<nb, AT, 0, st>>>(a->u0, seg0, h->N);
-    else
-      q16_to_f32_kernel<<<nb, AT, 0, st>>>(a->ckpt + size_t(sg - 1) * 5 * N, seg0, h->N);
-    ADJ_CUDA(h, cudaGetLastError());
-    for (int j = 1; j <= e - s; ++j)
-      ADJ_CUDA(h, forward_step(h, a->seg + size_t(j - 1) * 10 * N, a->seg + size_t(j) * 10 * N,
-                               uint32_t(s + j)));
+    if (!a->seg_filled) {
+      if (sg == 0)
+        init_from_u0_kernel<<<nb, AT, 0, st>>>(a->u0, seg0, h->N);
+      else
+        q16_to_f32_kernel<<<nb, AT, 0, st>>>(a->ckpt + size_t(sg - 1) * 5 * N, seg0, h->N);
+      ADJ_CUDA(h, cudaGetLastError());
+      for (int j = 1; j <= e - s; ++j)
+        ADJ_CUDA(h, forward_step(h, a->seg + size_t(j - 1) * 10 * N, a->seg + size_t(j) * 10 * N,
+                                 uint32_t(s + j)));
+    }
     for (int t = e - 1; t >= s; --t) {
       const int j = t - s;
       const float* m_t = a->seg + size_t(j) * 10 * N;
