@@ -240,6 +240,44 @@ def test_channel512_sampled_one_step(M, orc, storage):
     assert np.all(cells % nx < nx)
 
 
+def test_large1000_sampled_one_step(M, orc):
+    """The largest workload, 1000 x 400 x 400 (160 M cells, 16-bit, tau = 0.505)
+    with its procedural obstacle, inflow and outflow: one GPU step against the
+    oracle's update of sampled listed, inflow, outflow and fluid cells."""
+    wl = W.LARGE1000
+    mask, _ = W.procedural_obstacle(wl.shape)
+    N = wl.cells
+    rng = np.random.default_rng(29)
+    sim = M.Simulator(wl.shape, wl.tau, "q16", seed=8)
+    u = torch.zeros(3, N, device="cuda")
+    u[0] = 0.06
+    u += 0.01 * torch.randn(3, N, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    sim.set_state(torch.ones(N, device="cuda"), u)
+    del u
+    sim.set_solid(to_gpu(mask.ravel(), torch.uint8))
+    sim.set_inflow(1.0, (0.06, 0.0, 0.0))
+    sim.set_outflow()
+    typ = sim.types().cpu().numpy()
+    listed, _ = sim.boundary_list()
+    listed = listed.cpu().numpy().astype(np.int64)
+    sim.step(2)
+    g_in = read(sim)
+    sim.step(1)
+    cells = np.unique(np.concatenate([
+        rng.choice(listed, 3000, replace=False), rng.integers(0, N, 2000),
+        np.nonzero(typ == orc.INFLOW)[0][:300], np.nonzero(typ == orc.OUTFLOW)[0][:300]]))
+    cells = cells[typ[cells] != orc.SOLID]
+    ref = orc.step_cells(g_in, wl.shape, wl.tau, cells, typ=typ, inflow=[1.0, 0.06, 0.0, 0.0])
+    del g_in
+    rho, uu, _ = sim.get_moments()
+    idx = torch.from_numpy(cells).cuda()
+    got_rho = rho[idx].double().cpu().numpy()
+    got_u = uu[:, idx].double().cpu().numpy()
+    du = np.abs(got_u - ref[1:4]).max()
+    drho = np.abs(got_rho - ref[0]).max()
+    assert du <= 0.8 / 65535 * 1.01 and drho <= 0.7 / 65535 * 1.01, (du, drho)
+
+
 # ------------------------------------------------------------------ boundaries
 def _channel_case(shape=(48, 26, 22)):
     nx, ny, nz = shape
