@@ -170,7 +170,9 @@ MELBM_API int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int
 /* Differentiation (not in the paper; inverse problems motivate it, Sec. 1).
  * melbm_forward_checkpointed: from the initial velocity u0[3N] (device) with
  * rho = 1 and S = u0 u0, runs nsteps FP32-storage steps with the current force,
- * storing a 16-bit checkpoint (deterministic rounding) every K steps.
+ * storing a 16-bit checkpoint (deterministic rounding) every K steps; when
+ * nsteps <= K it keeps every FP32 state instead (K + 1 states of 40 N bytes) and
+ * the backward pass runs no recompute.
  * melbm_backward: given dL/d(rho, u, S) of the final state (10N device floats,
  * component-major as melbm_get_moments), writes dL/du0[3N] and dL/dF[3N]
  * (device; dL_dF may be NULL) by the hand-written discrete adjoint, recomputing

@@ -2,7 +2,8 @@
 
 ``MELBMFunction.apply(u0, F, sim, nsteps, K)`` runs ``nsteps`` FP32-storage steps
 from the initial state (rho = 1, u = u0, S = u0 u0) with the body force F, keeping
-a 16-bit checkpoint every K steps, and returns the final public moments as a
+a 16-bit checkpoint every K steps (every FP32 state when nsteps <= K, so that the
+backward pass needs no recompute), and returns the final public moments as a
 (10, N) tensor (rho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz).  Its backward
 calls melbm_backward: the hand-written adjoint kernels return dL/du0 and dL/dF.
 All arithmetic runs in the CUDA library; this module only passes tensors.
