@@ -5,6 +5,7 @@
 // adds the partials in a fixed order, so the result is deterministic.
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
+#include "reduce_cell.cuh"
 
 namespace melbm {
 
@@ -18,53 +19,31 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-__device__ __forceinline__ uint32_t rail_count(uint32_t w, uint32_t qmax_lo, uint32_t qmax_hi) {
-  const uint32_t lo = w & 0xFFFFu, hi = w >> 16;
-  return (lo == 0u || lo == qmax_lo) + (hi == 0u || hi == qmax_hi);
-}
-
 template <int STORAGE>
 __global__ void __launch_bounds__(RD_THREADS) reduce_partial_kernel(int64_t N, const void* buf,
                                                                    const uint8_t* type,
                                                                    double* partials, QGrids q) {
-  double mass = 0.0, ke = 0.0, sat = 0.0;
+  double dmass = 0.0, ke = 0.0;  // sums of rho - 1 and of rho |u|^2 / 2
+  uint32_t fluid = 0, rails = 0;
   for (int64_t n = int64_t(blockIdx.x) * RD_THREADS + threadIdx.x; n < N;
        n += int64_t(gridDim.x) * RD_THREADS) {
     if (type && type[n] == T_SOLID) continue;
-    double rho, u2;
-    if constexpr (STORAGE == ST_MIXED) {  // raw post-streaming sums rho - 1, rho u
-      const float* p = static_cast<const float*>(buf);
-      rho = 1.0 + double(p[n]);
-      const double jx = p[N + n], jy = p[2 * N + n], jz = p[3 * N + n];
-      u2 = (jx * jx + jy * jy + jz * jz) / (rho * rho);
-    } else {
-      const Stored s = load_stored<STORAGE>(buf, size_t(N), size_t(n), q);
-      rho = 1.0 + double(s.drho);
-      u2 = double(s.ux) * s.ux + double(s.uy) * s.uy + double(s.uz) * s.uz;
-    }
-    mass += rho;
-    ke += 0.5 * rho * u2;
-    if (STORAGE == ST_Q16) {
-      const uint32_t* b = static_cast<const uint32_t*>(buf);
-      uint32_t c = 0;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        // word 0 = (rho, ux), 1 = (uy, uz), 2..4 = rho S^neq
-        const uint32_t qm_lo = q.g[k == 0 ? 0 : (k == 1 ? 1 : 2)].qmax;
-        const uint32_t qm_hi = q.g[k < 2 ? 1 : 2].qmax;
-        c += rail_count(b[size_t(k) * N + n], qm_lo, qm_hi);
-      }
-      sat += double(c);
-    }
+    const CellTerms t = reduce_cell<STORAGE>(buf, size_t(N), size_t(n), &q);
+    dmass += double(t.drho);
+    ke += double(t.ke);
+    fluid += 1u;
+    rails += t.rails;
   }
+  // per thread: mass = cells + sum (rho - 1); at most 2^31 cells in all
+  double mass = double(fluid) + dmass, kes = ke, sat = double(rails);
   __shared__ double sm[3][RD_THREADS / 32];
   mass = warp_sum_d(mass);
-  ke = warp_sum_d(ke);
+  kes = warp_sum_d(kes);
   sat = warp_sum_d(sat);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     sm[0][wid] = mass;
-    sm[1][wid] = ke;
+    sm[1][wid] = kes;
     sm[2][wid] = sat;
   }
   __syncthreads();

@@ -23,6 +23,7 @@
 
 #include "../../include/melbm.h"
 #include "melbm_device.cuh"
+#include "reduce_cell.cuh"
 
 namespace melbm {
 namespace {
@@ -46,29 +47,24 @@ __global__ void __launch_bounds__(NA_THREADS) noalloc_partial_kernel(int64_t N, 
                                                                     double* partials) {
   const int64_t begin = int64_t(blockIdx.x) * NA_CHUNK;
   const int64_t end = begin + NA_CHUNK < N ? begin + NA_CHUNK : N;
-  double mass = 0.0, ke = 0.0, sat = 0.0;
+  double dmass = 0.0, ke = 0.0;
+  uint32_t fluid = 0, rails = 0;
   for (int64_t n = begin + threadIdx.x; n < end; n += NA_THREADS) {
     if (type && type[n] == T_SOLID) continue;
-    const Stored s = load_stored<STORAGE>(buf, size_t(N), size_t(n));
-    const double rho = 1.0 + double(s.drho);
-    mass += rho;
-    ke += 0.5 * rho * (double(s.ux) * s.ux + double(s.uy) * s.uy + double(s.uz) * s.uz);
-    if (STORAGE == ST_Q16) {
-      const uint32_t* b = static_cast<const uint32_t*>(buf);
-      for (int k = 0; k < 5; ++k) {
-        const uint32_t w = b[size_t(k) * size_t(N) + size_t(n)];
-        const uint32_t lo = w & 0xFFFFu, hi = w >> 16;
-        sat += double((lo == 0u || lo == 0xFFFFu) + (hi == 0u || hi == 0xFFFFu));
-      }
-    }
+    const CellTerms t = reduce_cell<STORAGE>(buf, size_t(N), size_t(n), nullptr);
+    dmass += double(t.drho);
+    ke += double(t.ke);
+    fluid += 1u;
+    rails += t.rails;
   }
+  double mass = double(fluid) + dmass, kes = ke, sat = double(rails);
   __shared__ double sm[3][NA_THREADS / 32];
   mass = warp_sum(mass);
-  ke = warp_sum(ke);
+  kes = warp_sum(kes);
   sat = warp_sum(sat);
   if ((threadIdx.x & 31) == 0) {
     sm[0][threadIdx.x >> 5] = mass;
-    sm[1][threadIdx.x >> 5] = ke;
+    sm[1][threadIdx.x >> 5] = kes;
     sm[2][threadIdx.x >> 5] = sat;
   }
   __syncthreads();
