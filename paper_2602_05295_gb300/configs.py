@@ -156,6 +156,20 @@ def run_channel512_d3q19(steps):
     return rec
 
 
+def run_scene720_d3q19(steps):
+    """A scene the size of the paper's D3Q19 scene (720 x 360 x 360, 93 M cells) with
+    a procedural obstacle, on D3Q19 with 16-bit storage: the recompute design and
+    the paper's mixed scheme, per-step time and memory."""
+    wl = W.SCENE720
+    mask, _ = W.scene720_obstacle(wl.shape)
+    out = []
+    for storage in ("q16", "mixed"):
+        rec = _channel(wl, mask, 0.05, steps, storage=storage, lattice=19)
+        rec["workload"] = wl.name
+        out.append(rec)
+    return out
+
+
 def run_channel512_moving(steps):
     """The sphere channel with the moment-based wall model: every sphere (the first
     254) is a body spinning about its own centre (surface speed 0.01, axis z), the
@@ -304,7 +318,7 @@ def run_bits_sweep(steps):
 
 RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256,
            "turbulence256_d3q19": run_turbulence256_d3q19, "channel512": run_channel512,
-           "channel512_d3q19": run_channel512_d3q19,
+           "channel512_d3q19": run_channel512_d3q19, "scene720_d3q19": run_scene720_d3q19,
            "channel512_moving": run_channel512_moving, "large1000": run_large1000, "adjoint128": run_adjoint128,
            "adjoint128_keep_all": run_adjoint128_keep_all, "bits_sweep": run_bits_sweep,
            "mixed_vs_recompute": run_mixed_vs_recompute}

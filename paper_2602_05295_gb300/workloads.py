@@ -50,7 +50,19 @@ LARGE1000 = Workload("large1000", (1000, 400, 400), 0.505, 1000, "q16",
 ADJOINT128 = Workload("adjoint128", (128, 128, 128), 0.55, 200, "f32",
                       "adjoint, 128^3 periodic, random-phase u0 (max 0.05), trainable force")
 
+# the grid size of the paper's one D3Q19 scene (Table 1), with a procedural obstacle
+# standing in for its mesh
+SCENE720 = Workload("scene720_d3q19", (720, 360, 360), 0.55, 1000, "q16",
+                    "D3Q19, 720x360x360 flow past 30 random boxes/ellipsoids, inflow u=(0.05,0,0)")
+
 ALL = (TGV32, TURB256, CHANNEL512, LARGE1000, ADJOINT128)
+
+
+def scene720_obstacle(shape=SCENE720.shape):
+    """The obstacle of the 720 x 360 x 360 scene: 30 boxes/ellipsoids, half-extents
+    in [8, 45], centres in x [100, 430), y [80, 280), z [80, 280), plus walls."""
+    return procedural_obstacle(shape, count=30, hmin=8.0, hmax=45.0, seed=SEED + 9,
+                               region=((100, 430), (80, 280), (80, 280)))
 
 
 # ----------------------------------------------------------------- velocity fields
