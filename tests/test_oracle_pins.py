@@ -1023,3 +1023,35 @@ def test_d3q19_moment_wall_moving_with_the_flow_keeps_uniform_flow(orc):
     assert np.abs(new[:, fluid] - m[:, fluid]).max() < 1e-14
     bb = orc.step19(m, shape, 0.7, typ=typ, wall=orc.Wall(0, body))
     assert np.abs(bb[1:4, fluid] - m[1:4, fluid]).max() > 1e-3
+
+
+def test_d3q19_sound_speed_and_acoustic_damping(orc):
+    """A standing acoustic wave rho = 1 + eps cos(k x) on the 19-velocity lattice
+    oscillates at c_s k with c_s^2 = 1/3 and decays at the rate of the D3Q27
+    closure, Gamma = k^2 ((2/3) nu + mu_v / 2), mu_v = 1/9 (the trace of S is reset
+    each step on both lattices)."""
+    nx, tau, eps = 64, 0.6, 1e-5
+    shape = (nx, 1, 1)
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    m = eq_state(1.0 + eps * np.cos(k * x), np.zeros((3, nx)))
+    amp = []
+    cur = m
+    T = 400
+    for t in range(T + 1):
+        amp.append(((cur[0] - 1.0) * np.cos(k * x)).sum() / (np.cos(k * x) ** 2).sum())
+        cur = orc.step19(cur, shape, tau)
+    a = np.array(amp) / eps
+    # fit a damped cosine exp(-g t) cos(w t) through its zero crossings and peaks
+    s = np.sign(a)
+    zc = np.nonzero(s[1:] * s[:-1] < 0)[0]
+    t0 = zc + a[zc] / (a[zc] - a[zc + 1])  # linear interpolation of each crossing
+    w = np.pi / np.diff(t0).mean()
+    cs_fit = w / k
+    assert abs(cs_fit / np.sqrt(CS2) - 1) < 1e-3, cs_fit
+    nu = CS2 * (tau - 0.5)
+    gamma = k * k * (2.0 / 3.0 * nu + 1.0 / 18.0)
+    env = np.abs(a[np.round(t0[:-1] + np.pi / w / 2).astype(int)])  # near the extrema
+    tt = np.round(t0[:-1] + np.pi / w / 2)
+    g_fit = -np.polyfit(tt, np.log(env), 1)[0]
+    assert abs(g_fit / gamma - 1) < 1e-2, (g_fit, gamma)
