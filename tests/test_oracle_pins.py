@@ -1055,3 +1055,52 @@ def test_d3q19_sound_speed_and_acoustic_damping(orc):
     tt = np.round(t0[:-1] + np.pi / w / 2)
     g_fit = -np.polyfit(tt, np.log(env), 1)[0]
     assert abs(g_fit / gamma - 1) < 1e-2, (g_fit, gamma)
+
+
+@pytest.mark.parametrize("lattice", [27, 19])
+def test_moving_wall_population_at_the_halfway_point(orc, lattice):
+    """Sec. 3.2 for one isolated solid cell s of a rigid body in fluid at rest: each
+    neighbour x = s + c has exactly one solid link, c, and after one step its
+    moments are those of the rest populations with population c replaced by the
+    reconstruction of (rho = 1, u^p, u^p u^p) at the halfway point p = s + c/2,
+    u^p = V + Om x (p - r0) -- the wall point and velocity set independently of the
+    step's own geometry."""
+    n = 6
+    shape = (n, n, n)
+    N = n ** 3
+    s = np.array([2, 2, 2])
+    body = np.zeros(N, np.uint8)
+    body[s[0] + n * (s[1] + n * s[2])] = 1
+    V, Om, r0 = np.array([0.003, -0.002, 0.001]), np.array([0.01, -0.02, 0.03]), np.array([1.3, 2.7, 2.2])
+    wall = orc.Wall(1, body, {1: (V, Om, r0)})
+    typ = orc.classify((body > 0).reshape(shape[::-1]))[0]
+    m = eq_state(1.0, np.zeros((3, N)))
+    if lattice == 19:
+        out = orc.step19(m, shape, 0.6, typ=typ, wall=wall)
+        _, c, w = orc.reconstruct19(m[:, 0])
+        def pop(i, mm):
+            return orc.reconstruct19(mm)[0][i]
+    else:
+        out = orc.step(m, shape, 0.6, typ=typ, wall=wall)
+        c, w = orc.lattice()
+        def pop(i, mm):
+            return orc.reconstruct(mm)[0, i]
+    checked = 0
+    for i, ci in enumerate(c):
+        if not ci.any():
+            continue
+        x = s + ci
+        nidx = x[0] + n * (x[1] + n * x[2])
+        p = s + 0.5 * ci
+        up = V + np.cross(Om, p - r0)
+        mw = np.concatenate([[1.0], up, [up[a] * up[b] for a, b in PAIRS]])
+        df = pop(i, mw) - w[i]  # the replaced population minus the rest one
+        rho = 1.0 + df
+        ci_f = ci.astype(float)
+        want_u = ci_f * df / rho
+        want_S = np.array([(ci_f[a] * ci_f[b] - CS2 * (a == b)) * df for a, b in PAIRS]) / rho
+        assert abs(out[0, nidx] - rho) < 1e-15
+        assert np.abs(out[1:4, nidx] - want_u).max() < 1e-15
+        assert np.abs(out[4:, nidx] - want_S).max() < 1e-15
+        checked += 1
+    assert checked == len(c) - 1
