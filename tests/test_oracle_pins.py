@@ -1004,6 +1004,13 @@ def test_d3q19_wall_momentum_exchange_balances_the_step(orc):
         F1 = orc.solid_force(m, shape, 0.6, typ, wall, F=F, body_id=1, lattice=19)
         F2 = orc.solid_force(m, shape, 0.6, typ, wall, F=F, body_id=2, lattice=19)
         assert np.allclose(F1[:3] + F2[:3], Fs[:3], rtol=0, atol=1e-13)
+        # the same motion described about r0 + d: T(r0 + d) = T(r0) - d x F
+        d = np.array([0.7, -1.3, 2.1])
+        V1 = np.add(motion[1][0], np.cross(motion[1][1], d))
+        m1 = {1: (V1, motion[1][1], list(np.add(motion[1][2], d))), 2: motion[2]}
+        F1s = orc.solid_force(m, shape, 0.6, typ, orc.Wall(model, body, m1), F=F, body_id=1,
+                              lattice=19)
+        assert np.allclose(F1s[3:], F1[3:] - np.cross(d, F1[:3]), rtol=0, atol=1e-12)
     # model 0 through the wall path equals the plain bounce-back step
     bb = orc.step19(m, shape, 0.6, F=F, typ=typ)
     assert np.abs(orc.step19(m, shape, 0.6, F=F, typ=typ, wall=orc.Wall(0, body)) - bb).max() == 0
