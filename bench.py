@@ -208,11 +208,14 @@ def job_mlups(cells_per_rank, steps, world, job_ms):
     return cells_per_rank * steps * world / (job_ms / 1e3) / 1e6
 
 
-def e2e_raw_run(torch, melbm, wl, u_np, steps, warmup):
+def e2e_raw_run(torch, melbm, wl, u_np, steps, warmup, pipelined=True):
     """End to end through the public API with host buffers, in the library's own
     state format: every step uploads the 16-bit stored state (20 B/cell) from
-    pinned host memory (melbm_set_raw_state), takes one step and reads the new
-    stored state back into pinned host memory (melbm_get_raw_state)."""
+    pinned host memory, takes one step and reads the new stored state back into
+    pinned host memory.  Pipelined: melbm_upload_raw_state_async /
+    melbm_step / melbm_download_raw_state_async, so that a step's download runs
+    beside the next step's upload (one sync at the end of the timed region);
+    otherwise the blocking melbm_set_raw_state / melbm_get_raw_state."""
     N = wl.cells
     sim = melbm.Simulator(wl.shape, wl.tau, "q16", seed=2602)
     rho = torch.ones(N, dtype=torch.float32, device="cuda")
@@ -222,17 +225,24 @@ def e2e_raw_run(torch, melbm, wl, u_np, steps, warmup):
     h_out = torch.empty(nb, dtype=torch.uint8).pin_memory()
 
     def one():
-        sim.set_raw_state(h_in, 0)
-        sim.step(1)
-        sim.get_raw_state(h_out)
+        if pipelined:
+            sim.upload_raw_state_async(h_in, 0)
+            sim.step(1)
+            sim.download_raw_state_async(h_out)
+        else:
+            sim.set_raw_state(h_in, 0)
+            sim.step(1)
+            sim.get_raw_state(h_out)
 
     for _ in range(warmup):
         one()
+    sim.sync_transfers()
     barrier(torch)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(steps):
         one()
+    sim.sync_transfers()
     torch.cuda.synchronize()
     el = max_over_ranks(torch, time.perf_counter() - t)
     sim.close()
@@ -424,12 +434,19 @@ def main():
     }
     if not args.no_e2e:
         ks = max(3, min(args.steps, 10))
-        el, bi, bo = e2e_raw_run(torch, melbm, wl, u_np, ks, 2)
+        el, bi, bo = e2e_raw_run(torch, melbm, wl, u_np, ks, 3)
         out["e2e"] = {"value": N * ks * world / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi,
                       "d2h_bytes_per_step": bo,
-                      "what": "per step: melbm_set_raw_state from pinned host (the 16-bit stored "
-                              "state), melbm_step(1), melbm_get_raw_state into pinned host"}
-        el, bi, bo = e2e_run(torch, melbm, wl, u_np, ks, 2)
+                      "what": "per step: melbm_upload_raw_state_async from pinned host (the 16-bit "
+                              "stored state), melbm_step(1), melbm_download_raw_state_async into "
+                              "pinned host; one melbm_sync_transfers at the end"}
+        el, bi, bo = e2e_raw_run(torch, melbm, wl, u_np, ks, 3, pipelined=False)
+        out["e2e_serial"] = {
+            "value": N * ks * world / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bo,
+            "what": "per step: melbm_set_raw_state, melbm_step(1), melbm_get_raw_state "
+                    "(blocking), pinned host"}
+        el, bi, bo = e2e_run(torch, melbm, wl, u_np, ks, 3)
         out["e2e_fp32_moments"] = {
             "value": N * ks * world / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi,
             "d2h_bytes_per_step": bo,

@@ -167,6 +167,27 @@ MELBM_API int melbm_state_bytes(melbm_t h, int64_t* bytes);
 MELBM_API int melbm_get_raw_state(melbm_t h, void* dst, int64_t bytes);
 MELBM_API int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int64_t time_index);
 
+/* Asynchronous raw-state transfers, for moving a state to or from pinned host
+ * memory while the GPU computes (with pageable host memory they still work but
+ * do not overlap).  They run on two streams of the handle's own, in issue order
+ * with the work already enqueued on the handle's stream, and return at once; the
+ * caller must neither change src nor read dst before melbm_sync_transfers.
+ *   melbm_upload_raw_state_async: the state src (bytes as for set_raw_state)
+ *     becomes the current state with time index time_index.  It lands in the
+ *     ping-pong buffer that does not hold the current state, so a download of
+ *     that state may still be in flight.
+ *   melbm_download_raw_state_async: copies the current state into dst; a
+ *     following melbm_step(h, 1) runs while it does (it reads that buffer and
+ *     writes the other one).
+ *   melbm_sync_transfers: blocks until every transfer issued has completed.
+ * melbm_step waits for the upload it steps from and for the downloads still
+ * reading a buffer it overwrites; every other call that touches the state
+ * waits for all transfers.  MELBM_MIXED storage returns MELBM_EINVAL. */
+MELBM_API int melbm_upload_raw_state_async(melbm_t h, const void* src, int64_t bytes,
+                                           int64_t time_index);
+MELBM_API int melbm_download_raw_state_async(melbm_t h, void* dst, int64_t bytes);
+MELBM_API int melbm_sync_transfers(melbm_t h);
+
 /* Differentiation (not in the paper; inverse problems motivate it, Sec. 1).
  * melbm_forward_checkpointed: from the initial velocity u0[3N] (device) with
  * rho = 1 and S = u0 u0, runs nsteps FP32-storage steps with the current force,

@@ -696,6 +696,7 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: the adjoint covers halfway bounce-back walls only");
   if (h->boundary_error)
     return adj_fail(h, MELBM_ESTATE, "melbm_forward_checkpointed: the last boundary setup failed");
+  ADJ_CUDA(h, join_transfers(h));
   const size_t N = size_t(h->N);
   AdjointState* a = h->adj;
   const int nck = (nsteps - 1) / K;  // checkpoints at t = K, 2K, ... < nsteps
@@ -771,6 +772,7 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
     return adj_fail(h, MELBM_ESTATE, "melbm_backward: the last boundary setup failed");
   if (!dL_dm || !dL_du0 || !is_dev(dL_dm) || !is_dev(dL_du0) || (dL_dF && !is_dev(dL_dF)))
     return adj_fail(h, MELBM_EINVAL, "melbm_backward: gradients must be device pointers");
+  ADJ_CUDA(h, join_transfers(h));
   const size_t N = size_t(h->N);
   const unsigned nb = blocks_for(h->N);
   const float omega = 1.0f / h->tau;

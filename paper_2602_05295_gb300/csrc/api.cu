@@ -228,6 +228,45 @@ int boundary_refusal(melbm_t h, const char* what) {
               "outflow again", what);
 }
 
+void release_transfers(melbm_t h) {
+  if (!h->transfers) return;
+  if (h->up_stream) cudaStreamSynchronize(h->up_stream);
+  if (h->down_stream) cudaStreamSynchronize(h->down_stream);
+  cudaEvent_t evs[4] = {h->ev_issue, h->ev_uploaded, h->ev_read[0], h->ev_read[1]};
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  if (h->up_stream) cudaStreamDestroy(h->up_stream);
+  if (h->down_stream) cudaStreamDestroy(h->down_stream);
+  h->up_stream = h->down_stream = nullptr;
+  h->ev_issue = h->ev_uploaded = h->ev_read[0] = h->ev_read[1] = nullptr;
+  h->transfers = false;
+}
+
+// Streams and events of the asynchronous raw-state transfers, created once.
+int ensure_transfers(melbm_t h) {
+  if (h->transfers) return MELBM_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->down_stream, cudaStreamNonBlocking);
+  cudaEvent_t* evs[4] = {&h->ev_issue, &h->ev_uploaded, &h->ev_read[0], &h->ev_read[1]};
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
+  h->transfers = true;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release_transfers(h);
+    return fail(h, MELBM_ECUDA, "creating the transfer streams: %s", cudaGetErrorString(e));
+  }
+  return MELBM_OK;
+}
+
+int check_raw_bytes(melbm_t h, const char* what, int64_t bytes) {
+  if (h->storage == MELBM_MIXED) return mixed_unsupported(h, what);
+  if (bytes != int64_t(state_bytes(h)))
+    return fail(h, MELBM_EINVAL, "%s: bytes %lld != %lld", what, (long long)bytes,
+                (long long)state_bytes(h));
+  return MELBM_OK;
+}
+
 }  // namespace
 
 namespace melbm {
@@ -246,6 +285,14 @@ cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out
                         h->lattice, h->stream);
   if (e == cudaSuccess && h->outflow_on && h->type)
     e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream);
+  return e;
+}
+
+cudaError_t join_transfers(melbm_sim* h) {
+  if (!h->transfers) return cudaSuccess;
+  cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_uploaded, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_read[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_read[1], 0);
   return e;
 }
 }  // namespace melbm
@@ -307,6 +354,7 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
 
 int melbm_destroy(melbm_t h) {
   if (!h) return MELBM_OK;
+  release_transfers(h);
   if (h->adj) adjoint_free(h->adj);
   dev_free(h, h->buf[0], buf_bytes(h, 0));
   dev_free(h, h->buf[1], buf_bytes(h, 1));
@@ -342,6 +390,7 @@ int melbm_set_seed(melbm_t h, uint32_t seed) {
 int melbm_set_state(melbm_t h, const float* rho, const float* u, const float* S) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_state: NULL handle");
   if (!rho || !u) return fail(h, MELBM_EINVAL, "melbm_set_state: rho and u are required");
+  MELBM_CUDA(h, join_transfers(h));
   const size_t N = size_t(h->N);
   const bool dev = is_device_ptr(rho) && is_device_ptr(u) && (!S || is_device_ptr(S));
   const float *r = rho, *uu = u, *ss = S;
@@ -374,6 +423,7 @@ int melbm_set_state(melbm_t h, const float* rho, const float* u, const float* S)
 int melbm_get_moments(melbm_t h, float* rho, float* u, float* S) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_get_moments: NULL handle");
   if (!rho && !u && !S) return fail(h, MELBM_EINVAL, "melbm_get_moments: no output");
+  MELBM_CUDA(h, join_transfers(h));
   const size_t N = size_t(h->N);
   const bool dev = (!rho || is_device_ptr(rho)) && (!u || is_device_ptr(u)) && (!S || is_device_ptr(S));
   if (dev && h->storage == MELBM_MIXED) {
@@ -481,6 +531,16 @@ int melbm_step(melbm_t h, int n) {
   if (n < 0) return fail(h, MELBM_EINVAL, "melbm_step: n = %d < 0", n);
   if (h->poisoned) return fail(h, MELBM_ESTATE, "melbm_step: an earlier CUDA failure left the state undefined; call melbm_set_state");
   if (h->boundary_error) return boundary_refusal(h, "melbm_step");
+  if (h->transfers && n > 0) {
+    // the uploaded state must have landed; a download may still read the input
+    // buffer, but not one that this call overwrites
+    MELBM_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_uploaded, 0));
+    if (n > 1) {
+      MELBM_CUDA(h, join_transfers(h));
+    } else {
+      MELBM_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_read[1 - h->cur], 0));
+    }
+  }
   for (int s = 0; s < n; ++s) {
     const uint32_t t_out = uint32_t(h->t + 1);
     if (h->storage == MELBM_MIXED) {
@@ -506,6 +566,7 @@ int melbm_step(melbm_t h, int n) {
 
 int melbm_reduce(melbm_t h, double* mass, double* ke) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_reduce: NULL handle");
+  MELBM_CUDA(h, join_transfers(h));
   const void* state = h->storage == MELBM_MIXED ? h->buf[1] : h->buf[h->cur];
   MELBM_CUDA(h, launch_reduce(h->storage, h->N, state, h->type, h->red_partials, h->red_out,
                               h->grids, h->stream));
@@ -539,10 +600,8 @@ int melbm_state_bytes(melbm_t h, int64_t* bytes) {
 
 int melbm_get_raw_state(melbm_t h, void* dst, int64_t bytes) {
   if (!h || !dst) return fail(h, MELBM_EINVAL, "melbm_get_raw_state: NULL argument");
-  if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_get_raw_state");
-  if (bytes != int64_t(state_bytes(h)))
-    return fail(h, MELBM_EINVAL, "melbm_get_raw_state: bytes %lld != %lld", (long long)bytes,
-                (long long)state_bytes(h));
+  if (int rc = check_raw_bytes(h, "melbm_get_raw_state", bytes)) return rc;
+  MELBM_CUDA(h, join_transfers(h));
   MELBM_CUDA(h, cudaMemcpyAsync(dst, h->buf[h->cur], size_t(bytes), cudaMemcpyDefault, h->stream));
   MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return MELBM_OK;
@@ -550,15 +609,57 @@ int melbm_get_raw_state(melbm_t h, void* dst, int64_t bytes) {
 
 int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int64_t time_index) {
   if (!h || !src) return fail(h, MELBM_EINVAL, "melbm_set_raw_state: NULL argument");
-  if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_set_raw_state");
-  if (bytes != int64_t(state_bytes(h)))
-    return fail(h, MELBM_EINVAL, "melbm_set_raw_state: bytes %lld != %lld", (long long)bytes,
-                (long long)state_bytes(h));
+  if (int rc = check_raw_bytes(h, "melbm_set_raw_state", bytes)) return rc;
   if (time_index < 0) return fail(h, MELBM_EINVAL, "melbm_set_raw_state: negative time index");
+  MELBM_CUDA(h, join_transfers(h));
   MELBM_CUDA(h, cudaMemcpyAsync(h->buf[h->cur], src, size_t(bytes), cudaMemcpyDefault, h->stream));
   MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->t = time_index;
   h->poisoned = false;
+  return MELBM_OK;
+}
+
+// The upload lands in the buffer that does not hold the current state, after the
+// work already issued on the handle's stream (a step may still read it) and after
+// any download still reading it; that buffer then becomes the current state.  The
+// download reads the current state after the work already issued and after the
+// upload that produced it.  Neither blocks the host.
+int melbm_upload_raw_state_async(melbm_t h, const void* src, int64_t bytes, int64_t time_index) {
+  if (!h || !src) return fail(h, MELBM_EINVAL, "melbm_upload_raw_state_async: NULL argument");
+  if (int rc = check_raw_bytes(h, "melbm_upload_raw_state_async", bytes)) return rc;
+  if (time_index < 0)
+    return fail(h, MELBM_EINVAL, "melbm_upload_raw_state_async: negative time index");
+  if (int rc = ensure_transfers(h)) return rc;
+  const int b = 1 - h->cur;
+  MELBM_CUDA(h, cudaEventRecord(h->ev_issue, h->stream));
+  MELBM_CUDA(h, cudaStreamWaitEvent(h->up_stream, h->ev_issue, 0));
+  MELBM_CUDA(h, cudaStreamWaitEvent(h->up_stream, h->ev_read[b], 0));
+  MELBM_CUDA(h, cudaMemcpyAsync(h->buf[b], src, size_t(bytes), cudaMemcpyDefault, h->up_stream));
+  MELBM_CUDA(h, cudaEventRecord(h->ev_uploaded, h->up_stream));
+  h->cur = b;
+  h->t = time_index;
+  h->poisoned = false;
+  return MELBM_OK;
+}
+
+int melbm_download_raw_state_async(melbm_t h, void* dst, int64_t bytes) {
+  if (!h || !dst) return fail(h, MELBM_EINVAL, "melbm_download_raw_state_async: NULL argument");
+  if (int rc = check_raw_bytes(h, "melbm_download_raw_state_async", bytes)) return rc;
+  if (int rc = ensure_transfers(h)) return rc;
+  MELBM_CUDA(h, cudaEventRecord(h->ev_issue, h->stream));
+  MELBM_CUDA(h, cudaStreamWaitEvent(h->down_stream, h->ev_issue, 0));
+  MELBM_CUDA(h, cudaStreamWaitEvent(h->down_stream, h->ev_uploaded, 0));
+  MELBM_CUDA(h, cudaMemcpyAsync(dst, h->buf[h->cur], size_t(bytes), cudaMemcpyDefault,
+                                h->down_stream));
+  MELBM_CUDA(h, cudaEventRecord(h->ev_read[h->cur], h->down_stream));
+  return MELBM_OK;
+}
+
+int melbm_sync_transfers(melbm_t h) {
+  if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_sync_transfers: NULL handle");
+  if (!h->transfers) return MELBM_OK;
+  MELBM_CUDA(h, cudaStreamSynchronize(h->up_stream));
+  MELBM_CUDA(h, cudaStreamSynchronize(h->down_stream));
   return MELBM_OK;
 }
 
@@ -651,6 +752,7 @@ int melbm_solid_force(melbm_t h, int body, double* out) {
         (rc = dev_alloc(h, (void**)&h->sf_out, 6 * 8)))
       return rc;
   }
+  MELBM_CUDA(h, join_transfers(h));
   MELBM_CUDA(h, launch_solid_force(h->storage, h->nx, h->ny, h->nz, h->buf[h->cur], h->force,
                                    1.0f / h->tau, h->list_cell, h->list_word, h->L, h->grids,
                                    h->wall_model, h->mask, h->bodies, body, h->sf_partials,
@@ -674,6 +776,7 @@ int melbm_set_bits(melbm_t h, int bits_rho_u, int bits_S) {
   int rc = ensure_staging(h, N * 40);
   if (rc) return rc;
   float* st = static_cast<float*>(h->staging);
+  MELBM_CUDA(h, join_transfers(h));
   MELBM_CUDA(h, launch_get_moments(h->storage, h->N, h->buf[h->cur], st, st + N, st + 4 * N,
                                    h->grids, h->stream));
   h->grids = make_qgrids(bits_rho_u, bits_S);

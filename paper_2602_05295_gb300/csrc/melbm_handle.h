@@ -58,6 +58,13 @@ struct melbm_sim {
   int64_t mem_bytes = 0;
   bool poisoned = false;
   bool boundary_error = false;  // the last boundary setup failed: lists are empty
+  // Asynchronous raw-state transfers (created at their first use): an upload and a
+  // download stream, and the events that order them against the handle's stream.
+  bool transfers = false;
+  cudaStream_t up_stream = nullptr, down_stream = nullptr;
+  cudaEvent_t ev_issue = nullptr;               // the handle's stream when a transfer is issued
+  cudaEvent_t ev_uploaded = nullptr;            // the last upload has landed
+  cudaEvent_t ev_read[2] = {nullptr, nullptr};  // the last download of buffer k has been read
   std::string err;
   melbm::AdjointState* adj = nullptr;  // checkpoints of melbm_forward_checkpointed
 };
@@ -66,4 +73,7 @@ namespace melbm {
 // Launch one forward step in -> out with the handle's boundaries (used by the
 // adjoint's recomputation); t_out is the time index of the output state.
 cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out);
+// Make the handle's stream wait for every asynchronous raw-state transfer issued
+// so far (a no-op when none was).
+cudaError_t join_transfers(melbm_sim* h);
 }  // namespace melbm

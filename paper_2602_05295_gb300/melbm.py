@@ -69,6 +69,9 @@ def lib():
         "melbm_state_bytes": [P, ctypes.POINTER(I64)],
         "melbm_get_raw_state": [P, P, I64],
         "melbm_set_raw_state": [P, P, I64, I64],
+        "melbm_upload_raw_state_async": [P, P, I64, I64],
+        "melbm_download_raw_state_async": [P, P, I64],
+        "melbm_sync_transfers": [P],
         "melbm_forward_checkpointed": [P, P, I, I],
         "melbm_backward": [P, P, P, P],
         "melbm_q16_encode": [P, I, I, I, U32, U32, I, P, P],
@@ -208,6 +211,25 @@ class Simulator:
         nb = self.state_bytes()
         _check(lib().melbm_set_raw_state(self._h, _ptr(src, nb, torch.uint8), nb, int(time_index)),
                self._h)
+
+    def upload_raw_state_async(self, src, time_index):
+        """Make the packed state in ``src`` (pinned host uint8 for overlap) the
+        current state, without blocking; ``src`` must stay unchanged until
+        :meth:`sync_transfers`."""
+        nb = self.state_bytes()
+        _check(lib().melbm_upload_raw_state_async(self._h, _ptr(src, nb, torch.uint8), nb,
+                                                  int(time_index)), self._h)
+
+    def download_raw_state_async(self, dst):
+        """Copy the current packed state into ``dst`` without blocking; ``dst`` is
+        valid after :meth:`sync_transfers`."""
+        nb = self.state_bytes()
+        _check(lib().melbm_download_raw_state_async(self._h, _ptr(dst, nb, torch.uint8), nb),
+               self._h)
+        return dst
+
+    def sync_transfers(self):
+        _check(lib().melbm_sync_transfers(self._h), self._h)
 
     # -------------------------------------------------------------- boundaries
     def set_solid(self, mask):
