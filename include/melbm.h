@@ -171,14 +171,17 @@ MELBM_API int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int
  * memory while the GPU computes (with pageable host memory they still work but
  * do not overlap).  They run on two streams of the handle's own, in issue order
  * with the work already enqueued on the handle's stream, and return at once; the
- * caller must neither change src nor read dst before melbm_sync_transfers.
+ * caller must neither change src nor read dst before melbm_sync_transfers.  The
+ * first upload allocates a third state buffer (melbm_state_bytes more device
+ * memory, held until melbm_destroy).
  *   melbm_upload_raw_state_async: the state src (bytes as for set_raw_state)
  *     becomes the current state with time index time_index.  It lands in the
- *     ping-pong buffer that does not hold the current state, so a download of
- *     that state may still be in flight.
+ *     third buffer, which then replaces the buffer of the current state, so it
+ *     runs beside a step still in flight and beside a download of that step's
+ *     result.
  *   melbm_download_raw_state_async: copies the current state into dst; a
  *     following melbm_step(h, 1) runs while it does (it reads that buffer and
- *     writes the other one).
+ *     writes another one).
  *   melbm_sync_transfers: blocks until every transfer issued has completed.
  * melbm_step waits for the upload it steps from and for the downloads still
  * reading a buffer it overwrites; every other call that touches the state

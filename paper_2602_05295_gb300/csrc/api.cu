@@ -232,25 +232,37 @@ void release_transfers(melbm_t h) {
   if (!h->transfers) return;
   if (h->up_stream) cudaStreamSynchronize(h->up_stream);
   if (h->down_stream) cudaStreamSynchronize(h->down_stream);
-  cudaEvent_t evs[4] = {h->ev_issue, h->ev_uploaded, h->ev_read[0], h->ev_read[1]};
-  for (cudaEvent_t ev : evs)
-    if (ev) cudaEventDestroy(ev);
+  cudaEvent_t* evs[8] = {&h->ev_issue,      &h->ev_uploaded,   &h->ev_read[0],
+                         &h->ev_read[1],    &h->ev_read[2],    &h->ev_retired[0],
+                         &h->ev_retired[1], &h->ev_retired[2]};
+  for (cudaEvent_t* ev : evs) {
+    if (*ev) cudaEventDestroy(*ev);
+    *ev = nullptr;
+  }
   if (h->up_stream) cudaStreamDestroy(h->up_stream);
   if (h->down_stream) cudaStreamDestroy(h->down_stream);
   h->up_stream = h->down_stream = nullptr;
-  h->ev_issue = h->ev_uploaded = h->ev_read[0] = h->ev_read[1] = nullptr;
+  dev_free(h, h->spare, state_bytes(h));
+  h->spare = nullptr;
   h->transfers = false;
 }
 
-// Streams and events of the asynchronous raw-state transfers, created once.
+// Streams, events and the spare buffer of the asynchronous raw-state transfers,
+// created once (the spare holds one state: 20 or 40 B per cell).
 int ensure_transfers(melbm_t h) {
   if (h->transfers) return MELBM_OK;
+  h->transfers = true;
+  if (int rc = dev_alloc(h, &h->spare, state_bytes(h))) {
+    release_transfers(h);
+    return rc;
+  }
   cudaError_t e = cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->down_stream, cudaStreamNonBlocking);
-  cudaEvent_t* evs[4] = {&h->ev_issue, &h->ev_uploaded, &h->ev_read[0], &h->ev_read[1]};
-  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+  cudaEvent_t* evs[8] = {&h->ev_issue,      &h->ev_uploaded,   &h->ev_read[0],
+                         &h->ev_read[1],    &h->ev_read[2],    &h->ev_retired[0],
+                         &h->ev_retired[1], &h->ev_retired[2]};
+  for (int k = 0; k < 8 && e == cudaSuccess; ++k)
     e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
-  h->transfers = true;
   if (e != cudaSuccess) {
     cudaGetLastError();
     release_transfers(h);
@@ -291,8 +303,7 @@ cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out
 cudaError_t join_transfers(melbm_sim* h) {
   if (!h->transfers) return cudaSuccess;
   cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_uploaded, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_read[0], 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_read[1], 0);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(h->stream, h->ev_read[k], 0);
   return e;
 }
 }  // namespace melbm
@@ -538,7 +549,7 @@ int melbm_step(melbm_t h, int n) {
     if (n > 1) {
       MELBM_CUDA(h, join_transfers(h));
     } else {
-      MELBM_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_read[1 - h->cur], 0));
+      MELBM_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_read[h->buf_id[1 - h->cur]], 0));
     }
   }
   for (int s = 0; s < n; ++s) {
@@ -619,24 +630,30 @@ int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int64_t time_
   return MELBM_OK;
 }
 
-// The upload lands in the buffer that does not hold the current state, after the
-// work already issued on the handle's stream (a step may still read it) and after
-// any download still reading it; that buffer then becomes the current state.  The
-// download reads the current state after the work already issued and after the
-// upload that produced it.  Neither blocks the host.
+// The upload lands in the spare buffer, after the work that was issued while the
+// spare was last in a slot and after any download still reading it; the spare then
+// takes the current state's slot and the buffer it replaces retires to the spare
+// (once the work issued so far has run: a step in flight may still write it, a
+// download read it).  So an upload runs beside the step in flight and beside the
+// download of its result.  The download reads the current state after the work
+// already issued and after the upload that produced it.  Neither blocks the host.
 int melbm_upload_raw_state_async(melbm_t h, const void* src, int64_t bytes, int64_t time_index) {
   if (!h || !src) return fail(h, MELBM_EINVAL, "melbm_upload_raw_state_async: NULL argument");
   if (int rc = check_raw_bytes(h, "melbm_upload_raw_state_async", bytes)) return rc;
   if (time_index < 0)
     return fail(h, MELBM_EINVAL, "melbm_upload_raw_state_async: negative time index");
   if (int rc = ensure_transfers(h)) return rc;
-  const int b = 1 - h->cur;
-  MELBM_CUDA(h, cudaEventRecord(h->ev_issue, h->stream));
-  MELBM_CUDA(h, cudaStreamWaitEvent(h->up_stream, h->ev_issue, 0));
-  MELBM_CUDA(h, cudaStreamWaitEvent(h->up_stream, h->ev_read[b], 0));
-  MELBM_CUDA(h, cudaMemcpyAsync(h->buf[b], src, size_t(bytes), cudaMemcpyDefault, h->up_stream));
+  const int s = h->spare_id, c = h->buf_id[h->cur];
+  MELBM_CUDA(h, cudaStreamWaitEvent(h->up_stream, h->ev_retired[s], 0));
+  MELBM_CUDA(h, cudaStreamWaitEvent(h->up_stream, h->ev_read[s], 0));
+  MELBM_CUDA(h, cudaMemcpyAsync(h->spare, src, size_t(bytes), cudaMemcpyDefault, h->up_stream));
   MELBM_CUDA(h, cudaEventRecord(h->ev_uploaded, h->up_stream));
-  h->cur = b;
+  MELBM_CUDA(h, cudaEventRecord(h->ev_retired[c], h->stream));
+  void* p = h->buf[h->cur];
+  h->buf[h->cur] = h->spare;
+  h->buf_id[h->cur] = s;
+  h->spare = p;
+  h->spare_id = c;
   h->t = time_index;
   h->poisoned = false;
   return MELBM_OK;
@@ -651,7 +668,7 @@ int melbm_download_raw_state_async(melbm_t h, void* dst, int64_t bytes) {
   MELBM_CUDA(h, cudaStreamWaitEvent(h->down_stream, h->ev_uploaded, 0));
   MELBM_CUDA(h, cudaMemcpyAsync(dst, h->buf[h->cur], size_t(bytes), cudaMemcpyDefault,
                                 h->down_stream));
-  MELBM_CUDA(h, cudaEventRecord(h->ev_read[h->cur], h->down_stream));
+  MELBM_CUDA(h, cudaEventRecord(h->ev_read[h->buf_id[h->cur]], h->down_stream));
   return MELBM_OK;
 }
 

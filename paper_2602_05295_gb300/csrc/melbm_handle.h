@@ -59,12 +59,19 @@ struct melbm_sim {
   bool poisoned = false;
   bool boundary_error = false;  // the last boundary setup failed: lists are empty
   // Asynchronous raw-state transfers (created at their first use): an upload and a
-  // download stream, and the events that order them against the handle's stream.
+  // download stream, a third state buffer (the spare) that uploads land in, and the
+  // events that order the transfers against the handle's stream.  The three state
+  // buffers are numbered 0, 1 (the initial pair) and 2 (the spare); buf_id[k] is
+  // the number of the buffer in slot buf[k], spare_id that of the spare.
   bool transfers = false;
   cudaStream_t up_stream = nullptr, down_stream = nullptr;
-  cudaEvent_t ev_issue = nullptr;               // the handle's stream when a transfer is issued
-  cudaEvent_t ev_uploaded = nullptr;            // the last upload has landed
-  cudaEvent_t ev_read[2] = {nullptr, nullptr};  // the last download of buffer k has been read
+  void* spare = nullptr;
+  int buf_id[2] = {0, 1};
+  int spare_id = 2;
+  cudaEvent_t ev_issue = nullptr;        // the handle's stream when a download is issued
+  cudaEvent_t ev_uploaded = nullptr;     // the last upload has landed
+  cudaEvent_t ev_read[3] = {};           // the last download of buffer k has read it
+  cudaEvent_t ev_retired[3] = {};        // the work issued while buffer k was in a slot
   std::string err;
   melbm::AdjointState* adj = nullptr;  // checkpoints of melbm_forward_checkpointed
 };

@@ -143,3 +143,70 @@ def test_upload_then_blocking_reads_and_refusals(M):
             mixed._h, ctypes.c_void_p(buf.data_ptr()), buf.numel()), mixed._h)
     mixed.sync_transfers()  # no transfers were issued: a no-op
     mixed.close()
+
+
+@pytest.mark.parametrize("seed", [7, 11])
+def test_random_interleavings_match_blocking(M, seed):
+    """A seeded random sequence of uploads (including back to back), steps of one
+    and two, downloads and reductions gives the same states and sums through the
+    asynchronous calls as through the blocking ones."""
+    import random
+    sim = make(M, "q16", True)
+    ins = inputs(sim, 3)
+    nb = sim.state_bytes()
+    rng = random.Random(seed)
+    ops = [rng.choice(["up", "up", "step1", "step1", "step2", "down", "down", "reduce"])
+           for _ in range(40)]
+
+    def run(asynchronous):
+        sim.set_raw_state(*ins[0])
+        outs, k = [], 0
+        for op in ops:
+            if op == "up":
+                h, t = ins[k % len(ins)]
+                k += 1
+                if asynchronous:
+                    sim.upload_raw_state_async(h, t)
+                else:
+                    sim.set_raw_state(h, t)
+            elif op == "step1":
+                sim.step(1)
+            elif op == "step2":
+                sim.step(2)
+            elif op == "down":
+                o = pinned(nb)
+                if asynchronous:
+                    sim.download_raw_state_async(o)
+                else:
+                    sim.get_raw_state(o)
+                outs.append(o)
+            else:
+                outs.append(sim.reduce())
+        o = pinned(nb)
+        if asynchronous:
+            sim.download_raw_state_async(o)
+        else:
+            sim.get_raw_state(o)
+        outs.append(o)
+        sim.sync_transfers()
+        return outs, sim.time_index
+
+    ref, t_ref = run(False)
+    got, t_got = run(True)
+    assert t_ref == t_got and len(ref) == len(got)
+    for i, (r, g) in enumerate(zip(ref, got)):
+        if isinstance(r, tuple):
+            assert r == g, (i, r, g)
+        else:
+            assert torch.equal(r, g), f"output {i} differs"
+    sim.close()
+
+
+def test_spare_buffer_is_accounted_and_freed(M):
+    sim = make(M, "f32", False)
+    before = sim.memory_bytes()
+    (h0, t0), = inputs(sim, 1)
+    sim.upload_raw_state_async(h0, t0)
+    sim.sync_transfers()
+    assert sim.memory_bytes() == before + sim.state_bytes()
+    sim.close()
