@@ -96,7 +96,8 @@ MELBM_API int melbm_create(int nx, int ny, int nz, int lattice, float tau, int s
 MELBM_API int melbm_destroy(melbm_t h);
 
 /* Stream on which all later work of the handle is enqueued (a cudaStream_t;
- * NULL = the legacy default stream). */
+ * NULL = the legacy default stream).  Work already enqueued on the previous
+ * stream is ordered before it (the new stream waits for it on the device). */
 MELBM_API int melbm_set_stream(melbm_t h, void* cuda_stream);
 
 /* Seed of the dither generator (Sec. 5.4 dithering), default 0.  The dither of

@@ -388,7 +388,17 @@ int melbm_destroy(melbm_t h) {
 
 int melbm_set_stream(melbm_t h, void* s) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_stream: NULL handle");
-  h->stream = static_cast<cudaStream_t>(s);
+  cudaStream_t next = static_cast<cudaStream_t>(s);
+  if (next != h->stream) {
+    // the new stream waits for the work already enqueued on the old one
+    cudaEvent_t ev;
+    MELBM_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(next, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "melbm_set_stream");
+  }
+  h->stream = next;
   return MELBM_OK;
 }
 

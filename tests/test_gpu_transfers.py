@@ -210,3 +210,29 @@ def test_spare_buffer_is_accounted_and_freed(M):
     sim.sync_transfers()
     assert sim.memory_bytes() == before + sim.state_bytes()
     sim.close()
+
+
+def test_set_stream_orders_pending_work(M):
+    """Work enqueued on the previous stream is ordered before work on the new one:
+    a read issued right after switching streams sees every pending step."""
+    shape = (128, 128, 128)
+    N = 128 ** 3
+    g = np.random.default_rng(5)
+    u = torch.from_numpy((0.03 * g.standard_normal((3, N))).astype(np.float32)).cuda()
+    rho = torch.ones(N, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    ref_sim = M.Simulator(shape, 0.55, "q16", seed=2, stream=s1)
+    ref_sim.set_state(rho, u)
+    torch.cuda.synchronize()
+    ref_sim.step(60)
+    ref = ref_sim.get_raw_state(pinned(ref_sim.state_bytes()))
+    ref_sim.close()
+    sim = M.Simulator(shape, 0.55, "q16", seed=2, stream=s1)
+    sim.set_state(rho, u)
+    torch.cuda.synchronize()
+    sim.step(60)  # still running on s1 when the stream changes
+    M._check(M.lib().melbm_set_stream(sim._h, ctypes.c_void_p(s2.cuda_stream)), sim._h)
+    got = sim.get_raw_state(pinned(sim.state_bytes()))
+    assert torch.equal(ref, got)
+    sim.close()
