@@ -343,6 +343,20 @@ def test_linear_stability_within_paper_velocity_bound(orc):
             assert rad <= 1 + 1e-12, (tau, U, rad)
 
 
+def test_linear_stability_at_the_papers_viscosities_and_diagonal_velocities(orc):
+    """The von Neumann check of Sec. 5.3 (numerical spectral analysis) at its
+    viscosities nu = 1e-3 and 1e-4 and its diagonal background flows u = (a, a):
+    max |lambda(k)| <= 1 over k = (kx, ky, 0) in [0, pi]^2 for a = 0, 0.1, 0.2."""
+    ks = np.linspace(0, np.pi, 13)
+    kgrid = np.array([[a, b, 0.0] for a in ks for b in ks])
+    for nu in (1e-3, 1e-4):
+        tau = 0.5 + nu / CS2
+        for a in (0.0, 0.1, 0.2):
+            G = orc.amplification_matrix(1.0, [a, a, 0.0], tau, kgrid)
+            rad = np.abs(np.linalg.eigvals(G)).max()
+            assert rad <= 1 + 1e-12, (nu, a, rad)
+
+
 # ------------------------------------------------------------------ P7 adjoint
 def _bc_case(orc, rng):
     shape = (7, 5, 4)
