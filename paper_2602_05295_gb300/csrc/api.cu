@@ -132,10 +132,10 @@ int ensure_staging(melbm_t h, size_t bytes) {
 }
 
 void free_list(melbm_t h) {
-  dev_free(h, h->src_table, size_t(h->L) * 27 * 4);
+  dev_free(h, h->lidx, h->lidx ? size_t(h->N) * 4 : 0);
   dev_free(h, h->src_cells, size_t(h->S) * 4);
-  dev_free(h, h->src_pop, size_t(h->S) * 27 * 4);
-  h->src_table = h->src_cells = nullptr;
+  dev_free(h, h->src_pop, size_t(h->L) * 27 * 4);
+  h->lidx = h->src_cells = nullptr;
   h->src_pop = nullptr;
   h->S = 0;
   dev_free(h, h->list_cell, size_t(h->L) * 4);
@@ -145,12 +145,12 @@ void free_list(melbm_t h) {
 }
 
 // The source set of the boundary update (after the list): the cells whose
-// post-collision state a listed cell reads, compacted in ascending order, and
-// the 27 source slots of every listed cell.  Temporaries: mark[N], slot_of[N].
+// post-collision state a listed cell reads, compacted in ascending order, the
+// list index of every FLUID_BOUNDARY cell, and the [27][L] table that phase A
+// fills every step.  Temporary: mark[N].
 int build_sources(melbm_t h) {
   const size_t N = size_t(h->N);
   uint8_t* mark = nullptr;
-  uint32_t* slot_of = nullptr;
   int rc = dev_alloc(h, (void**)&mark, N);
   if (rc) return rc;
   cudaError_t e = launch_source_setup_mark(h->nx, h->ny, h->nz, h->list_cell, h->list_word, h->L,
@@ -163,20 +163,17 @@ int build_sources(melbm_t h) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess && S) {
     h->S = S;  // before the allocations, so that free_list accounts for them
-    if ((rc = dev_alloc(h, (void**)&slot_of, N * 4)) ||
+    if ((rc = dev_alloc(h, (void**)&h->lidx, N * 4)) ||
         (rc = dev_alloc(h, (void**)&h->src_cells, size_t(S) * 4)) ||
-        (rc = dev_alloc(h, (void**)&h->src_table, size_t(h->L) * 27 * 4)) ||
-        (rc = dev_alloc(h, (void**)&h->src_pop, size_t(S) * 27 * 4))) {
+        (rc = dev_alloc(h, (void**)&h->src_pop, size_t(h->L) * 27 * 4))) {
       dev_free(h, mark, N);
-      dev_free(h, slot_of, slot_of ? N * 4 : 0);
       return rc;
     }
     e = launch_source_setup_fill(h->nx, h->ny, h->nz, h->list_cell, h->list_word, h->L, mark,
-                                 h->cl_offsets, h->src_cells, slot_of, h->src_table, h->stream);
+                                 h->cl_offsets, h->src_cells, h->lidx, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
   dev_free(h, mark, N);
-  if (slot_of) dev_free(h, slot_of, N * 4);
   if (e != cudaSuccess) return cuda_fail(h, e, "build_sources");
   return MELBM_OK;
 }
@@ -292,7 +289,7 @@ cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out
                          h->seed, h->grids, h->stream);
   if (e == cudaSuccess && h->L)
     e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
-                        h->list_word, h->L, h->src_cells, h->S, h->src_table, h->src_pop,
+                        h->list_word, h->L, h->src_cells, h->S, h->lidx, h->src_pop,
                         h->inflow, t_out, h->seed, h->grids, h->wall_model, h->mask, h->bodies,
                         h->lattice, h->stream);
   if (e == cudaSuccess && h->outflow_on && h->type)

@@ -5,9 +5,9 @@
 //     solid (in place of the paper's additive triangle correction, which needs a
 //     mesh; recomputing from the input gives the post-streaming moments directly,
 //     with no atomics and no second rounding of the 16-bit state).  The
-//     post-collision populations of every source were evaluated once by phase
-//     A (sources.cu); this kernel gathers, per direction, the one it needs
-//     through the cell's 27 source slots.
+//     post-collision populations that the listed cells read were evaluated
+//     once per source by phase A (sources.cu) and pushed into each cell's
+//     column of a [27][L] table, which this kernel reads contiguously.
 //     With the moment-based wall model (Sec. 3.2, solid coupling) a solid link
 //     instead receives the Hermite population of (rho, u^p, S^p) at the link's
 //     halfway point p, u^p the rigid velocity of the body the solid cell
@@ -31,9 +31,7 @@ struct BoundaryParams {
   const uint32_t* cells;
   const uint32_t* words;
   int64_t count;
-  const uint32_t* table;  // [27][count] source slots
-  const float* pop;       // [27][S] post-collision populations f+_i / w_i - 1 of the sources
-  int64_t S;
+  const float* pop;       // [27][count]: f_i / w_i - 1 streamed into each listed cell
   int wall_model;          // 0 halfway bounce-back, 1 moment-based reconstruction
   const uint8_t* mask;     // body id of every cell (wall model 1)
   const float* bodies;     // 256 x 9: V, Om, r0 of each body (wall model 1)
@@ -110,10 +108,8 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
     const bool solid = (word >> i) & 1u;
     if (MOVING && solid) continue;  // the moving-wall links follow below
     // f_i / w_i - 1: population i pulled from x - c_i, or, for a solid link,
-    // population opp(i) = 26 - i of x itself (bounce-back; the slot then holds x)
-    const uint32_t slot = __ldg(P.table + int64_t(i) * P.count + k);
-    const int j = solid ? 26 - i : i;
-    accumulate(cx, cy, cz, __ldg(P.pop + int64_t(j) * P.S + slot));
+    // population opp(i) = 26 - i of x itself (bounce-back), as phase A wrote it
+    accumulate(cx, cy, cz, __ldg(P.pop + int64_t(i) * P.count + k));
   }
   if constexpr (MOVING) {
     // the population of the moving wall for each solid link, each thread over
@@ -140,13 +136,13 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
 cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
                             const float* force, float omega, const uint32_t* cells,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
-                            int64_t S, const uint32_t* table, float* pop, const float inflow[4],
+                            int64_t S, const uint32_t* lidx, float* pop, const float inflow[4],
                             uint32_t t_out, uint32_t seed, const QGrids& q, int wall_model,
                             const uint8_t* mask, const float* bodies, int lattice,
                             cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  cudaError_t e = launch_source_collide(storage, size_t(nx) * ny * nz, in, force, omega, src_cells,
-                                        S, pop, q, lattice, st);
+  cudaError_t e = launch_source_collide(storage, nx, ny, nz, in, force, omega, src_cells, S, lidx,
+                                        words, count, pop, q, lattice, st);
   if (e != cudaSuccess) return e;
   BoundaryParams p;
   p.nx = nx;
@@ -159,9 +155,7 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
   p.cells = cells;
   p.words = words;
   p.count = count;
-  p.table = table;
   p.pop = pop;
-  p.S = S;
   p.in_rho = inflow[0];
   p.in_ux = inflow[1];
   p.in_uy = inflow[2];

@@ -30,11 +30,12 @@ struct melbm_sim {
   uint32_t* list_cell = nullptr;
   uint32_t* list_word = nullptr;
   int64_t L = 0;
-  // source set of the boundary update: S cells (ascending), 27 slots per listed
-  // cell ([27][L]) and the per-step post-collision populations ([27][S])
+  // source set of the boundary update: S cells (ascending), the list index of
+  // every FLUID_BOUNDARY cell (lidx[N], 0xFFFFFFFF elsewhere) and the per-step
+  // populations streamed into each listed cell ([27][L], written by phase A)
   uint32_t* src_cells = nullptr;
   int64_t S = 0;
-  uint32_t* src_table = nullptr;
+  uint32_t* lidx = nullptr;
   float* src_pop = nullptr;
   uint32_t* cl_counts = nullptr;
   uint32_t* cl_offsets = nullptr;

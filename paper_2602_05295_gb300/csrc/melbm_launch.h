@@ -77,7 +77,7 @@ cudaError_t launch_mixed_get_moments(int64_t N, const float* p, float* rho, floa
 cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
                             const float* force, float omega, const uint32_t* cells,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
-                            int64_t S, const uint32_t* table, float* pop, const float inflow[4],
+                            int64_t S, const uint32_t* lidx, float* pop, const float inflow[4],
                             uint32_t t_out, uint32_t seed, const QGrids& q, int wall_model,
                             const uint8_t* mask, const float* bodies, int lattice, cudaStream_t st);
 
@@ -94,7 +94,8 @@ cudaError_t launch_solid_force(int storage, int nx, int ny, int nz, const void* 
 // Source set of the boundary update (sources.cu).  Setup, after the list is
 // built: mark the sources (mark[N] bytes) and count them per block of
 // source_flag_blocks(N); after an exclusive scan of the counts, fill src_cells
-// (ascending), slot_of[N] and table[27][L].  Per step: phase A.
+// (ascending) and lidx[N] (the list index of each FLUID_BOUNDARY cell, else
+// 0xFFFFFFFF).  Per step: phase A, which writes pop[27][L].
 int64_t source_flag_blocks(int64_t N);
 cudaError_t launch_source_setup_mark(int nx, int ny, int nz, const uint32_t* cells,
                                      const uint32_t* words, int64_t L, uint8_t* mark,
@@ -102,10 +103,12 @@ cudaError_t launch_source_setup_mark(int nx, int ny, int nz, const uint32_t* cel
 cudaError_t launch_source_setup_fill(int nx, int ny, int nz, const uint32_t* cells,
                                      const uint32_t* words, int64_t L, const uint8_t* mark,
                                      const uint32_t* block_offsets, uint32_t* src_cells,
-                                     uint32_t* slot_of, uint32_t* table, cudaStream_t st);
-cudaError_t launch_source_collide(int storage, size_t N, const void* in, const float* force,
-                                  float omega, const uint32_t* src_cells, int64_t S, float* pop,
-                                  const QGrids& q, int lattice, cudaStream_t st);
+                                     uint32_t* lidx, cudaStream_t st);
+cudaError_t launch_source_collide(int storage, int nx, int ny, int nz, const void* in,
+                                  const float* force, float omega, const uint32_t* src_cells,
+                                  int64_t S, const uint32_t* lidx, const uint32_t* words,
+                                  int64_t L, float* pop, const QGrids& q, int lattice,
+                                  cudaStream_t st);
 
 // Outflow copy on the plane x = nx-1 (cells typed OUTFLOW), in place on buf.
 cudaError_t launch_outflow(int storage, int nx, int ny, int nz, void* buf, const uint8_t* type,
