@@ -70,10 +70,11 @@ cudaError_t launch_mixed_set_state(int64_t N, const float* rho, const float* u, 
 cudaError_t launch_mixed_get_moments(int64_t N, const float* p, float* rho, float* u, float* S,
                                      cudaStream_t st);
 
-// Boundary update over the list: phase A collides the S source cells and keeps
-// their 27 populations in pop[27][S] (sources.cu), then the boundary kernel
-// recomputes every listed cell (bounce-back through its 27 source slots in
-// table[27][count], inflow reset), in -> out.
+// Boundary update over the list: phase A collides the S source cells and pushes
+// the populations the listed cells read into pop[27][count] (sources.cu; lidx is
+// the list index of every FLUID_BOUNDARY cell), then the boundary kernel
+// recomputes every listed cell from its 27 entries (halfway bounce-back included,
+// inflow reset), in -> out.
 cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
                             const float* force, float omega, const uint32_t* cells,
                             const uint32_t* words, int64_t count, const uint32_t* src_cells,
