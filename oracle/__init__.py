@@ -70,6 +70,7 @@ def lib():
             for name in ("orc_step_f64", "orc_step_c128"):
                 getattr(L, name).argtypes = [I, I, I, D, P, P, P, P, I, P]
             L.orc_step_cells_f64.argtypes = [I, I, I, D, P, P, P, P, P, I64, P]
+            L.orc_step_planted_f64.argtypes = [I, I, I, D, P, P, P, P, I, P]
             L.orc_step_vjp_f64.argtypes = [I, I, I, D, P, P, P, P, P, P]
             L.orc_reduce.argtypes = [I64, P, P, P, P]
             L.orc_dither.argtypes = [U32, U32, U32, U32, U32, P]
@@ -203,6 +204,21 @@ def step(m, shape, tau, F=None, typ=None, inflow=None, n=1, literal_xyz=False, w
                                     wall.model, _p(wall.body), _p(wall.table), _p(out))
         cur, out = out, cur
     return cur
+
+
+PLANT_OUT_FROM_OLD, PLANT_OUT_FROM_SELF, PLANT_IN_S_ZERO = 1, 2, 3
+
+
+def step_planted(m, shape, tau, planted, F=None, typ=None, inflow=None):
+    """One D3Q27 step with a deliberately wrong special-cell rule (``PLANT_*``),
+    for the tests that show their pins reject it."""
+    nx, ny, nz = shape
+    cur = _f64(m)
+    out = np.empty_like(cur)
+    ta = None if typ is None else np.ascontiguousarray(typ, np.uint8)
+    lib().orc_step_planted_f64(nx, ny, nz, float(tau), _p(cur), _p(_f64(F)), _p(ta),
+                               _p(_inflow_arr(inflow)), int(planted), _p(out))
+    return out
 
 
 def step19(m, shape, tau, F=None, n=1, typ=None, inflow=None, wall=None):

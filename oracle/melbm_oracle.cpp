@@ -293,11 +293,19 @@ Mom<T> inflow_state(const double* inflow) {
   return o;
 }
 
+// Deliberately wrong special-cell rules, selectable only through
+// orc_step_planted_f64 so that the tests can show that their pins reject them:
+//   PLANT_OUT_FROM_OLD   outflow copies the pre-step state of (nx-2, y, z);
+//   PLANT_OUT_FROM_SELF  outflow copies x = nx-1 itself (no copy at all);
+//   PLANT_IN_S_ZERO      inflow resets S to 0 instead of u_in u_in.
+enum { PLANT_NONE = 0, PLANT_OUT_FROM_OLD = 1, PLANT_OUT_FROM_SELF = 2, PLANT_IN_S_ZERO = 3 };
+
 // One full step over the grid.  Pass 1 collides every non-solid cell; pass 2
 // pulls and re-forms the moments; pass 3 applies the zero-gradient outflow copy.
 template <class T>
 void step_grid(const Grid& g, double tau, const T* m, const T* F, const uint8_t* type,
-               const double* inflow, T* out, int literal_xyz, const WallSpec* w = nullptr) {
+               const double* inflow, T* out, int literal_xyz, const WallSpec* w = nullptr,
+               int planted = PLANT_NONE) {
   const int64_t N = g.N();
   std::vector<Mom<T>> mp(N);
 #pragma omp parallel for schedule(static)
@@ -313,17 +321,20 @@ void step_grid(const Grid& g, double tau, const T* m, const T* F, const uint8_t*
     if (t == SOLID) {
       store(out, N, n, load(m, N, n));  // solid cells keep their value
     } else if (t == INFLOW) {
-      store(out, N, n, inflow_state<T>(inflow));
+      Mom<T> v = inflow_state<T>(inflow);
+      if (planted == PLANT_IN_S_ZERO)
+        for (int k = 0; k < 6; ++k) v.S[k] = T(0.0);
+      store(out, N, n, v);
     } else {
       store(out, N, n, pull_and_moments(g, mp, type, F, n, literal_xyz, w));
     }
   }
-  if (type) {
+  if (type && planted != PLANT_OUT_FROM_SELF) {
 #pragma omp parallel for schedule(static)
     for (int64_t n = 0; n < N; ++n) {
       if (type[n] != OUTFLOW) continue;
       const int64_t s = n - 1;  // (nx-2, y, z): the outflow plane is x = nx-1
-      store(out, N, n, load(out, N, s));
+      store(out, N, n, load(planted == PLANT_OUT_FROM_OLD ? m : out, N, s));
     }
   }
 }
@@ -810,6 +821,13 @@ int64_t orc_classify(int nx, int ny, int nz, const uint8_t* mask, int inflow, in
 void orc_step_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
                   const uint8_t* type, const double* inflow, int literal_xyz, double* out) {
   step_grid<double>(Grid{nx, ny, nz}, tau, m, F, type, inflow, out, literal_xyz);
+}
+
+// The same step with one of the PLANT_* mistakes of the special-cell rules (test
+// ablation only; planted = 0 is orc_step_f64).
+void orc_step_planted_f64(int nx, int ny, int nz, double tau, const double* m, const double* F,
+                          const uint8_t* type, const double* inflow, int planted, double* out) {
+  step_grid<double>(Grid{nx, ny, nz}, tau, m, F, type, inflow, out, 0, nullptr, planted);
 }
 
 // One D3Q19 step (public state, component-major 10 x N; type and inflow as for

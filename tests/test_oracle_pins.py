@@ -297,6 +297,68 @@ def test_poiseuille_profile_with_bounce_back(orc):
     assert np.abs(m[2:4][:, fl]).max() < 1e-12
 
 
+# ------------------------------------------------------------------ special cells (configs 3-4)
+def _special_cell_violations(orc, m, out, typ, inflow, nx):
+    """The special-cell rules of the channel configurations (reading C9 of the
+    inflow / outflow / wall set-up): INFLOW cells hold exactly the inflow
+    equilibrium (rho_in, u_in, u_in u_in); OUTFLOW cells (x = nx-1) hold the NEW
+    state of (nx-2, y, z); SOLID cells keep their old value.  Returns the names
+    of the rules the pair (m -> out) breaks."""
+    bad = []
+    rho_in, u_in = inflow[0], np.asarray(inflow[1:4], np.float64)
+    want_in = np.concatenate([[rho_in], u_in, [u_in[a] * u_in[b] for a, b in PAIRS]])
+    i_in = np.nonzero(typ == orc.INFLOW)[0]
+    if not (len(i_in) and np.array_equal(out[:, i_in], np.repeat(want_in[:, None], len(i_in), 1))):
+        bad.append("inflow")
+    i_out = np.nonzero(typ == orc.OUTFLOW)[0]
+    if not (len(i_out) and np.all(i_out % nx == nx - 1)
+            and np.array_equal(out[:, i_out], out[:, i_out - 1])):
+        bad.append("outflow")
+    sol = typ == orc.SOLID
+    if not np.array_equal(out[:, sol], m[:, sol]):
+        bad.append("solid")
+    return bad
+
+
+def _special_cell_case(orc):
+    shape = (9, 6, 5)
+    rng = np.random.default_rng(27)
+    mask = W.channel_walls(shape)
+    mask[2, 3, 6] = 1  # an obstacle next to the plane x = nx-2
+    typ, _, _, _ = orc.classify(mask, True, True)
+    m = random_state(shape, rng)
+    F = 1e-4 * rng.standard_normal((3, m.shape[1]))
+    return shape, typ, m, F, [1.01, 0.03, -0.01, 0.02]
+
+
+def test_inflow_outflow_solid_cells(orc):
+    """One D3Q27 step of a walled channel with inflow, outflow and an obstacle:
+    every special cell follows its rule, and the plane x = nx-2 does change in the
+    step (so copying its pre-step state would be seen)."""
+    shape, typ, m, F, inflow = _special_cell_case(orc)
+    out = orc.step(m, shape, 0.6, F=F, typ=typ, inflow=inflow)
+    assert _special_cell_violations(orc, m, out, typ, inflow, shape[0]) == []
+    i_out = np.nonzero(typ == orc.OUTFLOW)[0]
+    assert np.abs(out[:, i_out - 1] - m[:, i_out - 1]).min(axis=0).max() > 0
+    assert np.abs(out[:, i_out - 1] - m[:, i_out - 1]).max() > 1e-4
+    # the x = nx-2 plane is an ordinary update: the sampled-cell step (which has
+    # no outflow pass) gives the same values there
+    got = orc.step_cells(m, shape, 0.6, i_out - 1, F=F, typ=typ, inflow=inflow)
+    assert np.abs(got - out[:, i_out - 1]).max() < 1e-15
+
+
+@pytest.mark.parametrize("planted,rule", [(1, "outflow"), (2, "outflow"), (3, "inflow")])
+def test_planted_special_cell_mistakes_are_caught(orc, planted, rule):
+    """Plausible slips in the special-cell rules -- the outflow copying the
+    pre-step state of x = nx-2 (1) or no copy, i.e. x = nx-1 itself (2), the
+    inflow resetting S to 0 (3) -- each break the pin above."""
+    shape, typ, m, F, inflow = _special_cell_case(orc)
+    good = orc.step_planted(m, shape, 0.6, 0, F=F, typ=typ, inflow=inflow)
+    assert np.array_equal(good, orc.step(m, shape, 0.6, F=F, typ=typ, inflow=inflow))
+    bad = orc.step_planted(m, shape, 0.6, planted, F=F, typ=typ, inflow=inflow)
+    assert _special_cell_violations(orc, m, bad, typ, inflow, shape[0]) == [rule]
+
+
 # ------------------------------------------------------------------ P6 linear modes
 def test_linear_modes_k0_and_hydrodynamic_limits(orc):
     tau = 0.6
