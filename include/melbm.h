@@ -128,15 +128,36 @@ MELBM_API int melbm_get_moments(melbm_t h, float* rho, float* u, float* S);
 MELBM_API int melbm_set_solid(melbm_t h, const uint8_t* mask);
 
 /* Equilibrium inflow on face 0 (x = 0): INFLOW cells are reset every step to
- * (rho, u, u u).  Re-classifies.  Only face 0 is supported. */
+ * (rho, u, u u), i.e. the Hermite equilibrium of Sec. 3.2 (S = u u) with the given
+ * density and velocity.  The paper's flow-past-solid scenes (Sec. 6.4 and Table 1)
+ * drive the flow by an inlet without stating its form; this Dirichlet-equilibrium reading
+ * is the one the oracle pins.  Typed and listed by the classification kernel
+ * (INFLOW outranks OUTFLOW and FLUID_BOUNDARY); the boundary kernel applies the
+ * reset after the fluid kernel (split design of Sec. 4.2).  Re-classifies
+ * (synchronises to read the list length).  Only face 0 is supported: another
+ * face returns MELBM_EINVAL; a failed re-classification leaves the handle
+ * refusing to step (MELBM_ESTATE) as for melbm_set_solid. */
 MELBM_API int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float uz);
 
-/* Zero-gradient outflow on face 1 (x = nx-1): OUTFLOW cells copy the stored
- * state of (nx-2, y, z) after each step.  Re-classifies.  Only face 1. */
+/* Zero-gradient outflow on face 1 (x = nx-1): after each step OUTFLOW cells copy
+ * the NEW stored state of (nx-2, y, z) (a cell of x = nx-1 is OUTFLOW only where
+ * (nx-2, y, z) is not solid).  Like the inflow, the paper's flow-past-solid
+ * scenes (Sec. 6.4) leave the outlet's form open; the zero-gradient copy is the reading
+ * the oracle pins.  It runs as its own small pass after the boundary kernel, one
+ * thread per (y, z).  Re-classifies (synchronises).  Only face 1: another face
+ * returns MELBM_EINVAL; failure handling as for melbm_set_inflow. */
 MELBM_API int melbm_set_outflow(melbm_t h, int face);
 
-/* Boundary list (device pointers, capacity entries each; either may be NULL).
- * cells[k] = n, words[k] = (type << 27) | link mask.  *count (host) = list length. */
+/* The compacted boundary-cell list built by the classification kernel -- the
+ * voxel analogue of the surface marking that the paper's solid correction uses
+ * to skip empty nodes (Sec. 4.2, "Accelerating solid intersection test"; Alg. 3
+ * visits only marked nodes).  cells[k] = n in ascending order, words[k] =
+ * (type << 27) | link mask, bit i of the mask set iff x - c_i is SOLID (periodic
+ * wrap); the list holds the INFLOW and FLUID_BOUNDARY cells.  cells and words
+ * are device pointers with room for `capacity` entries each (either may be
+ * NULL); *count (host pointer) receives the list length even when it exceeds
+ * capacity, in which case nothing is copied and MELBM_EINVAL is returned.
+ * Synchronises the handle's stream when it copies. */
 MELBM_API int melbm_get_boundary_list(melbm_t h, uint32_t* cells, uint32_t* words, int64_t capacity,
                             int64_t* count);
 
@@ -148,12 +169,37 @@ MELBM_API int melbm_get_types(melbm_t h, uint8_t* types);
  * Eq. rho_u_stress state (momentum gain F per step). */
 MELBM_API int melbm_set_force(melbm_t h, const float* F);
 
-/* Advance n >= 0 steps, asynchronously on the handle's stream. */
+/* Advance n >= 0 steps (Alg. 2 with the split design of Sec. 4.2), asynchronously
+ * on the handle's stream.  One step is
+ *   1. the fluid update kernel (Alg. 2) over every cell: load (and in 16-bit
+ *      storage dequantise, Sec. 5.4) the stored moments, collide in moment space
+ *      (App. A), rebuild the post-collision populations (Eq. three_order_f),
+ *      pull them from x - c_i (Eq. streaming), re-form the moments
+ *      (Eq. rho_u_stress) and store them (16-bit: range-reduced, dithered and
+ *      packed, Sec. 5.4), periodic in every direction;
+ *   2. with solids or inflow, the boundary kernels over the compacted list
+ *      (the solid correction of Sec. 4.2, here as halfway bounce-back or the
+ *      moment-based wall of Sec. 3.2 recomputing each listed cell, and the inflow
+ *      reset) -- MELBM_MIXED runs the paper's own additive atomicAdd correction
+ *      and re-quantisation instead;
+ *   3. with an outflow face, the zero-gradient copy onto x = nx-1.
+ * The state and time index advance by n.  Returns MELBM_EINVAL for n < 0 or a
+ * NULL handle, MELBM_ESTATE after a failed boundary setup, MELBM_ECUDA if a
+ * launch fails (the handle then refuses further steps).  Kernel faults surface
+ * at the next synchronising call. */
 MELBM_API int melbm_step(melbm_t h, int n);
 
 /* FP64 total mass sum(rho) and kinetic energy sum(rho |u|^2 / 2) over non-solid
- * cells (host pointers; synchronises).  In 16-bit storage returns
- * MELBM_WSATURATED (values still written) when any non-solid code is 0 or 65535. */
+ * cells (host pointers; synchronises).  Diagnostics of the update rather than a
+ * step of it: the fluid update conserves mass and momentum exactly in a periodic
+ * box (its moments are sums of streamed populations, Eq. rho_u_stress), and
+ * Sec. 5.4 motivates the dithered rounding by the drift that plain rounding
+ * would add, so these two sums are what the conservation and kinetic-energy
+ * checks of the 16-bit storage read.  Per cell the stored rho - 1 and
+ * rho |u|^2 / 2 are summed in FP64 in a fixed order (deterministic).  In 16-bit
+ * storage returns MELBM_WSATURATED (values still written) when any non-solid
+ * code is 0 or 2^b - 1 (saturation, Sec. 5.4 ranges).  MELBM_EINVAL for NULL
+ * pointers. */
 MELBM_API int melbm_reduce(melbm_t h, double* mass, double* kinetic_energy);
 
 /* Steps taken since the last melbm_set_state (host pointer). */
@@ -230,10 +276,16 @@ MELBM_API int melbm_q16_decode(const uint32_t* words, int64_t N, float* stored, 
  * held on every GPU that loads the library until the process exits, so N is
  * limited to 2^28 cells (larger N returns MELBM_EINVAL without any GPU work).
  * The first call on each device looks up the scratch address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All
- * calls share the scratch: calls that overlap on the GPU race and must be
- * serialised by the caller.  Returns MELBM_EINVAL for bad arguments and
- * MELBM_ECUDA if the address lookup or a launch fails (no message is stored). */
+ * with that device current and keeps it for the life of the process; make that
+ * first call before any stream capture.  A cudaDeviceReset (or any destruction of
+ * the device's primary context) may move the scratch and leaves that address
+ * stale: do not use this call on a device after a reset.  All calls share the
+ * scratch: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Q16 states are read on the default 16/16-bit grids only: a state
+ * written after melbm_set_bits with other widths gives wrong numbers (the
+ * call cannot tell).  Returns MELBM_EINVAL for bad arguments and MELBM_ECUDA if
+ * the address lookup or a launch fails, with a message for
+ * melbm_last_error(NULL). */
 MELBM_API int melbm_reduce_state_noalloc(const void* state, int storage, int64_t N,
                                          const uint8_t* type, double* out, void* cuda_stream);
 

@@ -297,6 +297,16 @@ cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out
   return e;
 }
 
+int handleless_fail(int code, const char* fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  g_err = msg;
+  return code;
+}
+
 cudaError_t join_transfers(melbm_sim* h) {
   if (!h->transfers) return cudaSuccess;
   cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_uploaded, 0);

@@ -81,6 +81,9 @@ namespace melbm {
 // Launch one forward step in -> out with the handle's boundaries (used by the
 // adjoint's recomputation); t_out is the time index of the output state.
 cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out);
+// Record the message of a failed call that has no handle (read by
+// melbm_last_error(NULL)) and return code.
+int handleless_fail(int code, const char* fmt, ...);
 // Make the handle's stream wait for every asynchronous raw-state transfer issued
 // so far (a no-op when none was).
 cudaError_t join_transfers(melbm_sim* h);

@@ -15,7 +15,11 @@
 // library holds it (NOALLOC_MAX_CHUNKS x 3 doubles = 96 KiB) until the process
 // exits.  Host code cannot use the array's name as a device address (on the host
 // it names a stand-in object), so the first call on each device looks the address
-// up with cudaGetSymbolAddress while that device is current, and caches it.
+// up with cudaGetSymbolAddress while that device is current, and caches it for the
+// life of the process.  A cudaDeviceReset (or anything else that destroys and
+// re-creates the device's primary context) reloads the module, which may move the
+// array; the cached address is then stale, so this entry point must not be used on
+// a device after such a reset.
 // Every call reuses the same array: calls that overlap on the GPU (from several
 // streams or host threads) race on it and must be serialised by the caller.  Each
 // call writes every partial it later reads, so nothing has to be cleared first.
@@ -23,6 +27,7 @@
 
 #include "../../include/melbm.h"
 #include "melbm_device.cuh"
+#include "melbm_handle.h"
 #include "reduce_cell.cuh"
 
 namespace melbm {
@@ -109,17 +114,23 @@ cudaError_t scratch_address(double** out) {
 extern "C" int melbm_reduce_state_noalloc(const void* state, int storage, int64_t N,
                                           const uint8_t* type, double* out, void* cuda_stream) {
   using namespace melbm;
-  if (!state || !out) return MELBM_EINVAL;
-  if (storage != MELBM_F32 && storage != MELBM_Q16) return MELBM_EINVAL;
-  if (N <= 0) return MELBM_EINVAL;
+  static const char* const fn = "melbm_reduce_state_noalloc";
+  if (!state || !out) return handleless_fail(MELBM_EINVAL, "%s: NULL state or out", fn);
+  if (storage != MELBM_F32 && storage != MELBM_Q16)
+    return handleless_fail(MELBM_EINVAL, "%s: storage %d is neither MELBM_F32 nor MELBM_Q16", fn,
+                           storage);
+  if (N <= 0) return handleless_fail(MELBM_EINVAL, "%s: N = %lld", fn, (long long)N);
   // The scratch array holds NOALLOC_MAX_CHUNKS partial sums of NA_CHUNK cells:
   // larger grids are refused rather than overrunning it.
   const int64_t nchunks = (N + NA_CHUNK - 1) / NA_CHUNK;
-  if (nchunks > NOALLOC_MAX_CHUNKS) return MELBM_EINVAL;
+  if (nchunks > NOALLOC_MAX_CHUNKS)
+    return handleless_fail(MELBM_EINVAL, "%s: N = %lld exceeds the %lld cells of its fixed scratch",
+                           fn, (long long)N, (long long)(NOALLOC_MAX_CHUNKS * NA_CHUNK));
   double* partials = nullptr;
-  if (scratch_address(&partials) != cudaSuccess) return MELBM_ECUDA;
+  cudaError_t e = scratch_address(&partials);
+  if (e != cudaSuccess)
+    return handleless_fail(MELBM_ECUDA, "%s: scratch address lookup: %s", fn, cudaGetErrorString(e));
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  cudaError_t e;
   if (storage == MELBM_Q16)
     noalloc_partial_kernel<ST_Q16><<<unsigned(nchunks), NA_THREADS, 0, st>>>(N, state, type, partials);
   else
@@ -129,5 +140,6 @@ extern "C" int melbm_reduce_state_noalloc(const void* state, int storage, int64_
     noalloc_final_kernel<<<1, 32, 0, st>>>(partials, nchunks, out);
     e = cudaGetLastError();
   }
-  return e == cudaSuccess ? MELBM_OK : MELBM_ECUDA;
+  if (e != cudaSuccess) return handleless_fail(MELBM_ECUDA, "%s: launch: %s", fn, cudaGetErrorString(e));
+  return MELBM_OK;
 }

@@ -87,6 +87,61 @@ def test_noalloc_reduce_with_solid_cells(M):
         assert abs(got[1] - ke) <= 1e-12 * abs(ke), (call, got[1], ke)
 
 
+def test_noalloc_reduce_counts_saturated_codes(M):
+    """A 16-bit state with codes pinned at both range limits: out[2] is the number
+    of non-solid codes equal to 0 or 65535, counted here from the raw words, on
+    two calls in a row; mass and energy still match melbm_reduce."""
+    import warnings
+    shape = (40, 20, 18)
+    N = int(np.prod(shape))
+    sim = M.Simulator(shape, 0.6, "q16", seed=8)
+    rng = np.random.default_rng(9)
+    for call in range(2):
+        rho = 1.0 + 0.01 * rng.standard_normal(N)
+        u = 0.05 * rng.standard_normal((3, N))
+        hit = rng.random(N) < 0.01 * (call + 1)
+        u[0, hit] = 0.5 * np.sign(rng.standard_normal(hit.sum()))  # beyond [-0.4, 0.4]
+        rho[rng.random(N) < 0.003] = 0.7                              # below the rho range
+        sim.set_state(torch.from_numpy(rho).float().cuda(), torch.from_numpy(u).float().cuda())
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", M.SaturationWarning)
+            mass, ke = sim.reduce()
+        words = sim.get_raw_state().view(torch.int32).reshape(5, N)
+        codes = M.words_to_codes(words).cpu().numpy()
+        want = int(((codes == 0) | (codes == 65535)).sum())
+        assert want > 0
+        got = _noalloc(M, sim)
+        assert got[2] == want, (call, got[2], want)
+        assert abs(got[0] - mass) <= 1e-12 * abs(mass)
+        assert abs(got[1] - ke) <= 1e-12 * abs(ke)
+
+
+def test_noalloc_reduce_allocates_no_device_memory(M):
+    """After a first call (which looks up the scratch address), further calls leave
+    the device's free memory unchanged."""
+    shape = (64, 32, 32)
+    sim = M.Simulator(shape, 0.6, "q16", seed=10)
+    rho, u = _state(shape, 11)
+    sim.set_state(rho, u)
+    raw = sim.get_raw_state()
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        rc = M.lib().melbm_reduce_state_noalloc(
+            ctypes.c_void_p(raw.data_ptr()), M.Q16, sim.N, None, ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(st))
+        assert rc == M.OK
+        torch.cuda.synchronize()
+
+    call()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+
+
 def test_noalloc_reduce_rejects_oversized_grid(M):
     buf = torch.zeros(16, dtype=torch.uint8, device="cuda")
     out = torch.zeros(3, dtype=torch.float64, device="cuda")
@@ -94,6 +149,8 @@ def test_noalloc_reduce_rejects_oversized_grid(M):
     rc = M.lib().melbm_reduce_state_noalloc(ctypes.c_void_p(buf.data_ptr()), M.Q16, too_many, None,
                                             ctypes.c_void_p(out.data_ptr()), None)
     assert rc == M.EINVAL
+    assert b"exceeds" in M.lib().melbm_last_error(None)
     rc = M.lib().melbm_reduce_state_noalloc(None, M.Q16, 10, None, ctypes.c_void_p(out.data_ptr()),
                                             None)
     assert rc == M.EINVAL
+    assert b"NULL" in M.lib().melbm_last_error(None)
