@@ -203,13 +203,106 @@ def run_channel512_moving(steps):
 
 
 def run_large1000(steps):
+    """The 160 M-cell obstacle scene in both storage forms: throughput and the
+    device memory each handle holds (melbm_memory_bytes)."""
     wl = W.LARGE1000
     mask, _ = W.procedural_obstacle(wl.shape)
-    rec = _channel(wl, mask, 0.06, steps)
-    # memory footprint of the two storage forms (state ping-pong only)
-    rec["state_pingpong_bytes"] = {"q16": 2 * 20 * wl.cells, "f32": 2 * 40 * wl.cells,
-                                   "paper_mixed": 60 * wl.cells}
+    out = []
+    for storage in ("q16", "f32"):
+        out.append(_channel(wl, mask, 0.06, steps, storage=storage))
+        torch.cuda.empty_cache()
+    return out
+
+
+def _flux_profile(sim, fluid, shape):
+    """Q(x) = sum over the fluid cells of plane x of rho u_x (FP64), shape (nx,)."""
+    nx, ny, nz = shape
+    rho, u, _ = sim.get_moments()
+    q = (rho.double() * u[0].double()) * fluid
+    out = q.reshape(nz, ny, nx).sum((0, 1)).cpu().numpy()
+    del rho, u
+    return out
+
+
+def _full_run(wl, mask, inflow_u, every=100):
+    """The workload run to its full length in 16-bit and in FP32 storage from the
+    same start (uniform inflow velocity, rho = 1): the FP64 mass and kinetic-energy
+    histories every `every` steps, the mass-flux profile Q(x) at the end, the
+    device memory of each handle and the MLUPS of the whole run (CUDA events around
+    the steps only)."""
+    N = wl.cells
+    u = np.zeros((3, N), np.float32)
+    u[0] = inflow_u
+    rho, ut = _state_from_velocity(u)
+    mt = torch.from_numpy(mask.ravel()).cuda()
+    runs = {}
+    for storage in ("q16", "f32"):
+        sim = melbm.Simulator(wl.shape, wl.tau, storage, seed=2602)
+        sim.set_state(rho, ut)
+        sim.set_solid(mt)
+        sim.set_inflow(1.0, (inflow_u, 0.0, 0.0))
+        sim.set_outflow()
+        fluid = (sim.types() != melbm.SOLID).double()
+        inlet_cells = int((sim.types().reshape(wl.shape[2], wl.shape[1], wl.shape[0])[:, :, 0]
+                           == melbm.INFLOW).sum().item())
+        M, E = [], []
+        m0, e0 = sim.reduce()
+        M.append(m0)
+        E.append(e0)
+        ms_total = 0.0
+        for t in range(every, wl.steps + 1, every):
+            a, b = _events()
+            a.record(sim.stream)
+            sim.step(every)
+            b.record(sim.stream)
+            torch.cuda.synchronize()
+            ms_total += a.elapsed_time(b)
+            m, e = sim.reduce()
+            M.append(m)
+            E.append(e)
+        Q = _flux_profile(sim, fluid, wl.shape)
+        runs[storage] = {"mass": np.array(M), "ke": np.array(E), "Q": Q,
+                         "memory_bytes": sim.memory_bytes(), "ms_per_step": ms_total / wl.steps,
+                         "inlet_cells": inlet_cells}
+        sim.close()
+        del fluid
+        torch.cuda.empty_cache()
+    q, f = runs["q16"], runs["f32"]
+    nx = wl.shape[0]
+    Q_in = 1.0 * inflow_u * f["inlet_cells"]
+    inner = slice(1, nx - 1)
+    rec = {"workload": wl.name + "_full", "steps": wl.steps, "cells": N,
+           "record_every": every,
+           "ke_rel_diff_max": float(np.abs(q["ke"] / f["ke"] - 1).max()),
+           "ke_end_over_start": {s: float(r["ke"][-1] / r["ke"][0]) for s, r in runs.items()},
+           "mass_change": {s: float((r["mass"][-1] - r["mass"][0]) / r["mass"][0])
+                           for s, r in runs.items()},
+           "mass_rel_diff_max": float(np.abs(q["mass"] / f["mass"] - 1).max()),
+           "flux_inflow_prescribed": Q_in,
+           "flux_mean_over_x": {s: float(r["Q"][inner].mean()) for s, r in runs.items()},
+           "flux_spread_over_x": {s: float((r["Q"][inner].max() - r["Q"][inner].min())
+                                           / r["Q"][inner].mean()) for s, r in runs.items()},
+           "flux_profile_rel_diff_max": float(np.abs(q["Q"][inner] / f["Q"][inner] - 1).max()),
+           "memory_bytes": {s: r["memory_bytes"] for s, r in runs.items()},
+           "MLUPS": {s: N / r["ms_per_step"] / 1e3 for s, r in runs.items()},
+           "ke_history": {s: [float(v) for v in r["ke"]] for s, r in runs.items()},
+           "mass_history": {s: [float(v) for v in r["mass"]] for s, r in runs.items()}}
     return rec
+
+
+def run_channel512_full(steps):
+    """The sphere channel for its full 2000 steps, 16-bit against FP32 storage."""
+    wl = W.CHANNEL512
+    mask, _ = W.sphere_pack(wl.shape)
+    return _full_run(wl, mask, 0.05)
+
+
+def run_large1000_full(steps):
+    """The 160 M-cell obstacle scene for its full 1000 steps, 16-bit against FP32
+    storage, with the measured device memory of both handles."""
+    wl = W.LARGE1000
+    mask, _ = W.procedural_obstacle(wl.shape)
+    return _full_run(wl, mask, 0.06)
 
 
 def run_adjoint128(steps, K=20):
@@ -321,7 +414,10 @@ RUNNERS = {"tgv32": run_tgv32, "turbulence256": run_turbulence256,
            "channel512_d3q19": run_channel512_d3q19, "scene720_d3q19": run_scene720_d3q19,
            "channel512_moving": run_channel512_moving, "large1000": run_large1000, "adjoint128": run_adjoint128,
            "adjoint128_keep_all": run_adjoint128_keep_all, "bits_sweep": run_bits_sweep,
-           "mixed_vs_recompute": run_mixed_vs_recompute}
+           "mixed_vs_recompute": run_mixed_vs_recompute, "channel512_full": run_channel512_full,
+           "large1000_full": run_large1000_full}
+# run only when asked for by name (--only): each takes minutes
+ON_REQUEST = {"channel512_full", "large1000_full"}
 
 
 def main():
@@ -331,7 +427,7 @@ def main():
     args = p.parse_args()
     melbm.lib()
     for name, fn in RUNNERS.items():
-        if args.only and name != args.only:
+        if (args.only and name != args.only) or (not args.only and name in ON_REQUEST):
             continue
         recs = fn(args.steps)
         for r in (recs if isinstance(recs, list) else [recs]):
