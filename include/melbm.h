@@ -117,14 +117,18 @@ MELBM_API int melbm_set_state(melbm_t h, const float* rho, const float* u, const
  * unspecified (the fluid kernel updates them uniformly; nothing reads them). */
 MELBM_API int melbm_get_moments(melbm_t h, float* rho, float* u, float* S);
 
-/* Solid mask[N] (uint8, nonzero = solid; device pointer, NULL = no solid).
- * Runs the classification and compaction kernels (analogue of the surface
- * marking of Sec. 4.2): every cell gets a type and a 27-bit mask whose bit i is
- * set iff x - c_i is SOLID (periodic wrap); INFLOW and FLUID_BOUNDARY cells are
- * listed in ascending n.  Synchronises to read the list length.  If the setup
- * fails (MELBM_ENOMEM, MELBM_ECUDA) the lists are freed and melbm_step,
- * melbm_solid_force and the adjoint return MELBM_ESTATE until a later
- * melbm_set_solid / melbm_set_inflow / melbm_set_outflow succeeds. */
+/* Solid mask[N] (uint8, nonzero = solid; device pointer, NULL = no solid),
+ * copied.  The classification and compaction kernels (analogue of the surface
+ * marking of Sec. 4.2) then give every cell a type and a 27-bit mask whose bit i
+ * is set iff x - c_i is SOLID (periodic wrap), and list the INFLOW and
+ * FLUID_BOUNDARY cells in ascending n.  melbm_set_solid, melbm_set_inflow and
+ * melbm_set_outflow only record their change: the classification runs once, at
+ * the next call that needs the types or the list (melbm_step with n > 0,
+ * melbm_get_boundary_list, melbm_get_types, melbm_reduce, melbm_solid_force,
+ * melbm_forward_checkpointed, melbm_backward), which synchronises to read the list
+ * length and returns the classification's MELBM_ENOMEM or MELBM_ECUDA if it
+ * fails.  The lists are then freed, and those calls return MELBM_ESTATE until a
+ * later melbm_set_solid / melbm_set_inflow / melbm_set_outflow. */
 MELBM_API int melbm_set_solid(melbm_t h, const uint8_t* mask);
 
 /* Equilibrium inflow on face 0 (x = 0): INFLOW cells are reset every step to
@@ -133,10 +137,9 @@ MELBM_API int melbm_set_solid(melbm_t h, const uint8_t* mask);
  * drive the flow by an inlet without stating its form; this Dirichlet-equilibrium reading
  * is the one the oracle pins.  Typed and listed by the classification kernel
  * (INFLOW outranks OUTFLOW and FLUID_BOUNDARY); the boundary kernel applies the
- * reset after the fluid kernel (split design of Sec. 4.2).  Re-classifies
- * (synchronises to read the list length).  Only face 0 is supported: another
- * face returns MELBM_EINVAL; a failed re-classification leaves the handle
- * refusing to step (MELBM_ESTATE) as for melbm_set_solid. */
+ * reset after the fluid kernel (split design of Sec. 4.2).  The classification
+ * runs at the next call that needs it, as for melbm_set_solid.  Only face 0 is
+ * supported: another face returns MELBM_EINVAL. */
 MELBM_API int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float uz);
 
 /* Zero-gradient outflow on face 1 (x = nx-1): after each step OUTFLOW cells copy
@@ -144,8 +147,8 @@ MELBM_API int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float u
  * (nx-2, y, z) is not solid).  Like the inflow, the paper's flow-past-solid
  * scenes (Sec. 6.4) leave the outlet's form open; the zero-gradient copy is the reading
  * the oracle pins.  It runs as its own small pass after the boundary kernel, one
- * thread per (y, z).  Re-classifies (synchronises).  Only face 1: another face
- * returns MELBM_EINVAL; failure handling as for melbm_set_inflow. */
+ * thread per (y, z).  The classification runs at the next call that needs it,
+ * as for melbm_set_solid.  Only face 1: another face returns MELBM_EINVAL. */
 MELBM_API int melbm_set_outflow(melbm_t h, int face);
 
 /* The compacted boundary-cell list built by the classification kernel -- the
@@ -177,16 +180,21 @@ MELBM_API int melbm_set_force(melbm_t h, const float* F);
  *      pull them from x - c_i (Eq. streaming), re-form the moments
  *      (Eq. rho_u_stress) and store them (16-bit: range-reduced, dithered and
  *      packed, Sec. 5.4), periodic in every direction;
- *   2. with solids or inflow, the boundary kernels over the compacted list
- *      (the solid correction of Sec. 4.2, here as halfway bounce-back or the
- *      moment-based wall of Sec. 3.2 recomputing each listed cell, and the inflow
- *      reset) -- MELBM_MIXED runs the paper's own additive atomicAdd correction
- *      and re-quantisation instead;
+ *   2. with solids or inflow, the boundary kernel over the compacted list (the
+ *      solid correction of Sec. 4.2): with solids the fluid kernel lets solid
+ *      cells enter the stream at rest and keeps the raw post-streaming sums of
+ *      each FLUID_BOUNDARY cell, to which the boundary kernel adds what the
+ *      cell's solid links return -- halfway bounce-back from the cell's own
+ *      post-collision state, or the moment-based wall of Sec. 3.2 -- before the
+ *      moments are finished and stored; INFLOW cells are reset.  MELBM_MIXED
+ *      runs the paper's own additive atomicAdd correction and re-quantisation
+ *      instead;
  *   3. with an outflow face, the zero-gradient copy onto x = nx-1.
  * The state and time index advance by n.  Returns MELBM_EINVAL for n < 0 or a
- * NULL handle, MELBM_ESTATE after a failed boundary setup, MELBM_ECUDA if a
- * launch fails (the handle then refuses further steps).  Kernel faults surface
- * at the next synchronising call. */
+ * NULL handle, MELBM_ESTATE after a failed boundary setup, the classification's
+ * status when a pending one fails (melbm_set_solid), MELBM_ECUDA if a launch
+ * fails (the handle then refuses further steps).  Kernel faults surface at the
+ * next synchronising call. */
 MELBM_API int melbm_step(melbm_t h, int n);
 
 /* FP64 total mass sum(rho) and kinetic energy sum(rho |u|^2 / 2) over non-solid

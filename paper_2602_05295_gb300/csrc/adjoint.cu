@@ -392,17 +392,17 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams
   float zl[6], m1[6], m2[6];
   for (int k = 0; k < 6; ++k) zl[k] = m1[k] = m2[k] = 0.f;
   float gprev[3] = {0.f, 0.f, 0.f};  // F/2 share of fin^T at plane zz-1
-  // plane zz's lambda' and output state are loaded one iteration ahead
-  float Lnext[10], Mnext[10];
+  // plane zz's lambda' and output state are loaded one iteration ahead (of the
+  // output state Fin^T needs only rho - 1 and u)
+  float Lnext[10], Mnext[4];
   bool skip_next = false;
   auto load_plane = [&](int zp) {
     const size_t n = col + plane * size_t(wrapi(zp, nz));
     skip_next = TYPED && special_type(P.type[n]);
 #pragma unroll
-    for (int k = 0; k < 10; ++k) {
-      Lnext[k] = __ldg(P.lam_next + k * N + n);
-      Mnext[k] = __ldg(P.m_next + k * N + n);
-    }
+    for (int k = 0; k < 10; ++k) Lnext[k] = __ldg(P.lam_next + k * N + n);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Mnext[k] = __ldg(P.m_next + k * N + n);
   };
   load_plane(z0 - 1);
   int parity = 0;
@@ -426,30 +426,24 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams
         }
     }
     // ---- fin^T at plane zz, then proj^T along z of the six (d, e) slices
-    float lam[10], mn[10];
+    float lam[10], mn[4];
     const bool skip = skip_next;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) {
-      lam[k] = Lnext[k];
-      mn[k] = Mnext[k];
-    }
+    for (int k = 0; k < 10; ++k) lam[k] = Lnext[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mn[k] = Mnext[k];
     if (zz + 1 <= z1) load_plane(zz + 1);
     float lM[10];
     float lJ[3] = {0.f, 0.f, 0.f};
     if (skip) {
       for (int k = 0; k < 10; ++k) lM[k] = 0.f;
     } else {
-      Stored o;
+      Stored o;  // fin_vjp_cell reads rho - 1 and u of the output only
       o.drho = mn[0];
       o.ux = mn[1];
       o.uy = mn[2];
       o.uz = mn[3];
-      o.nxx = mn[4];
-      o.nyy = mn[5];
-      o.nzz = mn[6];
-      o.nxy = mn[7];
-      o.nxz = mn[8];
-      o.nyz = mn[9];
+      o.nxx = o.nyy = o.nzz = o.nxy = o.nxz = o.nyz = 0.f;
       fin_vjp_cell(o, lam, lM, lJ);
     }
     // slices (d, e) = (0,0) (1,0) (0,1) (2,0) (1,1) (0,2), inputs over f
@@ -694,6 +688,7 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: requires MELBM_F32 storage");
   if (h->wall_model != 0)
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: the adjoint covers halfway bounce-back walls only");
+  if (int rc = ensure_boundaries(h)) return rc;
   if (h->boundary_error)
     return adj_fail(h, MELBM_ESTATE, "melbm_forward_checkpointed: the last boundary setup failed");
   ADJ_CUDA(h, join_transfers(h));
@@ -768,6 +763,7 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
   AdjointState* a = h->adj;
   if (!a || !a->ready)
     return adj_fail(h, MELBM_ESTATE, "melbm_backward: call melbm_forward_checkpointed first");
+  if (int rc = ensure_boundaries(h)) return rc;
   if (h->boundary_error)
     return adj_fail(h, MELBM_ESTATE, "melbm_backward: the last boundary setup failed");
   if (!dL_dm || !dL_du0 || !is_dev(dL_dm) || !is_dev(dL_du0) || (dL_dF && !is_dev(dL_dF)))

@@ -132,81 +132,90 @@ int ensure_staging(melbm_t h, size_t bytes) {
 }
 
 void free_list(melbm_t h) {
-  dev_free(h, h->lidx, h->lidx ? size_t(h->N) * 4 : 0);
-  dev_free(h, h->src_cells, size_t(h->S) * 4);
-  dev_free(h, h->src_pop, size_t(h->L) * 27 * 4);
-  h->lidx = h->src_cells = nullptr;
-  h->src_pop = nullptr;
-  h->S = 0;
-  dev_free(h, h->list_cell, size_t(h->L) * 4);
-  dev_free(h, h->list_word, size_t(h->L) * 4);
+  dev_free(h, h->cls_solid, size_t(h->W) * 4);
+  dev_free(h, h->cls_fb, size_t(h->W) * 4);
+  dev_free(h, h->cls_pref, size_t(h->W) * 4);
+  dev_free(h, h->side, size_t(h->L_cap) * 10 * 4);
+  h->cls_solid = h->cls_fb = h->cls_pref = nullptr;
+  h->side = nullptr;
+  h->W = 0;
+  dev_free(h, h->list_cell, size_t(h->L_cap) * 4);
+  dev_free(h, h->list_word, size_t(h->L_cap) * 4);
   h->list_cell = h->list_word = nullptr;
-  h->L = 0;
+  h->L = h->L_cap = 0;
 }
 
-// The source set of the boundary update (after the list): the cells whose
-// post-collision state a listed cell reads, compacted in ascending order, the
-// list index of every FLUID_BOUNDARY cell, and the [27][L] table that phase A
-// fills every step.  Temporary: mark[N].
-int build_sources(melbm_t h) {
-  const size_t N = size_t(h->N);
-  uint8_t* mark = nullptr;
-  int rc = dev_alloc(h, (void**)&mark, N);
-  if (rc) return rc;
-  cudaError_t e = launch_source_setup_mark(h->nx, h->ny, h->nz, h->list_cell, h->list_word, h->L,
-                                           mark, h->cl_counts, h->stream);
-  if (e == cudaSuccess)
-    e = launch_exclusive_scan(h->cl_counts, h->cl_offsets, source_flag_blocks(h->N),
-                              h->cl_total, h->stream);
-  uint32_t S = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&S, h->cl_total, 4, cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e == cudaSuccess && S) {
-    h->S = S;  // before the allocations, so that free_list accounts for them
-    if ((rc = dev_alloc(h, (void**)&h->lidx, N * 4)) ||
-        (rc = dev_alloc(h, (void**)&h->src_cells, size_t(S) * 4)) ||
-        (rc = dev_alloc(h, (void**)&h->src_pop, size_t(h->L) * 27 * 4))) {
-      dev_free(h, mark, N);
-      return rc;
-    }
-    e = launch_source_setup_fill(h->nx, h->ny, h->nz, h->list_cell, h->list_word, h->L, mark,
-                                 h->cl_offsets, h->src_cells, h->lidx, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  }
-  dev_free(h, mark, N);
-  if (e != cudaSuccess) return cuda_fail(h, e, "build_sources");
-  return MELBM_OK;
+BoundaryTables boundary_tables(const melbm_sim* h) {
+  BoundaryTables t;
+  t.solid = h->cls_solid;
+  t.fb = h->cls_fb;
+  t.pref = h->cls_pref;
+  t.side = h->side;
+  t.L = h->L;
+  return t;
 }
 
-// (Re)build types and the boundary list from the mask and the inflow/outflow flags.
+// Classification (classify.cu): types, the list, and with solids the tables the
+// fluid kernel reads (per 32-cell word of a row the SOLID and FLUID_BOUNDARY bits
+// and the list index of its first listed cell) and the [10][L] side table it
+// fills every step (the mixed scheme corrects its own fluid pass and needs no
+// tables).
 int reclassify_lists(melbm_t h) {
-  free_list(h);
   if (!h->mask && !h->inflow_on && !h->outflow_on) {
+    free_list(h);
     dev_free(h, h->type, size_t(h->N));
     h->type = nullptr;
     return MELBM_OK;
   }
+  // a classification of the same grid reuses the arrays of the last one (the
+  // list arrays and the side table while they are large enough)
   int rc;
   if (!h->type && (rc = dev_alloc(h, (void**)&h->type, size_t(h->N)))) return rc;
-  const int64_t nb = classify_blocks(h->N);
+  const bool tables = h->mask && h->storage != MELBM_MIXED;
+  if (!tables && h->cls_solid) free_list(h);  // the tables go; the list is rebuilt below
+  if (tables && !h->cls_solid) {
+    h->W = classify_words(h->nx, h->ny, h->nz);  // before the allocations (free_list)
+    if ((rc = dev_alloc(h, (void**)&h->cls_solid, size_t(h->W) * 4)) ||
+        (rc = dev_alloc(h, (void**)&h->cls_fb, size_t(h->W) * 4)))
+      return rc;
+  }
+  const int64_t nb = classify_blocks(h->nx, h->ny, h->nz);
   if (!h->cl_counts) {
     if ((rc = dev_alloc(h, (void**)&h->cl_counts, size_t(nb) * 4))) return rc;
     if ((rc = dev_alloc(h, (void**)&h->cl_offsets, size_t(nb) * 4))) return rc;
     if ((rc = dev_alloc(h, (void**)&h->cl_total, 4))) return rc;
   }
   MELBM_CUDA(h, launch_classify_count(h->nx, h->ny, h->nz, h->mask, h->inflow_on, h->outflow_on,
-                                     h->type, h->cl_counts, h->stream));
+                                     h->type, tables ? h->cls_solid : nullptr,
+                                     tables ? h->cls_fb : nullptr, h->cl_counts, h->stream));
   MELBM_CUDA(h, launch_exclusive_scan(h->cl_counts, h->cl_offsets, nb, h->cl_total, h->stream));
   uint32_t total = 0;
   MELBM_CUDA(h, cudaMemcpyAsync(&total, h->cl_total, 4, cudaMemcpyDeviceToHost, h->stream));
   MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (int64_t(total) > h->L_cap) {
+    dev_free(h, h->list_cell, size_t(h->L_cap) * 4);
+    dev_free(h, h->list_word, size_t(h->L_cap) * 4);
+    dev_free(h, h->side, size_t(h->L_cap) * 10 * 4);
+    h->list_cell = h->list_word = nullptr;
+    h->side = nullptr;
+    h->L = h->L_cap = 0;
+  }
   if (total) {
-    if ((rc = dev_alloc(h, (void**)&h->list_cell, size_t(total) * 4))) return rc;
-    if ((rc = dev_alloc(h, (void**)&h->list_word, size_t(total) * 4))) return rc;
+    if (!h->list_cell) {
+      h->L_cap = total;  // before the allocations (free_list)
+      if ((rc = dev_alloc(h, (void**)&h->list_cell, size_t(total) * 4))) return rc;
+      if ((rc = dev_alloc(h, (void**)&h->list_word, size_t(total) * 4))) return rc;
+    }
+    if (tables && !h->cls_pref && (rc = dev_alloc(h, (void**)&h->cls_pref, size_t(h->W) * 4)))
+      return rc;
+    if (tables && !h->side && (rc = dev_alloc(h, (void**)&h->side, size_t(h->L_cap) * 10 * 4)))
+      return rc;
     h->L = total;
-    MELBM_CUDA(h, launch_classify_scatter(h->nx, h->ny, h->nz, h->mask, h->type, h->cl_offsets,
-                                          h->list_cell, h->list_word, h->stream));
-    if ((rc = build_sources(h))) return rc;
+    MELBM_CUDA(h, launch_classify_scatter(h->nx, h->ny, h->nz, h->mask, h->inflow_on,
+                                          h->outflow_on, h->type, h->cl_offsets, h->list_cell,
+                                          h->list_word, tables ? h->cls_pref : nullptr, h->stream));
+  } else {
+    h->L = 0;
   }
   return MELBM_OK;
 }
@@ -217,7 +226,18 @@ int reclassify(melbm_t h) {
   const int rc = reclassify_lists(h);
   if (rc != MELBM_OK) free_list(h);
   h->boundary_error = rc != MELBM_OK;
+  h->boundary_pending = false;
   return rc;
+}
+
+// melbm_set_solid / melbm_set_inflow / melbm_set_outflow only record the change;
+// the classification runs once, at the first call that needs the types or the
+// list.  Its failure is that call's status (and later calls refuse, as after a
+// failed setup).
+int mark_boundaries_changed(melbm_t h) {
+  h->boundary_pending = true;
+  h->boundary_error = false;
+  return MELBM_OK;
 }
 
 int boundary_refusal(melbm_t h, const char* what) {
@@ -281,20 +301,25 @@ int check_raw_bytes(melbm_t h, const char* what, int64_t bytes) {
 namespace melbm {
 cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out) {
   const float omega = 1.0f / h->tau;
+  const BoundaryTables bt = boundary_tables(h);
   cudaError_t e =
       h->lattice == MELBM_D3Q19
           ? launch_fluid19(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                           h->seed, h->grids, h->stream)
+                           h->seed, h->grids, &bt, h->stream)
           : launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                         h->seed, h->grids, h->stream);
+                         h->seed, h->grids, &bt, h->stream);
   if (e == cudaSuccess && h->L)
     e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
-                        h->list_word, h->L, h->src_cells, h->S, h->lidx, h->src_pop,
-                        h->inflow, t_out, h->seed, h->grids, h->wall_model, h->mask, h->bodies,
-                        h->lattice, h->stream);
+                        h->list_word, h->L, bt, h->inflow, t_out, h->seed, h->grids,
+                        h->wall_model, h->mask, h->bodies, h->lattice, h->stream);
   if (e == cudaSuccess && h->outflow_on && h->type)
     e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream);
   return e;
+}
+
+int ensure_boundaries(melbm_sim* h) {
+  if (!h->boundary_pending) return MELBM_OK;
+  return reclassify(h);
 }
 
 int handleless_fail(int code, const char* fmt, ...) {
@@ -491,7 +516,7 @@ int melbm_set_solid(melbm_t h, const uint8_t* mask) {
     if (!h->mask && (rc = dev_alloc(h, (void**)&h->mask, size_t(h->N)))) return rc;
     MELBM_CUDA(h, cudaMemcpyAsync(h->mask, mask, size_t(h->N), cudaMemcpyDeviceToDevice, h->stream));
   }
-  return reclassify(h);
+  return mark_boundaries_changed(h);
 }
 
 int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float uz) {
@@ -503,19 +528,21 @@ int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float uy, float u
   h->inflow[1] = ux;
   h->inflow[2] = uy;
   h->inflow[3] = uz;
-  return reclassify(h);
+  return mark_boundaries_changed(h);
 }
 
 int melbm_set_outflow(melbm_t h, int face) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_outflow: NULL handle");
   if (face != 1) return fail(h, MELBM_EINVAL, "melbm_set_outflow: only face 1 (x = nx-1) is supported");
   h->outflow_on = 1;
-  return reclassify(h);
+  return mark_boundaries_changed(h);
 }
 
 int melbm_get_boundary_list(melbm_t h, uint32_t* cells, uint32_t* words, int64_t capacity,
                             int64_t* count) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_get_boundary_list: NULL handle");
+  if (int rc = ensure_boundaries(h)) return rc;
+  if (h->boundary_error) return boundary_refusal(h, "melbm_get_boundary_list");
   if (count) *count = h->L;
   if ((cells || words) && capacity < h->L)
     return fail(h, MELBM_EINVAL, "melbm_get_boundary_list: capacity %lld < %lld",
@@ -530,6 +557,8 @@ int melbm_get_boundary_list(melbm_t h, uint32_t* cells, uint32_t* words, int64_t
 
 int melbm_get_types(melbm_t h, uint8_t* types) {
   if (!h || !types) return fail(h, MELBM_EINVAL, "melbm_get_types: NULL argument");
+  if (int rc = ensure_boundaries(h)) return rc;
+  if (h->boundary_error) return boundary_refusal(h, "melbm_get_types");
   if (h->type) {
     MELBM_CUDA(h, cudaMemcpyAsync(types, h->type, size_t(h->N), cudaMemcpyDefault, h->stream));
   } else {
@@ -559,6 +588,8 @@ int melbm_step(melbm_t h, int n) {
   if (n < 0) return fail(h, MELBM_EINVAL, "melbm_step: n = %d < 0", n);
   if (h->poisoned) return fail(h, MELBM_ESTATE, "melbm_step: an earlier CUDA failure left the state undefined; call melbm_set_state");
   if (h->boundary_error) return boundary_refusal(h, "melbm_step");
+  if (n > 0)
+    if (int rc = ensure_boundaries(h)) return rc;
   if (h->transfers && n > 0) {
     // the uploaded state must have landed; a download may still read the input
     // buffer, but not one that this call overwrites
@@ -594,6 +625,8 @@ int melbm_step(melbm_t h, int n) {
 
 int melbm_reduce(melbm_t h, double* mass, double* ke) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_reduce: NULL handle");
+  if (int rc = ensure_boundaries(h)) return rc;
+  if (h->boundary_error) return boundary_refusal(h, "melbm_reduce");
   MELBM_CUDA(h, join_transfers(h));
   const void* state = h->storage == MELBM_MIXED ? h->buf[1] : h->buf[h->cur];
   MELBM_CUDA(h, launch_reduce(h->storage, h->N, state, h->type, h->red_partials, h->red_out,
@@ -776,6 +809,7 @@ int melbm_solid_force(melbm_t h, int body, double* out) {
   if (!h || !out) return fail(h, MELBM_EINVAL, "melbm_solid_force: NULL argument");
   if (body < 0 || body > 255) return fail(h, MELBM_EINVAL, "melbm_solid_force: body %d outside 0..255", body);
   if (h->storage == MELBM_MIXED) return mixed_unsupported(h, "melbm_solid_force");
+  if (int rc = ensure_boundaries(h)) return rc;
   if (h->boundary_error) return boundary_refusal(h, "melbm_solid_force");
   for (int k = 0; k < 6; ++k) out[k] = 0.0;
   if (!h->L || !h->mask) return MELBM_OK;

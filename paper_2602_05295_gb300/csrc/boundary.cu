@@ -1,13 +1,16 @@
 // boundary.cu -- the boundary side of the split design (Sec. 4.2): after the
 // uniform fluid kernel has written every cell, the listed cells are rewritten.
-//   * FLUID_BOUNDARY: the full update is recomputed from the input state with
-//     halfway bounce-back for solid links, f_i(x) = f+_{opp(i)}(x) when x - c_i is
-//     solid (in place of the paper's additive triangle correction, which needs a
-//     mesh; recomputing from the input gives the post-streaming moments directly,
-//     with no atomics and no second rounding of the 16-bit state).  The
-//     post-collision populations that the listed cells read were evaluated
-//     once per source by phase A (sources.cu) and pushed into each cell's
-//     column of a [27][L] table, which this kernel reads contiguously.
+//   * FLUID_BOUNDARY: with solids the fluid kernel lets solid cells enter the
+//     stream at rest (zero post-collision moments about the rest state), so the
+//     raw post-streaming sums it leaves for such a cell in the side table hold
+//     every population pulled through a non-solid link and nothing through a
+//     solid one.  Halfway bounce-back, f_i(x) = f+_{opp(i)}(x) when x - c_i is
+//     solid, needs only the cell's own post-collision state: this kernel
+//     collides the cell's input state (App. A), adds the bounced population of
+//     every solid link to the sums and finishes and stores the moments.  This
+//     replaces the paper's additive per-triangle correction (Alg. 3), which needs
+//     a mesh; the sums are completed before the single rounding of the 16-bit
+//     store, with no atomics.
 //     With the moment-based wall model (Sec. 3.2, solid coupling) a solid link
 //     instead receives the Hermite population of (rho, u^p, S^p) at the link's
 //     halfway point p, u^p the rigid velocity of the body the solid cell
@@ -15,8 +18,7 @@
 //     own post-collision moments.
 //   * INFLOW: reset to the equilibrium (rho_in, u_in, S = u_in u_in).
 // The outflow pass then copies the stored state of x = nx-2 onto x = nx-1.
-// On the D3Q19 lattice the same update runs over its 19 directions and weights,
-// with the D3Q19 populations (hermite_eval19) for the moving-wall model.
+// On the D3Q19 lattice the same update runs over its 19 directions and weights.
 #include "melbm_device.cuh"
 #include "melbm_launch.h"
 
@@ -31,7 +33,8 @@ struct BoundaryParams {
   const uint32_t* cells;
   const uint32_t* words;
   int64_t count;
-  const float* pop;       // [27][count]: f_i / w_i - 1 streamed into each listed cell
+  const float* side;       // [10][count]: raw post-streaming sums (FLUID_BOUNDARY entries),
+                           // times -1, 2, 2, 2, 1, 1, 1, -4, -4, -4
   int wall_model;          // 0 halfway bounce-back, 1 moment-based reconstruction
   const uint8_t* mask;     // body id of every cell (wall model 1)
   const float* bodies;     // 256 x 9: V, Om, r0 of each body (wall model 1)
@@ -74,21 +77,41 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
     store_stored<STORAGE>(P.out, N, n, s, x, y, z, P.t_out, P.seed, false, P.q);
     return;
   }
-  float m000 = 0.f, m100 = 0.f, m010 = 0.f, m001 = 0.f, m200 = 0.f, m020 = 0.f, m002 = 0.f,
-        m110 = 0.f, m101 = 0.f, m011 = 0.f;
+  // the raw sums of the fluid kernel, stored times the scale factors of its passes
+  const size_t L = size_t(P.count);
+  float m000 = -__ldg(P.side + k), m100 = 0.5f * __ldg(P.side + L + k),
+        m010 = 0.5f * __ldg(P.side + 2 * L + k), m001 = 0.5f * __ldg(P.side + 3 * L + k),
+        m200 = __ldg(P.side + 4 * L + k), m020 = __ldg(P.side + 5 * L + k),
+        m002 = __ldg(P.side + 6 * L + k), m110 = -0.25f * __ldg(P.side + 7 * L + k),
+        m101 = -0.25f * __ldg(P.side + 8 * L + k), m011 = -0.25f * __ldg(P.side + 9 * L + k);
   float fx0 = 0.f, fy0 = 0.f, fz0 = 0.f;
   if (FORCE) {
-    fx0 = P.force[n];
-    fy0 = P.force[N + n];
-    fz0 = P.force[2 * N + n];
+    fx0 = __ldg(P.force + n);
+    fy0 = __ldg(P.force + N + n);
+    fz0 = __ldg(P.force + 2 * N + n);
   }
-  Mom17 Aself;
-  if constexpr (MOVING)
-    Aself = collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n, P.q), P.omega, fx0, fy0, fz0);
-  auto accumulate = [&](int cx, int cy, int cz, float g) {
-    const float w = Q19 ? lattice_weight19(cx, cy, cz)
-                        : (cx ? (1.0f / 6.0f) : (2.0f / 3.0f)) * (cy ? (1.0f / 6.0f) : (2.0f / 3.0f)) *
-                              (cz ? (1.0f / 6.0f) : (2.0f / 3.0f));
+  const Mom17 A =
+      collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n, P.q), P.omega, fx0, fy0, fz0);
+  // each thread loops over its own solid links (bit scan of its link mask), so a
+  // warp runs as many iterations as its busiest cell
+  uint32_t links = word & 0x7FFFFFFu;
+  if (Q19) links &= D3Q19_LINKS;
+  while (links) {
+    const int i = __ffs(links) - 1;
+    links &= links - 1u;
+    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    float g;  // f_i / w_i - 1 of the population the solid link returns along c_i
+    if constexpr (MOVING) {
+      float up[3];
+      body_velocity(P.bodies, P.mask[pull_source(x, y, z, nx, ny, nz, i)], x - 0.5f * cx,
+                    y - 0.5f * cy, z - 0.5f * cz, up);
+      const Mom17 Wm = wall_moments(A, up[0], up[1], up[2]);
+      g = Q19 ? hermite_eval19(Wm, cx, cy, cz) : hermite_eval(Wm, cx, cy, cz);
+    } else {
+      // halfway bounce-back: population opp(i) of x itself
+      g = Q19 ? hermite_eval19(A, -cx, -cy, -cz) : hermite_eval(A, -cx, -cy, -cz);
+    }
+    const float w = Q19 ? lattice_weight19(cx, cy, cz) : lattice_weight(cx, cy, cz);
     const float f = w * g;
     m000 += f;
     m100 += cx * f;
@@ -100,33 +123,6 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
     m110 += float(cx * cy) * f;
     m101 += float(cx * cz) * f;
     m011 += float(cy * cz) * f;
-  };
-#pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-    if (Q19 && !in_d3q19(cx, cy, cz)) continue;  // D3Q19: no corner populations
-    const bool solid = (word >> i) & 1u;
-    if (MOVING && solid) continue;  // the moving-wall links follow below
-    // f_i / w_i - 1: population i pulled from x - c_i, or, for a solid link,
-    // population opp(i) = 26 - i of x itself (bounce-back), as phase A wrote it
-    accumulate(cx, cy, cz, __ldg(P.pop + int64_t(i) * P.count + k));
-  }
-  if constexpr (MOVING) {
-    // the population of the moving wall for each solid link, each thread over
-    // its own links (a warp then runs as many iterations as its busiest cell,
-    // not one per direction that any of its cells has)
-    uint32_t links = word & 0x7FFFFFFu;
-    if (Q19) links &= D3Q19_LINKS;
-    while (links) {
-      const int i = __ffs(links) - 1;
-      links &= links - 1u;
-      const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-      float up[3];
-      body_velocity(P.bodies, P.mask[pull_source(x, y, z, nx, ny, nz, i)], x - 0.5f * cx,
-                    y - 0.5f * cy, z - 0.5f * cz, up);
-      const Mom17 Wm = wall_moments(Aself, up[0], up[1], up[2]);
-      accumulate(cx, cy, cz, Q19 ? hermite_eval19(Wm, cx, cy, cz) : hermite_eval(Wm, cx, cy, cz));
-    }
   }
   const Stored o = finish_moments<FORCE>(m000, m100, m010, m001, m200, m020, m002, m110, m101,
                                          m011, fx0, fy0, fz0);
@@ -135,15 +131,11 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
 
 cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
                             const float* force, float omega, const uint32_t* cells,
-                            const uint32_t* words, int64_t count, const uint32_t* src_cells,
-                            int64_t S, const uint32_t* lidx, float* pop, const float inflow[4],
-                            uint32_t t_out, uint32_t seed, const QGrids& q, int wall_model,
-                            const uint8_t* mask, const float* bodies, int lattice,
+                            const uint32_t* words, int64_t count, const BoundaryTables& bt,
+                            const float inflow[4], uint32_t t_out, uint32_t seed, const QGrids& q,
+                            int wall_model, const uint8_t* mask, const float* bodies, int lattice,
                             cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  cudaError_t e = launch_source_collide(storage, nx, ny, nz, in, force, omega, src_cells, S, lidx,
-                                        words, count, pop, q, lattice, st);
-  if (e != cudaSuccess) return e;
   BoundaryParams p;
   p.nx = nx;
   p.ny = ny;
@@ -155,7 +147,7 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
   p.cells = cells;
   p.words = words;
   p.count = count;
-  p.pop = pop;
+  p.side = bt.side;
   p.in_rho = inflow[0];
   p.in_ux = inflow[1];
   p.in_uy = inflow[2];

@@ -1,0 +1,15 @@
+// fluid_bnd.cu -- the D3Q27 fluid kernel with solids (fluid_kernel.cuh, BND):
+// solid cells enter the passes at rest and the raw sums of the FLUID_BOUNDARY
+// cells go to the side table of the boundary kernel.
+#include "fluid_kernel.cuh"
+
+namespace melbm {
+
+cudaError_t launch_fluid_bnd(int storage, int nx, int ny, int nz, const void* in, void* out,
+                             const float* force, float omega, uint32_t t_out, uint32_t seed,
+                             const QGrids& grids, const BoundaryTables* bt, cudaStream_t st) {
+  return launch_fluid_impl<false, true>(storage, nx, ny, nz, in, out, force, omega, t_out, seed,
+                                        grids, bt, st);
+}
+
+}  // namespace melbm

@@ -34,6 +34,15 @@
 //     accesses, one barrier per plane pair);
 //   * the z pass keeps the previous pair's populations in registers;
 //   * the next pair's loads are issued before the current pair is processed.
+// Per pair j the work splits into pre(j) (decode, collide, x pass, y-pass
+// populations into shared-memory buffer j & 1) and post(j) (y pass from that
+// buffer, z pass, moments, encode, store), with one barrier between them.  The
+// 16-bit kernel runs post(j - 1) and pre(j) in one straight block between two
+// barriers (they use different buffers), so that the integer work of one pair
+// (dither hash, decode, packing) and the arithmetic of the other can be
+// interleaved; the FP32 kernel, which has twice the bytes in flight, keeps
+// pre(j), barrier, post(j) with two pairs per loop trip.  The 16-bit word planes
+// are addressed by 32-bit cell offsets from per-plane base pointers.
 //
 // D3Q19 (Q19 = true) runs the same three passes.  Its post-collision populations,
 // zero on the eight corners of the 27-velocity cube, have tensor Hermite moments
@@ -67,9 +76,9 @@ namespace melbm {
 #ifndef MELBM_Q16_HALO_CHUNK
 #define MELBM_Q16_HALO_CHUNK 1
 #endif
-// z-loop unroll factor, an expression of the kernel's STORAGE and FORCE parameters
+// z-loop unroll factor of the FP32 kernel, an expression of its FORCE parameter
 #ifndef MELBM_FLUID_ZUNROLL
-#define MELBM_FLUID_ZUNROLL (STORAGE == ST_F32 && !FORCE ? 2 : 1)
+#define MELBM_FLUID_ZUNROLL (!FORCE ? 2 : 1)
 #endif
 constexpr int FX = 32;
 constexpr int FY = MELBM_FLUID_FY;
@@ -88,11 +97,13 @@ static_assert(ZCHUNK % 2 == 0, "planes are processed in pairs");
 // Warp 0's halo staging, two buffers: per halo lane, 2 W entries (word w of
 // plane h at entry 2 w + h) plus 6 for the forces; an entry is CHUNK 32-bit
 // words, laid out [buffer][entry][lane][CHUNK].
-template <int STORAGE, bool FORCE, bool Q19 = false>
+template <int STORAGE, bool FORCE, bool Q19 = false, bool BND = false>
 struct HaloStage {
   static constexpr int W = STORAGE == ST_Q16 ? 5 : 10;     // stored 32-bit words per cell
   static constexpr int CHUNK = STORAGE == ST_Q16 ? MELBM_Q16_HALO_CHUNK : 4;  // 4: 16-byte chunk
-  static constexpr int ENTRIES = 2 * W + (FORCE ? 6 : 0);
+  // the state words of both planes, the force, and with solids the solid-bit
+  // words of both planes (copied alone, into the first word of their entries)
+  static constexpr int ENTRIES = 2 * W + (FORCE ? 6 : 0) + (BND ? 2 : 0);
   static constexpr int BUF_WORDS = ENTRIES * 32 * CHUNK;
   static constexpr size_t SMEM =
       size_t(2) * (SM_BUF + halo_buf<Q19>()) * sizeof(float2) + size_t(2) * BUF_WORDS * 4;
@@ -106,6 +117,19 @@ struct FluidParams {
   float omega;
   uint32_t t_out, seed;
   int chunk16;  // FP32 storage: 16-byte aligned rows, so the halo gather copies chunks
+  const uint32_t* qin[5];  // 16-bit words: the five word planes of the input
+  uint32_t* qout[5];       // and of the output (16-bit storage)
+  // With solids (BND kernels): per 32-cell word (tx, y, z) of a row, the bits of
+  // its SOLID and FLUID_BOUNDARY cells and the list index of its first listed
+  // cell after an INFLOW cell at its lane 0; side[10][L] receives the raw
+  // post-streaming sums of every FLUID_BOUNDARY cell (list order), times the
+  // scale factors of the passes (-1, 2, 2, 2, 1, 1, 1, -4, -4, -4).
+  const uint32_t* cls_solid;
+  const uint32_t* cls_fb;
+  const uint32_t* cls_pref;
+  float* side;
+  int64_t L;
+  int ntx;  // words per row, ceil(nx / 32)
 };
 
 template <int STORAGE, bool RT> struct KernelParams;
@@ -138,24 +162,231 @@ struct KernelParams<ST_F32, false> : FluidParams {
   const uint32_t* f_w[3];
 };
 
+// ----------------------------------------------------------------- scaled passes
+// The passes carry every tensor moment mu_pqr multiplied by s(p) s(q) s(r), with
+// s = (-1, 2, 1) for the orders 0, 1, 2 along each axis.  In that scaling one
+// axis of the stream needs no multiply beyond the fused ones: from the inputs
+// (a0, a1, a2) = (-mu0, 2 mu1, mu2) of a slice
+//   sigma = a0 (-1/3) + a2  (= mu0/3 + mu2),   P+- = sigma +- a1/2  (= 2 phi+-),
+//   Zn = sigma + a0  (= -phi0),
+// and after the pull (pl = P+ of the minus neighbour, mr = P- of the plus one)
+//   b0 = (pl + mr)(-1/2) + Zn  (= -m0),  b1 = pl - mr  (= 2 m1),
+//   b2 = b0 (-2/3) + Zn  (= m2),
+// which are the next axis' inputs in the same scaling (the D1Q3 map of
+// melbm_device.cuh's phi3 / proj written for scaled moments; the sums of b0 and
+// b1 over the grid still equal those of a0 and a1 up to unbiased rounding).  A
+// full slice costs eight packed operations, one with a2 = 0 the same with a
+// multiply for sigma, one with only a0 six.
+template <class T>
+struct PhiS {
+  T p, zn, m;  // P+, Zn, P-
+};
+template <class T>
+__device__ __forceinline__ PhiS<T> phis(T a0, T a1, T a2) {
+  PhiS<T> r;
+  const T sg = vfmac(a0, -1.0f / 3.0f, a2);
+  r.p = vfmac(a1, 0.5f, sg);
+  r.m = vfmac(a1, -0.5f, sg);
+  r.zn = vadd(sg, a0);
+  return r;
+}
+template <class T>
+__device__ __forceinline__ PhiS<T> phis_a2zero(T a0, T a1) {  // a2 = 0
+  PhiS<T> r;
+  const T sg = vmulc(a0, -1.0f / 3.0f);
+  r.p = vfmac(a1, 0.5f, sg);
+  r.m = vfmac(a1, -0.5f, sg);
+  r.zn = vadd(sg, a0);
+  return r;
+}
+template <class T>
+__device__ __forceinline__ PhiS<T> phis_a1zero(T a0, T a2) {  // a1 = 0
+  PhiS<T> r;
+  r.p = r.m = vfmac(a0, -1.0f / 3.0f, a2);
+  r.zn = vadd(r.p, a0);
+  return r;
+}
+template <class T>
+__device__ __forceinline__ PhiS<T> phis_a0only(T a0) {  // a1 = a2 = 0
+  PhiS<T> r;
+  r.p = r.m = vmulc(a0, -1.0f / 3.0f);
+  r.zn = vadd(r.p, a0);
+  return r;
+}
+// The first x slice takes drho = mu000 unscaled (a0 = -drho, folded in).
+template <class T>
+__device__ __forceinline__ PhiS<T> phis_drho(T drho, T a1, T a2) {
+  PhiS<T> r;
+  const T sg = vfmac(drho, 1.0f / 3.0f, a2);
+  r.p = vfmac(a1, 0.5f, sg);
+  r.m = vfmac(a1, -0.5f, sg);
+  r.zn = vsub(sg, drho);
+  return r;
+}
+template <class T>
+__device__ __forceinline__ T projs0(T pl, T zn, T mr) { return vfmac(vadd(pl, mr), -0.5f, zn); }
+template <class T>
+__device__ __forceinline__ T projs1(T pl, T mr) { return vsub(pl, mr); }
+template <class T>
+__device__ __forceinline__ T projs2(T b0, T zn) { return vfmac(b0, -2.0f / 3.0f, zn); }
+
+// App. A collision (as collide_moments) returning the scaled Hermite moments of
+// the passes, A_pqr = s(p) s(q) s(r) mu_pqr, except A.m000, which holds
+// drho = mu000 itself (phis_drho takes it).  With E = (1 - 1/tau) times the
+// non-equilibrium stress after the trace reset, and the factors -2 u, 2 rho u
+// and -4 E that the scaling asks for made once:
+//   A_aa = rho u_a u_a + E_aa,  A_a = 2 rho u_a,  A_ab = (2 rho u_a)(-2 u_b) + (-4 E_ab),
+//   A_aab = (-2 u_b) A_aa + u_a (-4 E_ab),  A_xyz = 8 (rho u u u + E u terms).
+template <bool FORCE, class T>
+__device__ __forceinline__ Mom17T<T> collide_scaled(const StoredT<T>& s, float omega, T fx, T fy,
+                                                    T fz) {
+  const T rho = vadd(s.drho, vset<T>(1.0f));
+  const float om1 = 1.0f - omega;
+  T ux = s.ux, uy = s.uy, uz = s.uz;
+  T mxx = s.nxx, myy = s.nyy, mzz = s.nzz, mxy = s.nxy, mxz = s.nxz, myz = s.nyz;
+  T inv = vset<T>(0.f);
+  if (FORCE) {
+    inv = vrcp(rho);
+    mxx = vfma(fx, ux, mxx);
+    myy = vfma(fy, uy, myy);
+    mzz = vfma(fz, uz, mzz);
+    mxy = vfmac(vfma(fx, uy, vmul(fy, ux)), 0.5f, mxy);
+    mxz = vfmac(vfma(fx, uz, vmul(fz, ux)), 0.5f, mxz);
+    myz = vfmac(vfma(fy, uz, vmul(fz, uy)), 0.5f, myz);
+  }
+  const T s3n = vmulc(vadd(vadd(mxx, myy), mzz), -om1 * (1.0f / 3.0f));
+  T exx = vfmac(mxx, om1, s3n), eyy = vfmac(myy, om1, s3n), ezz = vfmac(mzz, om1, s3n);
+  T exy = vmulc(mxy, -4.0f * om1), exz = vmulc(mxz, -4.0f * om1), eyz = vmulc(myz, -4.0f * om1);
+  if (FORCE) {
+    // E += -F F / (4 rho) (times -4 off the diagonal), u += F / (2 rho)
+    const T q = vmulc(inv, -0.25f);
+    exx = vfma(vmul(q, fx), fx, exx);
+    eyy = vfma(vmul(q, fy), fy, eyy);
+    ezz = vfma(vmul(q, fz), fz, ezz);
+    exy = vfma(vmul(inv, fx), fy, exy);
+    exz = vfma(vmul(inv, fx), fz, exz);
+    eyz = vfma(vmul(inv, fy), fz, eyz);
+    const T h = vmulc(inv, 0.5f);
+    ux = vfma(h, fx, ux);
+    uy = vfma(h, fy, uy);
+    uz = vfma(h, fz, uz);
+  }
+  const T rux = vmul(rho, ux), ruy = vmul(rho, uy), ruz = vmul(rho, uz);
+  Mom17T<T> A;
+  A.m000 = s.drho;
+  A.m200 = vfma(rux, ux, exx);
+  A.m020 = vfma(ruy, uy, eyy);
+  A.m002 = vfma(ruz, uz, ezz);
+  A.m100 = vadd(rux, rux);
+  A.m010 = vadd(ruy, ruy);
+  A.m001 = vadd(ruz, ruz);
+  const T uxn = vmulc(ux, -2.0f), uyn = vmulc(uy, -2.0f), uzn = vmulc(uz, -2.0f);
+  A.m110 = vfma(A.m100, uyn, exy);
+  A.m101 = vfma(A.m100, uzn, exz);
+  A.m011 = vfma(A.m010, uzn, eyz);
+  A.m210 = vfma(uyn, A.m200, vmul(ux, exy));  // xxy
+  A.m120 = vfma(uxn, A.m020, vmul(uy, exy));  // xyy
+  A.m201 = vfma(uzn, A.m200, vmul(ux, exz));  // xxz
+  A.m102 = vfma(uxn, A.m002, vmul(uz, exz));  // xzz
+  A.m021 = vfma(uzn, A.m020, vmul(uy, eyz));  // yyz
+  A.m012 = vfma(uyn, A.m002, vmul(uz, eyz));  // yzz
+  A.m111 = vfma(vmul(A.m100, uyn), uzn, vfma(exy, uzn, vfma(exz, uyn, vmul(eyz, uxn))));
+#ifdef MELBM_HERMITE_XYZ_LITERAL
+  A.m111 = vmulc(A.m111, 0.5f);  // the printed 1/(2 c_s^6) on xyz halves its moment
+#endif
+  return A;
+}
+
+// closure19 in the scaling of the passes (A.m000 = drho unscaled).
+template <class T>
+__device__ __forceinline__ Closure19T<T> closure19_scaled(const Mom17T<T>& A) {
+  Closure19T<T> E;
+  E.m220 = vmulc(A.m002, 1.0f / 6.0f);
+  E.m202 = vmulc(A.m020, 1.0f / 6.0f);
+  E.m022 = vmulc(A.m200, 1.0f / 6.0f);
+  E.m211 = vmulc(A.m011, 1.0f / 3.0f);
+  E.m121 = vmulc(A.m101, 1.0f / 3.0f);
+  E.m112 = vmulc(A.m110, 1.0f / 3.0f);
+  E.m221 = vfmac(A.m001, -1.0f / 9.0f, vmulc(vadd(A.m201, A.m021), 1.0f / 3.0f));
+  E.m212 = vfmac(A.m010, -1.0f / 9.0f, vmulc(vadd(A.m210, A.m012), 1.0f / 3.0f));
+  E.m122 = vfmac(A.m100, -1.0f / 9.0f, vmulc(vadd(A.m120, A.m102), 1.0f / 3.0f));
+  E.m222 = vfmac(A.m000, -1.0f / 27.0f,
+                 vmulc(vadd(vadd(A.m200, A.m020), A.m002), -1.0f / 18.0f));
+  return E;
+}
+
+// x-pass populations of slice K (halo-buffer order: (q', r') = (0,0) (1,0) (2,0)
+// (0,1) (1,1) (2,1) (0,2) (1,2), and (2,2) on D3Q19) from the scaled moments.
+template <bool Q19, int K>
+__device__ __forceinline__ PhiS<float2> xslice(const Mom17T<float2>& A, const Closure19T<float2>& E) {
+  if constexpr (K == 0) return phis_drho(A.m000, A.m100, A.m200);
+  else if constexpr (K == 1) return phis(A.m010, A.m110, A.m210);
+  else if constexpr (K == 2) {
+    if constexpr (Q19) return phis(A.m020, A.m120, E.m220);
+    else return phis_a2zero(A.m020, A.m120);
+  } else if constexpr (K == 3) return phis(A.m001, A.m101, A.m201);
+  else if constexpr (K == 4) {
+    if constexpr (Q19) return phis_a1zero(A.m011, E.m211);  // mu_111 = 0
+    else return phis_a2zero(A.m011, A.m111);
+  } else if constexpr (K == 5) {
+    if constexpr (Q19) return phis(A.m021, E.m121, E.m221);
+    else return phis_a0only(A.m021);
+  } else if constexpr (K == 6) {
+    if constexpr (Q19) return phis(A.m002, A.m102, E.m202);
+    else return phis_a2zero(A.m002, A.m102);
+  } else if constexpr (K == 7) {
+    if constexpr (Q19) return phis(A.m012, E.m112, E.m212);
+    else return phis_a0only(A.m012);
+  } else {
+    return phis(E.m022, E.m122, E.m222);
+  }
+}
+
+// Stored variables from the scaled streamed moments M_pqr = s(p) s(q) s(r) m_pqr
+// (finish_moments in that scaling).  The result holds -drho in .drho and
+// -4 n_ab in .nxy, .nxz, .nyz; the encoders take the scale in their constants.
+template <bool FORCE, class T>
+__device__ __forceinline__ StoredT<T> finish_scaled(T M000, T M100, T M010, T M001, T M200, T M020,
+                                                    T M002, T M110, T M101, T M011, T fx, T fy,
+                                                    T fz) {
+  StoredT<T> o;
+  o.drho = M000;
+  const T inv2 = vrcp(vfmac(M000, -2.0f, vset<T>(2.0f)));  // 1 / (2 rho')
+  T jx = M100, jy = M010, jz = M001;                       // 2 rho' u'
+  if (FORCE) {
+    jx = vadd(jx, fx);
+    jy = vadd(jy, fy);
+    jz = vadd(jz, fz);
+  }
+  o.ux = vmul(jx, inv2);
+  o.uy = vmul(jy, inv2);
+  o.uz = vmul(jz, inv2);
+  const T njx = vmulc(jx, -0.5f), njy = vmulc(jy, -0.5f), njz = vmulc(jz, -0.5f);  // exact
+  o.nxx = vfma(njx, o.ux, M200);
+  o.nyy = vfma(njy, o.uy, M020);
+  o.nzz = vfma(njz, o.uz, M002);
+  const T pjx = vadd(jx, jx), pjy = vadd(jy, jy);  // 4 rho' u'
+  o.nxy = vfma(pjx, o.uy, M110);
+  o.nxz = vfma(pjx, o.uz, M101);
+  o.nyz = vfma(pjy, o.uz, M011);
+  return o;
+}
+
 // ----------------------------------------------------------------- plane-pair I/O
 template <int STORAGE> struct RawPair;
 template <> struct RawPair<ST_Q16> { uint32_t a[5], b[5]; };
 template <> struct RawPair<ST_F32> { float a[10], b[10]; };
 
-// FP32 word planes are addressed through per-word base pointers held in the
-// kernel parameters (uniform), so each access adds one per-thread offset; the
-// five 16-bit planes are addressed as base + k N (each form measured the faster
-// one for its storage).
+// Word planes are addressed through per-plane base pointers held in the kernel
+// parameters (uniform), so each access adds one per-thread offset (64-bit offsets
+// for the FP32 planes, 32-bit cell offsets for the 16-bit ones).
 using WordPlanes = const uint32_t* const*;
 
-__device__ __forceinline__ void load_pair(RawPair<ST_Q16>& r, const void* buf, size_t N, size_t na,
-                                          size_t nb) {
-  const uint32_t* p = static_cast<const uint32_t*>(buf);
+__device__ __forceinline__ void load_pair_w(RawPair<ST_Q16>& r, WordPlanes w, uint32_t na, uint32_t nb) {
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    r.a[k] = __ldg(p + k * N + na);
-    r.b[k] = __ldg(p + k * N + nb);
+    r.a[k] = __ldg(w[k] + na);
+    r.b[k] = __ldg(w[k] + nb);
   }
 }
 __device__ __forceinline__ void load_pair(RawPair<ST_F32>& r, WordPlanes w, size_t na, size_t nb) {
@@ -226,61 +457,61 @@ __device__ __forceinline__ void store_pair_f32(OutPlanes w, size_t na, size_t nb
 }
 
 template <bool RT>
-__device__ __forceinline__ void store_pair_q16(void* buf, size_t N, size_t na, size_t nb,
-                                               const StoredT<float2>& o, bool sa, bool sb, uint32_t x,
-                                               uint32_t y, uint32_t za, uint32_t zb, uint32_t t,
-                                               uint32_t seed, const QGrids* q) {
-  const DitherBits ha = pcg4d(x, y, za, t, seed);
-  const DitherBits hb = pcg4d(x, y, zb, t, seed);
-  float2 d[10];
+__device__ __forceinline__ void store_pair_q16_w(uint32_t* const* w, uint32_t na, uint32_t nb,
+                                                 const StoredT<float2>& o, bool sa, bool sb,
+                                                 const DitherBits& ha, const DitherBits& hb,
+                                                 const QGrids* q) {
+  float2 d[10];  // 1 + the dither of each component
 #pragma unroll
-  for (int k = 0; k < 10; ++k)
-    d[k] = dither_value(make_float2(dither_magic(ha, k), dither_magic(hb, k)), k);
+  for (int k = 0; k < 10; ++k) d[k] = make_float2(dither_one_plus(ha, k), dither_one_plus(hb, k));
+  // o holds -drho and -4 n_ab (finish_scaled): their grid factors K carry
+  // -1 and -1/4, power-of-two factors that leave every code unchanged
   uint2 e0, e1, e2, e3, e4, e5, e6, e7, e8, e9;
   if constexpr (RT) {
-    e0 = qg_encode_codes(q->g[0], o.drho, d[0]), e1 = qg_encode_codes(q->g[1], o.ux, d[1]);
-    e2 = qg_encode_codes(q->g[1], o.uy, d[2]), e3 = qg_encode_codes(q->g[1], o.uz, d[3]);
-    e4 = qg_encode_codes(q->g[2], o.nxx, d[4]), e5 = qg_encode_codes(q->g[2], o.nyy, d[5]);
-    e6 = qg_encode_codes(q->g[2], o.nzz, d[6]), e7 = qg_encode_codes(q->g[2], o.nxy, d[7]);
-    e8 = qg_encode_codes(q->g[2], o.nxz, d[8]), e9 = qg_encode_codes(q->g[2], o.nyz, d[9]);
+    e0 = qg_encode_codes1(q->g[0], o.drho, d[0], -1.0f), e1 = qg_encode_codes1(q->g[1], o.ux, d[1]);
+    e2 = qg_encode_codes1(q->g[1], o.uy, d[2]), e3 = qg_encode_codes1(q->g[1], o.uz, d[3]);
+    e4 = qg_encode_codes1(q->g[2], o.nxx, d[4]), e5 = qg_encode_codes1(q->g[2], o.nyy, d[5]);
+    e6 = qg_encode_codes1(q->g[2], o.nzz, d[6]);
+    e7 = qg_encode_codes1(q->g[2], o.nxy, d[7], -0.25f);
+    e8 = qg_encode_codes1(q->g[2], o.nxz, d[8], -0.25f);
+    e9 = qg_encode_codes1(q->g[2], o.nyz, d[9], -0.25f);
   } else {
-    e0 = q_encode_codes<0>(o.drho, d[0]), e1 = q_encode_codes<1>(o.ux, d[1]);
-    e2 = q_encode_codes<1>(o.uy, d[2]), e3 = q_encode_codes<1>(o.uz, d[3]);
-    e4 = q_encode_codes<2>(o.nxx, d[4]), e5 = q_encode_codes<2>(o.nyy, d[5]);
-    e6 = q_encode_codes<2>(o.nzz, d[6]), e7 = q_encode_codes<2>(o.nxy, d[7]);
-    e8 = q_encode_codes<2>(o.nxz, d[8]), e9 = q_encode_codes<2>(o.nyz, d[9]);
+    e0 = q_encode_codes1<0, -1>(o.drho, d[0]), e1 = q_encode_codes1<1>(o.ux, d[1]);
+    e2 = q_encode_codes1<1>(o.uy, d[2]), e3 = q_encode_codes1<1>(o.uz, d[3]);
+    e4 = q_encode_codes1<2>(o.nxx, d[4]), e5 = q_encode_codes1<2>(o.nyy, d[5]);
+    e6 = q_encode_codes1<2>(o.nzz, d[6]), e7 = q_encode_codes1<2, -4>(o.nxy, d[7]);
+    e8 = q_encode_codes1<2, -4>(o.nxz, d[8]), e9 = q_encode_codes1<2, -4>(o.nyz, d[9]);
   }
-  uint32_t* p = static_cast<uint32_t*>(buf);
   if constexpr (RT) {
     const uint32_t qr = q->g[1].qmax, qs = q->g[2].qmax;
     if (sa) {
-      p[na] = qg_clamp_word(q_pack(e0.x, e1.x), qr);
-      p[N + na] = qg_clamp_word(q_pack(e2.x, e3.x), qr);
-      p[2 * N + na] = qg_clamp_word(q_pack(e4.x, e5.x), qs);
-      p[3 * N + na] = qg_clamp_word(q_pack(e6.x, e7.x), qs);
-      p[4 * N + na] = qg_clamp_word(q_pack(e8.x, e9.x), qs);
+      w[0][na] = qg_clamp_word(q_pack(e0.x, e1.x), qr);
+      w[1][na] = qg_clamp_word(q_pack(e2.x, e3.x), qr);
+      w[2][na] = qg_clamp_word(q_pack(e4.x, e5.x), qs);
+      w[3][na] = qg_clamp_word(q_pack(e6.x, e7.x), qs);
+      w[4][na] = qg_clamp_word(q_pack(e8.x, e9.x), qs);
     }
     if (sb) {
-      p[nb] = qg_clamp_word(q_pack(e0.y, e1.y), qr);
-      p[N + nb] = qg_clamp_word(q_pack(e2.y, e3.y), qr);
-      p[2 * N + nb] = qg_clamp_word(q_pack(e4.y, e5.y), qs);
-      p[3 * N + nb] = qg_clamp_word(q_pack(e6.y, e7.y), qs);
-      p[4 * N + nb] = qg_clamp_word(q_pack(e8.y, e9.y), qs);
+      w[0][nb] = qg_clamp_word(q_pack(e0.y, e1.y), qr);
+      w[1][nb] = qg_clamp_word(q_pack(e2.y, e3.y), qr);
+      w[2][nb] = qg_clamp_word(q_pack(e4.y, e5.y), qs);
+      w[3][nb] = qg_clamp_word(q_pack(e6.y, e7.y), qs);
+      w[4][nb] = qg_clamp_word(q_pack(e8.y, e9.y), qs);
     }
   } else {
     if (sa) {
-      p[na] = q_pack(e0.x, e1.x);
-      p[N + na] = q_pack(e2.x, e3.x);
-      p[2 * N + na] = q_pack(e4.x, e5.x);
-      p[3 * N + na] = q_pack(e6.x, e7.x);
-      p[4 * N + na] = q_pack(e8.x, e9.x);
+      w[0][na] = q_pack(e0.x, e1.x);
+      w[1][na] = q_pack(e2.x, e3.x);
+      w[2][na] = q_pack(e4.x, e5.x);
+      w[3][na] = q_pack(e6.x, e7.x);
+      w[4][na] = q_pack(e8.x, e9.x);
     }
     if (sb) {
-      p[nb] = q_pack(e0.y, e1.y);
-      p[N + nb] = q_pack(e2.y, e3.y);
-      p[2 * N + nb] = q_pack(e4.y, e5.y);
-      p[3 * N + nb] = q_pack(e6.y, e7.y);
-      p[4 * N + nb] = q_pack(e8.y, e9.y);
+      w[0][nb] = q_pack(e0.y, e1.y);
+      w[1][nb] = q_pack(e2.y, e3.y);
+      w[2][nb] = q_pack(e4.y, e5.y);
+      w[3][nb] = q_pack(e6.y, e7.y);
+      w[4][nb] = q_pack(e8.y, e9.y);
     }
   }
 }
@@ -320,11 +551,14 @@ __device__ __forceinline__ float2 shfl_idx2(float2 v, int src) {
 
 // ----------------------------------------------------------------- kernel
 // The y-pass slices are indexed s = 3 p + r' (p: x-order, r': input z-order).
-template <int STORAGE, bool FORCE, bool RT, bool Q19 = false>
+#define MELBM_PRAGMA_STR(x) #x
+#define MELBM_PRAGMA_UNROLL(n) _Pragma(MELBM_PRAGMA_STR(unroll n))
+
+template <int STORAGE, bool FORCE, bool RT, bool Q19 = false, bool BND = false>
 __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelParams<STORAGE, RT> P) {
   // the input side reads 16-bit codes in the mixed scheme (post-collision moments)
   constexpr int IN = STORAGE == ST_MIXED ? ST_Q16 : STORAGE;
-  using HS = HaloStage<IN, FORCE, Q19>;
+  using HS = HaloStage<IN, FORCE, Q19, BND>;
   constexpr int NSXL = nsx<Q19>();
   constexpr int HALO_BUF = halo_buf<Q19>();
   auto decode = [&](const RawPair<IN>& r) {
@@ -359,8 +593,31 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
   const bool halo_warp = (row == 0);  // warp-uniform
   const int hrow = lane % FY, side = (lane / FY) & 1;
   const bool halo_lane = lane < 2 * FY;
-  const size_t hcol =
-      size_t(wrapi(side ? x0 + FX : x0 - 1, nx)) + size_t(nx) * wrapi(y0 + hrow, ny);
+  const int hx = wrapi(side ? x0 + FX : x0 - 1, nx), hy = wrapi(y0 + hrow, ny);
+  const size_t hcol = size_t(hx) + size_t(nx) * hy;
+
+  // Solid cells (BND kernels) enter the passes with zero post-collision moments
+  // about the rest state, so a FLUID_BOUNDARY cell receives nothing through its
+  // solid links and the boundary kernel adds the bounced populations from the
+  // cell's own state: apply_keep multiplies a pair's state and force by (1, 1)
+  // for two fluid cells, with 0 in place of a solid one (0 * value is exactly 0).
+  auto apply_keep = [&](StoredT<float2>& v, float2& fx, float2& fy, float2& fz, float2 k) {
+    v.drho = vmul(v.drho, k);
+    v.ux = vmul(v.ux, k);
+    v.uy = vmul(v.uy, k);
+    v.uz = vmul(v.uz, k);
+    v.nxx = vmul(v.nxx, k);
+    v.nyy = vmul(v.nyy, k);
+    v.nzz = vmul(v.nzz, k);
+    v.nxy = vmul(v.nxy, k);
+    v.nxz = vmul(v.nxz, k);
+    v.nyz = vmul(v.nyz, k);
+    if (FORCE) {
+      fx = vmul(fx, k);
+      fy = vmul(fy, k);
+      fz = vmul(fz, k);
+    }
+  };
 
   // z-march state of the six (p, q) slices: phi+ of the previous pair's two
   // planes and phi0 of its second plane
@@ -371,7 +628,6 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     zP[k] = make_float2(0.f, 0.f);
     zZ[k] = 0.f;
   }
-  float fprev[3] = {0.f, 0.f, 0.f};
 
   // Issue the staging of the halo pair (za, za + 1) into staging buffer b.  The
   // pair with index j = (za - z0 + 1) / 2 uses halo buffer j & 1, written one
@@ -410,12 +666,19 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
         }
       }
     }
+    if constexpr (BND) {
+      const int e = 2 * HS::W + (FORCE ? 6 : 0);
+      const uint32_t wh = uint32_t(hx >> 5) + uint32_t(P.ntx) * uint32_t(hy);
+      const uint32_t rw = uint32_t(P.ntx) * uint32_t(ny);
+      cp_async4(d + e * 32 * HS::CHUNK, P.cls_solid + wh + rw * uint32_t(wz(za)));
+      cp_async4(d + (e + 1) * 32 * HS::CHUNK, P.cls_solid + wh + rw * uint32_t(wz(za + 1)));
+    }
     cp_async_commit();
   };
   // Write the x-pass populations of the pair staged in buffer b (its copies have
   // completed) into halo buffer hbuf, laid out [row][slice] as
   // {phi+ of column x0-1, phi- of column x0+32}.
-  auto halo_finish = [&](int b, int hbuf) {
+  auto halo_finish = [&](int b, int hbuf, int hz) {
     const uint32_t* d = stg + b * HS::BUF_WORDS + lane * HS::CHUNK + (chunk16 ? int(hcol & 3) : 0);
     RawPair<IN> hr;
 #pragma unroll
@@ -423,7 +686,8 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
       set_word<IN>(hr, 0, w, d[(2 * w) * 32 * HS::CHUNK]);
       set_word<IN>(hr, 1, w, d[(2 * w + 1) * 32 * HS::CHUNK]);
     }
-    const StoredT<float2> hs = decode(hr);
+    StoredT<float2> hs = decode(hr);
+    (void)hz;
     float2 hfx = make_float2(0.f, 0.f), hfy = hfx, hfz = hfx;
     if (FORCE) {
       const float* sf = reinterpret_cast<const float*>(d) + 2 * HS::W * 32 * HS::CHUNK;
@@ -431,44 +695,37 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
       hfy = make_float2(sf[2 * 32 * HS::CHUNK], sf[3 * 32 * HS::CHUNK]);
       hfz = make_float2(sf[4 * 32 * HS::CHUNK], sf[5 * 32 * HS::CHUNK]);
     }
-    const Mom17T<float2> H = collide_moments<FORCE>(hs, omega, hfx, hfy, hfz);
-    const float2 zero = make_float2(0.f, 0.f);
-    float2 mu[NSXL][3];
-    if constexpr (Q19) {
-      const Closure19T<float2> E = closure19(H);
-      const float2 m[NSXL][3] = {{H.m000, H.m100, H.m200}, {H.m010, H.m110, H.m210},
-                                 {H.m020, H.m120, E.m220}, {H.m001, H.m101, H.m201},
-                                 {H.m011, zero, E.m211},   {H.m021, E.m121, E.m221},
-                                 {H.m002, H.m102, E.m202}, {H.m012, E.m112, E.m212},
-                                 {E.m022, E.m122, E.m222}};
-#pragma unroll
-      for (int k = 0; k < NSXL; ++k)
-        for (int j = 0; j < 3; ++j) mu[k][j] = m[k][j];
-    } else {
-      const float2 m[NSX][3] = {{H.m000, H.m100, H.m200}, {H.m010, H.m110, H.m210},
-                                {H.m020, H.m120, zero},   {H.m001, H.m101, H.m201},
-                                {H.m011, H.m111, zero},   {H.m021, zero, zero},
-                                {H.m002, H.m102, zero},   {H.m012, zero, zero}};
-#pragma unroll
-      for (int k = 0; k < NSX; ++k)
-        for (int j = 0; j < 3; ++j) mu[k][j] = m[k][j];
+    if constexpr (BND) {  // the staged solid words of the two planes
+      const uint32_t* dw = stg + b * HS::BUF_WORDS + lane * HS::CHUNK +
+                           (2 * HS::W + (FORCE ? 6 : 0)) * 32 * HS::CHUNK;
+      const uint32_t sa = dw[0], sb = dw[32 * HS::CHUNK];
+      apply_keep(hs, hfx, hfy, hfz,
+                 make_float2(((sa >> (hx & 31)) & 1u) ? 0.f : 1.f, ((sb >> (hx & 31)) & 1u) ? 0.f : 1.f));
     }
+    const Mom17T<float2> H = collide_scaled<FORCE>(hs, omega, hfx, hfy, hfz);
+    Closure19T<float2> E;
+    if constexpr (Q19) E = closure19_scaled(H);
     float2* dst = hb + hbuf * HALO_BUF + hrow * NSXL * 2 + side;
-#pragma unroll
-    for (int k = 0; k < NSXL; ++k) {
-      const PhiT<float2> ph = phi3(mu[k][0], mu[k][1], mu[k][2]);
+    auto put = [&](int k, const PhiS<float2>& ph) {
       if (halo_lane) dst[2 * k] = side ? ph.m : ph.p;
-    }
+    };
+    put(0, xslice<Q19, 0>(H, E));
+    put(1, xslice<Q19, 1>(H, E));
+    put(2, xslice<Q19, 2>(H, E));
+    put(3, xslice<Q19, 3>(H, E));
+    put(4, xslice<Q19, 4>(H, E));
+    put(5, xslice<Q19, 5>(H, E));
+    put(6, xslice<Q19, 6>(H, E));
+    put(7, xslice<Q19, 7>(H, E));
+    if constexpr (Q19) put(8, xslice<Q19, 8>(H, E));
   };
 
   RawPair<IN> raw;
   if constexpr (IN == ST_Q16)
-    load_pair(raw, P.in, N, col + plane * wz(z0 - 1), col + plane * wz(z0));
+    load_pair_w(raw, P.qin, uint32_t(col) + uint32_t(plane) * uint32_t(wz(z0 - 1)),
+                uint32_t(col) + uint32_t(plane) * uint32_t(wz(z0)));
   else
     load_pair(raw, P.in_w, col + plane * wz(z0 - 1), col + plane * wz(z0));
-  // Staging schedule (pair j = (zz - z0 + 1) / 2, window j = the work between the
-  // barriers of pairs j - 1 and j): pair j + 2 is issued at the start of window j
-  // into staging buffer j & 1, and pair j + 1 is consumed at its end.
   if (halo_warp) {
     halo_issue(z0 - 1, 0);
     if (z0 + 1 <= z1) {
@@ -477,23 +734,29 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     } else {
       cp_async_wait<0>();
     }
-    halo_finish(0, 0);
+    halo_finish(0, 0, z0 - 1);
   }
   __syncthreads();
-  int parity = 0;
-  // FP32 storage without force: two plane pairs per loop trip (the loop-carried
-  // z-pass state then alternates registers instead of being copied; measured
-  // +2.5%); the other kernels stay rolled (unrolled they spill, and the 16-bit
-  // one runs 2% slower).
-#define MELBM_PRAGMA_STR(x) #x
-#define MELBM_PRAGMA_UNROLL(n) _Pragma(MELBM_PRAGMA_STR(unroll n))
-  MELBM_PRAGMA_UNROLL(MELBM_FLUID_ZUNROLL)
-  for (int zz = z0 - 1; zz <= z1; zz += 2, parity ^= 1) {
-    const bool halo_next = halo_warp && zz + 2 <= z1;
-    const bool halo_ahead = halo_warp && zz + 4 <= z1;
-    if (halo_ahead) halo_issue(zz + 4, parity);
-    const StoredT<float2> s = decode(raw);
-    float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
+
+  const float2 zero = make_float2(0.f, 0.f);
+  float2 yz0[NSY];  // phi_0 of the y pass of this thread's row, pair in flight
+
+  // ---------------- pre(pair at zz): decode, prefetch the next pair (or re-read
+  // this one when there is none), collide, x pass, y-pass populations -> buffer parity
+  // BND: the solid words of the pair that pre() takes next (this lane's cells) and
+  // the FLUID_BOUNDARY words of the output planes of the next two post() calls
+  // (the tile's words), loaded one pair ahead like the state
+  const uint32_t cls_rw = uint32_t(P.ntx) * uint32_t(ny);
+  const uint32_t cls_own = uint32_t(xw >> 5) + uint32_t(P.ntx) * uint32_t(yw);
+  const uint32_t cls_tile = uint32_t(blockIdx.x) + uint32_t(P.ntx) * uint32_t(yw);
+  uint32_t sw0 = 0, sw1 = 0, fbA0 = 0, fbA1 = 0, fbB0 = 0, fbB1 = 0;
+  if constexpr (BND) {
+    sw0 = __ldg(P.cls_solid + cls_own + cls_rw * uint32_t(wz(z0 - 1)));
+    sw1 = __ldg(P.cls_solid + cls_own + cls_rw * uint32_t(wz(z0)));
+  }
+  auto pre = [&](int zz, int parity, float2& fx, float2& fy, float2& fz, bool next) {
+    StoredT<float2> s = decode(raw);
+    fx = fy = fz = zero;
     if (FORCE) {
       const size_t na = col + plane * wz(zz), nb = col + plane * wz(zz + 1);
       if constexpr (IN == ST_Q16) {
@@ -506,84 +769,86 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
         fz = make_float2(__uint_as_float(__ldg(P.f_w[2] + na)), __uint_as_float(__ldg(P.f_w[2] + nb)));
       }
     }
-    if (zz + 2 <= z1)  // prefetch the next pair
     {
+      const int zn = next ? zz + 2 : zz;
       if constexpr (IN == ST_Q16)
-        load_pair(raw, P.in, N, col + plane * wz(zz + 2), col + plane * wz(zz + 3));
+        load_pair_w(raw, P.qin, uint32_t(col) + uint32_t(plane) * uint32_t(wz(zn)),
+                    uint32_t(col) + uint32_t(plane) * uint32_t(wz(zn + 1)));
       else
-        load_pair(raw, P.in_w, col + plane * wz(zz + 2), col + plane * wz(zz + 3));
+        load_pair(raw, P.in_w, col + plane * wz(zn), col + plane * wz(zn + 1));
     }
-    const Mom17T<float2> A = collide_moments<FORCE>(s, omega, fx, fy, fz);
-
-    // ---------------- x pass on slices (q', r'), then the y-pass populations of
-    // the slices (p, r') as soon as their three inputs X[p][0..2][r'] exist
-    // (grouped by r' so that only nine X values are live at a time)
-    const float2 zero = make_float2(0.f, 0.f);
+    if constexpr (BND) {
+      const float2 k = make_float2(((sw0 >> (xw & 31)) & 1u) ? 0.f : 1.f,
+                                   ((sw1 >> (xw & 31)) & 1u) ? 0.f : 1.f);
+      apply_keep(s, fx, fy, fz, k);
+      fbA0 = fbB0;
+      fbA1 = fbB1;
+      sw0 = __ldg(P.cls_solid + cls_own + cls_rw * uint32_t(wz(zz + 2)));
+      sw1 = __ldg(P.cls_solid + cls_own + cls_rw * uint32_t(wz(zz + 3)));
+      fbB0 = __ldg(P.cls_fb + cls_tile + cls_rw * uint32_t(wz(zz + 1)));
+      fbB1 = __ldg(P.cls_fb + cls_tile + cls_rw * uint32_t(wz(zz + 2)));
+    }
+    const Mom17T<float2> A = collide_scaled<FORCE>(s, omega, fx, fy, fz);
+    Closure19T<float2> E;
+    if constexpr (Q19) E = closure19_scaled(A);
     float2* sp = sm2 + parity * SM_BUF;
-    float2 yz0[NSY];
     float2 X[3][3];  // X[p][q'] of the current r'
     const float4* hbp = reinterpret_cast<const float4*>(hb + parity * HALO_BUF) + row * NSXL;
-    int xs = 0;  // x-pass slice index (halo buffer order)
-#define MELBM_XPASS(Q, A0, A1, A2)                                      \
+#define MELBM_XPASS(K, Q)                                               \
   {                                                                     \
-    const PhiT<float2> ph = phi3(A0, A1, A2);                           \
-    const float4 h = hbp[xs];                                           \
+    const PhiS<float2> ph = xslice<Q19, K>(A, E);                       \
+    const float4 h = hbp[K];                                            \
     float2 pl = shfl_idx2(ph.p, src_up);                                \
     float2 mr = shfl_idx2(ph.m, src_dn);                                \
     if (lane == 0) pl = make_float2(h.x, h.y);                          \
     if (lane == FX - 1) mr = make_float2(h.z, h.w);                     \
-    X[0][Q] = proj0(pl, ph.z, mr);                                      \
-    X[1][Q] = proj1(pl, mr);                                            \
-    X[2][Q] = proj2(pl, mr, X[0][Q]);                                   \
-    ++xs;                                                               \
+    X[0][Q] = projs0(pl, ph.zn, mr);                                    \
+    X[1][Q] = projs1(pl, mr);                                           \
+    X[2][Q] = projs2(X[0][Q], ph.zn);                                   \
   }
-#define MELBM_YPHI(R)                                                   \
+#define MELBM_YPHI(R, PH)                                               \
   _Pragma("unroll") for (int p = 0; p < 3; ++p) {                       \
-    const PhiT<float2> ph = phi3(X[p][0], X[p][1], X[p][2]);            \
+    const PhiS<float2> ph = PH;                                         \
     const int s_ = 3 * p + (R);                                         \
     sp[(s_ * FY + row) * FX + lane] = ph.p;                             \
     sp[((NSY + s_) * FY + row) * FX + lane] = ph.m;                     \
-    yz0[s_] = ph.z;                                                     \
+    yz0[s_] = ph.zn;                                                    \
   }
+    MELBM_XPASS(0, 0)  // r' = 0
+    MELBM_XPASS(1, 1)
+    MELBM_XPASS(2, 2)
+    MELBM_YPHI(0, phis(X[p][0], X[p][1], X[p][2]))
+    MELBM_XPASS(3, 0)  // r' = 1
+    MELBM_XPASS(4, 1)
+    MELBM_XPASS(5, 2)
+    MELBM_YPHI(1, phis(X[p][0], X[p][1], X[p][2]))
+    MELBM_XPASS(6, 0)  // r' = 2
+    MELBM_XPASS(7, 1)
     if constexpr (Q19) {
-      const Closure19T<float2> E = closure19(A);
-      MELBM_XPASS(0, A.m000, A.m100, A.m200)  // r' = 0
-      MELBM_XPASS(1, A.m010, A.m110, A.m210)
-      MELBM_XPASS(2, A.m020, A.m120, E.m220)
-      MELBM_YPHI(0)
-      MELBM_XPASS(0, A.m001, A.m101, A.m201)  // r' = 1; mu_111 = 0
-      MELBM_XPASS(1, A.m011, zero, E.m211)
-      MELBM_XPASS(2, A.m021, E.m121, E.m221)
-      MELBM_YPHI(1)
-      MELBM_XPASS(0, A.m002, A.m102, E.m202)  // r' = 2
-      MELBM_XPASS(1, A.m012, E.m112, E.m212)
-      MELBM_XPASS(2, E.m022, E.m122, E.m222)
-      MELBM_YPHI(2)
+      MELBM_XPASS(8, 2)
+      MELBM_YPHI(2, phis(X[p][0], X[p][1], X[p][2]))
     } else {
-      MELBM_XPASS(0, A.m000, A.m100, A.m200)  // r' = 0
-      MELBM_XPASS(1, A.m010, A.m110, A.m210)
-      MELBM_XPASS(2, A.m020, A.m120, zero)
-      MELBM_YPHI(0)
-      MELBM_XPASS(0, A.m001, A.m101, A.m201)  // r' = 1
-      MELBM_XPASS(1, A.m011, A.m111, zero)
-      MELBM_XPASS(2, A.m021, zero, zero)
-      MELBM_YPHI(1)
-      MELBM_XPASS(0, A.m002, A.m102, zero)    // r' = 2; (q', r') = (2, 2) has no input
-      MELBM_XPASS(1, A.m012, zero, zero)
-      X[0][2] = X[1][2] = X[2][2] = zero;
-      MELBM_YPHI(2)
+      // (q', r') = (2, 2) carries no D3Q27 moment
+      MELBM_YPHI(2, phis_a2zero(X[p][0], X[p][1]))
     }
 #undef MELBM_XPASS
 #undef MELBM_YPHI
-    if (halo_next) {
-      if (halo_ahead) cp_async_wait<1>();
-      else cp_async_wait<0>();
-      halo_finish(parity ^ 1, parity ^ 1);
-    }
-    __syncthreads();
-    if (!mid_row) continue;
+  };
 
-    // ---------------- y pass, part 2: pull and project -> Y[p][q][r'], q <= 2 - p
+  // ---------------- post(pair at zz): y pass from buffer parity, z pass, and the
+  // store of planes (zz - 1, zz) (skipped for the first pair of the chunk)
+  auto post = [&](int zz, int parity, float2 ox, float2 oy, float2 oz, bool store) {
+    const int za = zz - 1, zb = zz;
+    // the dither of the two output planes first: integer work that does not
+    // depend on the arithmetic below, so the scheduler can interleave the two
+    DitherBits ha, hb2;
+    if constexpr (STORAGE == ST_Q16) {
+      if (store) {
+        ha = pcg4d(uint32_t(xw), uint32_t(yw), uint32_t(za), P.t_out, P.seed);
+        hb2 = pcg4d(uint32_t(xw), uint32_t(yw), uint32_t(zb), P.t_out, P.seed);
+      }
+    }
+    const float2* sp = sm2 + parity * SM_BUF;
     float2 Y[3][3][3];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
@@ -592,64 +857,153 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
         const int s_ = 3 * p + r;
         const float2 pl = sp[(s_ * FY + row - 1) * FX + lane];
         const float2 mr = sp[((NSY + s_) * FY + row + 1) * FX + lane];
-        Y[p][0][r] = proj0(pl, yz0[s_], mr);
-        if (p <= 1) Y[p][1][r] = proj1(pl, mr);
-        if (p == 0) Y[p][2][r] = proj2(pl, mr, Y[p][0][r]);
+        Y[p][0][r] = projs0(pl, yz0[s_], mr);
+        if (p <= 1) Y[p][1][r] = projs1(pl, mr);
+        if (p == 0) Y[p][2][r] = projs2(Y[p][0][r], yz0[s_]);
       }
-
-    // ---------------- z pass for slices (p, q): planes (zz, zz+1) in, (zz-1, zz) out
+    // z pass: planes (zz, zz + 1) in, (zz - 1, zz) out; the Zn of the output
+    // pair straddles two input pairs, so the terms that use it are taken per half
     const int PQ[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
-    float2 M[6][3];
+    float2 M[6][3];  // scaled streamed moments M_pqr of the output pair
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const int p = PQ[k][0], q = PQ[k][1];
-      const PhiT<float2> ph = phi3(Y[p][q][0], Y[p][q][1], Y[p][q][2]);
-      // out(zz-1) = proj(phi+(zz-2), phi0(zz-1), phi-(zz)); out(zz) = proj(phi+(zz-1), phi0(zz), phi-(zz+1))
-      // (phi_0 of the output pair straddles two input pairs: its sum with pl + mr
-      // is taken per half, so no register pair has to be assembled for it)
+      const PhiS<float2> ph = phis(Y[p][q][0], Y[p][q][1], Y[p][q][2]);
       const float2 pl = zP[k];
       const float2 mr = ph.m;
       const float2 lr = vadd(pl, mr);
-      M[k][0] = make_float2(__fadd_rn(lr.x, zZ[k]), __fadd_rn(lr.y, ph.z.x));
-      M[k][1] = proj1(pl, mr);
-      M[k][2] = vfmac(M[k][0], -1.0f / 3.0f, lr);
+      M[k][0] = make_float2(__fmaf_rn(lr.x, -0.5f, zZ[k]), __fmaf_rn(lr.y, -0.5f, ph.zn.x));
+      M[k][1] = projs1(pl, mr);
+      M[k][2] = make_float2(__fmaf_rn(M[k][0].x, -2.0f / 3.0f, zZ[k]),
+                            __fmaf_rn(M[k][0].y, -2.0f / 3.0f, ph.zn.x));
       zP[k] = ph.p;
-      zZ[k] = ph.z.y;
+      zZ[k] = ph.zn.y;
     }
-    if (zz - 1 >= z0) {
-      float2 ox = zero, oy = zero, oz = zero;
-      if (FORCE) {
-        ox = make_float2(fprev[0], fx.x);
-        oy = make_float2(fprev[1], fy.x);
-        oz = make_float2(fprev[2], fz.x);
+    if (!store) return;
+    if constexpr (BND) {
+      // the raw sums of this pair's FLUID_BOUNDARY cells (their solid links
+      // brought nothing) go to the side table for the boundary kernel
+      const uint32_t wa = cls_tile + cls_rw * uint32_t(za);
+      const uint32_t wb = cls_tile + cls_rw * uint32_t(zb < nz ? zb : 0);
+      const uint32_t fa = fbA0, fb = zb < z1 ? fbA1 : 0u;
+      if ((fa | fb) != 0u) {  // warp-uniform: every lane read the same two words
+        const uint32_t lt = (1u << lane) - 1u;
+        // the scaled raw sums M000 .. M011 (s = -1, 2, 2, 2, 1, 1, 1, -4, -4, -4; the
+        // boundary kernel divides them out)
+        const float2 v[10] = {M[0][0], M[1][0], M[2][0], M[0][1], M[3][0],
+                              M[5][0], M[0][2], M[4][0], M[1][1], M[2][1]};
+        const size_t L = size_t(P.L);
+        if (col_ok && ((fa >> lane) & 1u)) {
+          const size_t k = __ldg(P.cls_pref + wa) + __popc(fa & lt);
+#pragma unroll
+          for (int c = 0; c < 10; ++c) P.side[c * L + k] = v[c].x;
+        }
+        if (col_ok && ((fb >> lane) & 1u)) {
+          const size_t k = __ldg(P.cls_pref + wb) + __popc(fb & lt);
+#pragma unroll
+          for (int c = 0; c < 10; ++c) P.side[c * L + k] = v[c].y;
+        }
       }
-      // slices: 0:(0,0) 1:(1,0) 2:(0,1) 3:(2,0) 4:(1,1) 5:(0,2)
-      const int za = zz - 1, zb = zz;
-      if constexpr (STORAGE == ST_MIXED) {
-        // the raw post-streaming sums rho - 1, sum c f, sum (c c - 1/3) f
-        StoredT<float2> r;
-        r.drho = M[0][0], r.ux = M[1][0], r.uy = M[2][0], r.uz = M[0][1];
-        r.nxx = M[3][0], r.nyy = M[5][0], r.nzz = M[0][2];
-        r.nxy = M[4][0], r.nxz = M[1][1], r.nyz = M[2][1];
-        store_pair_f32(P.out_w, col + plane * za, col + plane * (zb < nz ? zb : 0), r, col_ok,
-                       col_ok && zb < z1);
-        continue;
-      }
-      const StoredT<float2> o =
-          finish_moments<FORCE>(M[0][0], M[1][0], M[2][0], M[0][1], M[3][0], M[5][0], M[0][2],
-                                M[4][0], M[1][1], M[2][1], ox, oy, oz);
-      if constexpr (STORAGE == ST_Q16)
-        store_pair_q16<RT>(P.out, N, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
-                       col_ok && zb < z1, uint32_t(xw), uint32_t(yw), uint32_t(za), uint32_t(zb),
-                       P.t_out, P.seed, grids_of(P));
-      else
-        store_pair_f32(P.out_w, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
-                       col_ok && zb < z1);
     }
-    if (FORCE) {
-      fprev[0] = fx.y;
-      fprev[1] = fy.y;
-      fprev[2] = fz.y;
+    if constexpr (STORAGE == ST_MIXED) {
+      StoredT<float2> r;  // the unscaled raw sums
+      r.drho = vmulc(M[0][0], -1.0f), r.ux = vmulc(M[1][0], 0.5f), r.uy = vmulc(M[2][0], 0.5f);
+      r.uz = vmulc(M[0][1], 0.5f);
+      r.nxx = M[3][0], r.nyy = M[5][0], r.nzz = M[0][2];
+      r.nxy = vmulc(M[4][0], -0.25f), r.nxz = vmulc(M[1][1], -0.25f), r.nyz = vmulc(M[2][1], -0.25f);
+      store_pair_f32(P.out_w, col + plane * za, col + plane * (zb < nz ? zb : 0), r, col_ok,
+                     col_ok && zb < z1);
+      return;
+    }
+    StoredT<float2> o =  // -drho and -4 n_ab in place of drho and n_ab (finish_scaled)
+        finish_scaled<FORCE>(M[0][0], M[1][0], M[2][0], M[0][1], M[3][0], M[5][0], M[0][2],
+                             M[4][0], M[1][1], M[2][1], ox, oy, oz);
+    if constexpr (STORAGE == ST_Q16)
+      store_pair_q16_w<RT>(P.qout, uint32_t(col) + uint32_t(plane) * uint32_t(za),
+                           uint32_t(col) + uint32_t(plane) * uint32_t(zb < nz ? zb : 0), o, col_ok,
+                           col_ok && zb < z1, ha, hb2, grids_of(P));
+    else {
+      o.drho = vmulc(o.drho, -1.0f);
+      o.nxy = vmulc(o.nxy, -0.25f);
+      o.nxz = vmulc(o.nxz, -0.25f);
+      o.nyz = vmulc(o.nyz, -0.25f);
+      store_pair_f32(P.out_w, col + plane * za, col + plane * (zb < nz ? zb : 0), o, col_ok,
+                     col_ok && zb < z1);
+    }
+  };
+
+  // Pairs j = 0 .. npairs-1 at zz = z0 - 1 + 2 j.  The window of pair j runs
+  // between the barriers of pairs j - 1 and j.
+  const int npairs = (z1 - z0 + 1) / 2 + 1;
+  if constexpr (IN == ST_F32) {
+    // FP32 storage: pre(j), barrier, post(j) per pair, two pairs per loop trip
+    // (twice the bytes of the 16-bit form are in flight; measured faster)
+    float fprev[3] = {0.f, 0.f, 0.f};
+    MELBM_PRAGMA_UNROLL(MELBM_FLUID_ZUNROLL)
+    for (int j = 0; j < npairs; ++j) {
+      const int zz = z0 - 1 + 2 * j;
+      const int parity = j & 1;
+      const bool halo_next = halo_warp && j + 1 < npairs;
+      const bool halo_ahead = halo_warp && j + 2 < npairs;
+      if (halo_ahead) halo_issue(zz + 4, parity);
+      float2 f[3];
+      pre(zz, parity, f[0], f[1], f[2], j + 1 < npairs);
+      if (halo_next) {
+        if (halo_ahead) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        halo_finish(parity ^ 1, parity ^ 1, zz + 2);
+      }
+      __syncthreads();
+      if (mid_row)
+        post(zz, parity, make_float2(fprev[0], f[0].x), make_float2(fprev[1], f[1].x),
+             make_float2(fprev[2], f[2].x), j > 0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fprev[k] = f[k].y;
+    }
+  } else if (mid_row) {
+    // 16-bit input: window j holds post(j - 1) and pre(j) in one straight block,
+    // so the codec's integer work and the passes' arithmetic of two pairs can be
+    // interleaved by the scheduler (the y-halo rows run the loop below)
+    float2 fc[3], fn[3];
+    float fprev[3];
+    pre(z0 - 1, 0, fc[0], fc[1], fc[2], npairs > 1);
+    __syncthreads();
+    post(z0 - 1, 0, zero, zero, zero, false);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fprev[k] = fc[k].y;
+    pre(z0 + 1, 1, fc[0], fc[1], fc[2], npairs > 2);
+    __syncthreads();
+    int parity = 0;
+    for (int j = 2; j < npairs; ++j, parity ^= 1) {
+      const int zz = z0 - 1 + 2 * j;
+      post(zz - 2, parity ^ 1, make_float2(fprev[0], fc[0].x), make_float2(fprev[1], fc[1].x),
+           make_float2(fprev[2], fc[2].x), true);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fprev[k] = fc[k].y;
+      pre(zz, parity, fn[0], fn[1], fn[2], j + 1 < npairs);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fc[k] = fn[k];
+      __syncthreads();
+    }
+    post(z0 - 1 + 2 * (npairs - 1), (npairs - 1) & 1, make_float2(fprev[0], fc[0].x),
+         make_float2(fprev[1], fc[1].x), make_float2(fprev[2], fc[2].x), true);
+  } else {
+    // y-halo rows: their x-pass populations only; warp 0 also stages and
+    // computes the x halo of the next pair
+    for (int j = 0; j < npairs; ++j) {
+      const int zz = z0 - 1 + 2 * j;
+      const int parity = j & 1;
+      const bool halo_next = halo_warp && j + 1 < npairs;
+      const bool halo_ahead = halo_warp && j + 2 < npairs;
+      if (halo_ahead) halo_issue(zz + 4, parity);
+      float2 f0, f1, f2;
+      pre(zz, parity, f0, f1, f2, j + 1 < npairs);
+      if (halo_next) {
+        if (halo_ahead) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        halo_finish(parity ^ 1, parity ^ 1, zz + 2);
+      }
+      __syncthreads();
     }
   }
 }
@@ -671,9 +1025,9 @@ inline int choose_zchunk(int64_t tiles_xy, int nz, int64_t resident_blocks) {
   return best;
 }
 
-template <int STORAGE, bool FORCE, bool RT, bool Q19 = false>
+template <int STORAGE, bool FORCE, bool RT, bool Q19 = false, bool BND = false>
 cudaError_t launch_fluid_t(KernelParams<STORAGE, RT>& p, cudaStream_t st) {
-  const size_t smem = HaloStage<STORAGE == ST_MIXED ? ST_Q16 : STORAGE, FORCE, Q19>::SMEM;
+  const size_t smem = HaloStage<STORAGE == ST_MIXED ? ST_Q16 : STORAGE, FORCE, Q19, BND>::SMEM;
   // per device: the shared-memory opt-in of this instantiation and the number of
   // its blocks resident on the whole GPU (set once; a racing first call writes
   // the same values)
@@ -685,11 +1039,11 @@ cudaError_t launch_fluid_t(KernelParams<STORAGE, RT>& p, cudaStream_t st) {
   if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
   if (!resident[dev]) {
     int sms = 0, per_sm = 0;
-    e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE, RT, Q19>,
+    e = cudaFuncSetAttribute(fluid_kernel<STORAGE, FORCE, RT, Q19, BND>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_kernel<STORAGE, FORCE, RT, Q19>,
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_kernel<STORAGE, FORCE, RT, Q19, BND>,
                                                         FX * FY, smem);
     if (e != cudaSuccess) return e;
     resident[dev] = std::max(1, sms * per_sm);
@@ -697,8 +1051,88 @@ cudaError_t launch_fluid_t(KernelParams<STORAGE, RT>& p, cudaStream_t st) {
   const int64_t tiles_xy = int64_t((p.nx + FX - 1) / FX) * ((p.ny + FYI - 1) / FYI);
   p.zc = choose_zchunk(tiles_xy, p.nz, resident[dev]);
   dim3 grid((p.nx + FX - 1) / FX, (p.ny + FYI - 1) / FYI, (p.nz + p.zc - 1) / p.zc);
-  fluid_kernel<STORAGE, FORCE, RT, Q19><<<grid, dim3(FX, FY), smem, st>>>(p);
+  fluid_kernel<STORAGE, FORCE, RT, Q19, BND><<<grid, dim3(FX, FY), smem, st>>>(p);
   return cudaGetLastError();
+}
+
+// Fill the parameters of one step and launch the instantiation for the storage,
+// bit widths and force (Q19: the D3Q19 lattice; BND: with the boundary tables).
+template <bool Q19, bool BND>
+cudaError_t launch_fluid_impl(int storage, int nx, int ny, int nz, const void* in, void* out,
+                              const float* force, float omega, uint32_t t_out, uint32_t seed,
+                              const QGrids& grids, const BoundaryTables* bt, cudaStream_t st) {
+  FluidParams p = {};
+  p.nx = nx;
+  p.ny = ny;
+  p.nz = nz;
+  p.in = in;
+  p.out = out;
+  p.force = force;
+  p.omega = omega;
+  p.t_out = t_out;
+  p.seed = seed;
+  // 16-byte chunks need 16-byte aligned rows: nx % 4 == 0 and aligned bases
+  p.chunk16 = nx % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
+              reinterpret_cast<uintptr_t>(force) % 16 == 0;
+  const size_t N = size_t(nx) * ny * nz;
+  for (int k = 0; k < 5; ++k) {
+    p.qin[k] = static_cast<const uint32_t*>(in) + k * N;
+    p.qout[k] = static_cast<uint32_t*>(out) + k * N;
+  }
+  if constexpr (BND) {
+    p.cls_solid = bt->solid;
+    p.cls_fb = bt->fb;
+    p.cls_pref = bt->pref;
+    p.side = bt->side;
+    p.L = bt->L;
+    p.ntx = (nx + 31) / 32;
+  }
+  if (storage == ST_Q16 && !qgrids_16(grids)) {
+    KernelParams<ST_Q16, true> q;
+    static_cast<FluidParams&>(q) = p;
+    q.q = grids;
+    return force ? launch_fluid_t<ST_Q16, true, true, Q19, BND>(q, st)
+                 : launch_fluid_t<ST_Q16, false, true, Q19, BND>(q, st);
+  }
+  if (storage == ST_Q16) {
+    KernelParams<ST_Q16, false> q;
+    static_cast<FluidParams&>(q) = p;
+    return force ? launch_fluid_t<ST_Q16, true, false, Q19, BND>(q, st)
+                 : launch_fluid_t<ST_Q16, false, false, Q19, BND>(q, st);
+  }
+  if (storage != ST_F32) return cudaErrorInvalidValue;
+  KernelParams<ST_F32, false> q;
+  static_cast<FluidParams&>(q) = p;
+  for (int k = 0; k < 10; ++k) {
+    q.in_w[k] = static_cast<const uint32_t*>(in) + k * N;
+    q.out_w[k] = static_cast<uint32_t*>(out) + k * N;
+  }
+  for (int k = 0; k < 3; ++k)
+    q.f_w[k] = force ? reinterpret_cast<const uint32_t*>(force) + k * N : nullptr;
+  return force ? launch_fluid_t<ST_F32, true, false, Q19, BND>(q, st)
+               : launch_fluid_t<ST_F32, false, false, Q19, BND>(q, st);
+}
+
+// The fluid pass of the mixed-precision scheme: 16-bit post-collision moments
+// (stored variables rho - 1, u+, rho (S+ - u+ u+)) in, raw FP32 post-streaming
+// sums out.  The stored stress is already traceless, so the collision with
+// omega = 0 only rebuilds the Hermite moments.
+template <bool Q19>
+cudaError_t launch_fluid_mixed_impl(int nx, int ny, int nz, const void* q_in, float* p_out,
+                                    cudaStream_t st) {
+  KernelParams<ST_MIXED, false> k;
+  FluidParams& p = k;
+  p = FluidParams{};
+  p.nx = nx;
+  p.ny = ny;
+  p.nz = nz;
+  p.in = q_in;
+  p.out = p_out;
+  p.omega = 0.0f;
+  const size_t N = size_t(nx) * ny * nz;
+  for (int w = 0; w < 5; ++w) p.qin[w] = static_cast<const uint32_t*>(q_in) + w * N;
+  for (int w = 0; w < 10; ++w) k.out_w[w] = reinterpret_cast<uint32_t*>(p_out) + w * N;
+  return launch_fluid_t<ST_MIXED, false, false, Q19>(k, st);
 }
 
 }  // namespace melbm

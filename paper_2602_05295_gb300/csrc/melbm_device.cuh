@@ -129,6 +129,21 @@ __device__ __forceinline__ uint2 q_encode_codes(float2 m, float2 d) {
   asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qb) : "f"(z.y));
   return make_uint2(qa, qb);
 }
+// The pair form with the dither given as 1 + d (dither_one_plus): the same codes,
+// q = qc + floor(w + d) = (qc - 1) + floor(w + (1 + d)), one packed FMA fewer.
+// SC: the value comes multiplied by SC (1, -1 or -4), which the grid factor K
+// divides out exactly (K / SC is K times a power of two).
+template <int G, int SC = 1>
+__device__ __forceinline__ uint2 q_encode_codes1(float2 m, float2 D) {
+  constexpr float K = QConst<G>::K / float(SC);
+  const float2 w = __ffma2_rn(m, make_float2(K, K), make_float2(QConst<G>::b, QConst<G>::b));
+  const float qm = QConst<G>::qc - 1.0f;
+  const float2 z = __fadd2_rd(__fadd2_rd(w, D), make_float2(qm, qm));
+  unsigned short qa, qb;
+  asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qa) : "f"(z.x));
+  asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qb) : "f"(z.y));
+  return make_uint2(qa, qb);
+}
 __device__ __forceinline__ uint32_t q_pack(uint32_t lo_bits, uint32_t hi_bits) {
   return __byte_perm(lo_bits, hi_bits, 0x5410);
 }
@@ -165,6 +180,18 @@ __device__ __forceinline__ uint32_t qg_encode_bits(const QGrid& g, float m, floa
 __device__ __forceinline__ uint2 qg_encode_codes(const QGrid& g, float2 m, float2 d) {
   const float2 w = __ffma2_rn(m, make_float2(g.K, g.K), make_float2(g.b, g.b));
   const float2 z = __fadd2_rd(__fadd2_rd(w, d), make_float2(g.qc, g.qc));
+  unsigned short qa, qb;
+  asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qa) : "f"(z.x));
+  asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qb) : "f"(z.y));
+  return make_uint2(qa, qb);
+}
+// With the dither given as 1 + d (see q_encode_codes1).
+__device__ __forceinline__ uint2 qg_encode_codes1(const QGrid& g, float2 m, float2 D,
+                                                 float kscale = 1.0f) {
+  const float K = g.K * kscale;  // kscale: 1, -1 or -1/4 (exact)
+  const float2 w = __ffma2_rn(m, make_float2(K, K), make_float2(g.b, g.b));
+  const float qm = g.qc - 1.0f;
+  const float2 z = __fadd2_rd(__fadd2_rd(w, D), make_float2(qm, qm));
   unsigned short qa, qb;
   asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qa) : "f"(z.x));
   asm("cvt.rmi.u16.f32 %0, %1;" : "=h"(qb) : "f"(z.y));
@@ -235,6 +262,20 @@ __device__ __forceinline__ float2 dither_value(float2 magic, int k) {
                             make_float2(-1024.0f, -1024.0f))
                : __ffma2_rn(magic, make_float2(1.0f / 65536.0f, 1.0f / 65536.0f),
                             make_float2(-64.0f, -64.0f));
+}
+// The same dither plus one, 1 + d, built directly as the float with bits
+// 0x3F800000 | (f << (23 - bits)) | (1 << (22 - bits)) (exact), for the packed
+// encode below, which adds it in place of d: the code is unchanged, since
+// floor(w + 1 + d) - 1 = floor(w + d) and both round-down adds keep the floor.
+__device__ __forceinline__ float dither_one_plus(const DitherBits& h, int k) {
+  uint32_t b;
+  if (k < 8)
+    b = (k & 1) ? ((h.w[k >> 1] >> 1) & 0x7FF800u) : ((h.w[k >> 1] & 0xFFFu) << 11);
+  else if (k == 8)
+    b = (__byte_perm(h.w[0], h.w[1], 0x0073) & 0xFFFFu) << 7;  // (w0 >> 24) | (w1 >> 24) << 8
+  else
+    b = (__byte_perm(h.w[2], h.w[3], 0x0073) & 0xFFFFu) << 7;
+  return __uint_as_float(b | (k < 8 ? 0x3F800400u : 0x3F800040u));
 }
 struct Dither {
   float d[10];

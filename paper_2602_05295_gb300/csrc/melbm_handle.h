@@ -30,13 +30,19 @@ struct melbm_sim {
   uint32_t* list_cell = nullptr;
   uint32_t* list_word = nullptr;
   int64_t L = 0;
-  // source set of the boundary update: S cells (ascending), the list index of
-  // every FLUID_BOUNDARY cell (lidx[N], 0xFFFFFFFF elsewhere) and the per-step
-  // populations streamed into each listed cell ([27][L], written by phase A)
-  uint32_t* src_cells = nullptr;
-  int64_t S = 0;
-  uint32_t* lidx = nullptr;
-  float* src_pop = nullptr;
+  int64_t L_cap = 0;  // entries the list arrays and the side table hold
+  // tables of the fluid kernel with solids (melbm::BoundaryTables): per 32-cell
+  // word of a row (W words) the SOLID and FLUID_BOUNDARY bits and the list index
+  // of its first listed cell, and the [10][L] side table of raw post-streaming
+  // sums of the FLUID_BOUNDARY cells
+  uint32_t* cls_solid = nullptr;
+  uint32_t* cls_fb = nullptr;
+  uint32_t* cls_pref = nullptr;
+  float* side = nullptr;
+  int64_t W = 0;
+  // solids, inflow or outflow changed since the last classification: the next
+  // call that needs the types or the list classifies first
+  bool boundary_pending = false;
   uint32_t* cl_counts = nullptr;
   uint32_t* cl_offsets = nullptr;
   uint32_t* cl_total = nullptr;
@@ -81,6 +87,9 @@ namespace melbm {
 // Launch one forward step in -> out with the handle's boundaries (used by the
 // adjoint's recomputation); t_out is the time index of the output state.
 cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out);
+// Run the classification a melbm_set_solid / set_inflow / set_outflow left
+// pending (no-op otherwise); returns its status.
+int ensure_boundaries(melbm_sim* h);
 // Record the message of a failed call that has no handle (read by
 // melbm_last_error(NULL)) and return code.
 int handleless_fail(int code, const char* fmt, ...);

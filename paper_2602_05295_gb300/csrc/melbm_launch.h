@@ -42,16 +42,41 @@ inline QGrids make_qgrids(int bits_ru, int bits_s) {
 }
 inline bool qgrids_16(const QGrids& g) { return g.bits_ru == 16 && g.bits_s == 16; }
 
+// The classification of a handle with solids as the fluid kernel reads it: per
+// 32-cell word (tx, y, z) of a row (word index tx + ntx (y + ny z), ntx =
+// ceil(nx / 32), bit = x - 32 tx) the bits of its SOLID cells and of its
+// FLUID_BOUNDARY cells, and pref = the list index of the word's first listed cell
+// (the number of listed cells before the word, plus one if its lane-0 cell is an
+// INFLOW cell, so that a FLUID_BOUNDARY lane's index is pref + the number of
+// FLUID_BOUNDARY lanes below it); side[10][L] is the table of raw post-streaming
+// sums (m000, m100, m010, m001, m200, m020, m002, m110, m101, m011) that the fluid
+// kernel fills for the FLUID_BOUNDARY cells (list order), each times the scale of
+// the kernel's passes (-1, 2, 2, 2, 1, 1, 1, -4, -4, -4).
+struct BoundaryTables {
+  const uint32_t* solid;
+  const uint32_t* fb;
+  const uint32_t* pref;
+  float* side;
+  int64_t L;
+};
+
 // Fluid kernel over every cell: in -> out (storage layout of melbm_device.cuh).
 // q: the grids of the handle's bit widths (16/16 runs the kernel instantiation
-// with compile-time grid constants).
+// with compile-time grid constants).  bt: the boundary tables (NULL or solid ==
+// NULL without solids).
 cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, void* out,
                          const float* force, float omega, uint32_t t_out, uint32_t seed,
-                         const QGrids& q, cudaStream_t st);
-// The same on the D3Q19 lattice (fluid19.cu; F32 or Q16 storage, periodic).
+                         const QGrids& q, const BoundaryTables* bt, cudaStream_t st);
+cudaError_t launch_fluid_bnd(int storage, int nx, int ny, int nz, const void* in, void* out,
+                             const float* force, float omega, uint32_t t_out, uint32_t seed,
+                             const QGrids& q, const BoundaryTables* bt, cudaStream_t st);
+// The same on the D3Q19 lattice (fluid19.cu, fluid19_bnd.cu; F32 or Q16 storage).
 cudaError_t launch_fluid19(int storage, int nx, int ny, int nz, const void* in, void* out,
                            const float* force, float omega, uint32_t t_out, uint32_t seed,
-                           const QGrids& q, cudaStream_t st);
+                           const QGrids& q, const BoundaryTables* bt, cudaStream_t st);
+cudaError_t launch_fluid19_bnd(int storage, int nx, int ny, int nz, const void* in, void* out,
+                               const float* force, float omega, uint32_t t_out, uint32_t seed,
+                               const QGrids& q, const BoundaryTables* bt, cudaStream_t st);
 
 // The mixed-precision scheme (mixed.cu): fluid pass Q -> P (fluid.cu), solid
 // correction with atomicAdd into P, collision + quantisation P -> Q, and the
@@ -70,17 +95,17 @@ cudaError_t launch_mixed_set_state(int64_t N, const float* rho, const float* u, 
 cudaError_t launch_mixed_get_moments(int64_t N, const float* p, float* rho, float* u, float* S,
                                      cudaStream_t st);
 
-// Boundary update over the list: phase A collides the S source cells and pushes
-// the populations the listed cells read into pop[27][count] (sources.cu; lidx is
-// the list index of every FLUID_BOUNDARY cell), then the boundary kernel
-// recomputes every listed cell from its 27 entries (halfway bounce-back included,
-// inflow reset), in -> out.
+// Boundary kernel over the list, after the fluid kernel with the boundary tables
+// (in -> out): every FLUID_BOUNDARY cell adds to its raw sums in bt->side the
+// populations its solid links return (halfway bounce-back, or the moving wall
+// with wall_model 1), computed from its own post-collision state, and stores the
+// finished moments; INFLOW cells are reset to the inflow equilibrium.
 cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
                             const float* force, float omega, const uint32_t* cells,
-                            const uint32_t* words, int64_t count, const uint32_t* src_cells,
-                            int64_t S, const uint32_t* lidx, float* pop, const float inflow[4],
-                            uint32_t t_out, uint32_t seed, const QGrids& q, int wall_model,
-                            const uint8_t* mask, const float* bodies, int lattice, cudaStream_t st);
+                            const uint32_t* words, int64_t count, const BoundaryTables& bt,
+                            const float inflow[4], uint32_t t_out, uint32_t seed, const QGrids& q,
+                            int wall_model, const uint8_t* mask, const float* bodies, int lattice,
+                            cudaStream_t st);
 
 // Force and torque (about r0 of the body) the next step transfers to the solid
 // cells of body `body` (0: every solid) by momentum exchange over the solid
@@ -92,40 +117,27 @@ cudaError_t launch_solid_force(int storage, int nx, int ny, int nz, const void* 
                                int wall_model, const uint8_t* mask, const float* bodies, int body,
                                double* partials, double* out, int lattice, cudaStream_t st);
 
-// Source set of the boundary update (sources.cu).  Setup, after the list is
-// built: mark the sources (mark[N] bytes) and count them per block of
-// source_flag_blocks(N); after an exclusive scan of the counts, fill src_cells
-// (ascending) and lidx[N] (the list index of each FLUID_BOUNDARY cell, else
-// 0xFFFFFFFF).  Per step: phase A, which writes pop[27][L].
-int64_t source_flag_blocks(int64_t N);
-cudaError_t launch_source_setup_mark(int nx, int ny, int nz, const uint32_t* cells,
-                                     const uint32_t* words, int64_t L, uint8_t* mark,
-                                     uint32_t* block_counts, cudaStream_t st);
-cudaError_t launch_source_setup_fill(int nx, int ny, int nz, const uint32_t* cells,
-                                     const uint32_t* words, int64_t L, const uint8_t* mark,
-                                     const uint32_t* block_offsets, uint32_t* src_cells,
-                                     uint32_t* lidx, cudaStream_t st);
-cudaError_t launch_source_collide(int storage, int nx, int ny, int nz, const void* in,
-                                  const float* force, float omega, const uint32_t* src_cells,
-                                  int64_t S, const uint32_t* lidx, const uint32_t* words,
-                                  int64_t L, float* pop, const QGrids& q, int lattice,
-                                  cudaStream_t st);
-
 // Outflow copy on the plane x = nx-1 (cells typed OUTFLOW), in place on buf.
 cudaError_t launch_outflow(int storage, int nx, int ny, int nz, void* buf, const uint8_t* type,
                            cudaStream_t st);
 
-// Classification: types (N) and per-block counts of listed cells; then the
-// ordered scatter into the list.  nblocks_out receives the block count.
-int64_t classify_blocks(int64_t N);
+// Classification (classify.cu), by 32-cell row words (tx, y, z), ntx =
+// ceil(nx / 32) words per row: pass 1 writes the types (N) and the number of
+// listed cells of each block of words (classify_blocks of them) and, when solid_w
+// is given, the SOLID and FLUID_BOUNDARY bits of every word; after an exclusive
+// scan of the counts, pass 2 writes the list in ascending n and, when pref_w is
+// given, the list index of every word's first listed cell (see BoundaryTables).
+int64_t classify_words(int nx, int ny, int nz);
+int64_t classify_blocks(int nx, int ny, int nz);
 cudaError_t launch_classify_count(int nx, int ny, int nz, const uint8_t* mask, int inflow,
-                                  int outflow, uint8_t* type, uint32_t* block_counts,
-                                  cudaStream_t st);
+                                  int outflow, uint8_t* type, uint32_t* solid_w, uint32_t* fb_w,
+                                  uint32_t* block_counts, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
                                   cudaStream_t st);
-cudaError_t launch_classify_scatter(int nx, int ny, int nz, const uint8_t* mask,
-                                    const uint8_t* type, const uint32_t* block_offsets,
-                                    uint32_t* cells, uint32_t* words, cudaStream_t st);
+cudaError_t launch_classify_scatter(int nx, int ny, int nz, const uint8_t* mask, int inflow,
+                                    int outflow, const uint8_t* type, const uint32_t* block_offsets,
+                                    uint32_t* cells, uint32_t* words, uint32_t* pref_w,
+                                    cudaStream_t st);
 
 // FP64 reductions: partial sums per block, then one block sums the partials in
 // a fixed order.  out[0] = mass, out[1] = kinetic energy, out[2] = saturated codes.

@@ -91,12 +91,18 @@ def test_adjoint_matches_oracle_with_bounce_back_inflow_outflow(M, orc):
 
 
 def test_checkpointed_adjoint_against_fp64_central_differences(M, orc):
-    """Config adjoint128 scaled down (32^3, 40 steps, checkpoints every 10 stored
-    16-bit): directional derivatives of the kinetic energy in a 8^3 subregion along
-    16 seeded directions in (u0, F) match FP64 central differences of the oracle."""
+    """Config adjoint128 scaled down (32^3, 40 steps): directional derivatives of
+    the kinetic energy in a 8^3 subregion along 16 seeded directions in (u0, F)
+    against FP64 central differences of the oracle, per direction.  With every
+    FP32 state kept (K = 40, no recompute) each direction is within 1e-4 of its
+    own derivative.  With 16-bit checkpoints every 10 steps the recomputed
+    segments start from rounded states, which moves the linearisation point by up
+    to half a code step; that shifts every directional derivative by up to ~1e-5
+    of the largest one, so a direction whose derivative is far below the others
+    meets 1e-4 of its own value plus that floor: |ad - fd| <= 1e-4 |fd| +
+    1e-5 max|fd| (the stated bound of the checkpointed adjoint)."""
     shape = (32, 32, 32)
-    N = 32 ** 3
-    tau, nsteps, K = 0.55, 40, 10
+    tau, nsteps = 0.55, 40
     u0 = W.flat(W.random_phase_field(shape, 0.05, kmax=8, seed=35))
     F = W.flat(W.force_field(shape, 1e-5, seed=36))
     z, y, x = np.mgrid[0:32, 0:32, 0:32]
@@ -106,17 +112,20 @@ def test_checkpointed_adjoint_against_fp64_central_differences(M, orc):
         return 0.5 * (m[0] * (m[1:4] ** 2).sum(0))[region].sum()
 
     from paper_2602_05295_gb300.autograd import MELBMFunction, kinetic_energy_in_region
-    sim = M.Simulator(shape, tau, "f32")
-    u0_t = cuda(u0).requires_grad_(True)
-    F_t = cuda(F).requires_grad_(True)
-    m_T = MELBMFunction.apply(u0_t, F_t, sim, nsteps, K)
-    L = kinetic_energy_in_region(m_T, cuda(region, torch.bool))
-    L.backward()
-    gu = u0_t.grad.cpu().numpy().astype(np.float64)
-    gF = F_t.grad.cpu().numpy().astype(np.float64)
+
+    def grads(K):
+        sim = M.Simulator(shape, tau, "f32")
+        u0_t = cuda(u0).requires_grad_(True)
+        F_t = cuda(F).requires_grad_(True)
+        m_T = MELBMFunction.apply(u0_t, F_t, sim, nsteps, K)
+        kinetic_energy_in_region(m_T, cuda(region, torch.bool)).backward()
+        return u0_t.grad.cpu().numpy().astype(np.float64), F_t.grad.cpu().numpy().astype(np.float64)
+
+    gu, gF = grads(10)
+    gu_all, gF_all = grads(nsteps)
     rng = np.random.default_rng(37)
     scale_u, scale_F = np.abs(u0).max(), np.abs(F).max()
-    fds, ads = [], []
+    fds, ads, ads_all = [], [], []
     for _ in range(16):
         vu = rng.standard_normal(u0.shape) * scale_u
         vF = rng.standard_normal(F.shape) * scale_F
@@ -125,31 +134,34 @@ def test_checkpointed_adjoint_against_fp64_central_differences(M, orc):
         lm, _ = orc.forward_loss(u0 - eps * vu, F - eps * vF, shape, tau, nsteps, loss)
         fds.append((lp - lm) / (2 * eps))
         ads.append((gu * vu).sum() + (gF * vF).sum())
-    fds, ads = np.array(fds), np.array(ads)
-    # A random direction can give a derivative far below the others, where a
-    # per-direction relative error only measures that smallness; the errors are
-    # taken against the set's scale: relative l2 over the 16 derivatives, and each
-    # error against the largest derivative.
-    assert np.linalg.norm(ads - fds) / np.linalg.norm(fds) < 1e-4
-    assert np.abs(ads - fds).max() / np.abs(fds).max() < 1e-4
+        ads_all.append((gu_all * vu).sum() + (gF_all * vF).sum())
+    fds, ads, ads_all = np.array(fds), np.array(ads), np.array(ads_all)
+    rel_all = np.abs(ads_all - fds) / np.abs(fds)
+    assert rel_all.max() < 1e-4, rel_all
+    bound = 1e-4 * np.abs(fds) + 1e-5 * np.abs(fds).max()
+    assert np.all(np.abs(ads - fds) <= bound), (np.abs(ads - fds) / np.abs(fds), fds)
 
 
-def test_adjoint128_full_size_directional_derivatives(M, orc):
-    """Workload adjoint128 at full size: 128^3, tau = 0.55, 200 steps, 16-bit
-    checkpoints every 20 steps, loss = kinetic energy in [48, 80)^3.  Two seeded
-    directions in (u0, F) against FP64 central differences of the oracle (each
-    oracle forward is 4e8 cell updates, so the 16-direction check runs at 32^3)."""
+def test_adjoint128_full_size_directional_derivatives(M):
+    """Workload adjoint128 at its stated size: 128^3, tau = 0.55, 200 steps, 16-bit
+    checkpoints every 20 steps, loss = kinetic energy in [48, 80)^3.  The gradient
+    in (u0, F) along each of the 16 seeded directions matches the FP64 central
+    difference of the oracle (tests/golden/adjoint128_fd.json, written by
+    tests/golden/make_adjoint128_fd.py from the oracle alone) within 1e-4 of that
+    direction's own derivative."""
+    import json
+    import os
     from paper_2602_05295_gb300.autograd import MELBMFunction, kinetic_energy_in_region
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "adjoint128_fd.json")))
+    assert None not in gold["fd"], "the golden file is incomplete"
     wl = W.ADJOINT128
     shape, tau, nsteps = wl.shape, wl.tau, wl.steps
+    assert list(shape) == gold["shape"] and tau == gold["tau"] and nsteps == gold["nsteps"]
     u0 = W.flat(W.random_phase_field(shape, 0.05))
     F = W.flat(W.force_field(shape, 1e-5))
+    lo, hi = gold["region"]
     z, y, x = np.mgrid[0:128, 0:128, 0:128]
-    region = ((x >= 48) & (x < 80) & (y >= 48) & (y < 80) & (z >= 48) & (z < 80)).ravel()
-
-    def loss(m):
-        return 0.5 * (m[0] * (m[1:4] ** 2).sum(0))[region].sum()
-
+    region = ((x >= lo) & (x < hi) & (y >= lo) & (y < hi) & (z >= lo) & (z < hi)).ravel()
     sim = M.Simulator(shape, tau, "f32")
     u0_t = cuda(u0).requires_grad_(True)
     F_t = cuda(F).requires_grad_(True)
@@ -158,18 +170,16 @@ def test_adjoint128_full_size_directional_derivatives(M, orc):
     L.backward()
     gu = u0_t.grad.cpu().numpy().astype(np.float64)
     gF = F_t.grad.cpu().numpy().astype(np.float64)
-    rng = np.random.default_rng(38)
-    fds, ads = [], []
-    for _ in range(2):
-        vu = rng.standard_normal(u0.shape) * np.abs(u0).max()
-        vF = rng.standard_normal(F.shape) * np.abs(F).max()
-        eps = 1e-4
-        lp, _ = orc.forward_loss(u0 + eps * vu, F + eps * vF, shape, tau, nsteps, loss)
-        lm, _ = orc.forward_loss(u0 - eps * vu, F - eps * vF, shape, tau, nsteps, loss)
-        fds.append((lp - lm) / (2 * eps))
+    rng = np.random.default_rng(gold["direction_seed"])
+    su, sF = np.abs(u0).max(), np.abs(F).max()
+    ads = []
+    for _ in range(len(gold["fd"])):
+        vu = rng.standard_normal(u0.shape) * su
+        vF = rng.standard_normal(F.shape) * sF
         ads.append((gu * vu).sum() + (gF * vF).sum())
-    fds, ads = np.array(fds), np.array(ads)
-    assert np.abs(ads - fds).max() / np.abs(fds).max() < 1e-4, (ads, fds)
+    ads, fds = np.array(ads), np.array(gold["fd"])
+    rel = np.abs(ads - fds) / np.abs(fds)
+    assert rel.max() < 1e-4, (rel, ads, fds)
 
 
 @pytest.mark.parametrize("case", ["periodic", "channel"])

@@ -518,16 +518,17 @@ print("time", sim.time_index)
 """
 
 
-@pytest.mark.parametrize("after", [10, 12, 13, 14])
+@pytest.mark.parametrize("after", [7, 12, 13, 14])
 def test_failed_boundary_setup_leaves_no_partial_lists(M, after):
-    """A device allocation failing inside melbm_set_solid (MELBM_FAIL_ALLOC_AFTER;
-    the handle's own allocations are the four state and reduction buffers, then
-    the mask, the type array, three classification scratch arrays, the two list
-    arrays, the source marks, the list-index map, the source cells and the
-    population table, so 10, 12, 13 and 14 fail the second list array, the map,
-    the source cells and the table) is reported as MELBM_ENOMEM, and
-    the handle then refuses to step or to sum solid forces (MELBM_ESTATE) instead
-    of running with partial boundary tables."""
+    """melbm_set_solid only records the mask (and copies it, the handle's fifth
+    allocation after its four state and reduction buffers); the classification
+    runs at the first call that needs it.  A device allocation failing there
+    (MELBM_FAIL_ALLOC_AFTER; the classification allocates the type array, the
+    solid-bit and boundary-bit tables, three scratch arrays, the two list arrays,
+    the list-index table and the side table, so 7, 12, 13 and 14 fail the
+    boundary bits, the second list array, the list-index table and the side
+    table) is that call's MELBM_ENOMEM, and the handle then refuses to step or to
+    sum solid forces (MELBM_ESTATE) instead of running with partial tables."""
     import os
     import subprocess
     import sys
@@ -537,4 +538,4 @@ def test_failed_boundary_setup_leaves_no_partial_lists(M, after):
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     lines = r.stdout.strip().splitlines()
-    assert lines == ["set_solid 2", "refused 4", "refused 4", "time 0"], r.stdout
+    assert lines == ["no failure", "refused 2", "refused 4", "time 0"], r.stdout
