@@ -7,8 +7,8 @@
 //      dL/dF from the F/2 of Eq. rho_u_stress), zero for solid, inflow and
 //      outflow cells; then the transpose of the separable pull stream of the
 //      fluid kernel (Eq. streaming), back onto the 17 Hermite moments of each
-//      source cell, with three transposed 1D passes (z in registers, y through
-//      shared memory, x by shuffles); then (dColl/dm)^T (App. A transposed by
+//      source cell, with three transposed 1D passes (x by shuffles, y through
+//      shared memory, z in registers); then (dColl/dm)^T (App. A transposed by
 //      hand);
 //   2. adj_boundary_kernel, over the listed FLUID_BOUNDARY cells: the bounce-back
 //      terms f_i(x) = f+_opp(i)(x) of their own solid links, through the same
@@ -126,7 +126,7 @@ __global__ void outflow_vjp_kernel(float* lam, const uint8_t* type, int nx, int 
 // lJ: the adjoint of J, of which F/2 takes half.
 __device__ __forceinline__ void fin_vjp_cell(const Stored& o, const float lam[10], float lamM[10],
                                              float lJ[3]) {
-  const float rho = 1.0f + o.drho, inv = 1.0f / rho;
+  const float rho = 1.0f + o.drho, inv = __fdividef(1.0f, rho);  // rho ~ 1: 2-ulp reciprocal
   const float J[3] = {o.ux * rho, o.uy * rho, o.uz * rho};
   const float* lu = lam + 1;
   const float* ln = lam + 4;
@@ -165,7 +165,7 @@ __device__ void collide_vjp(const Stored& s, float omega, const float f[3], cons
   const int A[6] = {0, 1, 2, 0, 0, 1}, B[6] = {0, 1, 2, 1, 2, 2};
   float inv = 0.f;
   if (FORCE) {
-    inv = 1.0f / rho;
+    inv = __fdividef(1.0f, rho);
     for (int k = 0; k < 3; ++k) m[k] += f[k] * u[k];
     for (int k = 3; k < 6; ++k) m[k] += 0.5f * (f[A[k]] * u[B[k]] + f[B[k]] * u[A[k]]);
   }
@@ -324,15 +324,17 @@ __device__ __forceinline__ void add_population_adjoint19(int cx, int cy, int cz,
 // kernel: per axis, (mu0, mu1, mu2) -> phi = (phi+, phi0, phi-) with
 // s = mu0/6 + mu2/2, phi0 = mu0 - 2 s, phi+- = s +- mu1/2; pull phi+ from the
 // minus side and phi- from the plus side; project m0 = pl + z + mr, m1 = pl - mr,
-// m2 = (2/3)(pl + mr) - z/3.  Its transpose, per axis and in reverse order
-// (z, then y, then x), is the same three-point stencil read the other way:
+// m2 = (2/3)(pl + mr) - z/3.  Its transpose, per axis, is the same three-point
+// stencil read the other way (the three axis maps act on different indices of the
+// tensor moments, so their transposes may be applied in any order; the kernel
+// takes x, then y, then z, so that the x halo of a tile needs Fin^T alone):
 //   proj^T: lpl = l0 + l1 + (2/3) l2,  lmr = l0 - l1 + (2/3) l2,  lz = l0 - l2/3;
 //   push:   lphi+(x) = lpl(x + 1), lphi-(x) = lmr(x - 1), lphi0 = lz;
 //   phi^T:  ls = lphi+ + lphi- - 2 lphi0, lmu0 = lphi0 + ls/6, lmu1 = (lphi+ - lphi-)/2,
 //           lmu2 = ls/2.
-// Carried adjoints mirror the forward's moment counts: 10 -> 18 (z) -> 24 (y) -> 17 (x);
-// on D3Q19 the x pass yields all 27 tensor moments, folded back onto the 17 through
-// the transposed closure.
+// Carried adjoints: 10 -> 18 (x, six (q, r) slices) -> 27 (y, nine (p, r) slices)
+// -> 17 (z, eight (p, q) slices); on D3Q19 the z pass yields all 27 tensor moments
+// (nine slices), folded back onto the 17 through the transposed closure.
 struct LamT {
   float p, z, m;  // lpl, lz, lmr of one cell, before the push
 };
@@ -353,175 +355,295 @@ __device__ __forceinline__ void phi_t(float lp, float lz, float lm, float& l0, f
   l2 = 0.5f * ls;
 }
 
-constexpr int AFX = 32;             // lanes: columns x0 .. x0+31, lanes 0 and 31 halo
-constexpr int AFY = 16;             // warps: rows y0 .. y0+15, warps 0 and 15 halo
-constexpr int AIX = AFX - 2, AIY = AFY - 2;
-constexpr int ANS = 9;              // y-pass slices (d, r)
-constexpr int ASM = 2 * ANS * AFY * AFX;  // floats per buffer (lpl and lmr)
-constexpr size_t ADJ_SMEM = size_t(2) * ASM * sizeof(float);
+// Tile: 32 lanes (the columns x0 .. x0+31, fewer in a ragged last tile) by AFY
+// warps (the rows y0-1 .. y0+AFY-2, wrapped); warps 0 and AFY-1 are halo rows,
+// which take Fin^T, x^T and the y projection of their row and, instead of the
+// y^T, z^T and Coll^T of the owned rows, compute the x-halo cells of the tile
+// two planes ahead.
+#ifndef MELBM_ADJ_FY
+#define MELBM_ADJ_FY 16
+#endif
+constexpr int AFX = 32;
+constexpr int AFY = MELBM_ADJ_FY;
+constexpr int AIY = AFY - 2;  // rows a tile owns
+static_assert(AFY >= 3 && AFY <= AFX, "the halo warps give one lane to each row");
+// shared memory: the y-pass buffers, [parity][lpl, lmr][row][2][lane] float4 (the
+// y slices 0 .. 7) and [parity][lpl, lmr][row][lane] float (slice 8), then the
+// x-halo buffers [parity][left, right][row][8] float (six slices, padded)
+constexpr int AY4 = 2 * 2 * AFY * 2 * AFX;
+constexpr int AY1 = 2 * 2 * AFY * AFX;
+constexpr int AHB = 2 * 2 * AFY * 8;
+constexpr size_t ADJ_SMEM = size_t(AY4) * sizeof(float4) + size_t(AY1 + AHB) * sizeof(float);
 
+// Field planes are addressed through per-field base pointers held in the kernel
+// parameters (uniform), so each access adds one 32-bit per-thread cell offset
+// (the launcher requires 10 N < 2^32).
 struct AdjStreamParams {
   int nx, ny, nz, zc;
-  const float* lam_next;  // adjoint of the output state (10N, stored variables)
-  const float* m_next;    // output state (10N)
-  const float* m_t;       // input state (10N)
-  const float* force;     // 3N or null
-  const uint8_t* type;    // N or null
-  float* lam_out;         // adjoint of the input state (10N)
-  float* gF;              // 3N, accumulated
+  const float* lam_next[10];  // adjoint of the output state (stored variables)
+  const float* m_next[4];     // output state: rho - 1 and u
+  const float* m_t[10];       // input state
+  const float* force[3];      // null without force
+  const uint8_t* type;        // N or null
+  float* lam_out[10];         // adjoint of the input state
+  float* gF[3];               // accumulated dL/dF
   float omega;
 };
 
-// One thread per (x, y) column marching in z: fin^T and the z^T projection at
-// plane zz, the rest of z^T, y^T (shared memory), x^T (shuffles) and Coll^T
-// for the plane zz - 1.  Periodic in all directions; cells whose output does
-// not come from the stream contribute no adjoint (special_type), and solid cells
-// get none; the bounce-back terms of listed cells are added by adj_boundary_kernel.
+// Fin^T of one cell (rho - 1 and u of its output in M): lM, lJ; zero when the
+// output does not come from the stream.
+__device__ __forceinline__ void fin_t_or_zero(bool skip, const float L[10], const float M[4],
+                                              float lM[10], float lJ[3]) {
+  if (skip) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) lM[k] = 0.f;
+    lJ[0] = lJ[1] = lJ[2] = 0.f;
+    return;
+  }
+  Stored o;  // fin_vjp_cell reads rho - 1 and u of the output only
+  o.drho = M[0];
+  o.ux = M[1];
+  o.uy = M[2];
+  o.uz = M[3];
+  o.nxx = o.nyy = o.nzz = o.nxy = o.nxz = o.nyz = 0.f;
+  fin_vjp_cell(o, L, lM, lJ);
+}
+
+// The x projections of the six (q, r) slices (00) (10) (01) (20) (11) (02), inputs
+// over p, from the ten moment adjoints (M000 M100 M010 M001 M200 M020 M002 M110 M101 M011).
+__device__ __forceinline__ void x_proj(const float lM[10], LamT t[6]) {
+  t[0] = proj_t(lM[0], lM[1], lM[4]);
+  t[1] = proj_t(lM[2], lM[7], 0.f);
+  t[2] = proj_t(lM[3], lM[8], 0.f);
+  t[3] = proj_t(lM[5], 0.f, 0.f);
+  t[4] = proj_t(lM[9], 0.f, 0.f);
+  t[5] = proj_t(lM[6], 0.f, 0.f);
+}
+
+// A plane index in [-nz, 2 nz) wrapped into [0, nz).
+__device__ __forceinline__ uint32_t wrap_plane(int z, int nz) {
+  return uint32_t(z < 0 ? z + nz : (z >= nz ? z - nz : z));
+}
+
+// Block (bx, by, bz) owns the columns x0 .. x0+w-1 (x0 = 32 bx) of the rows
+// y0 .. y0+AIY-1 (y0 = AIY by) over the planes zs .. ze-1 of z-chunk bz; the grid
+// is one wave, so neighbouring tiles march through the same planes together and
+// their halo reads hit L2.  Iteration i handles plane zz = zs - 1 + i:
+//   A (every warp): Fin^T at zz, x^T (shuffles; lane 0 and the tile's last lane
+//     take the halo columns' values from shared memory), the y projection into
+//     shared-memory buffer i & 1; the next plane's loads are issued here;
+//   barrier;
+//   B (owned rows): y^T from the rows above and below, the z projection, and,
+//     for i >= 2, z^T and Coll^T of plane zz - 1, stored;
+//   B (halo warps): Fin^T and the x projection of the halo cells (x0 - 1, y) and
+//     (x0 + w, y) of every row at plane zz + 2, into halo buffer i & 1.
+// Periodic in all directions; cells whose output does not come from the stream
+// contribute no adjoint (special_type), and solid cells get none; the bounce-back
+// terms of listed cells are added by adj_boundary_kernel.
 template <bool FORCE, bool TYPED, bool Q19>
-__global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams P) {
-  extern __shared__ float asm_[];
+__global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(const __grid_constant__ AdjStreamParams P) {
+  extern __shared__ float4 adj_smem[];
+  constexpr int NZS = Q19 ? 9 : 8;  // z^T slices (p, q)
   const int lane = threadIdx.x, row = threadIdx.y;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
-  const size_t N = size_t(nx) * ny * nz, plane = size_t(nx) * ny;
-  const int x = int(blockIdx.x) * AIX - 1 + lane, y = int(blockIdx.y) * AIY - 1 + row;
-  const size_t col = size_t(wrapi(x, nx)) + size_t(nx) * wrapi(y, ny);
-  const bool mid_row = row >= 1 && row <= AFY - 2;
-  const bool own = mid_row && lane >= 1 && lane <= AFX - 2 && x < nx && y < ny;
-  const int z0 = int(blockIdx.z) * P.zc, z1 = min(z0 + P.zc, nz);
-  // z-march state per (d, e) slice: lz of plane zz-1, lmr of planes zz-1 and zz-2
-  float zl[6], m1[6], m2[6];
-  for (int k = 0; k < 6; ++k) zl[k] = m1[k] = m2[k] = 0.f;
-  float gprev[3] = {0.f, 0.f, 0.f};  // F/2 share of fin^T at plane zz-1
-  // plane zz's lambda' and output state are loaded one iteration ahead (of the
-  // output state Fin^T needs only rho - 1 and u)
+  const uint32_t plane = uint32_t(nx) * uint32_t(ny);
+  const int x0 = int(blockIdx.x) * AFX, y0 = int(blockIdx.y) * AIY;
+  const int zs = int(blockIdx.z) * P.zc, ze = min(zs + P.zc, nz);
+  const int w = min(AFX, nx - x0);  // columns of this tile; lane w - 1 takes the right halo
+  const bool owned_row = row >= 1 && row <= AFY - 2;  // warp-uniform
+  const bool own = owned_row && y0 - 1 + row < ny && lane < w;
+  const bool left_end = lane == 0, right_end = lane == w - 1;
+  const int yr = wrapi(y0 - 1 + row, ny);
+  const uint32_t col = uint32_t(min(x0 + lane, nx - 1)) + uint32_t(nx) * uint32_t(yr);
+  // halo warps: warp 0 the column left of the tile, warp AFY-1 the one right of it
+  const int hside = row == 0 ? 0 : 1;
+  const bool hlane = !owned_row && lane < AFY;
+  const uint32_t hcol = uint32_t(hside == 0 ? wrapi(x0 - 1, nx) : wrapi(x0 + w, nx)) +
+                        uint32_t(nx) * uint32_t(wrapi(y0 - 1 + lane, ny));
+  // shared memory
+  // (this thread's entries in parity 0; parity 1 is AY4 / 2 float4 or AY1 / 2 floats on)
+  float4* const yp4 = adj_smem + (0 * AFY + row) * 2 * AFX + lane;
+  float4* const ym4 = adj_smem + (1 * AFY + row) * 2 * AFX + lane;
+  float* const y1 = reinterpret_cast<float*>(adj_smem + AY4);
+  float* const yp1 = y1 + (0 * AFY + row) * AFX + lane;
+  float* const ym1 = y1 + (1 * AFY + row) * AFX + lane;
+  float* const hb = y1 + AY1;
+  const int n_it = ze - zs + 2;
+
+  // ---- halo cells: loads one step ahead of their use
+  float HL[10], HM[4];
+  bool hskip = false;
+  auto halo_loads = [&](int zp) {
+    if (!hlane) return;
+    const uint32_t n = hcol + plane * wrap_plane(zp, nz);
+    hskip = TYPED && special_type(P.type[n]);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) HL[k] = __ldg(P.lam_next[k] + n);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) HM[k] = __ldg(P.m_next[k] + n);
+  };
+  auto halo_finish = [&](int buf) {
+    if (!hlane) return;
+    float lM[10], lJ[3];
+    fin_t_or_zero(hskip, HL, HM, lM, lJ);
+    LamT t[6];
+    x_proj(lM, t);
+    float* h = hb + ((buf * 2 + hside) * AFY + lane) * 8;
+    // the left column pushes its lmr to x0, the right column its lpl to x0 + w - 1
+    *reinterpret_cast<float4*>(h) = hside == 0 ? make_float4(t[0].m, t[1].m, t[2].m, t[3].m)
+                                               : make_float4(t[0].p, t[1].p, t[2].p, t[3].p);
+    *reinterpret_cast<float2*>(h + 4) =
+        hside == 0 ? make_float2(t[4].m, t[5].m) : make_float2(t[4].p, t[5].p);
+  };
+
+  // ---- the tile's own cells: plane zz's lambda' and output state one step ahead
   float Lnext[10], Mnext[4];
   bool skip_next = false;
   auto load_plane = [&](int zp) {
-    const size_t n = col + plane * size_t(wrapi(zp, nz));
+    const uint32_t n = col + plane * wrap_plane(zp, nz);
     skip_next = TYPED && special_type(P.type[n]);
 #pragma unroll
-    for (int k = 0; k < 10; ++k) Lnext[k] = __ldg(P.lam_next + k * N + n);
+    for (int k = 0; k < 10; ++k) Lnext[k] = __ldg(P.lam_next[k] + n);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) Mnext[k] = __ldg(P.m_next + k * N + n);
+    for (int k = 0; k < 4; ++k) Mnext[k] = __ldg(P.m_next[k] + n);
   };
-  load_plane(z0 - 1);
-  int parity = 0;
-  for (int zz = z0 - 1; zz <= z1; ++zz, parity ^= 1) {
-    const int zo = zz - 1;  // the plane finished in this iteration
-    const bool out_plane = zo >= z0;
-    // the input state (and force, gradient) of plane zo, used after the passes
-    const bool do_out = out_plane && own;
+  load_plane(zs - 1);
+  halo_loads(zs - 1);
+  halo_finish(0);
+  halo_loads(zs);
+  halo_finish(1);
+  halo_loads(zs + 1);
+  __syncthreads();
+
+  float zl[NZS], m1[NZS], m2[NZS];  // z-march state per (p, q) slice
+#pragma unroll
+  for (int k = 0; k < NZS; ++k) zl[k] = m1[k] = m2[k] = 0.f;
+  float gprev[3] = {0.f, 0.f, 0.f};  // F/2 share of Fin^T at plane zz - 1
+  uint32_t no = col + plane * uint32_t(zs);  // the cell of plane zz - 1 once i >= 2
+#pragma unroll 2  // two trips per pass, so the carried registers alternate instead of moving
+  for (int i = 0; i < n_it; ++i) {
+    const int zz = zs - 1 + i;
+    const bool out_plane = i >= 2;  // plane zz - 1 is finished in this iteration
+    const int buf = i & 1;
+    // the input state (and force, gradient) of plane zz - 1, used in phase B
     float mt[10], fo[3] = {0.f, 0.f, 0.f}, go[3] = {0.f, 0.f, 0.f};
     bool solid_out = false;
-    const size_t no = col + plane * size_t(zo < 0 ? 0 : zo);
-    if (do_out) {
+    if (out_plane && own) {
       solid_out = TYPED && P.type[no] == T_SOLID;
 #pragma unroll
-      for (int k = 0; k < 10; ++k) mt[k] = __ldg(P.m_t + k * N + no);
+      for (int k = 0; k < 10; ++k) mt[k] = __ldg(P.m_t[k] + no);
       if (FORCE)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          fo[a] = __ldg(P.force + a * N + no);
-          go[a] = P.gF[a * N + no];
+          fo[a] = __ldg(P.force[a] + no);
+          go[a] = P.gF[a][no];
         }
     }
-    // ---- fin^T at plane zz, then proj^T along z of the six (d, e) slices
+    // ---- phase A: Fin^T at plane zz
     float lam[10], mn[4];
     const bool skip = skip_next;
 #pragma unroll
     for (int k = 0; k < 10; ++k) lam[k] = Lnext[k];
 #pragma unroll
     for (int k = 0; k < 4; ++k) mn[k] = Mnext[k];
-    if (zz + 1 <= z1) load_plane(zz + 1);
-    float lM[10];
-    float lJ[3] = {0.f, 0.f, 0.f};
-    if (skip) {
-      for (int k = 0; k < 10; ++k) lM[k] = 0.f;
-    } else {
-      Stored o;  // fin_vjp_cell reads rho - 1 and u of the output only
-      o.drho = mn[0];
-      o.ux = mn[1];
-      o.uy = mn[2];
-      o.uz = mn[3];
-      o.nxx = o.nyy = o.nzz = o.nxy = o.nxz = o.nyz = 0.f;
-      fin_vjp_cell(o, lam, lM, lJ);
+    if (i + 1 < n_it) load_plane(zz + 1);
+    float lM[10], lJ[3];
+    fin_t_or_zero(skip, lam, mn, lM, lJ);
+    // x^T: lpl from x + 1, lmr from x - 1; the tile's ends from the halo buffer
+    LamT tx[6];
+    x_proj(lM, tx);
+    const float* hl = hb + (buf * 2 * AFY + row) * 8;
+    const float* hr = hl + AFY * 8;
+    const float4 hl4 = *reinterpret_cast<const float4*>(hl);
+    const float2 hl2 = *reinterpret_cast<const float2*>(hl + 4);
+    const float4 hr4 = *reinterpret_cast<const float4*>(hr);
+    const float2 hr2 = *reinterpret_cast<const float2*>(hr + 4);
+    const float hlv[6] = {hl4.x, hl4.y, hl4.z, hl4.w, hl2.x, hl2.y};
+    const float hrv[6] = {hr4.x, hr4.y, hr4.z, hr4.w, hr2.x, hr2.y};
+    float X[6][3];  // [x slice (q, r)][p]
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      float lp = __shfl_down_sync(FULL, tx[s].p, 1);
+      float lm = __shfl_up_sync(FULL, tx[s].m, 1);
+      lm = left_end ? hlv[s] : lm;
+      lp = right_end ? hrv[s] : lp;
+      phi_t(lp, tx[s].z, lm, X[s][0], X[s][1], X[s][2]);
     }
-    // slices (d, e) = (0,0) (1,0) (0,1) (2,0) (1,1) (0,2), inputs over f
-    const LamT t[6] = {proj_t(lM[0], lM[3], lM[6]), proj_t(lM[1], lM[8], 0.f),
-                       proj_t(lM[2], lM[9], 0.f),   proj_t(lM[4], 0.f, 0.f),
-                       proj_t(lM[7], 0.f, 0.f),     proj_t(lM[5], 0.f, 0.f)};
-    float Z[6][3];  // lZ[(d, e)][r] of plane zo
-    for (int k = 0; k < 6; ++k) {
-      phi_t(t[k].p, zl[k], m2[k], Z[k][0], Z[k][1], Z[k][2]);
-      m2[k] = m1[k];
-      m1[k] = t[k].m;
-      zl[k] = t[k].z;
+    // y projection of the nine (p, r) slices (slot 3 p + r), inputs over q
+    float yp[9], ym[9], yz[9];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const LamT a = proj_t(X[0][p], X[1][p], X[3][p]);
+      const LamT b = proj_t(X[2][p], X[4][p], 0.f);
+      const LamT c = proj_t(X[5][p], 0.f, 0.f);
+      yp[3 * p] = a.p, ym[3 * p] = a.m, yz[3 * p] = a.z;
+      yp[3 * p + 1] = b.p, ym[3 * p + 1] = b.m, yz[3 * p + 1] = b.z;
+      yp[3 * p + 2] = c.p, ym[3 * p + 2] = c.m, yz[3 * p + 2] = c.z;
     }
+    const int o4 = buf * (AY4 / 2), o1 = buf * (AY1 / 2);
+    yp4[o4] = make_float4(yp[0], yp[1], yp[2], yp[3]);
+    yp4[o4 + AFX] = make_float4(yp[4], yp[5], yp[6], yp[7]);
+    ym4[o4] = make_float4(ym[0], ym[1], ym[2], ym[3]);
+    ym4[o4 + AFX] = make_float4(ym[4], ym[5], ym[6], ym[7]);
+    yp1[o1] = yp[8];
+    ym1[o1] = ym[8];
     const float gcur[3] = {gprev[0], gprev[1], gprev[2]};
     gprev[0] = 0.5f * lJ[0];
     gprev[1] = 0.5f * lJ[1];
     gprev[2] = 0.5f * lJ[2];
-    if (!out_plane) continue;  // block-uniform
-    // ---- y^T on slices (d, r): inputs over e
-    float* sp = asm_ + parity * ASM;
-    // lZ by (d, e): index of (d, e) in the six slices, -1 = absent
-    const int DE[3][3] = {{0, 2, 5}, {1, 4, -1}, {3, -1, -1}};
-    float yz[ANS];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float e0 = Z[DE[d][0]][r];
-        const float e1 = DE[d][1] >= 0 ? Z[DE[d][1]][r] : 0.f;
-        const float e2 = DE[d][2] >= 0 ? Z[DE[d][2]][r] : 0.f;
-        const LamT u = proj_t(e0, e1, e2);
-        const int s_ = 3 * d + r;
-        sp[(s_ * AFY + row) * AFX + lane] = u.p;
-        sp[((ANS + s_) * AFY + row) * AFX + lane] = u.m;
-        yz[s_] = u.z;
-      }
     __syncthreads();
-    if (!mid_row) continue;
-    float Y[3][3][3];  // lY[d][q][r]
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const int s_ = 3 * d + r;
-        const float lp = sp[(s_ * AFY + row + 1) * AFX + lane];         // lpl of y + 1
-        const float lm = sp[((ANS + s_) * AFY + row - 1) * AFX + lane];  // lmr of y - 1
-        phi_t(lp, yz[s_], lm, Y[d][0][r], Y[d][1][r], Y[d][2][r]);
+    if (!owned_row) {
+      // ---- phase B of the halo warps: plane zz + 2's halo cells into buffer i & 1
+      if (i + 2 < n_it) {
+        halo_finish(buf);
+        if (i + 3 < n_it) halo_loads(zz + 3);
       }
-    // ---- x^T on slices (q, r): inputs over d, exchanged by shuffles
-    float X[3][3][3];  // lmu[p][q][r]
+      continue;
+    }
+    // ---- phase B: y^T (lpl of y + 1, lmr of y - 1)
+    float Y[3][3][3];  // [p][r][q]
+    {
+      const float4 pa = yp4[o4 + 2 * AFX], pb = yp4[o4 + 3 * AFX];  // row + 1
+      const float4 ma = ym4[o4 - 2 * AFX], mb = ym4[o4 - AFX];      // row - 1
+      const float lp[9] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w, yp1[o1 + AFX]};
+      const float lm[9] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w, ym1[o1 - AFX]};
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
+      for (int s = 0; s < 9; ++s)
+        phi_t(lp[s], yz[s], lm[s], Y[s / 3][s % 3][0], Y[s / 3][s % 3][1], Y[s / 3][s % 3][2]);
+    }
+    // z projection of the (p, q) slices (00) (10) (01) (20) (02) (11) (21) (12) [(22)],
+    // inputs over r; z^T of plane zz - 1 with its carried lz and plane zz - 2's lmr
+    constexpr int ZP[9] = {0, 1, 0, 2, 0, 1, 2, 1, 2}, ZQ[9] = {0, 0, 1, 0, 2, 1, 1, 2, 2};
+    float Z[NZS][3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        if (!Q19 && q == 2 && r == 2) continue;  // no D3Q27 Hermite moment has q = r = 2
-        const LamT u = proj_t(Y[0][q][r], Y[1][q][r], Y[2][q][r]);
-        const float lp = __shfl_down_sync(FULL, u.p, 1);  // lpl of x + 1
-        const float lm = __shfl_up_sync(FULL, u.m, 1);    // lmr of x - 1
-        phi_t(lp, u.z, lm, X[0][q][r], X[1][q][r], X[2][q][r]);
-      }
+    for (int k = 0; k < NZS; ++k) {
+      const LamT t = proj_t(Y[ZP[k]][0][ZQ[k]], Y[ZP[k]][1][ZQ[k]], Y[ZP[k]][2][ZQ[k]]);
+      phi_t(t.p, zl[k], m2[k], Z[k][0], Z[k][1], Z[k][2]);
+      m2[k] = m1[k];
+      m1[k] = t.m;
+      zl[k] = t.z;
+    }
+    if (!out_plane) continue;
+    const uint32_t n_out = no;
+    no += plane;
     if (!own) continue;
-    // ---- Coll^T at plane zo
+    // ---- Coll^T at plane zz - 1
     if (solid_out) {
-      for (int k = 0; k < 10; ++k) P.lam_out[k * N + no] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 10; ++k) P.lam_out[k][n_out] = 0.f;
       continue;
     }
     // Mom17 order: 000 100 010 001 200 020 002 110 101 011 210 120 201 102 021 012 111
-    float lmu[17] = {X[0][0][0], X[1][0][0], X[0][1][0], X[0][0][1], X[2][0][0],
-                     X[0][2][0], X[0][0][2], X[1][1][0], X[1][0][1], X[0][1][1],
-                     X[2][1][0], X[1][2][0], X[2][0][1], X[1][0][2], X[0][2][1],
-                     X[0][1][2], X[1][1][1]};
+    float lmu[17] = {Z[0][0], Z[1][0], Z[2][0], Z[0][1], Z[3][0], Z[4][0],
+                     Z[0][2], Z[5][0], Z[1][1], Z[2][1], Z[6][0], Z[7][0],
+                     Z[3][1], Z[1][2], Z[4][1], Z[2][2], Z[5][1]};
     if constexpr (Q19) {
       // D3Q19: mu_111 = 0, and the ten further tensor moments are the linear
       // closure of the others (closure19), whose transpose adds their adjoints
       lmu[16] = 0.f;
-      const float l220 = X[2][2][0], l202 = X[2][0][2], l022 = X[0][2][2];
-      const float l211 = X[2][1][1], l121 = X[1][2][1], l112 = X[1][1][2];
-      const float l221 = X[2][2][1], l212 = X[2][1][2], l122 = X[1][2][2], l222 = X[2][2][2];
+      const float l202 = Z[3][2], l022 = Z[4][2], l112 = Z[5][2];
+      const float l211 = Z[6][1], l212 = Z[6][2], l121 = Z[7][1], l122 = Z[7][2];
+      const float l220 = Z[NZS - 1][0], l221 = Z[NZS - 1][1], l222 = Z[NZS - 1][2];
       lmu[6] -= l220 * (1.0f / 6.0f) + l222 * (1.0f / 18.0f);
       lmu[5] -= l202 * (1.0f / 6.0f) + l222 * (1.0f / 18.0f);
       lmu[4] -= l022 * (1.0f / 6.0f) + l222 * (1.0f / 18.0f);
@@ -553,9 +675,11 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(AdjStreamParams
     st.nyz = mt[9];
     float lin[10];
     collide_vjp<FORCE>(st, P.omega, fo, lmu, lin, lf);
-    for (int k = 0; k < 10; ++k) P.lam_out[k * N + no] = lin[k];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) P.lam_out[k][n_out] = lin[k];
     if (FORCE)
-      for (int a = 0; a < 3; ++a) P.gF[a * N + no] = go[a] + (lf[a] + gcur[a]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) P.gF[a][n_out] = go[a] + (lf[a] + gcur[a]);
   }
 }
 
@@ -620,10 +744,10 @@ cudaError_t launch_adj_stream_t(AdjStreamParams& p, cudaStream_t st) {
     sms[dev] = n > 0 ? n : 1;
   }
   // z-chunk: minimise waves (one block per SM) times the planes a block marches
-  const int64_t tiles = int64_t((p.nx + AIX - 1) / AIX) * ((p.ny + AIY - 1) / AIY);
+  const int64_t tiles = int64_t((p.nx + AFX - 1) / AFX) * ((p.ny + AIY - 1) / AIY);
   int best = 1;
   int64_t best_cost = INT64_MAX;
-  for (int zc = std::min(p.nz, 128); zc >= 1; --zc) {
+  for (int zc = std::min(p.nz, 256); zc >= 1; --zc) {
     const int64_t blocks = tiles * ((p.nz + zc - 1) / zc);
     const int64_t cost = (blocks + sms[dev] - 1) / sms[dev] * (zc + 2);
     if (cost < best_cost) {
@@ -632,22 +756,22 @@ cudaError_t launch_adj_stream_t(AdjStreamParams& p, cudaStream_t st) {
     }
   }
   p.zc = best;
-  const dim3 grid((p.nx + AIX - 1) / AIX, (p.ny + AIY - 1) / AIY, (p.nz + best - 1) / best);
+  const dim3 grid((p.nx + AFX - 1) / AFX, (p.ny + AIY - 1) / AIY, (p.nz + best - 1) / best);
   adj_stream_kernel<FORCE, TYPED, Q19><<<grid, dim3(AFX, AFY), ADJ_SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
 template <bool Q19>
-cudaError_t launch_adj_stream_l(AdjStreamParams& p, cudaStream_t st) {
-  if (p.force)
+cudaError_t launch_adj_stream_l(AdjStreamParams& p, bool force, cudaStream_t st) {
+  if (force)
     return p.type ? launch_adj_stream_t<true, true, Q19>(p, st)
                   : launch_adj_stream_t<true, false, Q19>(p, st);
   return p.type ? launch_adj_stream_t<false, true, Q19>(p, st)
                 : launch_adj_stream_t<false, false, Q19>(p, st);
 }
 
-cudaError_t launch_adj_stream(AdjStreamParams& p, int lattice, cudaStream_t st) {
-  return lattice == 19 ? launch_adj_stream_l<true>(p, st) : launch_adj_stream_l<false>(p, st);
+cudaError_t launch_adj_stream(AdjStreamParams& p, bool force, int lattice, cudaStream_t st) {
+  return lattice == 19 ? launch_adj_stream_l<true>(p, force, st) : launch_adj_stream_l<false>(p, force, st);
 }
 
 }  // namespace
@@ -688,6 +812,8 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: requires MELBM_F32 storage");
   if (h->wall_model != 0)
     return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: the adjoint covers halfway bounce-back walls only");
+  if (10 * uint64_t(h->N) >= (uint64_t(1) << 32))
+    return adj_fail(h, MELBM_EINVAL, "melbm_forward_checkpointed: the adjoint takes grids of fewer than 429496730 cells");
   if (int rc = ensure_boundaries(h)) return rc;
   if (h->boundary_error)
     return adj_fail(h, MELBM_ESTATE, "melbm_forward_checkpointed: the last boundary setup failed");
@@ -807,15 +933,19 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
       ap.ny = h->ny;
       ap.nz = h->nz;
       ap.zc = 0;
-      ap.lam_next = lam;
-      ap.m_next = m_next;
-      ap.m_t = m_t;
-      ap.force = h->force;
+      for (int k = 0; k < 10; ++k) {
+        ap.lam_next[k] = lam + k * N;
+        ap.m_t[k] = m_t + k * N;
+        ap.lam_out[k] = lam2 + k * N;
+      }
+      for (int k = 0; k < 4; ++k) ap.m_next[k] = m_next + k * N;
+      for (int a3 = 0; a3 < 3; ++a3) {
+        ap.force[a3] = h->force ? h->force + a3 * N : nullptr;
+        ap.gF[a3] = a->gF + a3 * N;
+      }
       ap.type = h->type;
-      ap.lam_out = lam2;
-      ap.gF = a->gF;
       ap.omega = omega;
-      ADJ_CUDA(h, launch_adj_stream(ap, h->lattice, st));
+      ADJ_CUDA(h, launch_adj_stream(ap, h->force != nullptr, h->lattice, st));
       if (h->L) {
         const unsigned lb = blocks_for(h->L);
         const bool q19 = h->lattice == MELBM_D3Q19;
