@@ -180,14 +180,21 @@ int reclassify_lists(melbm_t h) {
       return rc;
   }
   const int64_t nb = classify_blocks(h->nx, h->ny, h->nz);
+  const size_t Wb = size_t(classify_words(h->nx, h->ny, h->nz)) * 4;
   if (!h->cl_counts) {
     if ((rc = dev_alloc(h, (void**)&h->cl_counts, size_t(nb) * 4))) return rc;
     if ((rc = dev_alloc(h, (void**)&h->cl_offsets, size_t(nb) * 4))) return rc;
     if ((rc = dev_alloc(h, (void**)&h->cl_total, 4))) return rc;
+    if ((rc = dev_alloc(h, (void**)&h->cl_mbits, Wb))) return rc;
+    if ((rc = dev_alloc(h, (void**)&h->cl_lbits, Wb))) return rc;
   }
-  MELBM_CUDA(h, launch_classify_count(h->nx, h->ny, h->nz, h->mask, h->inflow_on, h->outflow_on,
+  if (h->mask)
+    MELBM_CUDA(h, launch_pack_mask(h->mask, h->nx, h->ny, h->nz, h->cl_mbits, h->stream));
+  const uint32_t* mbits = h->mask ? h->cl_mbits : nullptr;
+  MELBM_CUDA(h, launch_classify_count(h->nx, h->ny, h->nz, mbits, h->inflow_on, h->outflow_on,
                                      h->type, tables ? h->cls_solid : nullptr,
-                                     tables ? h->cls_fb : nullptr, h->cl_counts, h->stream));
+                                     tables ? h->cls_fb : nullptr, h->cl_lbits, h->cl_counts,
+                                     h->stream));
   MELBM_CUDA(h, launch_exclusive_scan(h->cl_counts, h->cl_offsets, nb, h->cl_total, h->stream));
   uint32_t total = 0;
   MELBM_CUDA(h, cudaMemcpyAsync(&total, h->cl_total, 4, cudaMemcpyDeviceToHost, h->stream));
@@ -211,8 +218,8 @@ int reclassify_lists(melbm_t h) {
     if (tables && !h->side && (rc = dev_alloc(h, (void**)&h->side, size_t(h->L_cap) * 10 * 4)))
       return rc;
     h->L = total;
-    MELBM_CUDA(h, launch_classify_scatter(h->nx, h->ny, h->nz, h->mask, h->inflow_on,
-                                          h->outflow_on, h->type, h->cl_offsets, h->list_cell,
+    MELBM_CUDA(h, launch_classify_scatter(h->nx, h->ny, h->nz, mbits, h->inflow_on,
+                                          h->outflow_on, h->cl_lbits, h->cl_offsets, h->list_cell,
                                           h->list_word, tables ? h->cls_pref : nullptr, h->stream));
   } else {
     h->L = 0;
@@ -407,6 +414,8 @@ int melbm_destroy(melbm_t h) {
   dev_free(h, h->cl_counts, 0);
   dev_free(h, h->cl_offsets, 0);
   dev_free(h, h->cl_total, 0);
+  dev_free(h, h->cl_mbits, 0);
+  dev_free(h, h->cl_lbits, 0);
   dev_free(h, h->force, 0);
   dev_free(h, h->staging, 0);
   dev_free(h, h->red_partials, 0);

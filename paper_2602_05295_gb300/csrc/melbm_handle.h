@@ -43,9 +43,14 @@ struct melbm_sim {
   // solids, inflow or outflow changed since the last classification: the next
   // call that needs the types or the list classifies first
   bool boundary_pending = false;
+  // classification scratch: listed cells per block of words and the blocks'
+  // first list indices, their total, the packed mask and the listed cells of
+  // every word (W words each)
   uint32_t* cl_counts = nullptr;
   uint32_t* cl_offsets = nullptr;
   uint32_t* cl_total = nullptr;
+  uint32_t* cl_mbits = nullptr;
+  uint32_t* cl_lbits = nullptr;
   int inflow_on = 0;
   float inflow[4] = {1.f, 0.f, 0.f, 0.f};
   int outflow_on = 0;

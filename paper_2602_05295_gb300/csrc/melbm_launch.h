@@ -122,20 +122,25 @@ cudaError_t launch_outflow(int storage, int nx, int ny, int nz, void* buf, const
                            cudaStream_t st);
 
 // Classification (classify.cu), by 32-cell row words (tx, y, z), ntx =
-// ceil(nx / 32) words per row: pass 1 writes the types (N) and the number of
+// ceil(nx / 32) words per row, word index tx + ntx (y + ny z), W of them:
+// pack_mask packs the mask to one bit per cell (W words); pass 1 writes the types
+// (N), the mask of listed cells of every word (lbits, W words), the number of
 // listed cells of each block of words (classify_blocks of them) and, when solid_w
 // is given, the SOLID and FLUID_BOUNDARY bits of every word; after an exclusive
-// scan of the counts, pass 2 writes the list in ascending n and, when pref_w is
-// given, the list index of every word's first listed cell (see BoundaryTables).
+// scan of the block counts, pass 2 writes the list in ascending n and, when pref_w
+// is given, the list index of every word's first listed cell (see BoundaryTables).
+// mbits NULL: no solids.
 int64_t classify_words(int nx, int ny, int nz);
 int64_t classify_blocks(int nx, int ny, int nz);
-cudaError_t launch_classify_count(int nx, int ny, int nz, const uint8_t* mask, int inflow,
+cudaError_t launch_pack_mask(const uint8_t* mask, int nx, int ny, int nz, uint32_t* bits,
+                             cudaStream_t st);
+cudaError_t launch_classify_count(int nx, int ny, int nz, const uint32_t* mbits, int inflow,
                                   int outflow, uint8_t* type, uint32_t* solid_w, uint32_t* fb_w,
-                                  uint32_t* block_counts, cudaStream_t st);
+                                  uint32_t* lbits, uint32_t* block_cnt, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
                                   cudaStream_t st);
-cudaError_t launch_classify_scatter(int nx, int ny, int nz, const uint8_t* mask, int inflow,
-                                    int outflow, const uint8_t* type, const uint32_t* block_offsets,
+cudaError_t launch_classify_scatter(int nx, int ny, int nz, const uint32_t* mbits, int inflow,
+                                    int outflow, const uint32_t* lbits, const uint32_t* block_off,
                                     uint32_t* cells, uint32_t* words, uint32_t* pref_w,
                                     cudaStream_t st);
 
