@@ -55,6 +55,86 @@ constexpr uint32_t d3q19_links() {
 constexpr uint32_t D3Q19_LINKS = d3q19_links();
 static_assert(D3Q19_LINKS == 0x2EBFEBAu, "19 directions");
 
+// The halfway bounce-back sums of one D3Q27 cell, all links at once.  With F(c)
+// = f+(c) - w(c) the cell's own post-collision populations (rest removed), a
+// solid link i returns F(-c_i), so the sums are  sum_{i in S} F(-c_i) e(c_i),
+// e = (1, c, c c - 1/3).  Substituting j = opp(i) = 26 - i they are the moments
+// of F masked by the reversed link set S'(j) = S(26 - j), with the odd (first)
+// moments negated.  F on the 27 directions is the tensor product of the D1Q3
+// population maps (phi3) applied along x, y and z to the 17 Hermite moments
+// (Eq. three_order_f), and the masked moments are three separable sums, so the
+// cost does not depend on the number of solid links.
+__device__ __forceinline__ void bounce_sums27(const Mom17& A, uint32_t links, float dm[10]) {
+  // x: the eight (q, r) slices (the (2, 2) slice carries no D3Q27 moment)
+  Phi X[3][3];  // X[q][r] over cx
+  X[0][0] = phi3(A.m000, A.m100, A.m200);
+  X[1][0] = phi3(A.m010, A.m110, A.m210);
+  X[2][0] = phi3(A.m020, A.m120, 0.f);
+  X[0][1] = phi3(A.m001, A.m101, A.m201);
+  X[1][1] = phi3(A.m011, A.m111, 0.f);
+  X[2][1] = phi3(A.m021, 0.f, 0.f);
+  X[0][2] = phi3(A.m002, A.m102, 0.f);
+  X[1][2] = phi3(A.m012, 0.f, 0.f);
+  X[2][2] = Phi{0.f, 0.f, 0.f};
+  const uint32_t rs = __brev(links) >> 5;  // bit j: the link opp(j) is solid
+  // y then z per x direction; F(cx, cy, cz) is bit (cx+1) + 3 (cy+1) + 9 (cz+1)
+  // of the reversed mask.  The masked populations are summed back to moments
+  // along z, y and x.
+  float Sx[3][6];  // per cx: the (q, r) moments (00) (10) (01) (20) (11) (02) of the masked F
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {  // a = cx + 1
+    auto comp = [&](const Phi& p) { return a == 2 ? p.p : (a == 1 ? p.z : p.m); };
+    Phi Y[3];  // Y[r] over cy
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Y[r] = phi3(comp(X[0][r]), comp(X[1][r]), comp(X[2][r]));
+    float T[3][3];  // T[cy+1][r'] : z-moments (r' = 0, 1, 2) of the masked column
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {  // b = cy + 1
+      auto compy = [&](const Phi& p) { return b == 2 ? p.p : (b == 1 ? p.z : p.m); };
+      const Phi Z = phi3(compy(Y[0]), compy(Y[1]), compy(Y[2]));
+      const int j0 = a + 3 * b;  // cz = -1; cz = 0 at j0 + 9, cz = +1 at j0 + 18
+      const float fm = (rs >> j0) & 1u ? Z.m : 0.f;
+      const float fz = (rs >> (j0 + 9)) & 1u ? Z.z : 0.f;
+      const float fp = (rs >> (j0 + 18)) & 1u ? Z.p : 0.f;
+      const float lr = fp + fm;
+      T[b][0] = lr + fz;
+      T[b][1] = fp - fm;
+      T[b][2] = __fmaf_rn(T[b][0], -1.0f / 3.0f, lr);
+    }
+    // y moments q of each z moment r'
+    auto ysum = [&](int r, int q) {
+      const float lr = T[2][r] + T[0][r];
+      if (q == 0) return lr + T[1][r];
+      if (q == 1) return T[2][r] - T[0][r];
+      return __fmaf_rn(lr + T[1][r], -1.0f / 3.0f, lr);
+    };
+    Sx[a][0] = ysum(0, 0);
+    Sx[a][1] = ysum(0, 1);
+    Sx[a][2] = ysum(1, 0);
+    Sx[a][3] = ysum(0, 2);
+    Sx[a][4] = ysum(1, 1);
+    Sx[a][5] = ysum(2, 0);
+  }
+  // x moments: (p, q, r) for the ten outputs; S[2] is cx = +1, S[0] cx = -1
+  auto xs = [&](int k, int p) {
+    const float lr = Sx[2][k] + Sx[0][k];
+    if (p == 0) return lr + Sx[1][k];
+    if (p == 1) return Sx[2][k] - Sx[0][k];
+    return __fmaf_rn(lr + Sx[1][k], -1.0f / 3.0f, lr);
+  };
+  // the reflection j = opp(i) flips the sign of the first moments
+  dm[0] = xs(0, 0);
+  dm[1] = -xs(0, 1);
+  dm[2] = -xs(1, 0);
+  dm[3] = -xs(2, 0);
+  dm[4] = xs(0, 2);
+  dm[5] = xs(3, 0);
+  dm[6] = xs(5, 0);
+  dm[7] = xs(1, 1);
+  dm[8] = xs(2, 1);
+  dm[9] = xs(4, 0);
+}
+
 template <int STORAGE, bool FORCE, bool MOVING, bool Q19 = false>
 __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -92,9 +172,24 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   }
   const Mom17 A =
       collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n, P.q), P.omega, fx0, fy0, fz0);
-  // each thread loops over its own solid links (bit scan of its link mask), so a
-  // warp runs as many iterations as its busiest cell
   uint32_t links = word & 0x7FFFFFFu;
+  if constexpr (!MOVING && !Q19) {
+    float dm[10];
+    bounce_sums27(A, links, dm);
+    m000 += dm[0];
+    m100 += dm[1];
+    m010 += dm[2];
+    m001 += dm[3];
+    m200 += dm[4];
+    m020 += dm[5];
+    m002 += dm[6];
+    m110 += dm[7];
+    m101 += dm[8];
+    m011 += dm[9];
+    links = 0;
+  }
+  // otherwise each thread loops over its own solid links (bit scan of its link
+  // mask), so a warp runs as many iterations as its busiest cell
   if (Q19) links &= D3Q19_LINKS;
   while (links) {
     const int i = __ffs(links) - 1;
