@@ -375,18 +375,18 @@ constexpr int AY1 = 2 * 2 * AFY * AFX;
 constexpr int AHB = 2 * 2 * AFY * 8;
 constexpr size_t ADJ_SMEM = size_t(AY4) * sizeof(float4) + size_t(AY1 + AHB) * sizeof(float);
 
-// Field planes are addressed through per-field base pointers held in the kernel
-// parameters (uniform), so each access adds one 32-bit per-thread cell offset
-// (the launcher requires 10 N < 2^32).
+// Each field is a [k][N] array of planes addressed from one base pointer with a
+// 32-bit index n + k N (the launcher requires 10 N < 2^32); per-plane pointers
+// in the parameters were reloaded from the constant bank at every access.
 struct AdjStreamParams {
   int nx, ny, nz, zc;
-  const float* lam_next[10];  // adjoint of the output state (stored variables)
-  const float* m_next[4];     // output state: rho - 1 and u
-  const float* m_t[10];       // input state
-  const float* force[3];      // null without force
-  const uint8_t* type;        // N or null
-  float* lam_out[10];         // adjoint of the input state
-  float* gF[3];               // accumulated dL/dF
+  const float* lam_next;  // [10][N] adjoint of the output state (stored variables)
+  const float* m_next;    // [4][N]: output state, rho - 1 and u (planes of a [10][N] state)
+  const float* m_t;       // [10][N] input state
+  const float* force;     // [3][N], null without force
+  const uint8_t* type;    // N or null
+  float* lam_out;         // [10][N] adjoint of the input state
+  float* gF;              // [3][N] accumulated dL/dF
   float omega;
 };
 
@@ -447,6 +447,7 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(const __grid_co
   const int lane = threadIdx.x, row = threadIdx.y;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const uint32_t plane = uint32_t(nx) * uint32_t(ny);
+  const uint32_t NN = plane * uint32_t(nz);  // cells: the plane stride of every field
   const int x0 = int(blockIdx.x) * AFX, y0 = int(blockIdx.y) * AIY;
   const int zs = int(blockIdx.z) * P.zc, ze = min(zs + P.zc, nz);
   const int w = min(AFX, nx - x0);  // columns of this tile; lane w - 1 takes the right halo
@@ -478,9 +479,9 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(const __grid_co
     const uint32_t n = hcol + plane * wrap_plane(zp, nz);
     hskip = TYPED && special_type(P.type[n]);
 #pragma unroll
-    for (int k = 0; k < 10; ++k) HL[k] = __ldg(P.lam_next[k] + n);
+    for (int k = 0; k < 10; ++k) HL[k] = __ldg(P.lam_next + (n + uint32_t(k) * NN));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) HM[k] = __ldg(P.m_next[k] + n);
+    for (int k = 0; k < 4; ++k) HM[k] = __ldg(P.m_next + (n + uint32_t(k) * NN));
   };
   auto halo_finish = [&](int buf) {
     if (!hlane) return;
@@ -503,9 +504,9 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(const __grid_co
     const uint32_t n = col + plane * wrap_plane(zp, nz);
     skip_next = TYPED && special_type(P.type[n]);
 #pragma unroll
-    for (int k = 0; k < 10; ++k) Lnext[k] = __ldg(P.lam_next[k] + n);
+    for (int k = 0; k < 10; ++k) Lnext[k] = __ldg(P.lam_next + (n + uint32_t(k) * NN));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) Mnext[k] = __ldg(P.m_next[k] + n);
+    for (int k = 0; k < 4; ++k) Mnext[k] = __ldg(P.m_next + (n + uint32_t(k) * NN));
   };
   load_plane(zs - 1);
   halo_loads(zs - 1);
@@ -531,12 +532,12 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(const __grid_co
     if (out_plane && own) {
       solid_out = TYPED && P.type[no] == T_SOLID;
 #pragma unroll
-      for (int k = 0; k < 10; ++k) mt[k] = __ldg(P.m_t[k] + no);
+      for (int k = 0; k < 10; ++k) mt[k] = __ldg(P.m_t + (no + uint32_t(k) * NN));
       if (FORCE)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          fo[a] = __ldg(P.force[a] + no);
-          go[a] = P.gF[a][no];
+          fo[a] = __ldg(P.force + (no + uint32_t(a) * NN));
+          go[a] = P.gF[no + uint32_t(a) * NN];
         }
     }
     // ---- phase A: Fin^T at plane zz
@@ -630,7 +631,7 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(const __grid_co
     // ---- Coll^T at plane zz - 1
     if (solid_out) {
 #pragma unroll
-      for (int k = 0; k < 10; ++k) P.lam_out[k][n_out] = 0.f;
+      for (int k = 0; k < 10; ++k) P.lam_out[n_out + uint32_t(k) * NN] = 0.f;
       continue;
     }
     // Mom17 order: 000 100 010 001 200 020 002 110 101 011 210 120 201 102 021 012 111
@@ -676,10 +677,10 @@ __global__ void __launch_bounds__(AFX* AFY, 1) adj_stream_kernel(const __grid_co
     float lin[10];
     collide_vjp<FORCE>(st, P.omega, fo, lmu, lin, lf);
 #pragma unroll
-    for (int k = 0; k < 10; ++k) P.lam_out[k][n_out] = lin[k];
+    for (int k = 0; k < 10; ++k) P.lam_out[n_out + uint32_t(k) * NN] = lin[k];
     if (FORCE)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) P.gF[a][n_out] = go[a] + (lf[a] + gcur[a]);
+      for (int a = 0; a < 3; ++a) P.gF[n_out + uint32_t(a) * NN] = go[a] + (lf[a] + gcur[a]);
   }
 }
 
@@ -933,16 +934,12 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
       ap.ny = h->ny;
       ap.nz = h->nz;
       ap.zc = 0;
-      for (int k = 0; k < 10; ++k) {
-        ap.lam_next[k] = lam + k * N;
-        ap.m_t[k] = m_t + k * N;
-        ap.lam_out[k] = lam2 + k * N;
-      }
-      for (int k = 0; k < 4; ++k) ap.m_next[k] = m_next + k * N;
-      for (int a3 = 0; a3 < 3; ++a3) {
-        ap.force[a3] = h->force ? h->force + a3 * N : nullptr;
-        ap.gF[a3] = a->gF + a3 * N;
-      }
+      ap.lam_next = lam;
+      ap.m_t = m_t;
+      ap.lam_out = lam2;
+      ap.m_next = m_next;
+      ap.force = h->force;
+      ap.gF = a->gF;
       ap.type = h->type;
       ap.omega = omega;
       ADJ_CUDA(h, launch_adj_stream(ap, h->force != nullptr, h->lattice, st));

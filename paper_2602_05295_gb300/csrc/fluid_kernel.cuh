@@ -66,7 +66,7 @@ namespace melbm {
 #define MELBM_FLUID_FY 16
 #endif
 #ifndef MELBM_FLUID_ZCHUNK
-#define MELBM_FLUID_ZCHUNK 128
+#define MELBM_FLUID_ZCHUNK 256
 #endif
 #ifndef MELBM_FLUID_MINB
 #define MELBM_FLUID_MINB 1
@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
   }
 }
 
-// z-chunk length: the even length (ZCHUNK = 128 down to 4) minimising the number of
+// z-chunk length: the even length (ZCHUNK = 256 down to 4) minimising the number of
 // waves times the plane pairs a block iterates over (chunk / 2 + 1, the first
 // pair feeding the z pass only), so that small grids still fill the GPU.
 inline int choose_zchunk(int64_t tiles_xy, int nz, int64_t resident_blocks) {
