@@ -283,8 +283,9 @@ def e2e_run(torch, melbm, wl, u_np, steps, warmup):
     return el, 40 * N, 40 * N
 
 
-def cpu_oracle_run(steps=2, warmup=1, planes=64):
-    """FP64 oracle on a 256 x 256 x `planes` periodic slab of the workload's field."""
+def cpu_oracle_run(steps=12, warmup=1, planes=128):
+    """FP64 oracle on a 256 x 256 x `planes` periodic slab of the workload's field
+    (about ten seconds on 16 cores)."""
     import oracle
     from paper_2602_05295_gb300 import workloads as W
     oracle.build()
@@ -308,20 +309,54 @@ def cpu_oracle_run(steps=2, warmup=1, planes=64):
                      f"{nx}x{ny}x{planes} slab of the 256^3 turbulence field ({cells} cells)"}
     # the same oracle on one thread, on a thinner slab
     threads = oracle.num_threads()
-    p1 = 4
+    p1, s1 = 8, 2
     m1 = oracle.initial_state_from_velocity(W.flat(u[:, :p1]))
     oracle.set_threads(1)
     try:
         m1 = oracle.step(m1, (nx, ny, p1), wl.tau)
         t1 = time.perf_counter()
-        oracle.step(m1, (nx, ny, p1), wl.tau)
+        oracle.step(m1, (nx, ny, p1), wl.tau, n=s1)
         el1 = time.perf_counter() - t1
     finally:
         oracle.set_threads(threads)
-    out["single_thread"] = {"value": nx * ny * p1 / el1 / 1e6, "unit": "MLUPS", "cores": 1,
-                            "sample": f"1 FP64 oracle step (after 1 warm-up) of a periodic "
+    out["single_thread"] = {"value": nx * ny * p1 * s1 / el1 / 1e6, "unit": "MLUPS", "cores": 1,
+                            "sample": f"{s1} FP64 oracle steps (after 1 warm-up) of a periodic "
                                       f"{nx}x{ny}x{p1} slab ({nx * ny * p1} cells)"}
+    out["boundary_workloads"] = cpu_oracle_boundary_samples()
     return out, el
+
+
+def cpu_oracle_boundary_samples():
+    """The FP64 oracle on z-slabs of the two obstacle workloads (sphere channel,
+    large procedural scene): its step with the cell types of the slab (solid,
+    fluid-boundary, inflow, outflow) from the uniform inflow state."""
+    import oracle
+    from paper_2602_05295_gb300 import workloads as W
+    res = []
+    for wl, make, u_in, planes, steps in ((W.CHANNEL512, W.sphere_pack, 0.05, 16, 6),
+                                          (W.LARGE1000, W.procedural_obstacle, 0.06, 8, 3)):
+        nx, ny, nz = wl.shape
+        mask, _ = make(wl.shape)
+        z0 = nz // 2 - planes // 2
+        slab = np.ascontiguousarray(mask[z0:z0 + planes])
+        typ = oracle.classify(slab, True, True)[0]
+        shape = (nx, ny, planes)
+        u = np.zeros((3, nx * ny * planes))
+        u[0] = u_in
+        m = oracle.initial_state_from_velocity(u)
+        inflow = [1.0, u_in, 0.0, 0.0]
+        m = oracle.step(m, shape, wl.tau, typ=typ, inflow=inflow)
+        t = time.perf_counter()
+        oracle.step(m, shape, wl.tau, typ=typ, inflow=inflow, n=steps)
+        el = time.perf_counter() - t
+        cells = nx * ny * planes
+        res.append({"workload": wl.name, "value": cells * steps / el / 1e6, "unit": "MLUPS",
+                    "cores": oracle.num_threads(), "kind": "oracle",
+                    "sample": f"{steps} FP64 oracle steps (after 1 warm-up) of planes "
+                              f"{z0}..{z0 + planes - 1} of the {nx}x{ny}x{nz} grid "
+                              f"({cells} cells, the slab periodic in z, inflow/outflow/solid "
+                              f"types of the slab)"})
+    return res
 
 
 def reference_arm(args):
