@@ -255,7 +255,10 @@ MELBM_API int melbm_sync_transfers(melbm_t h);
  * melbm_backward: given dL/d(rho, u, S) of the final state (10N device floats,
  * component-major as melbm_get_moments), writes dL/du0[3N] and dL/dF[3N]
  * (device; dL_dF may be NULL) by the hand-written discrete adjoint, recomputing
- * each segment in FP32 from its checkpoint.  Requires MELBM_F32 storage,
+ * each segment in FP32 from its checkpoint.  With checkpoints the handle holds two
+ * segment buffers (2 (K + 1) states of 40 N bytes) and recomputes segment s - 1 on
+ * a stream of its own while the adjoint runs over segment s; the call returns
+ * with all of its work ordered on the handle's stream.  Requires MELBM_F32 storage,
  * halfway bounce-back walls (wall model 0) and fewer than 429,496,730 cells
  * (10 N < 2^32; else MELBM_EINVAL); either lattice. */
 MELBM_API int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps, int K);

@@ -36,9 +36,17 @@ struct AdjointState {
   float* u0 = nullptr;        // 3N
   uint32_t* ckpt = nullptr;   // nck x 5N (16-bit states at t = K, 2K, ...)
   float* seg = nullptr;       // (K + 1) x 10N FP32 states of one segment
+  // With more than one segment the backward pass recomputes segment s - 1 into the
+  // second buffer on its own stream while the adjoint runs over segment s.
+  float* seg2 = nullptr;      // (K + 1) x 10N, only with checkpoints
+  cudaStream_t rs = nullptr;  // the recompute stream
+  cudaEvent_t ev_start = nullptr;    // work issued on the handle's stream so far
+  cudaEvent_t ev_rec[2] = {};        // the recompute into buffer b is done
+  cudaEvent_t ev_used[2] = {};       // the adjoint has finished reading buffer b
   float* lam = nullptr;       // 10N adjoint of the stored variables
   float* lam2 = nullptr;      // 10N
   float* gF = nullptr;        // 3N accumulated dL/dF
+  int64_t bytes = 0;          // device bytes held (melbm_memory_bytes)
 };
 
 void adjoint_free(AdjointState* a) {
@@ -46,9 +54,16 @@ void adjoint_free(AdjointState* a) {
   cudaFree(a->u0);
   cudaFree(a->ckpt);
   cudaFree(a->seg);
+  cudaFree(a->seg2);
   cudaFree(a->lam);
   cudaFree(a->lam2);
   cudaFree(a->gF);
+  if (a->rs) cudaStreamDestroy(a->rs);
+  if (a->ev_start) cudaEventDestroy(a->ev_start);
+  for (int b = 0; b < 2; ++b) {
+    if (a->ev_rec[b]) cudaEventDestroy(a->ev_rec[b]);
+    if (a->ev_used[b]) cudaEventDestroy(a->ev_used[b]);
+  }
   delete a;
 }
 
@@ -824,7 +839,7 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
   const int nck = (nsteps - 1) / K;  // checkpoints at t = K, 2K, ... < nsteps
   if (!a || a->N != h->N || a->K != K || a->nck < nck) {
     if (a) {
-      h->mem_bytes -= a->N * 4 * (3 + 10 * (a->K + 1) + 23) + a->N * 20 * int64_t(a->nck);
+      h->mem_bytes -= a->bytes;
       adjoint_free(a);
     }
     a = new (std::nothrow) AdjointState;
@@ -840,13 +855,21 @@ extern "C" int melbm_forward_checkpointed(melbm_t h, const float* u0, int nsteps
     if (e == cudaSuccess) e = cudaMalloc(&a->lam, N * 40);
     if (e == cudaSuccess) e = cudaMalloc(&a->lam2, N * 40);
     if (e == cudaSuccess) e = cudaMalloc(&a->gF, N * 12);
+    if (e == cudaSuccess && nck) e = cudaMalloc(&a->seg2, N * 40 * size_t(K + 1));
+    if (e == cudaSuccess && nck) e = cudaStreamCreateWithFlags(&a->rs, cudaStreamNonBlocking);
+    if (e == cudaSuccess && nck) e = cudaEventCreateWithFlags(&a->ev_start, cudaEventDisableTiming);
+    for (int b = 0; b < 2 && nck; ++b) {
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a->ev_rec[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a->ev_used[b], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       adjoint_free(a);
       h->adj = nullptr;
       return adj_fail(h, MELBM_ENOMEM, "melbm_forward_checkpointed: device allocation failed");
     }
-    h->mem_bytes += a->N * 4 * (3 + 10 * (K + 1) + 23) + a->N * 20 * int64_t(nck);
+    a->bytes = a->N * 4 * (3 + 10 * (K + 1) * (nck ? 2 : 1) + 23) + a->N * 20 * int64_t(nck);
+    h->mem_bytes += a->bytes;
   }
   a->ready = false;
   a->seg_filled = false;
@@ -907,23 +930,46 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
   const int nseg = (nsteps + K - 1) / K;
   float* lam = a->lam;
   float* lam2 = a->lam2;
+  // Segment sg's FP32 states live in buffer sg & 1 (seg or seg2).  The recompute
+  // of segment sg - 1 runs on the stream rs while the adjoint walks segment sg on
+  // the handle's stream; ev_rec orders each adjoint segment after its recompute,
+  // ev_used each recompute after the adjoint that last read its buffer.
+  auto segbuf = [&](int sg) { return (sg & 1) ? a->seg2 : a->seg; };
+  auto recompute = [&](int sg) -> cudaError_t {
+    const int s0 = sg * K, e0 = (s0 + K < nsteps) ? s0 + K : nsteps;
+    float* b = segbuf(sg);
+    if (sg == 0)
+      init_from_u0_kernel<<<nb, AT, 0, a->rs>>>(a->u0, b, h->N);
+    else
+      q16_to_f32_kernel<<<nb, AT, 0, a->rs>>>(a->ckpt + size_t(sg - 1) * 5 * N, b, h->N);
+    cudaError_t e = cudaGetLastError();
+    for (int j = 1; j <= e0 - s0 && e == cudaSuccess; ++j)
+      e = forward_step_on(h, b + size_t(j - 1) * 10 * N, b + size_t(j) * 10 * N, uint32_t(s0 + j),
+                          a->rs);
+    if (e == cudaSuccess) e = cudaEventRecord(a->ev_rec[sg & 1], a->rs);
+    return e;
+  };
+  if (!a->seg_filled) {
+    // the recompute stream follows everything issued on the handle's stream so far
+    ADJ_CUDA(h, cudaEventRecord(a->ev_start, st));
+    ADJ_CUDA(h, cudaStreamWaitEvent(a->rs, a->ev_start, 0));
+    ADJ_CUDA(h, recompute(nseg - 1));
+  }
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int s = sg * K, e = (s + K < nsteps) ? s + K : nsteps;
-    float* seg0 = a->seg;
+    const float* sb = a->seg_filled ? a->seg : segbuf(sg);
     if (!a->seg_filled) {
-      if (sg == 0)
-        init_from_u0_kernel<<<nb, AT, 0, st>>>(a->u0, seg0, h->N);
-      else
-        q16_to_f32_kernel<<<nb, AT, 0, st>>>(a->ckpt + size_t(sg - 1) * 5 * N, seg0, h->N);
-      ADJ_CUDA(h, cudaGetLastError());
-      for (int j = 1; j <= e - s; ++j)
-        ADJ_CUDA(h, forward_step(h, a->seg + size_t(j - 1) * 10 * N, a->seg + size_t(j) * 10 * N,
-                                 uint32_t(s + j)));
+      if (sg >= 1) {
+        // buffer (sg - 1) & 1 was last read by the adjoint of segment sg + 1
+        if (sg + 1 < nseg) ADJ_CUDA(h, cudaStreamWaitEvent(a->rs, a->ev_used[(sg + 1) & 1], 0));
+        ADJ_CUDA(h, recompute(sg - 1));
+      }
+      ADJ_CUDA(h, cudaStreamWaitEvent(st, a->ev_rec[sg & 1], 0));
     }
     for (int t = e - 1; t >= s; --t) {
       const int j = t - s;
-      const float* m_t = a->seg + size_t(j) * 10 * N;
-      const float* m_next = a->seg + size_t(j + 1) * 10 * N;
+      const float* m_t = sb + size_t(j) * 10 * N;
+      const float* m_next = sb + size_t(j + 1) * 10 * N;
       if (h->outflow_on && h->type) {
         outflow_vjp_kernel<<<blocks_for(int64_t(h->ny) * h->nz), AT, 0, st>>>(lam, h->type, h->nx,
                                                                              h->ny, h->nz);
@@ -964,6 +1010,7 @@ extern "C" int melbm_backward(melbm_t h, const float* dL_dm, float* dL_du0, floa
       lam = lam2;
       lam2 = tmp;
     }
+    if (!a->seg_filled) ADJ_CUDA(h, cudaEventRecord(a->ev_used[sg & 1], st));
   }
   a->lam = lam;
   a->lam2 = lam2;

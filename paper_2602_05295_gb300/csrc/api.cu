@@ -306,22 +306,27 @@ int check_raw_bytes(melbm_t h, const char* what, int64_t bytes) {
 }  // namespace
 
 namespace melbm {
-cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out) {
+cudaError_t forward_step_on(melbm_sim* h, const void* in, void* out, uint32_t t_out,
+                            cudaStream_t st) {
   const float omega = 1.0f / h->tau;
   const BoundaryTables bt = boundary_tables(h);
   cudaError_t e =
       h->lattice == MELBM_D3Q19
           ? launch_fluid19(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                           h->seed, h->grids, &bt, h->stream)
+                           h->seed, h->grids, &bt, st)
           : launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                         h->seed, h->grids, &bt, h->stream);
+                         h->seed, h->grids, &bt, st);
   if (e == cudaSuccess && h->L)
     e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
                         h->list_word, h->L, bt, h->inflow, t_out, h->seed, h->grids,
-                        h->wall_model, h->mask, h->bodies, h->lattice, h->stream);
+                        h->wall_model, h->mask, h->bodies, h->lattice, st);
   if (e == cudaSuccess && h->outflow_on && h->type)
-    e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->stream);
+    e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, st);
   return e;
+}
+
+cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out) {
+  return forward_step_on(h, in, out, t_out, h->stream);
 }
 
 int ensure_boundaries(melbm_sim* h) {

@@ -92,6 +92,10 @@ namespace melbm {
 // Launch one forward step in -> out with the handle's boundaries (used by the
 // adjoint's recomputation); t_out is the time index of the output state.
 cudaError_t forward_step(melbm_sim* h, const void* in, void* out, uint32_t t_out);
+// the same step issued on another stream (the boundary side table is shared: one
+// step at a time per handle)
+cudaError_t forward_step_on(melbm_sim* h, const void* in, void* out, uint32_t t_out,
+                            cudaStream_t st);
 // Run the classification a melbm_set_solid / set_inflow / set_outflow left
 // pending (no-op otherwise); returns its status.
 int ensure_boundaries(melbm_sim* h);
