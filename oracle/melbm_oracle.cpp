@@ -629,26 +629,34 @@ inline void pcg4d(uint32_t v[4]) {
   v[3] += v[1] * v[2];
 }
 
-// Ten dither values d_k in (0, 1) for one cell and one time index.
-// Components 0..7 take 12-bit fields f of the four words (bits 0-11 for even k,
-// bits 12-23 for odd k, word k/2); components 8 and 9 take 16-bit fields built
-// from the top bytes of words (0, 1) and (2, 3).  d = (f + 1/2) / 2^bits: the
-// midpoints of 2^bits equal cells of [0, 1), whose mean is exactly 1/2, so the
-// added noise d - 1/2 is zero-mean as Sec. 5.4 requires.
-inline int dither_bits(int k) { return k < 8 ? 12 : 16; }
+// Ten dither values d_k in (0, 1) for one cell and one time index (reading 7 of
+// the design notes: Sec. 5.4 fixes the noise -- zero-mean, uniform over one
+// quantisation unit -- but not its source).  Every component takes a 16-bit field
+// f: components 0..7 the low (even k) and high (odd k) halves of word k/2 of the
+// hash, component 8 the low half of v0 xor v2 and component 9 the high half of
+// v1 xor v3 (each uniform over the 2^16 fields, and independent of any single
+// other component's field).  d = (f + 1/2) / 2^16: the midpoints of 2^16 equal
+// cells of [0, 1), whose mean is exactly 1/2, so the added noise d - 1/2 is
+// zero-mean as Sec. 5.4 requires.
+inline int dither_bits(int) { return 16; }
 inline float dither_of_field(int k, uint32_t field) {
   return (float(field) + 0.5f) / float(1u << dither_bits(k));
 }
-inline void dither10(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t seed, float d[10]) {
+inline void dither_fields(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t seed,
+                          uint32_t f[10]) {
   uint32_t v[4] = {x, y, z, t ^ seed};
   pcg4d(v);
   for (int k = 0; k < 8; ++k) {
     const uint32_t w = v[k / 2];
-    const uint32_t field = (k % 2 == 0) ? (w & 0xFFFu) : ((w >> 12) & 0xFFFu);
-    d[k] = dither_of_field(k, field);
+    f[k] = (k % 2 == 0) ? (w & 0xFFFFu) : (w >> 16);
   }
-  d[8] = dither_of_field(8, (v[0] >> 24) | ((v[1] >> 24) << 8));
-  d[9] = dither_of_field(9, (v[2] >> 24) | ((v[3] >> 24) << 8));
+  f[8] = (v[0] ^ v[2]) & 0xFFFFu;
+  f[9] = (v[1] ^ v[3]) >> 16;
+}
+inline void dither10(uint32_t x, uint32_t y, uint32_t z, uint32_t t, uint32_t seed, float d[10]) {
+  uint32_t f[10];
+  dither_fields(x, y, z, t, seed, f);
+  for (int k = 0; k < 10; ++k) d[k] = dither_of_field(k, f[k]);
 }
 
 // Stored-variable ranges (Sec. 5.4 moment range analysis and range reduction):

@@ -635,8 +635,8 @@ def test_dither_is_uniform_and_rounding_unbiased(orc):
     so the rounding is unbiased: the mean of decode(encode(m)) over cells is m."""
     ds = np.array([orc.dither(x, y, z, 7, 123) for x in range(8) for y in range(8) for z in range(8)])
     assert ds.min() > 0 and ds.max() < 1
-    # the dither takes the midpoints (f + 1/2)/2^bits of equal cells of [0, 1)
-    for k, bits in enumerate([12] * 8 + [16] * 2):
+    # the dither takes the midpoints (f + 1/2)/2^16 of equal cells of [0, 1)
+    for k, bits in enumerate([16] * 10):
         f = ds[:, k] * 2 ** bits - 0.5
         assert np.array_equal(f, np.round(f)) and f.min() >= 0 and f.max() <= 2 ** bits - 1
     assert np.abs(ds.mean(0) - 0.5).max() < 0.05
@@ -654,13 +654,31 @@ def test_dither_is_uniform_and_rounding_unbiased(orc):
         assert np.abs(bias).max() < 5 * sigma + 1e-3, bias
 
 
+def test_dither_components_are_pairwise_independent(orc):
+    """The ten dither values of a cell come from one 128-bit hash: eight 16-bit
+    halves and two fields that are xors of halves of two other words.  Each is
+    uniform, and no two components are dependent: over 32768 cells the 8 x 8 joint
+    histogram of the top three bits of every pair of components is flat (chi-square
+    with 63 degrees of freedom below 120; a component that repeated another's field,
+    or the xor of its own word's halves with another, would give thousands)."""
+    ds = np.array([orc.dither(x, y, z, 11, 5) for x in range(32) for y in range(32)
+                   for z in range(32)])
+    top = np.floor(ds * 8).astype(int)
+    n = len(top)
+    for i in range(10):
+        for j in range(i + 1, 10):
+            h = np.bincount(top[:, i] * 8 + top[:, j], minlength=64)
+            chi2 = ((h - n / 64) ** 2 / (n / 64)).sum()
+            assert chi2 < 120, (i, j, chi2)
+
+
 def test_stochastic_rounding_is_unbiased_over_the_dither(orc):
     """Sec. 5.4: the dither is zero-mean uniform noise of one unit, so the expected
     code equals the value.  Enumerating every dither value: E[q] differs from the
-    exact code coordinate by at most half a dither quantum (1/8192 code for the
-    12-bit fields) plus the FP32 rounding of w, and by ~0 on average over values
-    spread across code cells (a dither f/4096 instead of (f + 1/2)/4096 would
-    under-round by 1/8192 code on average, a -1.3e-9 per-step drift of rho)."""
+    exact code coordinate by at most half a dither quantum (2^-17 code for the
+    16-bit fields) plus the FP32 rounding of w, and by ~0 on average over values
+    spread across code cells (a dither f/2^16 instead of (f + 1/2)/2^16 would
+    under-round by 2^-17 code on average, a -8e-11 per-step drift of rho)."""
     rng = np.random.default_rng(14)
     devs = {0: [], 1: [], 4: []}
     for k, centre, spread in ((0, 0.0, 0.01), (1, 0.0, 0.05), (4, 0.0, 0.005)):
@@ -668,7 +686,7 @@ def test_stochastic_rounding_is_unbiased_over_the_dither(orc):
             w = orc.code_coordinate(v, k) - orc.codec_constants(k)[0]
             # half a dither quantum + the FP32 rounding of w (half an ulp, plus
             # the relative error of the FP32 constant K times |w|)
-            bound = 1.0 / 8192 + float(np.spacing(np.float32(abs(w)))) / 2 + abs(w) * 2.0 ** -24
+            bound = 2.0 ** -17 + float(np.spacing(np.float32(abs(w)))) / 2 + abs(w) * 2.0 ** -24
             dev = orc.mean_code_over_dither(v, k) - orc.code_coordinate(v, k)
             assert abs(dev) <= bound, (k, v, dev, bound)
             devs[k].append(dev)
@@ -734,7 +752,7 @@ def test_codec_bits_error_bounds_saturation_and_unbiased_rounding(orc, bits):
     for k, spread in ((0, 0.01), (1, 0.05), (4, 0.005)):
         for val in (spread * rng.standard_normal(50)).astype(np.float32):
             w = orc.code_coordinate(val, k, bits) - orc.codec_constants(k, bits)[0]
-            bound = 1.0 / 8192 + float(np.spacing(np.float32(abs(w)))) / 2 + abs(w) * 2.0 ** -24
+            bound = 2.0 ** -17 + float(np.spacing(np.float32(abs(w)))) / 2 + abs(w) * 2.0 ** -24
             dev = orc.mean_code_over_dither(val, k, bits) - orc.code_coordinate(val, k, bits)
             assert abs(dev) <= bound, (bits, k, val, dev)
 
