@@ -463,7 +463,7 @@ __device__ __forceinline__ void store_pair_q16_w(uint32_t* const* w, uint32_t na
                                                  const QGrids* q) {
   float2 d[10];  // 1 + the dither of each component
 #pragma unroll
-  for (int k = 0; k < 10; ++k) d[k] = make_float2(dither_one_plus(ha, k), dither_one_plus(hb, k));
+  for (int k = 0; k < 10; ++k) d[k] = dither_one_plus2(ha, hb, k);
   // o holds -drho and -4 n_ab (finish_scaled): their grid factors K carry
   // -1 and -1/4, power-of-two factors that leave every code unchanged
   uint2 e0, e1, e2, e3, e4, e5, e6, e7, e8, e9;

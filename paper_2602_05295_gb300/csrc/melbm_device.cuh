@@ -210,10 +210,8 @@ __device__ __forceinline__ float2 qg_decode(const QGrid& g, float2 magic_q) {
 }
 
 // Counter-based dither: pcg4d of Jarzynski & Olano, "Hash Functions for GPU
-// Rendering", JCGT 9(3) 2020, on (x, y, z, t ^ seed).  Components 0..7 take the
-// 12-bit fields [0,12) (even) and [12,24) (odd) of word k/2; components 8 and 9
-// take 16 bits made of the top bytes of words (0,1) and (2,3).  The field f maps
-// to the dither (f + 1/2)/2^bits.
+// Rendering", JCGT 9(3) 2020, on (x, y, z, t ^ seed): 128 bits per cell and time
+// index, from which the ten components take 16-bit fields (below).
 struct DitherBits {
   uint32_t w[4];
 };
@@ -242,40 +240,33 @@ __device__ __forceinline__ DitherBits pcg4d(uint32_t x, uint32_t y, uint32_t z, 
   r.w[3] = v3;
   return r;
 }
-// The dither of field f (12 bits for k < 8, 16 bits for k = 8, 9) is the
-// midpoint d = (f + 1/2) / 2^bits, whose mean over f is exactly 1/2.  It is
-// built exactly: the float with bits 0x4A800000 | (2 f + 1) is 2^22 + f + 1/2, and
-// (2^22 + f + 1/2) / 2^12 - 2^10  or  (2^22 + f + 1/2) / 2^16 - 2^6  is d.
-__device__ __forceinline__ float dither_magic(const DitherBits& h, int k) {
-  uint32_t f2;  // 2 f
-  if (k < 8) f2 = (k & 1) ? ((h.w[k >> 1] >> 11) & 0x1FFEu) : ((h.w[k >> 1] << 1) & 0x1FFEu);
-  else if (k == 8) f2 = ((h.w[0] >> 24) | ((h.w[1] >> 24) << 8)) << 1;
-  else f2 = ((h.w[2] >> 24) | ((h.w[3] >> 24) << 8)) << 1;
-  return __uint_as_float(0x4A800000u | f2 | 1u);
+// The dither of component k: a 16-bit field f -- components 0..7 the low (even k)
+// and high (odd k) half of word k/2, component 8 the low half of w0 ^ w2,
+// component 9 the high half of w1 ^ w3 -- mapped to the midpoint
+// d = (f + 1/2) / 2^16, whose mean over f is exactly 1/2.  One byte permute places
+// f in the float 2^23 + f; from it d and 1 + d follow by one FMA each, exactly
+// (their values have at most 18 significant bits).
+__device__ __forceinline__ uint32_t dither_word(const DitherBits& h, int k) {
+  return k < 8 ? h.w[k >> 1] : (k == 8 ? (h.w[0] ^ h.w[2]) : (h.w[1] ^ h.w[3]));
 }
-__device__ __forceinline__ float dither_value(float magic, int k) {
-  return k < 8 ? __fmaf_rn(magic, 1.0f / 4096.0f, -1024.0f)
-               : __fmaf_rn(magic, 1.0f / 65536.0f, -64.0f);
+__device__ __forceinline__ float dither_magic(const DitherBits& h, int k) {  // 2^23 + f
+  return __uint_as_float(__byte_perm(dither_word(h, k), 0x4B000000u, (k & 1) ? 0x7632 : 0x7610));
 }
-__device__ __forceinline__ float2 dither_value(float2 magic, int k) {
-  return k < 8 ? __ffma2_rn(magic, make_float2(1.0f / 4096.0f, 1.0f / 4096.0f),
-                            make_float2(-1024.0f, -1024.0f))
-               : __ffma2_rn(magic, make_float2(1.0f / 65536.0f, 1.0f / 65536.0f),
-                            make_float2(-64.0f, -64.0f));
+constexpr float DITHER_SCALE = 1.0f / 65536.0f;
+constexpr float DITHER_OFF = -(128.0f - 1.0f / 131072.0f);      // d = magic 2^-16 + DITHER_OFF
+constexpr float DITHER_OFF1 = -(127.0f - 1.0f / 131072.0f);     // 1 + d
+__device__ __forceinline__ float dither_value(float magic) {
+  return __fmaf_rn(magic, DITHER_SCALE, DITHER_OFF);
 }
-// The same dither plus one, 1 + d, built directly as the float with bits
-// 0x3F800000 | (f << (23 - bits)) | (1 << (22 - bits)) (exact), for the packed
-// encode below, which adds it in place of d: the code is unchanged, since
-// floor(w + 1 + d) - 1 = floor(w + d) and both round-down adds keep the floor.
+// 1 + d, for the encode below, which adds it in place of d: the code is unchanged,
+// since floor(w + 1 + d) - 1 = floor(w + d) and both round-down adds keep the floor.
 __device__ __forceinline__ float dither_one_plus(const DitherBits& h, int k) {
-  uint32_t b;
-  if (k < 8)
-    b = (k & 1) ? ((h.w[k >> 1] >> 1) & 0x7FF800u) : ((h.w[k >> 1] & 0xFFFu) << 11);
-  else if (k == 8)
-    b = (__byte_perm(h.w[0], h.w[1], 0x0073) & 0xFFFFu) << 7;  // (w0 >> 24) | (w1 >> 24) << 8
-  else
-    b = (__byte_perm(h.w[2], h.w[3], 0x0073) & 0xFFFFu) << 7;
-  return __uint_as_float(b | (k < 8 ? 0x3F800400u : 0x3F800040u));
+  return __fmaf_rn(dither_magic(h, k), DITHER_SCALE, DITHER_OFF1);
+}
+// The same for the two cells of a pair (packed).
+__device__ __forceinline__ float2 dither_one_plus2(const DitherBits& a, const DitherBits& b, int k) {
+  return __ffma2_rn(make_float2(dither_magic(a, k), dither_magic(b, k)),
+                    make_float2(DITHER_SCALE, DITHER_SCALE), make_float2(DITHER_OFF1, DITHER_OFF1));
 }
 struct Dither {
   float d[10];
@@ -285,7 +276,7 @@ __device__ __forceinline__ Dither dither10(uint32_t x, uint32_t y, uint32_t z, u
   const DitherBits h = pcg4d(x, y, z, t, seed);
   Dither r;
 #pragma unroll
-  for (int k = 0; k < 10; ++k) r.d[k] = dither_value(dither_magic(h, k), k);
+  for (int k = 0; k < 10; ++k) r.d[k] = dither_value(dither_magic(h, k));
   return r;
 }
 
