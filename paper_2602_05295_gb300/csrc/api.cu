@@ -223,6 +223,11 @@ int reclassify_lists(melbm_t h) {
                                           h->list_word, tables ? h->cls_pref : nullptr, h->stream));
   } else {
     h->L = 0;
+    // the fluid kernel with solids reads every word's list index a pair ahead,
+    // listed cells or not: with an empty list the table is all zeros
+    if (tables && !h->cls_pref && (rc = dev_alloc(h, (void**)&h->cls_pref, size_t(h->W) * 4)))
+      return rc;
+    if (tables) MELBM_CUDA(h, cudaMemsetAsync(h->cls_pref, 0, size_t(h->W) * 4, h->stream));
   }
   return MELBM_OK;
 }

@@ -750,6 +750,10 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
   const uint32_t cls_own = uint32_t(xw >> 5) + uint32_t(P.ntx) * uint32_t(yw);
   const uint32_t cls_tile = uint32_t(blockIdx.x) + uint32_t(P.ntx) * uint32_t(yw);
   uint32_t sw0 = 0, sw1 = 0, fbA0 = 0, fbA1 = 0, fbB0 = 0, fbB1 = 0;
+  // and the list index of the first listed cell of those FLUID_BOUNDARY words, also
+  // a pair ahead: read where it is used, it stalled every warp holding such a cell
+  // for a memory latency, and the block with it at the next barrier
+  uint32_t pfA0 = 0, pfA1 = 0, pfB0 = 0, pfB1 = 0;
   if constexpr (BND) {
     sw0 = __ldg(P.cls_solid + cls_own + cls_rw * uint32_t(wz(z0 - 1)));
     sw1 = __ldg(P.cls_solid + cls_own + cls_rw * uint32_t(wz(z0)));
@@ -787,6 +791,10 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
       sw1 = __ldg(P.cls_solid + cls_own + cls_rw * uint32_t(wz(zz + 3)));
       fbB0 = __ldg(P.cls_fb + cls_tile + cls_rw * uint32_t(wz(zz + 1)));
       fbB1 = __ldg(P.cls_fb + cls_tile + cls_rw * uint32_t(wz(zz + 2)));
+      pfA0 = pfB0;
+      pfA1 = pfB1;
+      pfB0 = __ldg(P.cls_pref + cls_tile + cls_rw * uint32_t(wz(zz + 1)));
+      pfB1 = __ldg(P.cls_pref + cls_tile + cls_rw * uint32_t(wz(zz + 2)));
     }
     const Mom17T<float2> A = collide_scaled<FORCE>(s, omega, fx, fy, fz);
     Closure19T<float2> E;
@@ -883,8 +891,6 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     if constexpr (BND) {
       // the raw sums of this pair's FLUID_BOUNDARY cells (their solid links
       // brought nothing) go to the side table for the boundary kernel
-      const uint32_t wa = cls_tile + cls_rw * uint32_t(za);
-      const uint32_t wb = cls_tile + cls_rw * uint32_t(zb < nz ? zb : 0);
       const uint32_t fa = fbA0, fb = zb < z1 ? fbA1 : 0u;
       if ((fa | fb) != 0u) {  // warp-uniform: every lane read the same two words
         const uint32_t lt = (1u << lane) - 1u;
@@ -894,12 +900,12 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
                               M[5][0], M[0][2], M[4][0], M[1][1], M[2][1]};
         const size_t L = size_t(P.L);
         if (col_ok && ((fa >> lane) & 1u)) {
-          const size_t k = __ldg(P.cls_pref + wa) + __popc(fa & lt);
+          const size_t k = pfA0 + __popc(fa & lt);
 #pragma unroll
           for (int c = 0; c < 10; ++c) P.side[c * L + k] = v[c].x;
         }
         if (col_ok && ((fb >> lane) & 1u)) {
-          const size_t k = __ldg(P.cls_pref + wb) + __popc(fb & lt);
+          const size_t k = pfA1 + __popc(fb & lt);
 #pragma unroll
           for (int c = 0; c < 10; ++c) P.side[c * L + k] = v[c].y;
         }
