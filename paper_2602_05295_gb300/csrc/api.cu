@@ -135,7 +135,7 @@ void free_list(melbm_t h) {
   dev_free(h, h->cls_solid, size_t(h->W) * 4);
   dev_free(h, h->cls_fb, size_t(h->W) * 4);
   dev_free(h, h->cls_pref, size_t(h->W) * 4);
-  dev_free(h, h->side, size_t(h->L_cap) * 10 * 4);
+  dev_free(h, h->side, size_t(h->L_cap) * SIDE_FLOATS * 4);
   h->cls_solid = h->cls_fb = h->cls_pref = nullptr;
   h->side = nullptr;
   h->W = 0;
@@ -157,7 +157,7 @@ BoundaryTables boundary_tables(const melbm_sim* h) {
 
 // Classification (classify.cu): types, the list, and with solids the tables the
 // fluid kernel reads (per 32-cell word of a row the SOLID and FLUID_BOUNDARY bits
-// and the list index of its first listed cell) and the [10][L] side table it
+// and the list index of its first listed cell) and the [L][12] side table it
 // fills every step (the mixed scheme corrects its own fluid pass and needs no
 // tables).
 int reclassify_lists(melbm_t h) {
@@ -202,7 +202,7 @@ int reclassify_lists(melbm_t h) {
   if (int64_t(total) > h->L_cap) {
     dev_free(h, h->list_cell, size_t(h->L_cap) * 4);
     dev_free(h, h->list_word, size_t(h->L_cap) * 4);
-    dev_free(h, h->side, size_t(h->L_cap) * 10 * 4);
+    dev_free(h, h->side, size_t(h->L_cap) * SIDE_FLOATS * 4);
     h->list_cell = h->list_word = nullptr;
     h->side = nullptr;
     h->L = h->L_cap = 0;
@@ -215,7 +215,7 @@ int reclassify_lists(melbm_t h) {
     }
     if (tables && !h->cls_pref && (rc = dev_alloc(h, (void**)&h->cls_pref, size_t(h->W) * 4)))
       return rc;
-    if (tables && !h->side && (rc = dev_alloc(h, (void**)&h->side, size_t(h->L_cap) * 10 * 4)))
+    if (tables && !h->side && (rc = dev_alloc(h, (void**)&h->side, size_t(h->L_cap) * SIDE_FLOATS * 4)))
       return rc;
     h->L = total;
     MELBM_CUDA(h, launch_classify_scatter(h->nx, h->ny, h->nz, mbits, h->inflow_on,

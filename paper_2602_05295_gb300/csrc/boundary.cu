@@ -33,8 +33,8 @@ struct BoundaryParams {
   const uint32_t* cells;
   const uint32_t* words;
   int64_t count;
-  const float* side;       // [10][count]: raw post-streaming sums (FLUID_BOUNDARY entries),
-                           // times -1, 2, 2, 2, 1, 1, 1, -4, -4, -4
+  const float* side;       // [count][12]: raw post-streaming sums (FLUID_BOUNDARY entries),
+                           // times -1, 2, 2, 2, 1, 1, 1, -4, -4, -4, and two pad floats
   int wall_model;          // 0 halfway bounce-back, 1 moment-based reconstruction
   const uint8_t* mask;     // body id of every cell (wall model 1)
   const float* bodies;     // 256 x 9: V, Om, r0 of each body (wall model 1)
@@ -158,12 +158,11 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
     return;
   }
   // the raw sums of the fluid kernel, stored times the scale factors of its passes
-  const size_t L = size_t(P.count);
-  float m000 = -__ldg(P.side + k), m100 = 0.5f * __ldg(P.side + L + k),
-        m010 = 0.5f * __ldg(P.side + 2 * L + k), m001 = 0.5f * __ldg(P.side + 3 * L + k),
-        m200 = __ldg(P.side + 4 * L + k), m020 = __ldg(P.side + 5 * L + k),
-        m002 = __ldg(P.side + 6 * L + k), m110 = -0.25f * __ldg(P.side + 7 * L + k),
-        m101 = -0.25f * __ldg(P.side + 8 * L + k), m011 = -0.25f * __ldg(P.side + 9 * L + k);
+  const float4* rec = reinterpret_cast<const float4*>(P.side) + size_t(3) * size_t(k);
+  const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+  float m000 = -r0.x, m100 = 0.5f * r0.y, m010 = 0.5f * r0.z, m001 = 0.5f * r0.w,
+        m200 = r1.x, m020 = r1.y, m002 = r1.z, m110 = -0.25f * r1.w,
+        m101 = -0.25f * r2.x, m011 = -0.25f * r2.y;
   float fx0 = 0.f, fy0 = 0.f, fz0 = 0.f;
   if (FORCE) {
     fx0 = __ldg(P.force + n);

@@ -121,7 +121,7 @@ struct FluidParams {
   uint32_t* qout[5];       // and of the output (16-bit storage)
   // With solids (BND kernels): per 32-cell word (tx, y, z) of a row, the bits of
   // its SOLID and FLUID_BOUNDARY cells and the list index of its first listed
-  // cell after an INFLOW cell at its lane 0; side[10][L] receives the raw
+  // cell after an INFLOW cell at its lane 0; side[L][12] receives the raw
   // post-streaming sums of every FLUID_BOUNDARY cell (list order), times the
   // scale factors of the passes (-1, 2, 2, 2, 1, 1, 1, -4, -4, -4).
   const uint32_t* cls_solid;
@@ -898,16 +898,18 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
         // boundary kernel divides them out)
         const float2 v[10] = {M[0][0], M[1][0], M[2][0], M[0][1], M[3][0],
                               M[5][0], M[0][2], M[4][0], M[1][1], M[2][1]};
-        const size_t L = size_t(P.L);
+        float4* const rec = reinterpret_cast<float4*>(P.side);  // 3 float4 per entry
         if (col_ok && ((fa >> lane) & 1u)) {
-          const size_t k = pfA0 + __popc(fa & lt);
-#pragma unroll
-          for (int c = 0; c < 10; ++c) P.side[c * L + k] = v[c].x;
+          float4* r = rec + size_t(3) * (pfA0 + __popc(fa & lt));
+          r[0] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+          r[1] = make_float4(v[4].x, v[5].x, v[6].x, v[7].x);
+          r[2] = make_float4(v[8].x, v[9].x, 0.f, 0.f);
         }
         if (col_ok && ((fb >> lane) & 1u)) {
-          const size_t k = pfA1 + __popc(fb & lt);
-#pragma unroll
-          for (int c = 0; c < 10; ++c) P.side[c * L + k] = v[c].y;
+          float4* r = rec + size_t(3) * (pfA1 + __popc(fb & lt));
+          r[0] = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+          r[1] = make_float4(v[4].y, v[5].y, v[6].y, v[7].y);
+          r[2] = make_float4(v[8].y, v[9].y, 0.f, 0.f);
         }
       }
     }

@@ -33,7 +33,7 @@ struct melbm_sim {
   int64_t L_cap = 0;  // entries the list arrays and the side table hold
   // tables of the fluid kernel with solids (melbm::BoundaryTables): per 32-cell
   // word of a row (W words) the SOLID and FLUID_BOUNDARY bits and the list index
-  // of its first listed cell, and the [10][L] side table of raw post-streaming
+  // of its first listed cell, and the [L][12] side table of raw post-streaming
   // sums of the FLUID_BOUNDARY cells
   uint32_t* cls_solid = nullptr;
   uint32_t* cls_fb = nullptr;

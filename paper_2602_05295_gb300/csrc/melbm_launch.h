@@ -48,10 +48,13 @@ inline bool qgrids_16(const QGrids& g) { return g.bits_ru == 16 && g.bits_s == 1
 // FLUID_BOUNDARY cells, and pref = the list index of the word's first listed cell
 // (the number of listed cells before the word, plus one if its lane-0 cell is an
 // INFLOW cell, so that a FLUID_BOUNDARY lane's index is pref + the number of
-// FLUID_BOUNDARY lanes below it); side[10][L] is the table of raw post-streaming
-// sums (m000, m100, m010, m001, m200, m020, m002, m110, m101, m011) that the fluid
-// kernel fills for the FLUID_BOUNDARY cells (list order), each times the scale of
-// the kernel's passes (-1, 2, 2, 2, 1, 1, 1, -4, -4, -4).
+// FLUID_BOUNDARY lanes below it); side[L][SIDE_FLOATS] is the table of raw
+// post-streaming sums (m000, m100, m010, m001, m200, m020, m002, m110, m101, m011,
+// then two pad floats) that the fluid kernel fills for the FLUID_BOUNDARY cells
+// (list order), each times the scale of the kernel's passes (-1, 2, 2, 2, 1, 1, 1,
+// -4, -4, -4).  One 48-byte record per cell is written by three 16-byte stores of
+// the cell's lane, so runs of neighbouring cells fill whole sectors.
+constexpr int SIDE_FLOATS = 12;
 struct BoundaryTables {
   const uint32_t* solid;
   const uint32_t* fb;
