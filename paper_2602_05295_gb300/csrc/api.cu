@@ -315,16 +315,20 @@ cudaError_t forward_step_on(melbm_sim* h, const void* in, void* out, uint32_t t_
                             cudaStream_t st) {
   const float omega = 1.0f / h->tau;
   const BoundaryTables bt = boundary_tables(h);
-  cudaError_t e =
-      h->lattice == MELBM_D3Q19
+  cudaError_t e = cudaSuccess;
+  if (h->L)  // the bounce-back sums of the listed cells, from their input state
+    e = launch_bounce(h->storage, h->nx, h->ny, h->nz, in, h->force, omega, h->list_cell,
+                      h->list_word, h->L, bt, h->grids, h->wall_model, h->mask, h->bodies,
+                      h->lattice, st);
+  if (e == cudaSuccess)
+    e = h->lattice == MELBM_D3Q19
           ? launch_fluid19(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
                            h->seed, h->grids, &bt, st)
           : launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
                          h->seed, h->grids, &bt, st);
-  if (e == cudaSuccess && h->L)
-    e = launch_boundary(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, h->list_cell,
-                        h->list_word, h->L, bt, h->inflow, t_out, h->seed, h->grids,
-                        h->wall_model, h->mask, h->bodies, h->lattice, st);
+  if (e == cudaSuccess && h->inflow_on && h->type)
+    e = launch_inflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->inflow, t_out, h->seed,
+                      h->grids, st);
   if (e == cudaSuccess && h->outflow_on && h->type)
     e = launch_outflow(h->storage, h->nx, h->ny, h->nz, out, h->type, st);
   return e;

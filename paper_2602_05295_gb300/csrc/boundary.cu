@@ -1,22 +1,23 @@
-// boundary.cu -- the boundary side of the split design (Sec. 4.2): after the
-// uniform fluid kernel has written every cell, the listed cells are rewritten.
-//   * FLUID_BOUNDARY: with solids the fluid kernel lets solid cells enter the
-//     stream at rest (zero post-collision moments about the rest state), so the
-//     raw post-streaming sums it leaves for such a cell in the side table hold
-//     every population pulled through a non-solid link and nothing through a
-//     solid one.  Halfway bounce-back, f_i(x) = f+_{opp(i)}(x) when x - c_i is
-//     solid, needs only the cell's own post-collision state: this kernel
-//     collides the cell's input state (App. A), adds the bounced population of
-//     every solid link to the sums and finishes and stores the moments.  This
-//     replaces the paper's additive per-triangle correction (Alg. 3), which needs
-//     a mesh; the sums are completed before the single rounding of the 16-bit
-//     store, with no atomics.
+// boundary.cu -- the boundary side of the split design (Sec. 4.2).
+//   * FLUID_BOUNDARY: halfway bounce-back, f_i(x) = f+_{opp(i)}(x) when x - c_i is
+//     solid, changes only the populations of the cell's solid links, and what
+//     they return depends on the cell's own post-collision state alone.  Moments
+//     are linear in f, so the new moments are the sums over the non-solid links
+//     (what the fluid kernel pulls when solid cells enter its passes at rest)
+//     plus the sums of the returned populations.  The bounce kernel computes the
+//     latter first, per listed cell, from its input state (App. A collision) into
+//     a side record; the fluid kernel adds the record to its pulled sums and
+//     rounds and stores the finished moments once, in its own coalesced stores.
+//     This replaces the paper's additive per-triangle correction (Alg. 3), which
+//     needs a mesh: the sums are completed before the single rounding of the
+//     16-bit store, with no atomics and no second pass over the output.
 //     With the moment-based wall model (Sec. 3.2, solid coupling) a solid link
-//     instead receives the Hermite population of (rho, u^p, S^p) at the link's
+//     instead returns the Hermite population of (rho, u^p, S^p) at the link's
 //     halfway point p, u^p the rigid velocity of the body the solid cell
 //     belongs to (its mask value) and S^p = u^p u^p + (S - u u) from the cell's
 //     own post-collision moments.
-//   * INFLOW: reset to the equilibrium (rho_in, u_in, S = u_in u_in).
+//   * INFLOW: reset to the equilibrium (rho_in, u_in, S = u_in u_in) after the
+//     fluid kernel, by a pass over face 0.
 // The outflow pass then copies the stored state of x = nx-2 onto x = nx-1.
 // On the D3Q19 lattice the same update runs over its 19 directions and weights.
 #include "melbm_device.cuh"
@@ -27,19 +28,16 @@ namespace melbm {
 struct BoundaryParams {
   int nx, ny, nz;
   const void* in;
-  void* out;
   const float* force;
   float omega;
   const uint32_t* cells;
   const uint32_t* words;
   int64_t count;
-  const float* side;       // [count][12]: raw post-streaming sums (FLUID_BOUNDARY entries),
+  float* side;             // [count][12]: the bounce-back sums of the FLUID_BOUNDARY entries,
                            // times -1, 2, 2, 2, 1, 1, 1, -4, -4, -4, and two pad floats
   int wall_model;          // 0 halfway bounce-back, 1 moment-based reconstruction
   const uint8_t* mask;     // body id of every cell (wall model 1)
   const float* bodies;     // 256 x 9: V, Om, r0 of each body (wall model 1)
-  float in_rho, in_ux, in_uy, in_uz;
-  uint32_t t_out, seed;
   QGrids q;
 };
 
@@ -135,34 +133,20 @@ __device__ __forceinline__ void bounce_sums27(const Mom17& A, uint32_t links, fl
   dm[9] = xs(4, 0);
 }
 
+// Bounce kernel, before the fluid kernel (in -> side): for every FLUID_BOUNDARY
+// cell of the list, the sums of the populations its solid links return -- from
+// the cell's own post-collision state alone -- written into its side record in
+// the scaling of the fluid kernel's passes (-1, 2, 2, 2, 1, 1, 1, -4, -4, -4),
+// which adds them to the pulled sums before its one rounding and store.
 template <int STORAGE, bool FORCE, bool MOVING, bool Q19 = false>
-__global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
+__global__ void __launch_bounds__(128) bounce_kernel(BoundaryParams P) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= P.count) return;
+  const uint32_t word = P.words[k];
+  if ((word >> 27) != T_FLUID_BOUNDARY) return;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const size_t N = size_t(nx) * ny * nz;
   const uint32_t n = P.cells[k];
-  const uint32_t word = P.words[k];
-  const uint32_t type = word >> 27;
-  const int x = int(n % uint32_t(nx));
-  const int y = int((n / uint32_t(nx)) % uint32_t(ny));
-  const int z = int(n / (uint32_t(nx) * uint32_t(ny)));
-  if (type == T_INFLOW) {
-    Stored s;
-    s.drho = P.in_rho - 1.0f;
-    s.ux = P.in_ux;
-    s.uy = P.in_uy;
-    s.uz = P.in_uz;
-    s.nxx = s.nyy = s.nzz = s.nxy = s.nxz = s.nyz = 0.f;
-    store_stored<STORAGE>(P.out, N, n, s, x, y, z, P.t_out, P.seed, false, P.q);
-    return;
-  }
-  // the raw sums of the fluid kernel, stored times the scale factors of its passes
-  const float4* rec = reinterpret_cast<const float4*>(P.side) + size_t(3) * size_t(k);
-  const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
-  float m000 = -r0.x, m100 = 0.5f * r0.y, m010 = 0.5f * r0.z, m001 = 0.5f * r0.w,
-        m200 = r1.x, m020 = r1.y, m002 = r1.z, m110 = -0.25f * r1.w,
-        m101 = -0.25f * r2.x, m011 = -0.25f * r2.y;
   float fx0 = 0.f, fy0 = 0.f, fz0 = 0.f;
   if (FORCE) {
     fx0 = __ldg(P.force + n);
@@ -172,82 +156,77 @@ __global__ void __launch_bounds__(128) boundary_kernel(BoundaryParams P) {
   const Mom17 A =
       collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n, P.q), P.omega, fx0, fy0, fz0);
   uint32_t links = word & 0x7FFFFFFu;
+  float dm[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if constexpr (!MOVING && !Q19) {
-    float dm[10];
     bounce_sums27(A, links, dm);
-    m000 += dm[0];
-    m100 += dm[1];
-    m010 += dm[2];
-    m001 += dm[3];
-    m200 += dm[4];
-    m020 += dm[5];
-    m002 += dm[6];
-    m110 += dm[7];
-    m101 += dm[8];
-    m011 += dm[9];
-    links = 0;
-  }
-  // otherwise each thread loops over its own solid links (bit scan of its link
-  // mask), so a warp runs as many iterations as its busiest cell
-  if (Q19) links &= D3Q19_LINKS;
-  while (links) {
-    const int i = __ffs(links) - 1;
-    links &= links - 1u;
-    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-    float g;  // f_i / w_i - 1 of the population the solid link returns along c_i
-    if constexpr (MOVING) {
-      float up[3];
-      body_velocity(P.bodies, P.mask[pull_source(x, y, z, nx, ny, nz, i)], x - 0.5f * cx,
-                    y - 0.5f * cy, z - 0.5f * cz, up);
-      const Mom17 Wm = wall_moments(A, up[0], up[1], up[2]);
-      g = Q19 ? hermite_eval19(Wm, cx, cy, cz) : hermite_eval(Wm, cx, cy, cz);
-    } else {
-      // halfway bounce-back: population opp(i) of x itself
-      g = Q19 ? hermite_eval19(A, -cx, -cy, -cz) : hermite_eval(A, -cx, -cy, -cz);
+  } else {
+    // each thread loops over its own solid links (bit scan of its link mask), so
+    // a warp runs as many iterations as its busiest cell
+    const int x = int(n % uint32_t(nx));
+    const int y = int((n / uint32_t(nx)) % uint32_t(ny));
+    const int z = int(n / (uint32_t(nx) * uint32_t(ny)));
+    if (Q19) links &= D3Q19_LINKS;
+    while (links) {
+      const int i = __ffs(links) - 1;
+      links &= links - 1u;
+      const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+      float g;  // f_i / w_i - 1 of the population the solid link returns along c_i
+      if constexpr (MOVING) {
+        float up[3];
+        body_velocity(P.bodies, P.mask[pull_source(x, y, z, nx, ny, nz, i)], x - 0.5f * cx,
+                      y - 0.5f * cy, z - 0.5f * cz, up);
+        const Mom17 Wm = wall_moments(A, up[0], up[1], up[2]);
+        g = Q19 ? hermite_eval19(Wm, cx, cy, cz) : hermite_eval(Wm, cx, cy, cz);
+      } else {
+        // halfway bounce-back: population opp(i) of x itself
+        g = Q19 ? hermite_eval19(A, -cx, -cy, -cz) : hermite_eval(A, -cx, -cy, -cz);
+      }
+      const float w = Q19 ? lattice_weight19(cx, cy, cz) : lattice_weight(cx, cy, cz);
+      const float f = w * g;
+      dm[0] += f;
+      dm[1] += cx * f;
+      dm[2] += cy * f;
+      dm[3] += cz * f;
+      dm[4] += (cx * cx - (1.0f / 3.0f)) * f;
+      dm[5] += (cy * cy - (1.0f / 3.0f)) * f;
+      dm[6] += (cz * cz - (1.0f / 3.0f)) * f;
+      dm[7] += float(cx * cy) * f;
+      dm[8] += float(cx * cz) * f;
+      dm[9] += float(cy * cz) * f;
     }
-    const float w = Q19 ? lattice_weight19(cx, cy, cz) : lattice_weight(cx, cy, cz);
-    const float f = w * g;
-    m000 += f;
-    m100 += cx * f;
-    m010 += cy * f;
-    m001 += cz * f;
-    m200 += (cx * cx - (1.0f / 3.0f)) * f;
-    m020 += (cy * cy - (1.0f / 3.0f)) * f;
-    m002 += (cz * cz - (1.0f / 3.0f)) * f;
-    m110 += float(cx * cy) * f;
-    m101 += float(cx * cz) * f;
-    m011 += float(cy * cz) * f;
   }
-  const Stored o = finish_moments<FORCE>(m000, m100, m010, m001, m200, m020, m002, m110, m101,
-                                         m011, fx0, fy0, fz0);
-  store_stored<STORAGE>(P.out, N, n, o, x, y, z, P.t_out, P.seed, false, P.q);
+  // the scale factors are powers of two: the fluid kernel's sum is the same
+  float4* rec = reinterpret_cast<float4*>(P.side) + size_t(3) * size_t(k);
+  rec[0] = make_float4(-dm[0], 2.0f * dm[1], 2.0f * dm[2], 2.0f * dm[3]);
+  rec[1] = make_float4(dm[4], dm[5], dm[6], -4.0f * dm[7]);
+  rec[2] = make_float4(-4.0f * dm[8], -4.0f * dm[9], 0.f, 0.f);
 }
 
-cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
-                            const float* force, float omega, const uint32_t* cells,
-                            const uint32_t* words, int64_t count, const BoundaryTables& bt,
-                            const float inflow[4], uint32_t t_out, uint32_t seed, const QGrids& q,
-                            int wall_model, const uint8_t* mask, const float* bodies, int lattice,
-                            cudaStream_t st) {
-  if (count <= 0) return cudaSuccess;
-  BoundaryParams p;
+template <bool FORCE, bool MOVING, bool Q19>
+cudaError_t launch_bounce_l(int storage, BoundaryParams& p, unsigned blocks, cudaStream_t st) {
+  if (storage == ST_Q16)
+    bounce_kernel<ST_Q16, FORCE, MOVING, Q19><<<blocks, 128, 0, st>>>(p);
+  else
+    bounce_kernel<ST_F32, FORCE, MOVING, Q19><<<blocks, 128, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bounce(int storage, int nx, int ny, int nz, const void* in, const float* force,
+                          float omega, const uint32_t* cells, const uint32_t* words, int64_t count,
+                          const BoundaryTables& bt, const QGrids& q, int wall_model,
+                          const uint8_t* mask, const float* bodies, int lattice, cudaStream_t st) {
+  if (count <= 0 || !bt.side) return cudaSuccess;
+  BoundaryParams p = {};
   p.nx = nx;
   p.ny = ny;
   p.nz = nz;
   p.in = in;
-  p.out = out;
   p.force = force;
   p.omega = omega;
   p.cells = cells;
   p.words = words;
   p.count = count;
   p.side = bt.side;
-  p.in_rho = inflow[0];
-  p.in_ux = inflow[1];
-  p.in_uy = inflow[2];
-  p.in_uz = inflow[3];
-  p.t_out = t_out;
-  p.seed = seed;
   p.q = q;
   p.wall_model = wall_model;
   p.mask = mask;
@@ -255,42 +234,49 @@ cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in,
   const unsigned blocks = unsigned((count + 127) / 128);
   const bool mv = wall_model == 1;
   if (lattice == 19) {
-    if (storage == ST_Q16) {
-      if (force) {
-        if (mv) boundary_kernel<ST_Q16, true, true, true><<<blocks, 128, 0, st>>>(p);
-        else boundary_kernel<ST_Q16, true, false, true><<<blocks, 128, 0, st>>>(p);
-      } else {
-        if (mv) boundary_kernel<ST_Q16, false, true, true><<<blocks, 128, 0, st>>>(p);
-        else boundary_kernel<ST_Q16, false, false, true><<<blocks, 128, 0, st>>>(p);
-      }
-    } else {
-      if (force) {
-        if (mv) boundary_kernel<ST_F32, true, true, true><<<blocks, 128, 0, st>>>(p);
-        else boundary_kernel<ST_F32, true, false, true><<<blocks, 128, 0, st>>>(p);
-      } else {
-        if (mv) boundary_kernel<ST_F32, false, true, true><<<blocks, 128, 0, st>>>(p);
-        else boundary_kernel<ST_F32, false, false, true><<<blocks, 128, 0, st>>>(p);
-      }
-    }
-    return cudaGetLastError();
+    if (force) return mv ? launch_bounce_l<true, true, true>(storage, p, blocks, st)
+                         : launch_bounce_l<true, false, true>(storage, p, blocks, st);
+    return mv ? launch_bounce_l<false, true, true>(storage, p, blocks, st)
+              : launch_bounce_l<false, false, true>(storage, p, blocks, st);
   }
-  if (storage == ST_Q16) {
-    if (force) {
-      if (mv) boundary_kernel<ST_Q16, true, true><<<blocks, 128, 0, st>>>(p);
-      else boundary_kernel<ST_Q16, true, false><<<blocks, 128, 0, st>>>(p);
-    } else {
-      if (mv) boundary_kernel<ST_Q16, false, true><<<blocks, 128, 0, st>>>(p);
-      else boundary_kernel<ST_Q16, false, false><<<blocks, 128, 0, st>>>(p);
-    }
-  } else {
-    if (force) {
-      if (mv) boundary_kernel<ST_F32, true, true><<<blocks, 128, 0, st>>>(p);
-      else boundary_kernel<ST_F32, true, false><<<blocks, 128, 0, st>>>(p);
-    } else {
-      if (mv) boundary_kernel<ST_F32, false, true><<<blocks, 128, 0, st>>>(p);
-      else boundary_kernel<ST_F32, false, false><<<blocks, 128, 0, st>>>(p);
-    }
-  }
+  if (force) return mv ? launch_bounce_l<true, true, false>(storage, p, blocks, st)
+                       : launch_bounce_l<true, false, false>(storage, p, blocks, st);
+  return mv ? launch_bounce_l<false, true, false>(storage, p, blocks, st)
+            : launch_bounce_l<false, false, false>(storage, p, blocks, st);
+}
+
+// ----------------------------------------------------------------- inflow
+// After the fluid kernel: the INFLOW cells of face 0 (x = 0) are reset to the
+// equilibrium (rho_in, u_in, u_in u_in); one thread per (y, z).
+template <int STORAGE>
+__global__ void inflow_kernel(int nx, int ny, int nz, void* out, const uint8_t* type, float in_rho,
+                              float in_ux, float in_uy, float in_uz, uint32_t t_out, uint32_t seed,
+                              QGrids q) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // (y, z) index
+  if (k >= int64_t(ny) * nz) return;
+  const size_t N = size_t(nx) * ny * nz;
+  const size_t n = size_t(nx) * size_t(k);
+  if (type[n] != T_INFLOW) return;
+  Stored s;
+  s.drho = in_rho - 1.0f;
+  s.ux = in_ux;
+  s.uy = in_uy;
+  s.uz = in_uz;
+  s.nxx = s.nyy = s.nzz = s.nxy = s.nxz = s.nyz = 0.f;
+  store_stored<STORAGE>(out, N, n, s, 0, int(k % ny), int(k / ny), t_out, seed, false, q);
+}
+
+cudaError_t launch_inflow(int storage, int nx, int ny, int nz, void* out, const uint8_t* type,
+                          const float inflow[4], uint32_t t_out, uint32_t seed, const QGrids& q,
+                          cudaStream_t st) {
+  const int64_t M = int64_t(ny) * nz;
+  const unsigned blocks = unsigned((M + 255) / 256);
+  if (storage == ST_Q16)
+    inflow_kernel<ST_Q16><<<blocks, 256, 0, st>>>(nx, ny, nz, out, type, inflow[0], inflow[1],
+                                                  inflow[2], inflow[3], t_out, seed, q);
+  else
+    inflow_kernel<ST_F32><<<blocks, 256, 0, st>>>(nx, ny, nz, out, type, inflow[0], inflow[1],
+                                                  inflow[2], inflow[3], t_out, seed, q);
   return cudaGetLastError();
 }
 

@@ -105,8 +105,11 @@ struct HaloStage {
   // words of both planes (copied alone, into the first word of their entries)
   static constexpr int ENTRIES = 2 * W + (FORCE ? 6 : 0) + (BND ? 2 : 0);
   static constexpr int BUF_WORDS = ENTRIES * 32 * CHUNK;
-  static constexpr size_t SMEM =
-      size_t(2) * (SM_BUF + halo_buf<Q19>()) * sizeof(float2) + size_t(2) * BUF_WORDS * 4;
+  // with solids, the bounce-back records of the pair a thread stores next: five
+  // 16-byte slots per thread (two per plane, and one for both planes' last 8 bytes)
+  static constexpr size_t REC_BYTES = BND ? size_t(5) * FY * FX * 16 : 0;
+  static constexpr size_t SMEM = size_t(2) * (SM_BUF + halo_buf<Q19>()) * sizeof(float2) +
+                                 size_t(2) * BUF_WORDS * 4 + REC_BYTES;
 };
 
 struct FluidParams {
@@ -121,9 +124,10 @@ struct FluidParams {
   uint32_t* qout[5];       // and of the output (16-bit storage)
   // With solids (BND kernels): per 32-cell word (tx, y, z) of a row, the bits of
   // its SOLID and FLUID_BOUNDARY cells and the list index of its first listed
-  // cell after an INFLOW cell at its lane 0; side[L][12] receives the raw
-  // post-streaming sums of every FLUID_BOUNDARY cell (list order), times the
-  // scale factors of the passes (-1, 2, 2, 2, 1, 1, 1, -4, -4, -4).
+  // cell after an INFLOW cell at its lane 0; side[L][12] holds, for every
+  // FLUID_BOUNDARY cell (list order), the sums of the populations its solid links
+  // return, times the scale factors of the passes (-1, 2, 2, 2, 1, 1, 1, -4, -4,
+  // -4), written by the bounce kernel before this one.
   const uint32_t* cls_solid;
   const uint32_t* cls_fb;
   const uint32_t* cls_pref;
@@ -522,6 +526,14 @@ __device__ __forceinline__ void cp_async4(uint32_t* smem, const void* gmem) {
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async16_l2(uint32_t* smem, const void* gmem) {
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -568,6 +580,8 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
   extern __shared__ float2 sm2[];
   float2* const hb = sm2 + 2 * SM_BUF;  // halo populations [buffer][row][slice][side]
   uint32_t* const stg = reinterpret_cast<uint32_t*>(hb + 2 * HALO_BUF);  // warp 0 staging
+  // bounce-back record slots (BND): slot c of thread (row, lane) at [c][row][lane]
+  float4* const recs = reinterpret_cast<float4*>(stg + 2 * HS::BUF_WORDS);
   const int lane = threadIdx.x, row = threadIdx.y;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const size_t N = size_t(nx) * ny * nz;
@@ -795,6 +809,27 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
       pfA1 = pfB1;
       pfB0 = __ldg(P.cls_pref + cls_tile + cls_rw * uint32_t(wz(zz + 1)));
       pfB1 = __ldg(P.cls_pref + cls_tile + cls_rw * uint32_t(wz(zz + 2)));
+      // the bounce-back records of the pair the next post() stores (words fbA):
+      // staged into this thread's slots now, added to the pulled sums there
+      if (mid_row) {  // warp-uniform: only the stored rows (the halo warps' groups stay apart)
+        const uint32_t lt = (1u << lane) - 1u;
+        const float4* rec = reinterpret_cast<const float4*>(P.side);
+        float4* slot = recs + row * FX + lane;
+        constexpr int CS = FY * FX;  // slot stride
+        if (col_ok && ((fbA0 >> lane) & 1u)) {
+          const float4* r = rec + size_t(3) * (pfA0 + __popc(fbA0 & lt));
+          cp_async16(slot, r);
+          cp_async16(slot + CS, r + 1);
+          cp_async8(slot + 4 * CS, r + 2);
+        }
+        if (col_ok && ((fbA1 >> lane) & 1u)) {
+          const float4* r = rec + size_t(3) * (pfA1 + __popc(fbA1 & lt));
+          cp_async16(slot + 2 * CS, r);
+          cp_async16(slot + 3 * CS, r + 1);
+          cp_async8(reinterpret_cast<float2*>(slot + 4 * CS) + 1, r + 2);
+        }
+        cp_async_commit();
+      }
     }
     const Mom17T<float2> A = collide_scaled<FORCE>(s, omega, fx, fy, fz);
     Closure19T<float2> E;
@@ -889,27 +924,26 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     }
     if (!store) return;
     if constexpr (BND) {
-      // the raw sums of this pair's FLUID_BOUNDARY cells (their solid links
-      // brought nothing) go to the side table for the boundary kernel
+      // this pair's FLUID_BOUNDARY cells pulled nothing through their solid links:
+      // add what those links return (the bounce kernel's records, staged by pre())
       const uint32_t fa = fbA0, fb = zb < z1 ? fbA1 : 0u;
-      if ((fa | fb) != 0u) {  // warp-uniform: every lane read the same two words
-        const uint32_t lt = (1u << lane) - 1u;
-        // the scaled raw sums M000 .. M011 (s = -1, 2, 2, 2, 1, 1, 1, -4, -4, -4; the
-        // boundary kernel divides them out)
-        const float2 v[10] = {M[0][0], M[1][0], M[2][0], M[0][1], M[3][0],
-                              M[5][0], M[0][2], M[4][0], M[1][1], M[2][1]};
-        float4* const rec = reinterpret_cast<float4*>(P.side);  // 3 float4 per entry
+      // warp-uniform (every lane read the same two words); wait for every copy
+      // pre() issued, also those of a plane past the chunk that is not stored
+      if ((fbA0 | fbA1) != 0u) cp_async_wait<0>();
+      if ((fa | fb) != 0u) {
+        const float4* slot = recs + row * FX + lane;
+        constexpr int CS = FY * FX;
         if (col_ok && ((fa >> lane) & 1u)) {
-          float4* r = rec + size_t(3) * (pfA0 + __popc(fa & lt));
-          r[0] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
-          r[1] = make_float4(v[4].x, v[5].x, v[6].x, v[7].x);
-          r[2] = make_float4(v[8].x, v[9].x, 0.f, 0.f);
+          const float4 r0 = slot[0], r1 = slot[CS], r2 = slot[4 * CS];
+          M[0][0].x += r0.x, M[1][0].x += r0.y, M[2][0].x += r0.z, M[0][1].x += r0.w;
+          M[3][0].x += r1.x, M[5][0].x += r1.y, M[0][2].x += r1.z, M[4][0].x += r1.w;
+          M[1][1].x += r2.x, M[2][1].x += r2.y;
         }
         if (col_ok && ((fb >> lane) & 1u)) {
-          float4* r = rec + size_t(3) * (pfA1 + __popc(fb & lt));
-          r[0] = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
-          r[1] = make_float4(v[4].y, v[5].y, v[6].y, v[7].y);
-          r[2] = make_float4(v[8].y, v[9].y, 0.f, 0.f);
+          const float4 r0 = slot[2 * CS], r1 = slot[3 * CS], r2 = slot[4 * CS];
+          M[0][0].y += r0.x, M[1][0].y += r0.y, M[2][0].y += r0.z, M[0][1].y += r0.w;
+          M[3][0].y += r1.x, M[5][0].y += r1.y, M[0][2].y += r1.z, M[4][0].y += r1.w;
+          M[1][1].y += r2.z, M[2][1].y += r2.w;
         }
       }
     }

@@ -48,12 +48,12 @@ inline bool qgrids_16(const QGrids& g) { return g.bits_ru == 16 && g.bits_s == 1
 // FLUID_BOUNDARY cells, and pref = the list index of the word's first listed cell
 // (the number of listed cells before the word, plus one if its lane-0 cell is an
 // INFLOW cell, so that a FLUID_BOUNDARY lane's index is pref + the number of
-// FLUID_BOUNDARY lanes below it); side[L][SIDE_FLOATS] is the table of raw
-// post-streaming sums (m000, m100, m010, m001, m200, m020, m002, m110, m101, m011,
-// then two pad floats) that the fluid kernel fills for the FLUID_BOUNDARY cells
-// (list order), each times the scale of the kernel's passes (-1, 2, 2, 2, 1, 1, 1,
-// -4, -4, -4).  One 48-byte record per cell is written by three 16-byte stores of
-// the cell's lane, so runs of neighbouring cells fill whole sectors.
+// FLUID_BOUNDARY lanes below it); side[L][SIDE_FLOATS] is the table of the sums
+// (m000, m100, m010, m001, m200, m020, m002, m110, m101, m011, then two pad floats)
+// of the populations the solid links of each FLUID_BOUNDARY cell return (list
+// order), each times the scale of the fluid kernel's passes (-1, 2, 2, 2, 1, 1, 1,
+// -4, -4, -4): the bounce kernel writes them, the fluid kernel adds them to the
+// sums it pulls.  One 48-byte record per cell, moved as three 16-byte pieces.
 constexpr int SIDE_FLOATS = 12;
 struct BoundaryTables {
   const uint32_t* solid;
@@ -98,17 +98,21 @@ cudaError_t launch_mixed_set_state(int64_t N, const float* rho, const float* u, 
 cudaError_t launch_mixed_get_moments(int64_t N, const float* p, float* rho, float* u, float* S,
                                      cudaStream_t st);
 
-// Boundary kernel over the list, after the fluid kernel with the boundary tables
-// (in -> out): every FLUID_BOUNDARY cell adds to its raw sums in bt->side the
-// populations its solid links return (halfway bounce-back, or the moving wall
-// with wall_model 1), computed from its own post-collision state, and stores the
-// finished moments; INFLOW cells are reset to the inflow equilibrium.
-cudaError_t launch_boundary(int storage, int nx, int ny, int nz, const void* in, void* out,
-                            const float* force, float omega, const uint32_t* cells,
-                            const uint32_t* words, int64_t count, const BoundaryTables& bt,
-                            const float inflow[4], uint32_t t_out, uint32_t seed, const QGrids& q,
-                            int wall_model, const uint8_t* mask, const float* bodies, int lattice,
-                            cudaStream_t st);
+// Bounce kernel over the list, before the fluid kernel with the boundary tables
+// (reads in): every FLUID_BOUNDARY cell writes into its bt.side record the sums of
+// the populations its solid links return (halfway bounce-back, or the moving wall
+// with wall_model 1), computed from its own post-collision state, in the scaling
+// of the fluid kernel's passes; the fluid kernel adds them before its store.  No-op
+// without a side table (no solids).
+cudaError_t launch_bounce(int storage, int nx, int ny, int nz, const void* in, const float* force,
+                          float omega, const uint32_t* cells, const uint32_t* words, int64_t count,
+                          const BoundaryTables& bt, const QGrids& q, int wall_model,
+                          const uint8_t* mask, const float* bodies, int lattice, cudaStream_t st);
+// After the fluid kernel: the INFLOW cells of face 0 (type[] from the
+// classification) are reset to the inflow equilibrium (rho, ux, uy, uz).
+cudaError_t launch_inflow(int storage, int nx, int ny, int nz, void* out, const uint8_t* type,
+                          const float inflow[4], uint32_t t_out, uint32_t seed, const QGrids& q,
+                          cudaStream_t st);
 
 // Force and torque (about r0 of the body) the next step transfers to the solid
 // cells of body `body` (0: every solid) by momentum exchange over the solid
