@@ -61,19 +61,36 @@ static_assert(D3Q19_LINKS == 0x2EBFEBAu, "19 directions");
 // moments negated.  F on the 27 directions is the tensor product of the D1Q3
 // population maps (phi3) applied along x, y and z to the 17 Hermite moments
 // (Eq. three_order_f), and the masked moments are three separable sums, so the
-// cost does not depend on the number of solid links.
-__device__ __forceinline__ void bounce_sums27(const Mom17& A, uint32_t links, float dm[10]) {
-  // x: the eight (q, r) slices (the (2, 2) slice carries no D3Q27 moment)
+// cost does not depend on the number of solid links.  On D3Q19 (Q19) the same
+// maps take the cell's 27 tensor moments: the 16 with mu_111 = 0 and the ten of
+// closure19, for which the tensor product gives the D3Q19 populations (zero on
+// the corners) exactly; the link set holds D3Q19 directions only.
+template <bool Q19>
+__device__ __forceinline__ void bounce_sums(const Mom17& A, uint32_t links, float dm[10]) {
   Phi X[3][3];  // X[q][r] over cx
-  X[0][0] = phi3(A.m000, A.m100, A.m200);
-  X[1][0] = phi3(A.m010, A.m110, A.m210);
-  X[2][0] = phi3(A.m020, A.m120, 0.f);
-  X[0][1] = phi3(A.m001, A.m101, A.m201);
-  X[1][1] = phi3(A.m011, A.m111, 0.f);
-  X[2][1] = phi3(A.m021, 0.f, 0.f);
-  X[0][2] = phi3(A.m002, A.m102, 0.f);
-  X[1][2] = phi3(A.m012, 0.f, 0.f);
-  X[2][2] = Phi{0.f, 0.f, 0.f};
+  if constexpr (Q19) {
+    const Closure19T<float> E = closure19(A);
+    X[0][0] = phi3(A.m000, A.m100, A.m200);
+    X[1][0] = phi3(A.m010, A.m110, A.m210);
+    X[2][0] = phi3(A.m020, A.m120, E.m220);
+    X[0][1] = phi3(A.m001, A.m101, A.m201);
+    X[1][1] = phi3(A.m011, 0.f, E.m211);
+    X[2][1] = phi3(A.m021, E.m121, E.m221);
+    X[0][2] = phi3(A.m002, A.m102, E.m202);
+    X[1][2] = phi3(A.m012, E.m112, E.m212);
+    X[2][2] = phi3(E.m022, E.m122, E.m222);
+  } else {
+    // x: the eight (q, r) slices (the (2, 2) slice carries no D3Q27 moment)
+    X[0][0] = phi3(A.m000, A.m100, A.m200);
+    X[1][0] = phi3(A.m010, A.m110, A.m210);
+    X[2][0] = phi3(A.m020, A.m120, 0.f);
+    X[0][1] = phi3(A.m001, A.m101, A.m201);
+    X[1][1] = phi3(A.m011, A.m111, 0.f);
+    X[2][1] = phi3(A.m021, 0.f, 0.f);
+    X[0][2] = phi3(A.m002, A.m102, 0.f);
+    X[1][2] = phi3(A.m012, 0.f, 0.f);
+    X[2][2] = Phi{0.f, 0.f, 0.f};
+  }
   const uint32_t rs = __brev(links) >> 5;  // bit j: the link opp(j) is solid
   // y then z per x direction; F(cx, cy, cz) is bit (cx+1) + 3 (cy+1) + 9 (cz+1)
   // of the reversed mask.  The masked populations are summed back to moments
@@ -157,8 +174,8 @@ __global__ void __launch_bounds__(128) bounce_kernel(BoundaryParams P) {
       collide_moments<FORCE>(load_stored<STORAGE>(P.in, N, n, P.q), P.omega, fx0, fy0, fz0);
   uint32_t links = word & 0x7FFFFFFu;
   float dm[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if constexpr (!MOVING && !Q19) {
-    bounce_sums27(A, links, dm);
+  if constexpr (!MOVING) {
+    bounce_sums<Q19>(A, Q19 ? (links & D3Q19_LINKS) : links, dm);
   } else {
     // each thread loops over its own solid links (bit scan of its link mask), so
     // a warp runs as many iterations as its busiest cell
