@@ -283,6 +283,41 @@ def e2e_run(torch, melbm, wl, u_np, steps, warmup):
     return el, 40 * N, 40 * N
 
 
+def channel_run(torch, melbm, steps, warmup):
+    """The 512x256x256 sphere channel (300 spheres, walls, inflow u = (0.05, 0, 0),
+    outflow; 16-bit storage): device time of `steps` steps (bounce kernel, fluid
+    kernel with the boundary tables, inflow and outflow passes) after `warmup`."""
+    from paper_2602_05295_gb300 import workloads as W
+    wl = W.CHANNEL512
+    N = wl.cells
+    mask, _ = W.sphere_pack(wl.shape)
+    sim = melbm.Simulator(wl.shape, wl.tau, "q16", seed=2602)
+    u = torch.zeros(3, N, dtype=torch.float32, device="cuda")
+    u[0] = 0.05
+    sim.set_state(torch.ones(N, dtype=torch.float32, device="cuda"), u)
+    sim.set_solid(torch.from_numpy(mask.ravel()).cuda())
+    sim.set_inflow(1.0, (0.05, 0.0, 0.0))
+    sim.set_outflow()
+    cells, _ = sim.boundary_list()
+    for _ in range(warmup):
+        sim.step(1)
+    st = sim.stream
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(torch)
+    torch.cuda.synchronize()
+    t0.record(st)
+    for _ in range(steps):
+        sim.step(1)
+    t1.record(st)
+    torch.cuda.synchronize()
+    barrier(torch)
+    total = t0.elapsed_time(t1)
+    listed = int(cells.numel())
+    mem = sim.memory_bytes()
+    sim.close()
+    return total, listed, mem
+
+
 def cpu_oracle_run(steps=12, warmup=1, planes=128):
     """FP64 oracle on a 256 x 256 x `planes` periodic slab of the workload's field
     (about ten seconds on 16 cores)."""
@@ -424,6 +459,9 @@ def main():
     d_total, d_kern, _ = time_storage(torch, melbm, wl, u_np, "q16", d_steps, args.warmup,
                                       lattice=19)
     d_total = max_over_ranks(torch, d_total)
+    c_steps = max(3, min(args.steps, 200))
+    c_total, c_listed, c_mem = channel_run(torch, melbm, c_steps, args.warmup)
+    c_total = max_over_ranks(torch, c_total)
 
     clk = clocks.summary()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -463,6 +501,13 @@ def main():
         "d3q19_q16": {"value": job_mlups(N, d_steps, world, d_total), "unit": "MLUPS",
                       "steps": d_steps, "ms_per_step": d_total / d_steps,
                       "roofline": roof("q16_d3q19", d_kern)},
+        "channel512_q16": {
+            "value": job_mlups(512 * 256 * 256, c_steps, world, c_total), "unit": "MLUPS",
+            "steps": c_steps, "ms_per_step": c_total / c_steps, "listed_cells": c_listed,
+            "memory_bytes": c_mem,
+            "workload": "512x256x256 channel, 300 seeded spheres (13.5% solid) and walls, "
+                        "inflow u=(0.05,0,0), outflow, tau=0.55, 16-bit storage: bounce kernel, "
+                        "fluid kernel with boundary tables, inflow and outflow passes per step"},
         "memory_bytes": {"q16": q_mem, "f32": f_mem},
         "gpu_launches": args.steps,
         "clocks": clk,
