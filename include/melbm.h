@@ -4,13 +4,15 @@
  * which every cell stores only its ten low-order moments (rho, u, S) instead of
  * the 27 (19) populations (arXiv 2602.05295, Sec. 3.2).  One step (Sec. 4.2, Alg. 2 and the
  * split-kernel design) is:
- *   1. a branch-free fluid kernel over all cells: load the moments, collide in
+ *   1. with solids, a kernel over a compacted list of boundary cells: what the
+ *      solid links of each cell return (halfway bounce-back or moving walls),
+ *      from the cell's own post-collision state;
+ *   2. a branch-free fluid kernel over all cells: load the moments, collide in
  *      moment space (App. A), rebuild the post-collision populations by the
  *      third-order Hermite expansion (Eq. three_order_f), pull them from the
- *      neighbours (Eq. streaming) and re-form the moments (Eq. rho_u_stress);
- *   2. a boundary kernel over a compacted list of boundary cells: halfway
- *      bounce-back recompute of cells with solid links and the inflow reset;
- *   3. a zero-gradient copy onto the outflow plane.
+ *      neighbours (Eq. streaming), add the returned populations of step 1 and
+ *      re-form the moments (Eq. rho_u_stress);
+ *   3. the inflow reset and a zero-gradient copy onto the outflow plane.
  * Moments are stored either as FP32 or in the paper's 16-bit stability-bounded
  * fixed-point form (Sec. 5.4): rho in [0.8, 1.5], u in [-0.4, 0.4] and
  * rho S^neq = rho (S - u u) in [-0.1, 0.1], dithered rounding, two codes per
@@ -136,7 +138,7 @@ MELBM_API int melbm_set_solid(melbm_t h, const uint8_t* mask);
  * density and velocity.  The paper's flow-past-solid scenes (Sec. 6.4 and Table 1)
  * drive the flow by an inlet without stating its form; this Dirichlet-equilibrium reading
  * is the one the oracle pins.  Typed and listed by the classification kernel
- * (INFLOW outranks OUTFLOW and FLUID_BOUNDARY); the boundary kernel applies the
+ * (INFLOW outranks OUTFLOW and FLUID_BOUNDARY); a pass over face 0 applies the
  * reset after the fluid kernel (split design of Sec. 4.2).  The classification
  * runs at the next call that needs it, as for melbm_set_solid.  Only face 0 is
  * supported: another face returns MELBM_EINVAL. */
@@ -146,8 +148,8 @@ MELBM_API int melbm_set_inflow(melbm_t h, int face, float rho, float ux, float u
  * the NEW stored state of (nx-2, y, z) (a cell of x = nx-1 is OUTFLOW only where
  * (nx-2, y, z) is not solid).  Like the inflow, the paper's flow-past-solid
  * scenes (Sec. 6.4) leave the outlet's form open; the zero-gradient copy is the reading
- * the oracle pins.  It runs as its own small pass after the boundary kernel, one
- * thread per (y, z).  The classification runs at the next call that needs it,
+ * the oracle pins.  It runs as its own small pass after the fluid kernel and the
+ * inflow reset, one thread per (y, z).  The classification runs at the next call that needs it,
  * as for melbm_set_solid.  Only face 1: another face returns MELBM_EINVAL. */
 MELBM_API int melbm_set_outflow(melbm_t h, int face);
 
@@ -174,22 +176,22 @@ MELBM_API int melbm_set_force(melbm_t h, const float* F);
 
 /* Advance n >= 0 steps (Alg. 2 with the split design of Sec. 4.2), asynchronously
  * on the handle's stream.  One step is
- *   1. the fluid update kernel (Alg. 2) over every cell: load (and in 16-bit
+ *   1. with solids, the bounce kernel over the compacted list (the solid
+ *      correction of Sec. 4.2, done first): for each FLUID_BOUNDARY cell the sums
+ *      of what its solid links return -- halfway bounce-back from the cell's own
+ *      post-collision state, or the moment-based wall of Sec. 3.2 -- into a
+ *      record per listed cell;
+ *   2. the fluid update kernel (Alg. 2) over every cell: load (and in 16-bit
  *      storage dequantise, Sec. 5.4) the stored moments, collide in moment space
  *      (App. A), rebuild the post-collision populations (Eq. three_order_f),
- *      pull them from x - c_i (Eq. streaming), re-form the moments
- *      (Eq. rho_u_stress) and store them (16-bit: range-reduced, dithered and
- *      packed, Sec. 5.4), periodic in every direction;
- *   2. with solids or inflow, the boundary kernel over the compacted list (the
- *      solid correction of Sec. 4.2): with solids the fluid kernel lets solid
- *      cells enter the stream at rest and keeps the raw post-streaming sums of
- *      each FLUID_BOUNDARY cell, to which the boundary kernel adds what the
- *      cell's solid links return -- halfway bounce-back from the cell's own
- *      post-collision state, or the moment-based wall of Sec. 3.2 -- before the
- *      moments are finished and stored; INFLOW cells are reset.  MELBM_MIXED
- *      runs the paper's own additive atomicAdd correction and re-quantisation
- *      instead;
- *   3. with an outflow face, the zero-gradient copy onto x = nx-1.
+ *      pull them from x - c_i (Eq. streaming; solid cells enter at rest, so a
+ *      solid link brings nothing), add the record of each FLUID_BOUNDARY cell,
+ *      re-form the moments (Eq. rho_u_stress) and store them once (16-bit:
+ *      range-reduced, dithered and packed, Sec. 5.4), periodic in every
+ *      direction.  MELBM_MIXED runs the paper's own additive atomicAdd
+ *      correction and re-quantisation instead;
+ *   3. with an inflow face, the reset of its INFLOW cells; with an outflow face,
+ *      the zero-gradient copy onto x = nx-1.
  * The state and time index advance by n.  Returns MELBM_EINVAL for n < 0 or a
  * NULL handle, MELBM_ESTATE after a failed boundary setup, the classification's
  * status when a pending one fails (melbm_set_solid), MELBM_ECUDA if a launch
