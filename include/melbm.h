@@ -192,11 +192,16 @@ MELBM_API int melbm_set_force(melbm_t h, const float* F);
  *      correction and re-quantisation instead;
  *   3. with an inflow face, the reset of its INFLOW cells; with an outflow face,
  *      the zero-gradient copy onto x = nx-1.
+ * In 16-bit storage without solids the rows of a fluid-kernel block synchronise
+ * through per-row barriers whose waits are bounded (milliseconds); a wait that
+ * runs out sets a word of the handle in mapped host memory instead of hanging.
  * The state and time index advance by n.  Returns MELBM_EINVAL for n < 0 or a
  * NULL handle, MELBM_ESTATE after a failed boundary setup, the classification's
  * status when a pending one fails (melbm_set_solid), MELBM_ECUDA if a launch
- * fails (the handle then refuses further steps).  Kernel faults surface at the
- * next synchronising call. */
+ * fails or if a barrier wait of an earlier step ran out (the handle then refuses
+ * further steps with MELBM_ESTATE until melbm_set_state, melbm_set_raw_state or
+ * melbm_upload_raw_state_async gives it a new state).  Kernel faults surface at
+ * the next synchronising call. */
 MELBM_API int melbm_step(melbm_t h, int n);
 
 /* FP64 total mass sum(rho) and kinetic energy sum(rho |u|^2 / 2) over non-solid
@@ -209,7 +214,8 @@ MELBM_API int melbm_step(melbm_t h, int n);
  * rho |u|^2 / 2 are summed in FP64 in a fixed order (deterministic).  In 16-bit
  * storage returns MELBM_WSATURATED (values still written) when any non-solid
  * code is 0 or 2^b - 1 (saturation, Sec. 5.4 ranges).  MELBM_EINVAL for NULL
- * pointers. */
+ * pointers; MELBM_ECUDA (sums undefined) when a barrier wait of a step before
+ * it ran out (see melbm_step). */
 MELBM_API int melbm_reduce(melbm_t h, double* mass, double* kinetic_energy);
 
 /* Steps taken since the last melbm_set_state (host pointer). */

@@ -40,6 +40,31 @@ int cuda_fail(melbm_t h, cudaError_t e, const char* where) {
   return fail(h, MELBM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+// A bounded barrier wait of an earlier fluid-kernel launch ran out: the state it
+// wrote is undefined.  Reported once (the word is cleared); the handle then
+// refuses to step until a new state is set.
+int kernel_fault(melbm_t h, const char* where) {
+  volatile uint32_t* f = h->fault_host;
+  if (!f || *f == 0u) return MELBM_OK;
+  *f = 0u;
+  h->poisoned = true;
+  return fail(h, MELBM_ECUDA,
+              "%s: a barrier wait of the fluid kernel ran out; the state is undefined, "
+              "call melbm_set_state",
+              where);
+}
+
+// A new state replaces one that a fault may have left: the fault of the work
+// issued before it is no longer this state's (cleared once that work has run).
+int clear_fault(melbm_t h, const char* where) {
+  volatile uint32_t* f = h->fault_host;
+  if (!f || *f == 0u) return MELBM_OK;
+  const cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, where);
+  *f = 0u;
+  return MELBM_OK;
+}
+
 #define MELBM_CUDA(h, call)                                       \
   do {                                                            \
     cudaError_t e_ = (call);                                      \
@@ -323,9 +348,9 @@ cudaError_t forward_step_on(melbm_sim* h, const void* in, void* out, uint32_t t_
   if (e == cudaSuccess)
     e = h->lattice == MELBM_D3Q19
           ? launch_fluid19(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                           h->seed, h->grids, &bt, st)
+                           h->seed, h->grids, &bt, st, h->fault_dev, h->stall_test)
           : launch_fluid(h->storage, h->nx, h->ny, h->nz, in, out, h->force, omega, t_out,
-                         h->seed, h->grids, &bt, st);
+                         h->seed, h->grids, &bt, st, h->fault_dev, h->stall_test);
   if (e == cudaSuccess && h->inflow_on && h->type)
     e = launch_inflow(h->storage, h->nx, h->ny, h->nz, out, h->type, h->inflow, t_out, h->seed,
                       h->grids, st);
@@ -395,6 +420,21 @@ int melbm_create(int nx, int ny, int nz, int lattice, float tau, int storage, me
     melbm_destroy(h);
     return rc;
   }
+  {
+    cudaError_t e = cudaHostAlloc((void**)&h->fault_host, sizeof(uint32_t), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+      *h->fault_host = 0u;
+      e = cudaHostGetDevicePointer((void**)&h->fault_dev, h->fault_host, 0);
+    }
+    if (e != cudaSuccess) {
+      cuda_fail(h, e, "melbm_create: the kernel fault word");
+      g_err = h->err;
+      melbm_destroy(h);
+      return MELBM_ECUDA;
+    }
+    const char* v = std::getenv("MELBM_TEST_STALL_BARRIER");
+    h->stall_test = (v && std::atoi(v) != 0) ? 1 : 0;
+  }
   // rest state (rho = 1, u = 0, S = 0) at time index 0
   cudaError_t e;
   if (storage == MELBM_MIXED) {
@@ -437,6 +477,7 @@ int melbm_destroy(melbm_t h) {
   dev_free(h, h->bodies, 256 * 9 * 4);
   dev_free(h, h->sf_partials, size_t(solid_force_blocks()) * 6 * 8);
   dev_free(h, h->sf_out, 6 * 8);
+  if (h->fault_host) cudaFreeHost(h->fault_host);
   delete h;
   return MELBM_OK;
 }
@@ -467,6 +508,7 @@ int melbm_set_state(melbm_t h, const float* rho, const float* u, const float* S)
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_set_state: NULL handle");
   if (!rho || !u) return fail(h, MELBM_EINVAL, "melbm_set_state: rho and u are required");
   MELBM_CUDA(h, join_transfers(h));
+  if (int rc = clear_fault(h, "melbm_set_state")) return rc;
   const size_t N = size_t(h->N);
   const bool dev = is_device_ptr(rho) && is_device_ptr(u) && (!S || is_device_ptr(S));
   const float *r = rho, *uu = u, *ss = S;
@@ -609,6 +651,7 @@ int melbm_step(melbm_t h, int n) {
   if (!h) return fail(nullptr, MELBM_EINVAL, "melbm_step: NULL handle");
   const Range range("melbm_step");
   if (n < 0) return fail(h, MELBM_EINVAL, "melbm_step: n = %d < 0", n);
+  if (int rc = kernel_fault(h, "melbm_step")) return rc;
   if (h->poisoned) return fail(h, MELBM_ESTATE, "melbm_step: an earlier CUDA failure left the state undefined; call melbm_set_state");
   if (h->boundary_error) return boundary_refusal(h, "melbm_step");
   if (n > 0)
@@ -657,6 +700,7 @@ int melbm_reduce(melbm_t h, double* mass, double* ke) {
   double out[3];
   MELBM_CUDA(h, cudaMemcpyAsync(out, h->red_out, sizeof out, cudaMemcpyDeviceToHost, h->stream));
   MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (int rc = kernel_fault(h, "melbm_reduce")) return rc;
   if (mass) *mass = out[0];
   if (ke) *ke = out[1];
   if (h->storage == MELBM_Q16 && out[2] > 0.0)
@@ -696,6 +740,7 @@ int melbm_set_raw_state(melbm_t h, const void* src, int64_t bytes, int64_t time_
   if (int rc = check_raw_bytes(h, "melbm_set_raw_state", bytes)) return rc;
   if (time_index < 0) return fail(h, MELBM_EINVAL, "melbm_set_raw_state: negative time index");
   MELBM_CUDA(h, join_transfers(h));
+  if (int rc = clear_fault(h, "melbm_set_raw_state")) return rc;
   MELBM_CUDA(h, cudaMemcpyAsync(h->buf[h->cur], src, size_t(bytes), cudaMemcpyDefault, h->stream));
   MELBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->t = time_index;
@@ -716,6 +761,7 @@ int melbm_upload_raw_state_async(melbm_t h, const void* src, int64_t bytes, int6
   if (time_index < 0)
     return fail(h, MELBM_EINVAL, "melbm_upload_raw_state_async: negative time index");
   if (int rc = ensure_transfers(h)) return rc;
+  if (int rc = clear_fault(h, "melbm_upload_raw_state_async")) return rc;
   const int s = h->spare_id, c = h->buf_id[h->cur];
   MELBM_CUDA(h, cudaStreamWaitEvent(h->up_stream, h->ev_retired[s], 0));
   MELBM_CUDA(h, cudaStreamWaitEvent(h->up_stream, h->ev_read[s], 0));

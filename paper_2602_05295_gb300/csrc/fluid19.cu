@@ -8,12 +8,13 @@ namespace melbm {
 
 cudaError_t launch_fluid19(int storage, int nx, int ny, int nz, const void* in, void* out,
                            const float* force, float omega, uint32_t t_out, uint32_t seed,
-                           const QGrids& grids, const BoundaryTables* bt, cudaStream_t st) {
+                           const QGrids& grids, const BoundaryTables* bt, cudaStream_t st,
+                           uint32_t* fault, int stall_test) {
   if (bt && bt->solid)
     return launch_fluid19_bnd(storage, nx, ny, nz, in, out, force, omega, t_out, seed, grids, bt,
                               st);
   return launch_fluid_impl<true, false>(storage, nx, ny, nz, in, out, force, omega, t_out, seed,
-                                        grids, nullptr, st);
+                                        grids, nullptr, st, fault, stall_test);
 }
 
 cudaError_t launch_fluid_mixed19(int nx, int ny, int nz, const void* q_in, float* p_out,

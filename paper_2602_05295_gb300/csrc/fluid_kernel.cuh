@@ -134,6 +134,13 @@ struct FluidParams {
   float* side;
   int64_t L;
   int ntx;  // words per row, ceil(nx / 32)
+  // 16-bit kernels without the tables synchronise their rows by per-row barriers
+  // whose waits are bounded: a wait that runs out sets *fault (mapped host memory,
+  // may be null) and returns.  stall_test != 0 initialises warp 0's barriers for
+  // twice the arrivals they receive, so that the waits on them run out (a test
+  // of that path; nothing else sets it).
+  uint32_t* fault;
+  int stall_test;
 };
 
 template <int STORAGE, bool RT> struct KernelParams;
@@ -566,8 +573,45 @@ __device__ __forceinline__ float2 shfl_idx2(float2 v, int src) {
 #define MELBM_PRAGMA_STR(x) #x
 #define MELBM_PRAGMA_UNROLL(n) _Pragma(MELBM_PRAGMA_STR(unroll n))
 
+// mbarriers in shared memory (arrival counts of whole warps)
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(uint32_t(__cvta_generic_to_shared(b))),
+               "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(uint32_t(__cvta_generic_to_shared(b)))
+               : "memory");
+}
+// Wait for the phase of parity `par` to complete, polling at most 2^18 times
+// (milliseconds; a wait of the kernel below lasts about one plane pair, a few
+// microseconds).  When it runs out, *fault is set and the wait returns.
+constexpr int MB_MAX_POLLS = 1 << 18;
+__device__ __forceinline__ void mb_wait(uint64_t* b, uint32_t par, uint32_t* fault) {
+  const uint32_t a = uint32_t(__cvta_generic_to_shared(b));
+  for (int it = 0; it < MB_MAX_POLLS; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(par)
+        : "memory");
+    if (done) return;
+  }
+  if (fault) *reinterpret_cast<volatile uint32_t*>(fault) = 1u;
+}
+
 template <int STORAGE, bool FORCE, bool RT, bool Q19 = false, bool BND = false>
 __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelParams<STORAGE, RT> P) {
+  // 16-bit storage without the tables: the rows synchronise through per-row
+  // barriers (measured faster there; the FP32 kernel spills with them, and the
+  // tables' kernel ran slower)
+  constexpr bool LOCAL_SYNC = STORAGE == ST_Q16 && !BND;
+  // one barrier per row and one of the whole block, in a set for the even and a
+  // set for the odd barriers of the pair loop: a row can be one barrier ahead of
+  // a row that waits on it, never two, so the phase parity of a set is unambiguous
+  __shared__ uint64_t rowbar[LOCAL_SYNC ? 2 : 1][FY + 1];
   // the input side reads 16-bit codes in the mixed scheme (post-collision moments)
   constexpr int IN = STORAGE == ST_MIXED ? ST_Q16 : STORAGE;
   using HS = HaloStage<IN, FORCE, Q19, BND>;
@@ -750,7 +794,35 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     }
     halo_finish(0, 0, z0 - 1);
   }
+  if constexpr (LOCAL_SYNC) {
+    if (row == 0 && lane < 2) {
+      for (int r = 0; r < FY; ++r) mb_init(&rowbar[lane][r], (r == 0 && P.stall_test) ? 2 * FX : FX);
+      mb_init(&rowbar[lane][FY], FX * FY);
+    }
+  }
   __syncthreads();
+  // The i-th barrier of the pair loop after the first two (which stay block-wide):
+  // a row waits for its two neighbour rows, whose y-exchange slots it reads and
+  // overwrites next, and for warp 0, whose x-halo buffer it reads next; warp 0
+  // waits for the whole block before it overwrites a halo buffer.
+  auto sync_rows = [&](int i) {
+    if constexpr (LOCAL_SYNC) {
+      uint64_t* const b = rowbar[i & 1];
+      const uint32_t par = uint32_t(i >> 1) & 1u;
+      mb_arrive(&b[row]);
+      mb_arrive(&b[FY]);
+      if (row == 0) {
+        mb_wait(&b[FY], par, P.fault);
+      } else {
+        mb_wait(&b[row - 1], par, P.fault);
+        if (row + 1 < FY) mb_wait(&b[row + 1], par, P.fault);
+        mb_wait(&b[0], par, P.fault);
+      }
+    } else {
+      (void)i;
+      __syncthreads();
+    }
+  };
 
   const float2 zero = make_float2(0.f, 0.f);
   float2 yz0[NSY];  // phi_0 of the y pass of this thread's row, pair in flight
@@ -1025,7 +1097,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
       pre(zz, parity, fn[0], fn[1], fn[2], j + 1 < npairs);
 #pragma unroll
       for (int k = 0; k < 3; ++k) fc[k] = fn[k];
-      __syncthreads();
+      sync_rows(j - 2);
     }
     post(z0 - 1 + 2 * (npairs - 1), (npairs - 1) & 1, make_float2(fprev[0], fc[0].x),
          make_float2(fprev[1], fc[1].x), make_float2(fprev[2], fc[2].x), true);
@@ -1045,7 +1117,8 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
         else cp_async_wait<0>();
         halo_finish(parity ^ 1, parity ^ 1, zz + 2);
       }
-      __syncthreads();
+      if (j < 2) __syncthreads();
+      else sync_rows(j - 2);
     }
   }
 }
@@ -1102,8 +1175,11 @@ cudaError_t launch_fluid_t(KernelParams<STORAGE, RT>& p, cudaStream_t st) {
 template <bool Q19, bool BND>
 cudaError_t launch_fluid_impl(int storage, int nx, int ny, int nz, const void* in, void* out,
                               const float* force, float omega, uint32_t t_out, uint32_t seed,
-                              const QGrids& grids, const BoundaryTables* bt, cudaStream_t st) {
+                              const QGrids& grids, const BoundaryTables* bt, cudaStream_t st,
+                              uint32_t* fault = nullptr, int stall_test = 0) {
   FluidParams p = {};
+  p.fault = fault;
+  p.stall_test = stall_test;
   p.nx = nx;
   p.ny = ny;
   p.nz = nz;

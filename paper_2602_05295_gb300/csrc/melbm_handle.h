@@ -69,6 +69,12 @@ struct melbm_sim {
   double* red_out = nullptr;
   int64_t mem_bytes = 0;
   bool poisoned = false;
+  // A word of mapped host memory that the fluid kernel sets when one of its
+  // bounded barrier waits runs out (host and device addresses); stall_test makes
+  // those waits run out (MELBM_TEST_STALL_BARRIER=1 at melbm_create, for tests).
+  uint32_t* fault_host = nullptr;
+  uint32_t* fault_dev = nullptr;
+  int stall_test = 0;
   bool boundary_error = false;  // the last boundary setup failed: lists are empty
   // Asynchronous raw-state transfers (created at their first use): an upload and a
   // download stream, a third state buffer (the spare) that uploads land in, and the

@@ -66,17 +66,21 @@ struct BoundaryTables {
 // Fluid kernel over every cell: in -> out (storage layout of melbm_device.cuh).
 // q: the grids of the handle's bit widths (16/16 runs the kernel instantiation
 // with compile-time grid constants).  bt: the boundary tables (NULL or solid ==
-// NULL without solids).
+// NULL without solids).  fault: a word of mapped host memory (device address, or
+// NULL) that the 16-bit kernel without tables sets to 1 when one of its bounded
+// barrier waits runs out; stall_test != 0 makes those waits run out (tests).
 cudaError_t launch_fluid(int storage, int nx, int ny, int nz, const void* in, void* out,
                          const float* force, float omega, uint32_t t_out, uint32_t seed,
-                         const QGrids& q, const BoundaryTables* bt, cudaStream_t st);
+                         const QGrids& q, const BoundaryTables* bt, cudaStream_t st,
+                         uint32_t* fault = nullptr, int stall_test = 0);
 cudaError_t launch_fluid_bnd(int storage, int nx, int ny, int nz, const void* in, void* out,
                              const float* force, float omega, uint32_t t_out, uint32_t seed,
                              const QGrids& q, const BoundaryTables* bt, cudaStream_t st);
 // The same on the D3Q19 lattice (fluid19.cu, fluid19_bnd.cu; F32 or Q16 storage).
 cudaError_t launch_fluid19(int storage, int nx, int ny, int nz, const void* in, void* out,
                            const float* force, float omega, uint32_t t_out, uint32_t seed,
-                           const QGrids& q, const BoundaryTables* bt, cudaStream_t st);
+                           const QGrids& q, const BoundaryTables* bt, cudaStream_t st,
+                           uint32_t* fault = nullptr, int stall_test = 0);
 cudaError_t launch_fluid19_bnd(int storage, int nx, int ny, int nz, const void* in, void* out,
                                const float* force, float omega, uint32_t t_out, uint32_t seed,
                                const QGrids& q, const BoundaryTables* bt, cudaStream_t st);
