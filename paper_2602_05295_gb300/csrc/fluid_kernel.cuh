@@ -608,6 +608,11 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
   // barriers (measured faster there; the FP32 kernel spills with them, and the
   // tables' kernel ran slower)
   constexpr bool LOCAL_SYNC = STORAGE == ST_Q16 && !BND;
+  // The y exchange of the FP32 kernel without the tables moves slices r and r + 3
+  // of a row as one 128-bit value (slice r + 6 as a 64-bit one): 12 instead of 18
+  // shared-memory accesses per thread and plane pair, measured faster there (the
+  // 16-bit kernel with its row barriers measured slower with it)
+  constexpr bool YPAIR = STORAGE == ST_F32 && !BND;
   // one barrier per row and one of the whole block, in a set for the even and a
   // set for the odd barriers of the pair loop: a row can be one barrier ahead of
   // a row that waits on it, never two, so the phase parity of a set is unambiguous
@@ -621,7 +626,7 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     if constexpr (IN == ST_Q16 && RT) return decode_pair(r, P.q);
     else return decode_pair(r);
   };
-  extern __shared__ float2 sm2[];
+  extern __shared__ __align__(16) float2 sm2[];
   float2* const hb = sm2 + 2 * SM_BUF;  // halo populations [buffer][row][slice][side]
   uint32_t* const stg = reinterpret_cast<uint32_t*>(hb + 2 * HALO_BUF);  // warp 0 staging
   // bounce-back record slots (BND): slot c of thread (row, lane) at [c][row][lane]
@@ -907,6 +912,10 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     Closure19T<float2> E;
     if constexpr (Q19) E = closure19_scaled(A);
     float2* sp = sm2 + parity * SM_BUF;
+    // YPAIR layout: six float4 groups (phi+ of slices (r', r' + 3) at group r',
+    // phi- at group 3 + r'), then six float2 groups (slice r' + 6)
+    float4* const sp4 = reinterpret_cast<float4*>(sp);
+    float2* const sp2 = sp + 12 * FY * FX;
     float2 X[3][3];  // X[p][q'] of the current r'
     const float4* hbp = reinterpret_cast<const float4*>(hb + parity * HALO_BUF) + row * NSXL;
 #define MELBM_XPASS(K, Q)                                               \
@@ -921,13 +930,36 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     X[1][Q] = projs1(pl, mr);                                           \
     X[2][Q] = projs2(X[0][Q], ph.zn);                                   \
   }
-#define MELBM_YPHI(R, PH)                                               \
-  _Pragma("unroll") for (int p = 0; p < 3; ++p) {                       \
-    const PhiS<float2> ph = PH;                                         \
-    const int s_ = 3 * p + (R);                                         \
-    sp[(s_ * FY + row) * FX + lane] = ph.p;                             \
-    sp[((NSY + s_) * FY + row) * FX + lane] = ph.m;                     \
-    yz0[s_] = ph.zn;                                                    \
+#define MELBM_YPHI(R, PH)                                                              \
+  if constexpr (YPAIR) {                                                               \
+    PhiS<float2> a_, b_, c_;                                                           \
+    {                                                                                  \
+      constexpr int p = 0;                                                             \
+      a_ = PH;                                                                         \
+    }                                                                                  \
+    {                                                                                  \
+      constexpr int p = 1;                                                             \
+      b_ = PH;                                                                         \
+    }                                                                                  \
+    yz0[(R)] = a_.zn;                                                                  \
+    yz0[3 + (R)] = b_.zn;                                                              \
+    sp4[((R) * FY + row) * FX + lane] = make_float4(a_.p.x, a_.p.y, b_.p.x, b_.p.y);   \
+    sp4[((3 + (R)) * FY + row) * FX + lane] = make_float4(a_.m.x, a_.m.y, b_.m.x, b_.m.y); \
+    {                                                                                  \
+      constexpr int p = 2;                                                             \
+      c_ = PH;                                                                         \
+    }                                                                                  \
+    yz0[6 + (R)] = c_.zn;                                                              \
+    sp2[((R) * FY + row) * FX + lane] = c_.p;                                          \
+    sp2[((3 + (R)) * FY + row) * FX + lane] = c_.m;                                    \
+  } else {                                                                             \
+    _Pragma("unroll") for (int p = 0; p < 3; ++p) {                                    \
+      const PhiS<float2> ph = PH;                                                      \
+      const int s_ = 3 * p + (R);                                                      \
+      sp[(s_ * FY + row) * FX + lane] = ph.p;                                          \
+      sp[((NSY + s_) * FY + row) * FX + lane] = ph.m;                                  \
+      yz0[s_] = ph.zn;                                                                 \
+    }                                                                                  \
   }
     MELBM_XPASS(0, 0)  // r' = 0
     MELBM_XPASS(1, 1)
@@ -965,17 +997,39 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
     }
     const float2* sp = sm2 + parity * SM_BUF;
     float2 Y[3][3][3];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
+    if constexpr (YPAIR) {
+      const float4* const sp4 = reinterpret_cast<const float4*>(sp);
+      const float2* const sp2 = sp + 12 * FY * FX;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const int s_ = 3 * p + r;
-        const float2 pl = sp[(s_ * FY + row - 1) * FX + lane];
-        const float2 mr = sp[((NSY + s_) * FY + row + 1) * FX + lane];
-        Y[p][0][r] = projs0(pl, yz0[s_], mr);
-        if (p <= 1) Y[p][1][r] = projs1(pl, mr);
-        if (p == 0) Y[p][2][r] = projs2(Y[p][0][r], yz0[s_]);
+        // phi+ of the row above and phi- of the row below, slices r, r + 3, r + 6
+        const float4 a = sp4[(r * FY + row - 1) * FX + lane];
+        const float4 b = sp4[((3 + r) * FY + row + 1) * FX + lane];
+        const float2 pls[3] = {make_float2(a.x, a.y), make_float2(a.z, a.w),
+                               sp2[(r * FY + row - 1) * FX + lane]};
+        const float2 mrs[3] = {make_float2(b.x, b.y), make_float2(b.z, b.w),
+                               sp2[((3 + r) * FY + row + 1) * FX + lane]};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const int s_ = 3 * p + r;
+          Y[p][0][r] = projs0(pls[p], yz0[s_], mrs[p]);
+          if (p <= 1) Y[p][1][r] = projs1(pls[p], mrs[p]);
+          if (p == 0) Y[p][2][r] = projs2(Y[p][0][r], yz0[s_]);
+        }
       }
+    } else {
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int s_ = 3 * p + r;
+          const float2 pl = sp[(s_ * FY + row - 1) * FX + lane];
+          const float2 mr = sp[((NSY + s_) * FY + row + 1) * FX + lane];
+          Y[p][0][r] = projs0(pl, yz0[s_], mr);
+          if (p <= 1) Y[p][1][r] = projs1(pl, mr);
+          if (p == 0) Y[p][2][r] = projs2(Y[p][0][r], yz0[s_]);
+        }
+    }
     // z pass: planes (zz, zz + 1) in, (zz - 1, zz) out; the Zn of the output
     // pair straddles two input pairs, so the terms that use it are taken per half
     const int PQ[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
