@@ -192,9 +192,10 @@ MELBM_API int melbm_set_force(melbm_t h, const float* F);
  *      correction and re-quantisation instead;
  *   3. with an inflow face, the reset of its INFLOW cells; with an outflow face,
  *      the zero-gradient copy onto x = nx-1.
- * In 16-bit storage without solids the rows of a fluid-kernel block synchronise
- * through per-row barriers whose waits are bounded (milliseconds); a wait that
- * runs out sets a word of the handle in mapped host memory instead of hanging.
+ * In 16-bit storage at 16/16 bits without solids the rows of a fluid-kernel
+ * block synchronise through per-row barriers whose waits are bounded
+ * (milliseconds); a wait that runs out sets a word of the handle in mapped host
+ * memory instead of hanging.
  * The state and time index advance by n.  Returns MELBM_EINVAL for n < 0 or a
  * NULL handle, MELBM_ESTATE after a failed boundary setup, the classification's
  * status when a pending one fails (melbm_set_solid), MELBM_ECUDA if a launch

@@ -604,10 +604,10 @@ __device__ __forceinline__ void mb_wait(uint64_t* b, uint32_t par, uint32_t* fau
 
 template <int STORAGE, bool FORCE, bool RT, bool Q19 = false, bool BND = false>
 __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelParams<STORAGE, RT> P) {
-  // 16-bit storage without the tables: the rows synchronise through per-row
-  // barriers (measured faster there; the FP32 kernel spills with them, and the
-  // tables' kernel ran slower)
-  constexpr bool LOCAL_SYNC = STORAGE == ST_Q16 && !BND;
+  // 16-bit storage on the 16/16 grids without the tables: the rows synchronise
+  // through per-row barriers (measured faster there; the FP32 kernel, the kernel
+  // with the tables and the runtime-grid kernel each ran slower with them)
+  constexpr bool LOCAL_SYNC = STORAGE == ST_Q16 && !BND && !RT;
   // The y exchange of the FP32 kernel without the tables moves slices r and r + 3
   // of a row as one 128-bit value (slice r + 6 as a 64-bit one): 12 instead of 18
   // shared-memory accesses per thread and plane pair, measured faster there (the
