@@ -608,11 +608,12 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
   // through per-row barriers (measured faster there; the FP32 kernel, the kernel
   // with the tables and the runtime-grid kernel each ran slower with them)
   constexpr bool LOCAL_SYNC = STORAGE == ST_Q16 && !BND && !RT;
-  // The y exchange of the FP32 kernel without the tables moves slices r and r + 3
-  // of a row as one 128-bit value (slice r + 6 as a 64-bit one): 12 instead of 18
-  // shared-memory accesses per thread and plane pair, measured faster there (the
-  // 16-bit kernel with its row barriers measured slower with it)
-  constexpr bool YPAIR = STORAGE == ST_F32 && !BND;
+  // The y exchange of the FP32 kernel without the tables and without a force
+  // moves slices r and r + 3 of a row as one 128-bit value (slice r + 6 as a
+  // 64-bit one): 12 instead of 18 shared-memory accesses per thread and plane
+  // pair, measured faster there (the 16-bit kernel with its row barriers and the
+  // FP32 kernel with a force measured slower with it)
+  constexpr bool YPAIR = STORAGE == ST_F32 && !BND && !FORCE;
   // one barrier per row and one of the whole block, in a set for the even and a
   // set for the odd barriers of the pair loop: a row can be one barrier ahead of
   // a row that waits on it, never two, so the phase parity of a set is unambiguous
