@@ -579,16 +579,14 @@ __device__ __forceinline__ void mb_init(uint64_t* b, uint32_t count) {
                "r"(count)
                : "memory");
 }
-__device__ __forceinline__ void mb_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(uint32_t(__cvta_generic_to_shared(b)))
-               : "memory");
+__device__ __forceinline__ void mb_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 // Wait for the phase of parity `par` to complete, polling at most 2^18 times
 // (milliseconds; a wait of the kernel below lasts about one plane pair, a few
 // microseconds).  When it runs out, *fault is set and the wait returns.
 constexpr int MB_MAX_POLLS = 1 << 18;
-__device__ __forceinline__ void mb_wait(uint64_t* b, uint32_t par, uint32_t* fault) {
-  const uint32_t a = uint32_t(__cvta_generic_to_shared(b));
+__device__ __forceinline__ void mb_wait(uint32_t a, uint32_t par, uint32_t* fault) {
   for (int it = 0; it < MB_MAX_POLLS; ++it) {
     uint32_t done;
     asm volatile(
@@ -811,18 +809,19 @@ __global__ void __launch_bounds__(FX* FY, MELBM_FLUID_MINB) fluid_kernel(KernelP
   // a row waits for its two neighbour rows, whose y-exchange slots it reads and
   // overwrites next, and for warp 0, whose x-halo buffer it reads next; warp 0
   // waits for the whole block before it overwrites a halo buffer.
+  const uint32_t rb0 = uint32_t(__cvta_generic_to_shared(&rowbar[0][0]));
   auto sync_rows = [&](int i) {
     if constexpr (LOCAL_SYNC) {
-      uint64_t* const b = rowbar[i & 1];
+      const uint32_t b = rb0 + ((i & 1) ? uint32_t(8 * (FY + 1)) : 0u);
       const uint32_t par = uint32_t(i >> 1) & 1u;
-      mb_arrive(&b[row]);
-      mb_arrive(&b[FY]);
+      mb_arrive(b + 8u * row);
+      mb_arrive(b + 8u * FY);
       if (row == 0) {
-        mb_wait(&b[FY], par, P.fault);
+        mb_wait(b + 8u * FY, par, P.fault);
       } else {
-        mb_wait(&b[row - 1], par, P.fault);
-        if (row + 1 < FY) mb_wait(&b[row + 1], par, P.fault);
-        mb_wait(&b[0], par, P.fault);
+        mb_wait(b + 8u * (row - 1), par, P.fault);
+        if (row + 1 < FY) mb_wait(b + 8u * (row + 1), par, P.fault);
+        if (row != 1) mb_wait(b, par, P.fault);
       }
     } else {
       (void)i;
